@@ -1,0 +1,292 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle itself
+(closed forms, an independent sparse-matrix construction of the operator, dense direct
+solves, adjoint identities, orders of accuracy, the paper's own Eq. 18 update)."""
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from paper_2602_01888_gb300 import inputs as I
+import _indep as X
+
+
+def _eps_of(O, inst):
+    P = O.prepare(inst)
+    return P
+
+
+# ---------------------------------------------------------------- coefficient build
+def test_identity_map_is_the_textbook_five_point_laplacian(oracle):
+    inst = I.identity_poisson(9)
+    P = oracle.prepare(inst)
+    assert np.all(P.D == 1.0) and np.all(P.exx == 1.0) and np.all(P.eyy == 1.0)
+    assert np.all(P.exy == 0.0)
+    h2 = 1.0 / inst.grid.hx ** 2
+    A = P.A
+    assert np.all(A.cNE == 0.0) and np.all(A.cNW == 0.0)
+    assert np.all(A.cE[:, :-1] == -h2) and np.all(A.cN[:-1, :] == -h2)
+    assert np.all(A.diag[1:-1, 1:-1] == 4 * h2)
+
+
+def test_eps_matches_matrix_form_of_eq10(oracle):
+    """Components (Eqs. 12-15) vs eps = det(J) J^-1 eps' J^-T evaluated as matrices."""
+    rng = np.random.default_rng(7)
+    for _ in range(5):
+        a11, a22 = rng.uniform(0.5, 2.0, 2)
+        a12, a21 = rng.uniform(-0.4, 0.4, 2)
+        inst = I.affine_quadratic(9, (a11, a12, a21, a22))
+        s = rng.uniform(0.5, 20.0, inst.grid.shape)
+        J = oracle.jacobian(inst.grid, inst.map)
+        D, exx, exy, eyy, st = oracle.eps_tensor(J, s)
+        assert st == 0
+        Jm = np.array([[a11, a12], [a21, a22]])
+        Ji = np.linalg.inv(Jm)
+        E = np.linalg.det(Jm) * Ji @ Ji.T
+        assert np.allclose(exx, s * E[0, 0], rtol=1e-14, atol=0)
+        assert np.allclose(exy, s * E[0, 1], rtol=1e-14, atol=1e-15)
+        assert np.allclose(eyy, s * E[1, 1], rtol=1e-14, atol=0)
+
+
+def test_det_eps_is_one_for_identity_material(oracle):
+    for inst in (I.config1(33), I.annulus_log(33), I.inclusion_instance(65, 0.25, 1.0, 1),
+                 I.circle_poisson(33)):
+        P = oracle.prepare(inst)
+        det = P.exx * P.eyy - P.exy ** 2
+        assert np.abs(det - 1).max() < 1e-12, inst.name
+
+
+def test_polar_closed_form(oracle):
+    inst = I.annulus_log(33)
+    P = oracle.prepare(inst)
+    r, _ = inst.grid.coords()
+    assert np.allclose(P.exx, r, rtol=1e-14)
+    assert np.allclose(P.eyy, 1.0 / r, rtol=1e-14)
+    assert np.abs(P.exy).max() < 1e-15
+    assert np.allclose(P.D, r, rtol=1e-14)
+
+
+def test_sinh_closed_form_offdiagonal_vanishes(oracle):
+    g = I.Grid(33, 33, -3.0, -3.0, 6.0, 6.0)
+    mp = I.MapSpec("sinh", (5.0, 0.6))
+    D, exx, exy, eyy, st = oracle.eps_tensor(oracle.jacobian(g, mp))
+    x, y = g.coords()
+    cx, cy = np.cosh(0.6 * x), np.cosh(0.6 * y)
+    assert np.all(exy == 0.0)
+    assert np.allclose(exx, cy / cx, rtol=1e-14) and np.allclose(eyy, cx / cy, rtol=1e-14)
+    assert np.allclose(D, 9.0 * cx * cy, rtol=1e-14)
+
+
+def test_central_difference_tensor_converges_at_second_order(oracle):
+    errs = []
+    for n in (33, 65, 129):
+        inst = I.config1(n)
+        xp, yp = inst.map.physical(inst.grid)
+        Pa = oracle.prepare(inst)
+        gm = I.MapSpec("grid", (), xp, yp)
+        D, exx, exy, eyy, _ = oracle.eps_tensor(oracle.jacobian(inst.grid, gm))
+        errs.append(max(np.abs(exx - Pa.exx).max(), np.abs(exy - Pa.exy).max(),
+                        np.abs(eyy - Pa.eyy).max(), np.abs(D - Pa.D).max()))
+    orders = [math.log2(errs[k] / errs[k + 1]) for k in range(2)]
+    assert all(1.9 < o < 2.15 for o in orders), orders
+
+
+def test_folded_map_is_reported(oracle):
+    inst = I.affine_quadratic(9, (1.0, 0.0, 0.0, -1.0))
+    _, _, _, _, st = oracle.eps_tensor(oracle.jacobian(inst.grid, inst.map))
+    assert st == 5
+
+
+def test_charge_conservation_eq11(oracle):
+    """sum b hx hy = integral of rho' over the physical domain (= 8 for config 1) + O(h^2)."""
+    errs = []
+    for n in (33, 65, 129):
+        inst = I.config1(n)
+        P = oracle.prepare(inst)
+        errs.append(abs(P.b.sum() * inst.grid.hx * inst.grid.hy - 8.0))
+    assert errs[-1] < 1e-3
+    assert errs[0] / errs[1] > 3.5 and errs[1] / errs[2] > 3.5
+
+
+# ---------------------------------------------------------------- operator
+@pytest.mark.parametrize("case", ["sine", "inclusion", "annulus", "rect"])
+def test_operator_equals_difference_matrix_construction(oracle, case):
+    inst = {"sine": lambda: I.config1(17),
+            "inclusion": lambda: I.inclusion_instance(33, 0.25, 10.0, 3),
+            "annulus": lambda: I.annulus_log(17),
+            "rect": lambda: I.Instance("rect", I.Grid(17, 9, 0.0, 0.0, 1.0, 0.6),
+                                       I.MapSpec("sine_warp", (0.08,)), np.ones((9, 17)))}[case]()
+    P = oracle.prepare(inst)
+    A_ref = X.full_operator(inst.grid, P.exx, P.exy, P.eyy)
+    u = X.unknown_ids(inst.grid)
+    # every stored coupling of an unknown row equals the matrix entry
+    A_or = X.coupling_matrix(inst.grid, P.A)
+    Aref_uu = A_ref[u][:, u]
+    assert abs(A_or - Aref_uu).max() <= 1e-10 * abs(Aref_uu).max()
+    # diagonal = minus the sum of all eight couplings (Dirichlet columns included)
+    rows = A_ref[u]
+    assert np.abs(np.asarray(rows.sum(axis=1)).ravel()).max() <= 1e-9 * abs(Aref_uu).max()
+    # symmetric
+    assert abs(A_or - A_or.T).max() == 0.0
+
+
+def test_affine_quadratic_is_reproduced_exactly(oracle):
+    for a in ((1.0, 0.3, -0.2, 1.1), (1.3, -0.5, 0.4, 0.9)):
+        inst = I.affine_quadratic(33, a)
+        phi, cyc, hist, P = oracle.solve_instance(inst, rtol=1e-14)
+        err = np.abs(phi - inst.exact).max() / np.abs(inst.exact).max()
+        assert err < 1e-12, (a, err)
+
+
+@pytest.mark.parametrize("n,case", [(9, "sine"), (17, "sine"), (17, "inclusion"), (17, "annulus")])
+def test_multigrid_solution_equals_dense_direct_solve(oracle, n, case):
+    inst = {"sine": lambda: I.config1(n),
+            "inclusion": lambda: I.inclusion_instance(n, 0.25, 25.0, 4),
+            "annulus": lambda: I.annulus_log(n)}[case]()
+    P = oracle.prepare(inst)
+    Auu, rhs = X.system(inst.grid, P.exx, P.exy, P.eyy, P.b, P.phi0)
+    x = np.linalg.solve(Auu.toarray(), rhs)
+    np.linalg.cholesky(Auu.toarray())  # SPD
+    phi, cyc, hist = oracle.solve(P.A, P.b, P.phi0, rtol=1e-14, coarse_max=4)
+    assert cyc >= 1
+    m = inst.grid.interior_mask()
+    assert np.abs(phi[m] - x).max() <= 1e-12 * np.abs(x).max()
+    # and through flexible-free PCG
+    phi2, _, _ = oracle.pcg_solve(P.A, P.b, P.phi0, rtol=1e-14, coarse_max=4)
+    assert np.abs(phi2[m] - x).max() <= 1e-12 * np.abs(x).max()
+
+
+# ---------------------------------------------------------------- transfers / coarse operator
+@pytest.mark.parametrize("periodic", [False, True])
+def test_restriction_is_a_quarter_of_the_prolongation_transpose(oracle, periodic):
+    gf = I.annulus_grid(33) if periodic else I.Grid(33, 17)
+    nxc, nyc = (gf.nx - 1) // 2 + 1, (gf.ny - 1) // 2 + 1
+    gc = I.Grid(nxc, nyc, gf.x0, gf.y0, gf.lx, gf.ly, gf.periodic_y)
+    rng = np.random.default_rng(3)
+    r = rng.standard_normal(gf.shape) * gf.interior_mask()
+    e = rng.standard_normal(gc.shape) * gc.interior_mask()
+    Rr = oracle.restrict(gf.nx, gf.ny, periodic, r)
+    Pe = oracle.prolong_add(gf.nx, gf.ny, periodic, e, np.zeros(gf.shape))
+    lhs = 4.0 * np.sum(Rr * e)
+    rhs = np.sum(r * Pe)
+    assert abs(lhs - rhs) <= 1e-12 * (abs(lhs) + 1)
+    # P against the independent sparse bilinear matrix
+    Psp = X.prolongation(gf, gc)
+    assert np.allclose(Pe[gf.interior_mask()], Psp @ e[gc.interior_mask()], rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("case", ["sine", "inclusion", "annulus"])
+def test_galerkin_equals_sparse_triple_product(oracle, case):
+    inst = {"sine": lambda: I.config1(33), "inclusion": lambda: I.inclusion_instance(33, 0.25, 10.0, 5),
+            "annulus": lambda: I.annulus_log(33)}[case]()
+    P = oracle.prepare(inst)
+    gf = inst.grid
+    gc = I.Grid((gf.nx - 1) // 2 + 1, (gf.ny - 1) // 2 + 1, gf.x0, gf.y0, gf.lx, gf.ly, gf.periodic_y)
+    Ac = oracle.galerkin(P.A)
+    Af = X.full_operator(gf, P.exx, P.exy, P.eyy)
+    u = X.unknown_ids(gf)
+    Pm = X.prolongation(gf, gc)
+    AH = 0.25 * (Pm.T @ Af[u][:, u] @ Pm)
+    AH_or = X.coupling_matrix(gc, Ac)
+    assert abs(AH_or - AH).max() <= 1e-11 * abs(AH).max()
+
+
+# ---------------------------------------------------------------- smoother
+def test_gauss_seidel_colour_phase_zeroes_its_residual(oracle):
+    inst = I.inclusion_instance(33, 0.25, 10.0, 6)
+    P = oracle.prepare(inst)
+    rng = np.random.default_rng(0)
+    phi = rng.standard_normal(inst.grid.shape) * inst.grid.interior_mask()
+    for c, (ci, cj) in enumerate(((0, 0), (1, 1), (1, 0), (0, 1))):
+        phi = oracle.gs_colour(P.A, phi, P.b, c)
+        r = oracle.residual(P.A, phi, P.b)
+        sel = np.zeros(inst.grid.shape, dtype=bool)
+        sel[cj::2, ci::2] = True
+        sel &= inst.grid.interior_mask()
+        scale = np.abs(P.A.diag[inst.grid.interior_mask()]).max() * np.abs(phi).max()
+        assert np.abs(r[sel]).max() <= 1e-14 * scale
+        other = inst.grid.interior_mask() & ~sel
+        assert np.abs(r[other]).max() > 1e-6 * scale  # the property is not trivially true
+
+
+def test_vcycle_contraction_in_textbook_range(oracle):
+    inst = I.identity_poisson(65)
+    phi, cyc, hist, _ = oracle.solve_instance(inst, rtol=1e-12)
+    rho = hist[2:8] / hist[1:7]
+    assert 0.02 < np.median(rho) < 0.2
+
+
+# ---------------------------------------------------------------- accuracy (Sec. 4)
+def _orders(oracle, make, sizes):
+    errs = []
+    for n in sizes:
+        inst = make(n)
+        phi, *_ = oracle.solve_instance(inst, rtol=1e-13)
+        errs.append(oracle.error_norms(inst.exact, phi))
+    return [[math.log2(errs[k][q] / errs[k + 1][q]) for q in range(3)] for k in range(len(sizes) - 1)]
+
+
+def test_second_order_manufactured_sine_warp(oracle):
+    o = _orders(oracle, I.config1, (33, 65, 129))
+    assert all(1.9 < v < 2.1 for v in o[-1]), o
+
+
+def test_second_order_annulus_log_solution(oracle):
+    o = _orders(oracle, I.annulus_log, (33, 65, 129))
+    assert all(1.9 < v < 2.1 for v in o[-1]), o
+
+
+def test_second_order_circle_poisson_eq43(oracle):
+    """L2 and L1 converge at second order; L_inf approaches it more slowly (about 1.6 at
+    these sizes) because the square-to-circle boundary map of Eq. 44 makes det J vanish
+    at the four corners of the computational square."""
+    o = _orders(oracle, I.circle_poisson, (65, 129, 257))
+    assert 1.8 < o[-1][1] < 2.2 and 1.8 < o[-1][2] < 2.2, o
+    assert o[-1][0] > 1.5, o
+
+
+def test_second_order_circle_laplace_eq45(oracle):
+    o = _orders(oracle, I.circle_laplace, (65, 129, 257))
+    assert all(1.8 < v < 2.2 for v in o[-1]), o
+
+
+def test_paper_eq18_operator_converges_to_the_same_solution(oracle):
+    """The literal Eq. 18 update (non-symmetric) with SOR converges at second order to the
+    continuum solution, like the symmetric form the solver uses."""
+    errs = []
+    for n in (17, 33, 65):
+        inst = I.config1(n)
+        P = oracle.prepare(inst)
+        rho = inst.rho_phys * P.D
+        phi, it = oracle.paper_sor(inst.grid, P.exx, P.exy, P.eyy, rho, P.phi0, omega=1.875, tol=1e-13)
+        errs.append(np.abs(phi - inst.exact).max())
+        sym, *_ = oracle.solve_instance(inst, rtol=1e-13)
+        assert np.abs(phi - sym).max() < 5 * np.abs(sym - inst.exact).max() + 1e-12
+    assert math.log2(errs[-2] / errs[-1]) > 1.85
+
+
+# ---------------------------------------------------------------- input generators
+def test_inclusion_grid_boundary_data_and_positivity(oracle):
+    inst = I.inclusion_instance(129, 0.25, 10.0, 1)
+    xp, yp = inst.map.xp, inst.map.yp
+    i0 = inst.meta["i0"]
+    n = 129
+    i1 = n - 1 - i0
+    g = inst.grid
+    x, y = g.coords()
+    # outer boundary: identity
+    for sl in (np.s_[0, :], np.s_[-1, :], np.s_[:, 0], np.s_[:, -1]):
+        assert np.all(xp[sl] == x[sl]) and np.all(yp[sl] == y[sl])
+    # ring: on the circle of radius r (Eq. 44)
+    r = inst.meta["r"]
+    ring = np.zeros(g.shape, bool)
+    ring[i0:i1 + 1, i0] = ring[i0:i1 + 1, i1] = ring[i0, i0:i1 + 1] = ring[i1, i0:i1 + 1] = True
+    rad = np.hypot(xp[ring] - 0.5, yp[ring] - 0.5)
+    assert np.allclose(rad, r, rtol=1e-13)
+    # discrete harmonic elsewhere
+    lap = I._lap_apply(np.array(xp), g.hx, g.hy) * g.hx * g.hy
+    free = ~ring
+    free[0, :] = free[-1, :] = free[:, 0] = free[:, -1] = False
+    assert np.abs(lap[free]).max() < 1e-12
+    P = oracle.prepare(inst)
+    assert P.status == 0 and P.D.min() > 0

@@ -1,0 +1,116 @@
+/*
+ * mg_kernels.h - single-kernel entry points of libmg on caller-owned device memory.
+ *
+ * Each call enqueues one step of the solver on `stream` (a cudaStream_t; NULL = the
+ * legacy default stream) and returns at once; results appear in stream order.  All
+ * pointers are device pointers owned by the caller.  Arrays use the pitched layout:
+ * node (i, j) at a[i + pitch * j], rows j = 0 .. nyr-1 with nyr = ny - 1 if periodic in
+ * y, else ny; pitch >= nx.  Return values: 0 = enqueued, 1 = bad argument (null pointer,
+ * size, pitch), 4 = CUDA launch error.  Nothing is allocated.
+ *
+ * Operator storage (see mg.h): cE, cN, cNE, cNW hold the couplings of node (i, j) to
+ * (i+1, j), (i, j+1), (i+1, j+1), (i-1, j+1); diag and dinv = 1/diag the diagonal.
+ */
+#ifndef MG_KERNELS_H_
+#define MG_KERNELS_H_
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+  int nx, ny, periodic, pitch;
+  double *cE, *cN, *cNE, *cNW, *diag, *dinv;
+} mgk_op_f64;
+
+typedef struct {
+  int nx, ny, periodic, pitch;
+  float *cE, *cN, *cNE, *cNW, *diag, *dinv;
+} mgk_op_f32;
+
+/*
+ * Coefficient build, analytic map (kind: MG_MAP_* of mg.h, params as there): Jacobian
+ * J_ab = dx'_a/dx_b (Eq. 1) at node x = x0 + i hx, y = y0 + j hy; D = det J; eps from
+ * Eqs. 12-15 times eps_phys (nullable, pitched; Eq. 10 with eps' = s I).  *folded
+ * (device int) is set to 1 where D <= 0 and left unchanged elsewhere.
+ */
+int mgk_eps_analytic(int kind, const double *params4, int nx, int ny, int periodic, double x0,
+                     double y0, double hx, double hy, const double *eps_phys, int pitch, double *D,
+                     double *exx, double *exy, double *eyy, int *folded, void *stream);
+
+/*
+ * Coefficient build from a mapped grid: Jacobian by the central differences of
+ * Eqs. 39-42 (one-sided second order at the ends of a non-periodic line; a periodic y
+ * line wraps, adding (jump_x, jump_y) across the seam), then as mgk_eps_analytic.
+ */
+int mgk_eps_grid(int nx, int ny, int periodic, double hx, double hy, const double *xp,
+                 const double *yp, double jump_x, double jump_y, const double *eps_phys, int pitch,
+                 double *D, double *exx, double *exy, double *eyy, int *folded, void *stream);
+
+/*
+ * Fine-level operator A = -L_h from nodal eps (symmetric conservative form of the
+ * Eq. 18 stencil): E/N couplings -(face mean of eps_xx / eps_yy)/h^2, corner couplings
+ * from (Dx E Dy + Dy E Dx) with E = diag(eps_xy), diagonal = -(sum of the 8 couplings)
+ * at unknowns, 1 at Dirichlet nodes.  Couplings missing at the grid edge are 0.
+ */
+int mgk_assemble(const mgk_op_f64 *A, double hx, double hy, const double *exx, const double *exy,
+                 const double *eyy, void *stream);
+
+/* b = rho_phys * D at unknowns (Eq. 11), 0 at Dirichlet nodes. */
+int mgk_rhs(const mgk_op_f64 *A, const double *rho_phys, const double *D, double *b, void *stream);
+
+/* Galerkin coarse operator A_H = (1/4) P^T A_h P with bilinear P (Sec. 3: A_H of Eq. 23). */
+int mgk_galerkin(const mgk_op_f64 *fine, const mgk_op_f64 *coarse, void *stream);
+
+/* FP32 copy of an operator (rounded to nearest). */
+int mgk_op_to_f32(const mgk_op_f64 *src, const mgk_op_f32 *dst, void *stream);
+
+/* Four-colour Gauss-Seidel (omega = 1, Sec. 2.1), `sweeps` sweeps in colour order
+ * (0,0),(1,1),(1,0),(0,1) of (i mod 2, j mod 2), or the reverse order when reverse != 0.
+ * phi is updated in place at unknowns. */
+int mgk_smooth_f64(const mgk_op_f64 *A, double *phi, const double *b, int sweeps, int reverse,
+                   void *stream);
+int mgk_smooth_f32(const mgk_op_f32 *A, float *phi, const float *b, int sweeps, int reverse,
+                   void *stream);
+
+/* Weighted Jacobi: phi += omega (b - A phi) / diag at unknowns, `sweeps` times; tmp is a
+ * pitched scratch array of the same shape. */
+int mgk_jacobi_f64(const mgk_op_f64 *A, double *phi, const double *b, double *tmp, int sweeps,
+                   double omega, void *stream);
+
+/* r = b - A phi at unknowns, 0 at Dirichlet nodes (Eq. 20). */
+int mgk_residual_f64(const mgk_op_f64 *A, const double *phi, const double *b, double *r,
+                     void *stream);
+
+/* Residual (Eq. 20) fused with full-weighting restriction r_H = I_h^H r_h (Sec. 3):
+ * bH(I,J) = sum of (1/16)[1 2 1; 2 4 2; 1 2 1] r around fine node (2I, 2J); bH has
+ * the coarse sizes ((nx-1)/2+1, (ny-1)/2+1) and pitch pitch_c; coarse Dirichlet nodes get 0. */
+int mgk_resid_restrict_f64(const mgk_op_f64 *A, const double *phi, const double *b, double *bH,
+                           int pitch_c, void *stream);
+int mgk_resid_restrict_f32(const mgk_op_f32 *A, const float *phi, const float *b, float *bH,
+                           int pitch_c, void *stream);
+
+/* phi += I_H^h eH (bilinear interpolation, Eq. 24) at fine unknowns; A gives the fine
+ * sizes and pitch, eH the coarse array with pitch pitch_c. */
+int mgk_prolong_add_f64(const mgk_op_f64 *A, double *phi, const double *eH, int pitch_c,
+                        void *stream);
+int mgk_prolong_add_f32(const mgk_op_f32 *A, float *phi, const float *eH, int pitch_c,
+                        void *stream);
+
+/* Coarsest-level inverse: assembles the dense matrix of the unknowns of A (m <= 256 of
+ * them, lexicographic order, i fastest) and inverts it in place by Gauss-Jordan
+ * elimination in one CTA; inv holds m*m doubles.  *status (device int) = 0, or 11
+ * when a pivot is not positive (operator not SPD). */
+int mgk_coarse_factor(const mgk_op_f64 *A, double *inv, int *status, void *stream);
+
+/* x = A^-1 b on the coarsest level using the inverse from mgk_coarse_factor (one CTA);
+ * Dirichlet nodes of x are left unchanged. */
+int mgk_coarse_solve_f64(const mgk_op_f64 *A, const double *inv, const double *b, double *x,
+                         void *stream);
+int mgk_coarse_solve_f32(const mgk_op_f32 *A, const double *inv, const float *b, float *x,
+                         void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MG_KERNELS_H_ */

@@ -1,0 +1,450 @@
+// Setup kernels: coefficient build (Eqs. 1, 10-15, 39-42), fine-level operator,
+// right-hand side (Eq. 11), Galerkin coarse operators (Sec. 3) and the coarsest-level
+// inverse.  All FP64; they run once per problem (or per geometry update).
+#include "mg_common.cuh"
+#include "mg_kernels.h"
+#include "mg_launch.h"
+
+namespace mg {
+
+static const double kPi = 3.14159265358979323846;
+
+// eps = det(J) J^-1 (s I) J^-T for J = [[a, b], [c, d]] (Eqs. 10, 12-15).
+__device__ __forceinline__ void store_eps(double a, double b, double c, double d, double s,
+                                          size_t k, double* D, double* exx, double* exy,
+                                          double* eyy, int* folded) {
+  const double det = a * d - b * c;
+  if (!(det > 0.0)) atomicOr(folded, 1);
+  D[k] = det;
+  exx[k] = s * (d * d + b * b) / det;   // Eq. 12
+  exy[k] = s * (-d * c - b * a) / det;  // Eq. 13 = Eq. 14
+  eyy[k] = s * (c * c + a * a) / det;   // Eq. 15
+}
+
+__global__ void k_eps_analytic(int kind, double p0, double p1, double p2, double p3, int nx,
+                               int nyr, double x0, double y0, double hx, double hy,
+                               const double* __restrict__ eps, int pitch, double* D, double* exx,
+                               double* exy, double* eyy, int* folded) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= nx || j >= nyr) return;
+  const double x = x0 + i * hx, y = y0 + j * hy;
+  double a = 1.0, b = 0.0, c = 0.0, d = 1.0;  // Jxx Jxy Jyx Jyy
+  switch (kind) {
+    case 1: {  // sine warp
+      double sx, cx, sy, cy, s2x, c2x;
+      sincos(kPi * x, &sx, &cx);
+      sincos(kPi * y, &sy, &cy);
+      sincos(2.0 * kPi * x, &s2x, &c2x);
+      a = 1.0 + p0 * kPi * cx * sy;
+      b = p0 * kPi * sx * cy;
+      c = p0 * 2.0 * kPi * c2x * sy;
+      d = 1.0 + p0 * kPi * s2x * cy;
+      break;
+    }
+    case 2: {  // polar, Eq. 29
+      double sy, cy;
+      sincos(y, &sy, &cy);
+      a = cy;
+      b = -x * sy;
+      c = sy;
+      d = x * cy;
+      break;
+    }
+    case 3:  // sinh stretching, Eq. 52
+      a = p0 * p1 * cosh(p1 * x);
+      d = p0 * p1 * cosh(p1 * y);
+      break;
+    case 4:  // affine
+      a = p0;
+      b = p1;
+      c = p2;
+      d = p3;
+      break;
+    default:
+      break;
+  }
+  const size_t k = (size_t)j * pitch + i;
+  store_eps(a, b, c, d, eps ? eps[k] : 1.0, k, D, exx, exy, eyy, folded);
+}
+
+// d/dx: central difference (Eqs. 39, 41), one-sided second order at the line ends.
+__device__ __forceinline__ double ddx(const double* __restrict__ f, size_t r, int i, int nx,
+                                      double hx) {
+  if (i == 0) return (-3.0 * f[r] + 4.0 * f[r + 1] - f[r + 2]) / (2.0 * hx);
+  if (i == nx - 1) return (3.0 * f[r + nx - 1] - 4.0 * f[r + nx - 2] + f[r + nx - 3]) / (2.0 * hx);
+  return (f[r + i + 1] - f[r + i - 1]) / (2.0 * hx);
+}
+
+// d/dy (Eqs. 40, 42); a periodic line wraps and adds `jump` across the seam.
+__device__ __forceinline__ double ddy(const double* __restrict__ f, int i, int j, int ny, int nyr,
+                                      int periodic, int pitch, double hy, double jump) {
+  if (periodic) {
+    const double fp = (j + 1 >= nyr) ? f[(size_t)(j + 1 - nyr) * pitch + i] + jump
+                                     : f[(size_t)(j + 1) * pitch + i];
+    const double fm = (j - 1 < 0) ? f[(size_t)(j - 1 + nyr) * pitch + i] - jump
+                                  : f[(size_t)(j - 1) * pitch + i];
+    return (fp - fm) / (2.0 * hy);
+  }
+  if (j == 0)
+    return (-3.0 * f[i] + 4.0 * f[(size_t)pitch + i] - f[2 * (size_t)pitch + i]) / (2.0 * hy);
+  if (j == ny - 1)
+    return (3.0 * f[(size_t)(ny - 1) * pitch + i] - 4.0 * f[(size_t)(ny - 2) * pitch + i] +
+            f[(size_t)(ny - 3) * pitch + i]) / (2.0 * hy);
+  return (f[(size_t)(j + 1) * pitch + i] - f[(size_t)(j - 1) * pitch + i]) / (2.0 * hy);
+}
+
+__global__ void k_eps_grid(int nx, int ny, int nyr, int periodic, double hx, double hy,
+                           const double* __restrict__ xp, const double* __restrict__ yp,
+                           double jump_x, double jump_y, const double* __restrict__ eps,
+                           int pitch, double* D, double* exx, double* exy, double* eyy,
+                           int* folded) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= nx || j >= nyr) return;
+  const size_t r = (size_t)j * pitch, k = r + i;
+  const double a = ddx(xp, r, i, nx, hx);                                  // Eq. 39
+  const double b = ddy(xp, i, j, ny, nyr, periodic, pitch, hy, jump_x);    // Eq. 40
+  const double c = ddx(yp, r, i, nx, hx);                                  // Eq. 41
+  const double d = ddy(yp, i, j, ny, nyr, periodic, pitch, hy, jump_y);    // Eq. 42
+  store_eps(a, b, c, d, eps ? eps[k] : 1.0, k, D, exx, exy, eyy, folded);
+}
+
+// Couplings of the symmetric conservative 9-point operator A = -L_h.
+__global__ void k_assemble_couplings(int nx, int ny, int nyr, int periodic, int pitch, double ihx2,
+                                     double ihy2, double ixy4, const double* __restrict__ exx,
+                                     const double* __restrict__ exy,
+                                     const double* __restrict__ eyy, double* cE, double* cN,
+                                     double* cNE, double* cNW) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= nx || j >= nyr) return;
+  const size_t k = (size_t)j * pitch + i;
+  const bool has_up = periodic || (j + 1 <= ny - 1);
+  const int ju = (j + 1 == nyr) ? 0 : j + 1;
+  const size_t ku = (size_t)ju * pitch + i;
+  double e = 0.0, n = 0.0, ne = 0.0, nw = 0.0;
+  if (i + 1 <= nx - 1) e = -0.5 * (exx[k] + exx[k + 1]) * ihx2;
+  if (has_up) {
+    n = -0.5 * (eyy[k] + eyy[ku]) * ihy2;
+    if (i + 1 <= nx - 1) ne = -(exy[k + 1] + exy[ku]) * ixy4;  // to (i+1, j+1)
+    if (i >= 1) nw = (exy[k - 1] + exy[ku]) * ixy4;             // to (i-1, j+1)
+  }
+  cE[k] = e;
+  cN[k] = n;
+  cNE[k] = ne;
+  cNW[k] = nw;
+}
+
+// diag = -(sum of the 8 couplings) at unknowns (zero row sums), 1 at Dirichlet nodes.
+__global__ void k_assemble_diag(int nx, int ny, int nyr, int periodic, int pitch,
+                                const double* __restrict__ cE, const double* __restrict__ cN,
+                                const double* __restrict__ cNE, const double* __restrict__ cNW,
+                                double* diag, double* dinv) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= nx || j >= nyr) return;
+  const size_t k = (size_t)j * pitch + i;
+  const bool unk = (i >= 1 && i <= nx - 2) && (periodic || (j >= 1 && j <= ny - 2));
+  if (!unk) {
+    diag[k] = 1.0;
+    dinv[k] = 1.0;
+    return;
+  }
+  const int jd = (j == 0) ? nyr - 1 : j - 1;
+  const size_t ks = (size_t)jd * pitch + i;
+  const double s = cE[k] + cE[k - 1] + cN[k] + cN[ks] + cNE[k] + cNE[ks - 1] + cNW[k] + cNW[ks + 1];
+  diag[k] = -s;
+  dinv[k] = 1.0 / (-s);
+}
+
+__global__ void k_rhs(int nx, int ny, int nyr, int periodic, int pitch,
+                      const double* __restrict__ rho, int rho_pitch, const double* __restrict__ D,
+                      double* b) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= nx || j >= nyr) return;
+  const bool unk = (i >= 1 && i <= nx - 2) && (periodic || (j >= 1 && j <= ny - 2));
+  const size_t k = (size_t)j * pitch + i;
+  b[k] = unk ? rho[(size_t)j * rho_pitch + i] * D[k] : 0.0;  // Eq. 11
+}
+
+// Bilinear weight of a fine offset d from a coarse node (in fine units).
+__device__ __forceinline__ double pw(int d) { return d == 0 ? 1.0 : ((d == 1 || d == -1) ? 0.5 : 0.0); }
+
+// A[(fi,fj),(fi+di,fj+dj)] through the symmetric storage of the fine level.
+__device__ __forceinline__ double fine_entry(const Lvl<double>& F, int fi, int fj, int di, int dj) {
+  const size_t r0 = (size_t)fj * F.pitch, rd = (size_t)row_dn(fj, F.nyr) * F.pitch;
+  if (dj == 0) {
+    if (di == 0) return F.diag[r0 + fi];
+    return di > 0 ? F.cE[r0 + fi] : F.cE[r0 + fi - 1];
+  }
+  if (dj > 0) {
+    if (di == 0) return F.cN[r0 + fi];
+    return di > 0 ? F.cNE[r0 + fi] : F.cNW[r0 + fi];
+  }
+  if (di == 0) return F.cN[rd + fi];
+  return di < 0 ? F.cNE[rd + fi - 1] : F.cNW[rd + fi + 1];
+}
+
+// A_H = (1/4) P^T A_h P: for each coarse unknown I, row(I, I+o) = (1/4) sum_k sum_l
+// P(k, I) A(k, l) P(l, I+o) over fine k in the 3x3 support of I and the 9 stencil
+// neighbours l of k.
+__global__ void k_galerkin(Lvl<double> F, int nxc, int nyc, int nyrc, int pitchc, double* cE,
+                           double* cN, double* cNE, double* cNW, double* diag, double* dinv) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = blockIdx.y * blockDim.y + threadIdx.y;
+  if (I >= nxc || J >= nyrc) return;
+  const size_t K = (size_t)J * pitchc + I;
+  const bool unk = (I >= 1 && I <= nxc - 2) && (F.periodic || (J >= 1 && J <= nyc - 2));
+  if (!unk) {
+    cE[K] = cN[K] = cNE[K] = cNW[K] = 0.0;
+    diag[K] = dinv[K] = 1.0;
+    return;
+  }
+  double row[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) row[a][b] = 0.0;
+#pragma unroll 1
+  for (int kj = -1; kj <= 1; ++kj) {
+    int fj = 2 * J + kj;
+    if (fj < 0) fj += F.nyr;
+    if (fj >= F.nyr) fj -= F.nyr;
+#pragma unroll 1
+    for (int ki = -1; ki <= 1; ++ki) {
+      const int fi = 2 * I + ki;
+      const double wk = 0.25 * pw(ki) * pw(kj);
+#pragma unroll
+      for (int lj = -1; lj <= 1; ++lj)
+#pragma unroll
+        for (int li = -1; li <= 1; ++li) {
+          const double a = wk * fine_entry(F, fi, fj, li, lj);
+          const int dx = ki + li, dy = kj + lj;
+#pragma unroll
+          for (int oj = -1; oj <= 1; ++oj)
+#pragma unroll
+            for (int oi = -1; oi <= 1; ++oi) {
+              const double wl = pw(dx - 2 * oi) * pw(dy - 2 * oj);
+              if (wl != 0.0) row[oi + 1][oj + 1] += a * wl;
+            }
+        }
+    }
+  }
+  diag[K] = row[1][1];
+  dinv[K] = 1.0 / row[1][1];
+  cE[K] = row[2][1];
+  cN[K] = row[1][2];
+  cNE[K] = row[2][2];
+  cNW[K] = row[0][2];
+}
+
+__global__ void k_op_to_f32(int nx, int nyr, int ps, int pd, const double* __restrict__ a0,
+                            const double* __restrict__ a1, const double* __restrict__ a2,
+                            const double* __restrict__ a3, const double* __restrict__ a4,
+                            const double* __restrict__ a5, float* b0, float* b1, float* b2,
+                            float* b3, float* b4, float* b5) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= nx || j >= nyr) return;
+  const size_t s = (size_t)j * ps + i, d = (size_t)j * pd + i;
+  b0[d] = (float)a0[s];
+  b1[d] = (float)a1[s];
+  b2[d] = (float)a2[s];
+  b3[d] = (float)a3[s];
+  b4[d] = (float)a4[s];
+  b5[d] = (float)a5[s];
+}
+
+// Dense matrix of the coarsest level's unknowns, inverted in place by Gauss-Jordan
+// elimination (SPD: no pivoting).  One CTA of kCoarseThreads threads.
+__global__ void __launch_bounds__(kCoarseThreads) k_coarse_factor(Lvl<double> L, double* M,
+                                                                  int* status) {
+  __shared__ double col[kCoarseMax];
+  __shared__ double rowk[kCoarseMax];
+  const int ux = L.nx - 2;
+  const int uy = L.periodic ? L.nyr : L.ny - 2;
+  const int m = ux * uy;
+  const int j0 = L.periodic ? 0 : 1;
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) M[e] = 0.0;
+  __syncthreads();
+  for (int p = threadIdx.x; p < m; p += blockDim.x) {
+    const int i = 1 + p % ux, j = j0 + p / ux;
+    for (int dj = -1; dj <= 1; ++dj)
+      for (int di = -1; di <= 1; ++di) {
+        const int ni = i + di;
+        int nj = j + dj;
+        if (L.periodic) nj = (nj + L.nyr) % L.nyr;
+        const bool unk = (ni >= 1 && ni <= L.nx - 2) &&
+                         (L.periodic || (nj >= 1 && nj <= L.ny - 2));
+        if (!unk) continue;
+        const int q = (ni - 1) + ux * (nj - j0);
+        M[(size_t)p * m + q] += fine_entry(L, i, j, di, dj);
+      }
+  }
+  __syncthreads();
+  for (int k = 0; k < m; ++k) {
+    const double piv = M[(size_t)k * m + k];
+    if (!(piv > 0.0)) {
+      if (threadIdx.x == 0) *status = 11;
+      return;  // uniform: every thread read the same pivot
+    }
+    const double ip = 1.0 / piv;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) col[i] = M[(size_t)i * m + k];
+    __syncthreads();
+    for (int jj = threadIdx.x; jj < m; jj += blockDim.x) {
+      const double v = (jj == k) ? ip : M[(size_t)k * m + jj] * ip;
+      rowk[jj] = v;
+      M[(size_t)k * m + jj] = v;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+      const int i = e / m, jj = e % m;
+      if (i == k) continue;
+      const double f = col[i];
+      M[e] = (jj == k) ? -f * ip : M[e] - f * rowk[jj];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *status = 0;
+}
+
+// ------------------------------------------------------------------ host launchers
+static dim3 grid2(int nx, int ny, dim3 b) { return dim3((nx + b.x - 1) / b.x, (ny + b.y - 1) / b.y); }
+
+cudaError_t launch_eps_analytic(int kind, const double* prm, int nx, int ny, int periodic,
+                                double x0, double y0, double hx, double hy, const double* eps,
+                                int pitch, double* D, double* exx, double* exy, double* eyy,
+                                int* folded, cudaStream_t s) {
+  const int nyr = rows_stored(ny, periodic);
+  dim3 b(32, 8);
+  k_eps_analytic<<<grid2(nx, nyr, b), b, 0, s>>>(kind, prm[0], prm[1], prm[2], prm[3], nx, nyr, x0,
+                                                 y0, hx, hy, eps, pitch, D, exx, exy, eyy, folded);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_eps_grid(int nx, int ny, int periodic, double hx, double hy, const double* xp,
+                            const double* yp, double jx, double jy, const double* eps, int pitch,
+                            double* D, double* exx, double* exy, double* eyy, int* folded,
+                            cudaStream_t s) {
+  const int nyr = rows_stored(ny, periodic);
+  dim3 b(32, 8);
+  k_eps_grid<<<grid2(nx, nyr, b), b, 0, s>>>(nx, ny, nyr, periodic, hx, hy, xp, yp, jx, jy, eps,
+                                             pitch, D, exx, exy, eyy, folded);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_assemble(const OpF64& A, double hx, double hy, const double* exx,
+                            const double* exy, const double* eyy, cudaStream_t s) {
+  const int nyr = rows_stored(A.ny, A.periodic);
+  dim3 b(32, 8);
+  k_assemble_couplings<<<grid2(A.nx, nyr, b), b, 0, s>>>(
+      A.nx, A.ny, nyr, A.periodic, A.pitch, 1.0 / (hx * hx), 1.0 / (hy * hy), 1.0 / (4.0 * hx * hy),
+      exx, exy, eyy, A.cE, A.cN, A.cNE, A.cNW);
+  k_assemble_diag<<<grid2(A.nx, nyr, b), b, 0, s>>>(A.nx, A.ny, nyr, A.periodic, A.pitch, A.cE,
+                                                    A.cN, A.cNE, A.cNW, A.diag, A.dinv);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rhs(const OpF64& A, const double* rho, int rho_pitch, const double* D, double* b,
+                       cudaStream_t s) {
+  const int nyr = rows_stored(A.ny, A.periodic);
+  dim3 bl(32, 8);
+  k_rhs<<<grid2(A.nx, nyr, bl), bl, 0, s>>>(A.nx, A.ny, nyr, A.periodic, A.pitch, rho, rho_pitch, D,
+                                            b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_galerkin(const OpF64& F, const OpF64& C, cudaStream_t s) {
+  const int nyrc = rows_stored(C.ny, C.periodic);
+  dim3 b(32, 4);
+  k_galerkin<<<grid2(C.nx, nyrc, b), b, 0, s>>>(lvl_of(F), C.nx, C.ny, nyrc, C.pitch, C.cE, C.cN,
+                                                C.cNE, C.cNW, C.diag, C.dinv);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_op_to_f32(const OpF64& A, const OpF32& B, cudaStream_t s) {
+  const int nyr = rows_stored(A.ny, A.periodic);
+  dim3 b(32, 8);
+  k_op_to_f32<<<grid2(A.nx, nyr, b), b, 0, s>>>(A.nx, nyr, A.pitch, B.pitch, A.cE, A.cN, A.cNE,
+                                                A.cNW, A.diag, A.dinv, B.cE, B.cN, B.cNE, B.cNW,
+                                                B.diag, B.dinv);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coarse_factor(const OpF64& A, double* inv, int* status, cudaStream_t s) {
+  k_coarse_factor<<<1, kCoarseThreads, 0, s>>>(lvl_of(A), inv, status);
+  return cudaGetLastError();
+}
+
+}  // namespace mg
+
+// ------------------------------------------------------------------ C ABI (mg_kernels.h)
+using namespace mg;
+
+static bool op_ok(const mgk_op_f64* A) {
+  return A && A->nx >= 3 && A->ny >= 3 && A->pitch >= A->nx && A->cE && A->cN && A->cNE && A->cNW &&
+         A->diag && A->dinv && (!A->periodic || A->ny >= 3);
+}
+
+extern "C" int mgk_eps_analytic(int kind, const double* params4, int nx, int ny, int periodic,
+                                double x0, double y0, double hx, double hy, const double* eps_phys,
+                                int pitch, double* D, double* exx, double* exy, double* eyy,
+                                int* folded, void* stream) {
+  if (kind < 0 || kind > 4 || !params4 || nx < 3 || ny < 3 || pitch < nx || !D || !exx || !exy ||
+      !eyy || !folded)
+    return 1;
+  return launch_eps_analytic(kind, params4, nx, ny, periodic, x0, y0, hx, hy, eps_phys, pitch, D,
+                             exx, exy, eyy, folded, (cudaStream_t)stream) == cudaSuccess ? 0 : 4;
+}
+
+extern "C" int mgk_eps_grid(int nx, int ny, int periodic, double hx, double hy, const double* xp,
+                            const double* yp, double jump_x, double jump_y, const double* eps_phys,
+                            int pitch, double* D, double* exx, double* exy, double* eyy,
+                            int* folded, void* stream) {
+  if (nx < 3 || ny < 3 || (periodic ? ny - 1 : ny) < 3 || pitch < nx || !xp || !yp || !D || !exx ||
+      !exy || !eyy || !folded)
+    return 1;
+  return launch_eps_grid(nx, ny, periodic, hx, hy, xp, yp, jump_x, jump_y, eps_phys, pitch, D, exx,
+                         exy, eyy, folded, (cudaStream_t)stream) == cudaSuccess ? 0 : 4;
+}
+
+extern "C" int mgk_assemble(const mgk_op_f64* A, double hx, double hy, const double* exx,
+                            const double* exy, const double* eyy, void* stream) {
+  if (!op_ok(A) || !exx || !exy || !eyy || !(hx > 0) || !(hy > 0)) return 1;
+  return launch_assemble(op_from(*A), hx, hy, exx, exy, eyy, (cudaStream_t)stream) == cudaSuccess
+             ? 0 : 4;
+}
+
+extern "C" int mgk_rhs(const mgk_op_f64* A, const double* rho_phys, const double* D, double* b,
+                       void* stream) {
+  if (!A || A->nx < 3 || A->ny < 3 || A->pitch < A->nx || !rho_phys || !D || !b) return 1;
+  return launch_rhs(op_from(*A), rho_phys, A->pitch, D, b, (cudaStream_t)stream) == cudaSuccess
+             ? 0 : 4;
+}
+
+extern "C" int mgk_galerkin(const mgk_op_f64* fine, const mgk_op_f64* coarse, void* stream) {
+  if (!op_ok(fine) || !op_ok(coarse) || (fine->nx - 1) % 2 || (fine->ny - 1) % 2 ||
+      coarse->nx != (fine->nx - 1) / 2 + 1 || coarse->ny != (fine->ny - 1) / 2 + 1 ||
+      coarse->periodic != fine->periodic)
+    return 1;
+  return launch_galerkin(op_from(*fine), op_from(*coarse), (cudaStream_t)stream) == cudaSuccess
+             ? 0 : 4;
+}
+
+extern "C" int mgk_op_to_f32(const mgk_op_f64* src, const mgk_op_f32* dst, void* stream) {
+  if (!op_ok(src) || !dst || dst->nx != src->nx || dst->ny != src->ny || dst->pitch < dst->nx ||
+      !dst->cE || !dst->cN || !dst->cNE || !dst->cNW || !dst->diag || !dst->dinv)
+    return 1;
+  return launch_op_to_f32(op_from(*src), op_from(*dst), (cudaStream_t)stream) == cudaSuccess ? 0
+                                                                                                : 4;
+}
+
+extern "C" int mgk_coarse_factor(const mgk_op_f64* A, double* inv, int* status, void* stream) {
+  if (!op_ok(A) || !inv || !status) return 1;
+  const int uy = A->periodic ? A->ny - 1 : A->ny - 2;
+  if ((A->nx - 2) * uy > kCoarseMax || uy < 1) return 1;
+  return launch_coarse_factor(op_from(*A), inv, status, (cudaStream_t)stream) == cudaSuccess ? 0
+                                                                                               : 4;
+}

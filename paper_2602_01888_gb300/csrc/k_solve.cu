@@ -1,0 +1,450 @@
+// Solve-loop kernels on the finest level (FP64): initialisation, residual norms and the
+// convergence test (stopping rule ||r|| / ||r_0|| <= rtol, Sec. 3 "repeated until
+// convergence"), flexible conjugate-gradient updates around the multigrid
+// preconditioner, and the FP32 <-> FP64 hand-over of iterative refinement.
+//
+// Reductions are deterministic: every block writes one partial sum (fixed-order tree),
+// and the last block to finish sums the partials in index order.  Node loops use a grid
+// of at most kRedBlocks blocks that strides over the rows.
+#include <cuda_runtime.h>
+
+#include "mg_common.cuh"
+#include "mg_launch.h"
+#include "mg_solve_kernels.h"
+
+namespace mg {
+
+constexpr int kNT = 256;
+
+#define NODE_LOOP(L)                                                            \
+  for (int j = blockIdx.y; j < (L).nyr; j += gridDim.y)                         \
+    for (int i = blockIdx.x * kNT + threadIdx.x; i < (L).nx; i += gridDim.x * kNT)
+
+__device__ __forceinline__ unsigned nblocks() { return gridDim.x * gridDim.y; }
+__device__ __forceinline__ unsigned bid() { return blockIdx.y * gridDim.x + blockIdx.x; }
+
+// Convergence decision, run by one thread of the last block.
+// recursive != 0: rr comes from the recursively updated CG residual; meeting rtol then
+// only requests a check of the true residual (residual replacement) in the next pass.
+__device__ void decide(SolveState* st, double rr, cudaGraphConditionalHandle h, int has_h,
+                       int recursive = 0) {
+  const double rel = sqrt(rr) / st->r0;
+  st->rr = rr;
+  st->rel = rel;
+  if (st->hist_n < 256) st->hist[st->hist_n] = rel;
+  st->hist_n += 1;
+  int done = 0;
+  if (!(rel < 1e30)) {  // NaN or Inf
+    st->status = 7;
+    done = 1;
+  } else if (rel <= st->rtol) {
+    st->status = 0;
+    if (recursive) st->verify = 1; else done = 1;
+  } else if (st->it >= st->max_iters) {
+    st->status = 6;
+    done = 1;
+  }
+  // power-of-two scaling that brings the rms of r to [1, 2) before the FP32 cycle
+  const double rms = sqrt(rr / (double)st->n_unknowns);
+  if (rms > 0.0 && rms < 1e300) {
+    const int e = ilogb(rms);
+    st->scale = ldexp(1.0, -e);
+    st->inv_scale = ldexp(1.0, e);
+  } else {
+    st->scale = st->inv_scale = 1.0;
+  }
+  st->done = done;
+  if (has_h) cudaGraphSetConditional(h, done ? 0u : 1u);
+}
+
+// x: Dirichlet ring from bc (or 0), unknowns from the warm start (or 0); b = rho' D (Eq. 11).
+__global__ void __launch_bounds__(kNT) k_solve_init(Lvl<double> L, const SolveArgs* __restrict__ a,
+                                                    const double* __restrict__ D,
+                                                    double* __restrict__ x, double* __restrict__ b,
+                                                    SolveState* st) {
+  const int up = a->user_pitch;
+  NODE_LOOP(L) {
+    const size_t k = (size_t)j * L.pitch + i, u = (size_t)j * up + i;
+    if (is_unknown(L, i, j)) {
+      x[k] = a->warm ? a->phi_in[u] : 0.0;
+      b[k] = a->rho[u] * D[k];
+    } else {
+      x[k] = a->bc ? a->bc[u] : 0.0;
+      b[k] = 0.0;
+    }
+  }
+  if (bid() == 0 && threadIdx.x == 0) {
+    st->it = 0;
+    st->done = 0;
+    st->status = 0;
+    st->hist_n = 0;
+    st->verify = 0;
+    st->guard = 0;
+    st->rtol = a->rtol;
+    st->max_iters = a->max_iters;
+    st->beta = 0.0;
+    st->pq_old = 0.0;
+    st->scale = st->inv_scale = 1.0;
+    st->n_unknowns = a->n_unknowns;
+  }
+}
+
+// r = b - A x (written when r != nullptr), ||r||^2 and the reference ||r_0||^2 with the
+// unknowns set to zero; the last block sets r0, decides, and sets the graph condition.
+__global__ void __launch_bounds__(kNT) k_resid_init(Lvl<double> L, const double* __restrict__ x,
+                                                    const double* __restrict__ b,
+                                                    double* __restrict__ r, SolveState* st,
+                                                    double* part, cudaGraphConditionalHandle h,
+                                                    int has_h) {
+  __shared__ double sh[kNT / 32];
+  __shared__ int flag;
+  double s_rr = 0.0, s_r0 = 0.0;
+  NODE_LOOP(L) {
+    const size_t k = (size_t)j * L.pitch + i;
+    double rv = 0.0;
+    if (is_unknown(L, i, j)) {
+      rv = b[k] - fma(L.diag[k], x[k], offdiag(L, x, i, j));
+      // residual of the same ring with zero unknowns: only Dirichlet neighbours count
+      const int jd = row_dn(j, L.nyr), ju = row_up(j, L.nyr);
+      const size_t r0 = (size_t)j * L.pitch, rd = (size_t)jd * L.pitch, ru = (size_t)ju * L.pitch;
+      double t = 0.0;
+      if (!is_unknown(L, i + 1, j)) t += L.cE[r0 + i] * x[r0 + i + 1];
+      if (!is_unknown(L, i - 1, j)) t += L.cE[r0 + i - 1] * x[r0 + i - 1];
+      if (!is_unknown(L, i, ju)) t += L.cN[r0 + i] * x[ru + i];
+      if (!is_unknown(L, i, jd)) t += L.cN[rd + i] * x[rd + i];
+      if (!is_unknown(L, i + 1, ju)) t += L.cNE[r0 + i] * x[ru + i + 1];
+      if (!is_unknown(L, i - 1, jd)) t += L.cNE[rd + i - 1] * x[rd + i - 1];
+      if (!is_unknown(L, i - 1, ju)) t += L.cNW[r0 + i] * x[ru + i - 1];
+      if (!is_unknown(L, i + 1, jd)) t += L.cNW[rd + i + 1] * x[rd + i + 1];
+      const double z = b[k] - t;
+      s_r0 += z * z;
+      s_rr += rv * rv;
+    }
+    if (r) r[k] = rv;
+  }
+  const double a0 = block_sum<kNT>(s_rr, sh);
+  const double a1 = block_sum<kNT>(s_r0, sh);
+  if (threadIdx.x == 0) {
+    part[bid()] = a0;
+    part[nblocks() + bid()] = a1;
+  }
+  if (last_block_arrival(&st->ticket[0], nblocks(), &flag)) {
+    const double rr = reduce_partials<kNT>(part, nblocks(), sh);
+    const double q0 = reduce_partials<kNT>(part + nblocks(), nblocks(), sh);
+    if (threadIdx.x == 0) {
+      st->r0 = (q0 > 0.0) ? sqrt(q0) : 1.0;
+      decide(st, rr, h, has_h);
+    }
+  }
+}
+
+// ||b - A x||^2 for the plain-cycle loop; optional r output; the last block decides.
+__global__ void __launch_bounds__(kNT) k_resid_check(Lvl<double> L, const double* __restrict__ x,
+                                                     const double* __restrict__ b,
+                                                     double* __restrict__ r, SolveState* st,
+                                                     double* part, cudaGraphConditionalHandle h,
+                                                     int has_h) {
+  __shared__ double sh[kNT / 32];
+  __shared__ int flag;
+  double s = 0.0;
+  NODE_LOOP(L) {
+    const size_t k = (size_t)j * L.pitch + i;
+    double rv = 0.0;
+    if (is_unknown(L, i, j)) {
+      rv = b[k] - fma(L.diag[k], x[k], offdiag(L, x, i, j));
+      s += rv * rv;
+    }
+    if (r) r[k] = rv;
+  }
+  const double a0 = block_sum<kNT>(s, sh);
+  if (threadIdx.x == 0) part[bid()] = a0;
+  if (last_block_arrival(&st->ticket[1], nblocks(), &flag)) {
+    const double rr = reduce_partials<kNT>(part, nblocks(), sh);
+    if (threadIdx.x == 0) decide(st, rr, h, has_h);
+  }
+}
+
+// b32 = fp32(r * scale) (scale: power of two from the last decision).
+__global__ void __launch_bounds__(kNT) k_r_to_f32(Lvl<double> L, const double* __restrict__ r,
+                                                  float* __restrict__ b32, int pitch32,
+                                                  const SolveState* __restrict__ st) {
+  if (st->done) return;
+  const double sc = st->scale;
+  NODE_LOOP(L) { b32[(size_t)j * pitch32 + i] = (float)(r[(size_t)j * L.pitch + i] * sc); }
+}
+
+// Plain-cycle refinement step: x += inv_scale * e32 at unknowns; iteration counter.
+__global__ void __launch_bounds__(kNT) k_add_f32(Lvl<double> L, double* __restrict__ x,
+                                                 const float* __restrict__ e32, int pitch32,
+                                                 SolveState* st) {
+  if (st->done) return;
+  const double is = st->inv_scale;
+  NODE_LOOP(L) {
+    if (is_unknown(L, i, j)) x[(size_t)j * L.pitch + i] += is * (double)e32[(size_t)j * pitch32 + i];
+  }
+}
+
+// Last node of every loop body: counts passes and ends the loop after 2 max_iters + 8
+// of them even if no convergence decision was reached (status: not converged).
+__global__ void k_loop_guard(SolveState* st, cudaGraphConditionalHandle h) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  st->guard += 1;
+  if (!st->done && st->guard > 2 * st->max_iters + 8) {
+    st->done = 1;
+    st->status = 6;
+    cudaGraphSetConditional(h, 0u);
+  }
+}
+
+__global__ void k_iter_inc(SolveState* st) {
+  if (!st->done && threadIdx.x == 0 && blockIdx.x == 0) st->it += 1;
+}
+
+// ---- flexible CG (FCG(1)): p = z + beta p_old, beta = -(z . q_old) / (p_old . q_old);
+// alpha = (p . r) / (p . q); x += alpha p; r -= alpha q.
+template <typename TZ>
+__global__ void __launch_bounds__(kNT) k_fcg_zq(Lvl<double> L, const TZ* __restrict__ z, int zp,
+                                                const double* __restrict__ q, SolveState* st,
+                                                double* part) {
+  if (st->done || st->it == 0) {
+    if (!st->done && bid() == 0 && threadIdx.x == 0) st->beta = 0.0;
+    return;
+  }
+  __shared__ double sh[kNT / 32];
+  __shared__ int flag;
+  const double is = (sizeof(TZ) == 4) ? st->inv_scale : 1.0;
+  double s = 0.0;
+  NODE_LOOP(L) {
+    if (is_unknown(L, i, j)) s += (is * (double)z[(size_t)j * zp + i]) * q[(size_t)j * L.pitch + i];
+  }
+  const double a0 = block_sum<kNT>(s, sh);
+  if (threadIdx.x == 0) part[bid()] = a0;
+  if (last_block_arrival(&st->ticket[2], nblocks(), &flag)) {
+    const double zq = reduce_partials<kNT>(part, nblocks(), sh);
+    if (threadIdx.x == 0) {
+      st->zq = zq;
+      st->beta = (st->pq_old != 0.0) ? -zq / st->pq_old : 0.0;
+    }
+  }
+}
+
+template <typename TZ>
+__global__ void __launch_bounds__(kNT) k_fcg_p(Lvl<double> L, const TZ* __restrict__ z, int zp,
+                                               double* __restrict__ p, const SolveState* st) {
+  if (st->done) return;
+  const double is = (sizeof(TZ) == 4) ? st->inv_scale : 1.0;
+  const double beta = st->beta;
+  const bool first = (st->it == 0);
+  NODE_LOOP(L) {
+    if (!is_unknown(L, i, j)) continue;
+    const size_t k = (size_t)j * L.pitch + i;
+    const double zz = is * (double)z[(size_t)j * zp + i];
+    p[k] = first ? zz : fma(beta, p[k], zz);
+  }
+}
+
+__global__ void __launch_bounds__(kNT) k_fcg_q(Lvl<double> L, const double* __restrict__ p,
+                                               const double* __restrict__ r,
+                                               double* __restrict__ q, SolveState* st,
+                                               double* part) {
+  if (st->done) return;
+  __shared__ double sh[kNT / 32];
+  __shared__ int flag;
+  double spq = 0.0, spr = 0.0;
+  NODE_LOOP(L) {
+    const size_t k = (size_t)j * L.pitch + i;
+    double qv = 0.0;
+    if (is_unknown(L, i, j)) {
+      qv = fma(L.diag[k], p[k], offdiag(L, p, i, j));
+      spq += p[k] * qv;
+      spr += p[k] * r[k];
+    }
+    q[k] = qv;
+  }
+  const double a0 = block_sum<kNT>(spq, sh);
+  const double a1 = block_sum<kNT>(spr, sh);
+  if (threadIdx.x == 0) {
+    part[bid()] = a0;
+    part[nblocks() + bid()] = a1;
+  }
+  if (last_block_arrival(&st->ticket[3], nblocks(), &flag)) {
+    const double pq = reduce_partials<kNT>(part, nblocks(), sh);
+    const double pr = reduce_partials<kNT>(part + nblocks(), nblocks(), sh);
+    if (threadIdx.x == 0) {
+      st->pq = pq;
+      st->pr = pr;
+      st->alpha = (pq != 0.0) ? pr / pq : 0.0;
+      st->pq_old = pq;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kNT) k_fcg_update(Lvl<double> L, double* __restrict__ x,
+                                                    double* __restrict__ r,
+                                                    const double* __restrict__ p,
+                                                    const double* __restrict__ q, SolveState* st,
+                                                    double* part, cudaGraphConditionalHandle h,
+                                                    int has_h) {
+  if (st->done) return;
+  __shared__ double sh[kNT / 32];
+  __shared__ int flag;
+  const double alpha = st->alpha;
+  double s = 0.0;
+  NODE_LOOP(L) {
+    if (!is_unknown(L, i, j)) continue;
+    const size_t k = (size_t)j * L.pitch + i;
+    x[k] = fma(alpha, p[k], x[k]);
+    const double rv = fma(-alpha, q[k], r[k]);
+    r[k] = rv;
+    s += rv * rv;
+  }
+  const double a0 = block_sum<kNT>(s, sh);
+  if (threadIdx.x == 0) part[bid()] = a0;
+  if (last_block_arrival(&st->ticket[4], nblocks(), &flag)) {
+    const double rr = reduce_partials<kNT>(part, nblocks(), sh);
+    if (threadIdx.x == 0) {
+      st->it += 1;
+      decide(st, rr, h, has_h, 1);
+    }
+  }
+}
+
+// Residual replacement: when the recursive residual met rtol, r = b - A x is recomputed;
+// the solve stops only if the true residual meets rtol, else CG continues from it.
+__global__ void __launch_bounds__(kNT) k_fcg_verify(Lvl<double> L, const double* __restrict__ x,
+                                                    const double* __restrict__ b,
+                                                    double* __restrict__ r, SolveState* st,
+                                                    double* part, cudaGraphConditionalHandle h,
+                                                    int has_h) {
+  if (st->done || !st->verify) return;
+  __shared__ double sh[kNT / 32];
+  __shared__ int flag;
+  double s = 0.0;
+  NODE_LOOP(L) {
+    const size_t k = (size_t)j * L.pitch + i;
+    double rv = 0.0;
+    if (is_unknown(L, i, j)) {
+      rv = b[k] - fma(L.diag[k], x[k], offdiag(L, x, i, j));
+      s += rv * rv;
+    }
+    r[k] = rv;
+  }
+  const double a0 = block_sum<kNT>(s, sh);
+  if (threadIdx.x == 0) part[bid()] = a0;
+  if (last_block_arrival(&st->ticket[5], nblocks(), &flag)) {
+    const double rr = reduce_partials<kNT>(part, nblocks(), sh);
+    if (threadIdx.x == 0) {
+      st->verify = 0;
+      decide(st, rr, h, has_h, 0);
+    }
+  }
+}
+
+// phi_out (caller layout) = x at every node.
+__global__ void __launch_bounds__(kNT) k_copy_out(Lvl<double> L, const double* __restrict__ x,
+                                                  const SolveArgs* __restrict__ a) {
+  const int up = a->user_pitch;
+  double* out = a->phi_out;
+  NODE_LOOP(L) { out[(size_t)j * up + i] = x[(size_t)j * L.pitch + i]; }
+}
+
+// ------------------------------------------------------------------ launchers
+dim3 red_grid(int nx, int nyr) {
+  const int gx = (nx + kNT - 1) / kNT;
+  int gy = kRedBlocks / gx;
+  if (gy < 1) gy = 1;
+  if (gy > nyr) gy = nyr;
+  return dim3(gx, gy);
+}
+
+#define CHK() return cudaGetLastError()
+
+cudaError_t launch_solve_init(const OpF64& A, const SolveArgs* a, const double* D, double* x,
+                              double* b, SolveState* st, cudaStream_t s) {
+  const Lvl<double> L = lvl_of(A);
+  k_solve_init<<<red_grid(L.nx, L.nyr), kNT, 0, s>>>(L, a, D, x, b, st);
+  CHK();
+}
+cudaError_t launch_resid_init(const OpF64& A, const double* x, const double* b, double* r,
+                              SolveState* st, double* part, cudaGraphConditionalHandle h,
+                              int has_h, cudaStream_t s) {
+  const Lvl<double> L = lvl_of(A);
+  k_resid_init<<<red_grid(L.nx, L.nyr), kNT, 0, s>>>(L, x, b, r, st, part, h, has_h);
+  CHK();
+}
+cudaError_t launch_resid_check(const OpF64& A, const double* x, const double* b, double* r,
+                               SolveState* st, double* part, cudaGraphConditionalHandle h,
+                               int has_h, cudaStream_t s) {
+  const Lvl<double> L = lvl_of(A);
+  k_resid_check<<<red_grid(L.nx, L.nyr), kNT, 0, s>>>(L, x, b, r, st, part, h, has_h);
+  CHK();
+}
+cudaError_t launch_r_to_f32(const OpF64& A, const double* r, float* b32, int pitch32,
+                            const SolveState* st, cudaStream_t s) {
+  const Lvl<double> L = lvl_of(A);
+  k_r_to_f32<<<red_grid(L.nx, L.nyr), kNT, 0, s>>>(L, r, b32, pitch32, st);
+  CHK();
+}
+cudaError_t launch_add_f32(const OpF64& A, double* x, const float* e32, int pitch32,
+                           SolveState* st, cudaStream_t s) {
+  const Lvl<double> L = lvl_of(A);
+  k_add_f32<<<red_grid(L.nx, L.nyr), kNT, 0, s>>>(L, x, e32, pitch32, st);
+  CHK();
+}
+cudaError_t launch_loop_guard(SolveState* st, cudaGraphConditionalHandle h, cudaStream_t s) {
+  k_loop_guard<<<1, 32, 0, s>>>(st, h);
+  CHK();
+}
+cudaError_t launch_iter_inc(SolveState* st, cudaStream_t s) {
+  k_iter_inc<<<1, 32, 0, s>>>(st);
+  CHK();
+}
+template <typename TZ>
+cudaError_t launch_fcg_zq(const OpF64& A, const TZ* z, int zp, const double* q, SolveState* st,
+                          double* part, cudaStream_t s) {
+  const Lvl<double> L = lvl_of(A);
+  k_fcg_zq<TZ><<<red_grid(L.nx, L.nyr), kNT, 0, s>>>(L, z, zp, q, st, part);
+  CHK();
+}
+template <typename TZ>
+cudaError_t launch_fcg_p(const OpF64& A, const TZ* z, int zp, double* p, const SolveState* st,
+                         cudaStream_t s) {
+  const Lvl<double> L = lvl_of(A);
+  k_fcg_p<TZ><<<red_grid(L.nx, L.nyr), kNT, 0, s>>>(L, z, zp, p, st);
+  CHK();
+}
+template cudaError_t launch_fcg_zq<double>(const OpF64&, const double*, int, const double*,
+                                           SolveState*, double*, cudaStream_t);
+template cudaError_t launch_fcg_zq<float>(const OpF64&, const float*, int, const double*,
+                                          SolveState*, double*, cudaStream_t);
+template cudaError_t launch_fcg_p<double>(const OpF64&, const double*, int, double*,
+                                          const SolveState*, cudaStream_t);
+template cudaError_t launch_fcg_p<float>(const OpF64&, const float*, int, double*,
+                                         const SolveState*, cudaStream_t);
+cudaError_t launch_fcg_q(const OpF64& A, const double* p, const double* r, double* q,
+                         SolveState* st, double* part, cudaStream_t s) {
+  const Lvl<double> L = lvl_of(A);
+  k_fcg_q<<<red_grid(L.nx, L.nyr), kNT, 0, s>>>(L, p, r, q, st, part);
+  CHK();
+}
+cudaError_t launch_fcg_update(const OpF64& A, double* x, double* r, const double* p,
+                              const double* q, SolveState* st, double* part,
+                              cudaGraphConditionalHandle h, int has_h, cudaStream_t s) {
+  const Lvl<double> L = lvl_of(A);
+  k_fcg_update<<<red_grid(L.nx, L.nyr), kNT, 0, s>>>(L, x, r, p, q, st, part, h, has_h);
+  CHK();
+}
+cudaError_t launch_fcg_verify(const OpF64& A, const double* x, const double* b, double* r,
+                              SolveState* st, double* part, cudaGraphConditionalHandle h,
+                              int has_h, cudaStream_t s) {
+  const Lvl<double> L = lvl_of(A);
+  k_fcg_verify<<<red_grid(L.nx, L.nyr), kNT, 0, s>>>(L, x, b, r, st, part, h, has_h);
+  CHK();
+}
+cudaError_t launch_copy_out(const OpF64& A, const double* x, const SolveArgs* a, cudaStream_t s) {
+  const Lvl<double> L = lvl_of(A);
+  k_copy_out<<<red_grid(L.nx, L.nyr), kNT, 0, s>>>(L, x, a);
+  CHK();
+}
+
+}  // namespace mg

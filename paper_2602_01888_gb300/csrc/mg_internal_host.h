@@ -1,0 +1,94 @@
+// Host-side structures of libmg (context, pool, problem) shared by its C++ sources.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <mutex>
+#include <unordered_map>
+#include <vector>
+
+#include "mg.h"
+#include "mg_launch.h"
+#include "mg_solve_kernels.h"
+
+namespace mg {
+
+constexpr int kMaxLevels = 24;
+constexpr int kBatchStreams = 8;
+
+mg_status set_error(mg_status s, const char* fmt, ...);
+
+// Device memory pool: slabs from cudaMalloc, best-fit sub-allocation with coalescing.
+class Pool {
+ public:
+  void* alloc(size_t n);
+  void release(void* p);
+  size_t used() const { return used_; }
+  ~Pool();
+  size_t budget_ = 0;
+
+ private:
+  struct Slab {
+    char* base = nullptr;
+    size_t size = 0;
+    std::map<size_t, size_t> free_;  // offset -> length
+  };
+  std::vector<Slab> slabs_;
+  std::unordered_map<void*, std::pair<int, size_t>> live_;
+  size_t reserved_ = 0, used_ = 0;
+  size_t slab_min_ = (size_t)64 << 20;
+  std::mutex mu_;
+};
+
+struct LevelMem {
+  OpF64 A{};
+  double *x = nullptr, *b = nullptr, *t = nullptr;
+  OpF32 A32{};
+  float *x32 = nullptr, *b32 = nullptr, *t32 = nullptr;
+};
+
+struct GraphEntry {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+}  // namespace mg
+
+struct mg_ctx {
+  int device = 0;
+  mg::Pool pool;
+  cudaStream_t stream = nullptr, own_stream = nullptr, cap_stream = nullptr, cap_stream2 = nullptr;
+  cudaStream_t batch[mg::kBatchStreams] = {};
+};
+
+struct mg_problem {
+  mg_ctx* ctx = nullptr;
+  mg_grid_desc grid{};
+  int nlev = 0, coarse_max = 64, mixed = 0;
+  int nxs[mg::kMaxLevels] = {}, nys[mg::kMaxLevels] = {};
+  mg::LevelMem lev[mg::kMaxLevels];
+  double *D = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
+  double* inv = nullptr;
+  int m = 0;
+  double* part = nullptr;
+  mg::SolveState* st = nullptr;
+  mg::SolveArgs* args = nullptr;
+  int* flags = nullptr;
+  double* stage = nullptr;  // device copies of host inputs/outputs (3 node arrays)
+  mg::SolveArgs* h_args = nullptr;
+  mg::SolveState* h_state = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  double setup_ms = 0.0;
+  std::map<uint64_t, mg::GraphEntry> graphs;
+  std::vector<void*> allocs;
+};
+
+namespace mg {
+mg_status enqueue_solve(mg_problem* P, const mg_solve_opts& o, const double* rho, const double* bc,
+                        const double* phi_in, double* phi_out, cudaStream_t s);
+mg_status finish_solve(mg_problem* P, mg_solve_stats* stats);
+mg_status batch_solve_impl(mg_ctx* ctx, int count, mg_problem* const* probs,
+                           const double* const* rho, const double* const* bc, double* const* phi,
+                           mg_mem_kind mem, const mg_solve_opts& o, mg_solve_stats* stats);
+}  // namespace mg

@@ -1,0 +1,92 @@
+// Host-side views and kernel launchers shared by the translation units of libmg.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "mg_common.cuh"
+#include "mg_kernels.h"
+
+namespace mg {
+
+constexpr int kCoarseMax = 256;      // unknowns of the coarsest level (dense inverse)
+constexpr int kCoarseThreads = 256;  // threads of the single-CTA coarsest kernels
+constexpr int kRRX = 16, kRRY = 16;  // coarse tile of the residual + restriction kernel
+
+template <typename T>
+struct Op {
+  int nx, ny, periodic, pitch;
+  T *cE, *cN, *cNE, *cNW, *diag, *dinv;
+};
+using OpF64 = Op<double>;
+using OpF32 = Op<float>;
+
+template <typename T>
+inline Lvl<T> lvl_of(const Op<T>& A) {
+  Lvl<T> L;
+  L.nx = A.nx;
+  L.ny = A.ny;
+  L.nyr = rows_stored(A.ny, A.periodic);
+  L.periodic = A.periodic;
+  L.pitch = A.pitch;
+  L.cE = A.cE;
+  L.cN = A.cN;
+  L.cNE = A.cNE;
+  L.cNW = A.cNW;
+  L.diag = A.diag;
+  L.dinv = A.dinv;
+  return L;
+}
+
+inline OpF64 op_from(const mgk_op_f64& a) {
+  return OpF64{a.nx, a.ny, a.periodic, a.pitch, a.cE, a.cN, a.cNE, a.cNW, a.diag, a.dinv};
+}
+inline OpF32 op_from(const mgk_op_f32& a) {
+  return OpF32{a.nx, a.ny, a.periodic, a.pitch, a.cE, a.cN, a.cNE, a.cNW, a.diag, a.dinv};
+}
+
+inline int coarse_unknowns(int nx, int ny, int periodic) {
+  return (nx - 2) * (periodic ? ny - 1 : ny - 2);
+}
+
+// ---- setup (k_setup.cu)
+cudaError_t launch_eps_analytic(int kind, const double* prm, int nx, int ny, int periodic,
+                                double x0, double y0, double hx, double hy, const double* eps,
+                                int pitch, double* D, double* exx, double* exy, double* eyy,
+                                int* folded, cudaStream_t s);
+cudaError_t launch_eps_grid(int nx, int ny, int periodic, double hx, double hy, const double* xp,
+                            const double* yp, double jx, double jy, const double* eps, int pitch,
+                            double* D, double* exx, double* exy, double* eyy, int* folded,
+                            cudaStream_t s);
+cudaError_t launch_assemble(const OpF64& A, double hx, double hy, const double* exx,
+                            const double* exy, const double* eyy, cudaStream_t s);
+cudaError_t launch_rhs(const OpF64& A, const double* rho, int rho_pitch, const double* D, double* b,
+                       cudaStream_t s);
+cudaError_t launch_galerkin(const OpF64& F, const OpF64& C, cudaStream_t s);
+cudaError_t launch_op_to_f32(const OpF64& A, const OpF32& B, cudaStream_t s);
+cudaError_t launch_coarse_factor(const OpF64& A, double* inv, int* status, cudaStream_t s);
+
+// ---- cycle (k_cycle.cu).  `skip` (nullable device int): when *skip != 0 the kernel
+// returns at once (used inside the solve graph after convergence).
+template <typename T>
+cudaError_t launch_gs_colour(const Op<T>& A, T* phi, const T* b, int colour, const int* skip,
+                             cudaStream_t s);
+template <typename T>
+cudaError_t launch_smooth(const Op<T>& A, T* phi, const T* b, int sweeps, int reverse,
+                          const int* skip, cudaStream_t s);
+template <typename T>
+cudaError_t launch_residual(const Op<T>& A, const T* phi, const T* b, T* r, const int* skip,
+                            cudaStream_t s);
+template <typename T>
+cudaError_t launch_jacobi(const Op<T>& A, T* phi, const T* b, T* tmp, int sweeps, double omega,
+                          const int* skip, cudaStream_t s);
+// phiH (nullable) is zeroed on the coarse grid at the same time.
+template <typename T>
+cudaError_t launch_resid_restrict(const Op<T>& A, const T* phi, const T* b, T* bH, T* phiH,
+                                  int pitch_c, const int* skip, cudaStream_t s);
+template <typename T>
+cudaError_t launch_prolong_add(const Op<T>& A, T* phi, const T* eH, int pitch_c, const int* skip,
+                               cudaStream_t s);
+template <typename T>
+cudaError_t launch_coarse_solve(const Op<T>& A, const double* inv, const T* b, T* x,
+                                const int* skip, cudaStream_t s);
+
+}  // namespace mg

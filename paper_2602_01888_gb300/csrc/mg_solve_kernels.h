@@ -1,0 +1,58 @@
+// Launchers of the solve-loop kernels (k_solve.cu) used by the host orchestration.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "mg_common.cuh"
+#include "mg_launch.h"
+
+namespace mg {
+
+constexpr int kRedBlocks = 1216;  // upper bound of blocks (and partial sums) per reduction
+
+// Per-solve arguments read by the kernels through device memory, so one captured graph
+// serves every call: the caller's arrays (contiguous rows of user_pitch elements).
+struct SolveArgs {
+  const double* rho;
+  const double* bc;      // nullable
+  const double* phi_in;  // warm start
+  double* phi_out;
+  int user_pitch;
+  int warm;
+  int max_iters;
+  int pad;
+  double rtol;
+  long long n_unknowns;
+};
+
+dim3 red_grid(int nx, int nyr);
+cudaError_t launch_solve_init(const OpF64& A, const SolveArgs* a, const double* D, double* x,
+                              double* b, SolveState* st, cudaStream_t s);
+cudaError_t launch_resid_init(const OpF64& A, const double* x, const double* b, double* r,
+                              SolveState* st, double* part, cudaGraphConditionalHandle h,
+                              int has_h, cudaStream_t s);
+cudaError_t launch_resid_check(const OpF64& A, const double* x, const double* b, double* r,
+                               SolveState* st, double* part, cudaGraphConditionalHandle h,
+                               int has_h, cudaStream_t s);
+cudaError_t launch_r_to_f32(const OpF64& A, const double* r, float* b32, int pitch32,
+                            const SolveState* st, cudaStream_t s);
+cudaError_t launch_add_f32(const OpF64& A, double* x, const float* e32, int pitch32,
+                           SolveState* st, cudaStream_t s);
+cudaError_t launch_iter_inc(SolveState* st, cudaStream_t s);
+cudaError_t launch_loop_guard(SolveState* st, cudaGraphConditionalHandle h, cudaStream_t s);
+template <typename TZ>
+cudaError_t launch_fcg_zq(const OpF64& A, const TZ* z, int zp, const double* q, SolveState* st,
+                          double* part, cudaStream_t s);
+template <typename TZ>
+cudaError_t launch_fcg_p(const OpF64& A, const TZ* z, int zp, double* p, const SolveState* st,
+                         cudaStream_t s);
+cudaError_t launch_fcg_q(const OpF64& A, const double* p, const double* r, double* q,
+                         SolveState* st, double* part, cudaStream_t s);
+cudaError_t launch_fcg_update(const OpF64& A, double* x, double* r, const double* p,
+                              const double* q, SolveState* st, double* part,
+                              cudaGraphConditionalHandle h, int has_h, cudaStream_t s);
+cudaError_t launch_fcg_verify(const OpF64& A, const double* x, const double* b, double* r,
+                              SolveState* st, double* part, cudaGraphConditionalHandle h,
+                              int has_h, cudaStream_t s);
+cudaError_t launch_copy_out(const OpF64& A, const double* x, const SolveArgs* a, cudaStream_t s);
+
+}  // namespace mg

@@ -1,0 +1,729 @@
+// Host orchestration of libmg: contexts with a device memory pool, resident problems
+// (coefficient build + multigrid hierarchy), solves captured as CUDA graphs whose
+// iteration loop is a device-driven WHILE node, and batched solves.  C ABI of mg.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "mg.h"
+#include "mg_launch.h"
+#include "mg_solve_kernels.h"
+#include "mg_internal_host.h"
+
+namespace mg {
+
+// ------------------------------------------------------------------ errors
+static thread_local char g_err[512] = "";
+
+mg_status set_error(mg_status s, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+  return s;
+}
+
+#define CU(call)                                                                        \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return set_error(MG_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));   \
+  } while (0)
+
+// ------------------------------------------------------------------ memory pool
+// Slabs of device memory obtained with cudaMalloc; best-fit ranges inside them,
+// coalesced on release; total slab bytes capped by the context's budget.
+void* Pool::alloc(size_t n) {
+  std::lock_guard<std::mutex> lk(mu_);
+  n = (n + 255) & ~size_t(255);
+  if (n == 0) n = 256;
+  for (int pass = 0; pass < 2; ++pass) {
+    int best_s = -1;
+    size_t best_off = 0, best_len = SIZE_MAX;
+    for (size_t s = 0; s < slabs_.size(); ++s)
+      for (auto& fr : slabs_[s].free_)
+        if (fr.second >= n && fr.second < best_len) {
+          best_s = (int)s;
+          best_off = fr.first;
+          best_len = fr.second;
+        }
+    if (best_s >= 0) {
+      Slab& sl = slabs_[best_s];
+      sl.free_.erase(best_off);
+      if (best_len > n) sl.free_[best_off + n] = best_len - n;
+      char* p = sl.base + best_off;
+      live_[p] = {best_s, n};
+      used_ += n;
+      return p;
+    }
+    if (pass == 1) break;
+    size_t want = std::max(n, slab_min_);
+    if (reserved_ + want > budget_) want = n;
+    if (reserved_ + want > budget_) return nullptr;
+    void* base = nullptr;
+    if (cudaMalloc(&base, want) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    Slab sl;
+    sl.base = (char*)base;
+    sl.size = want;
+    sl.free_[0] = want;
+    slabs_.push_back(sl);
+    reserved_ += want;
+  }
+  return nullptr;
+}
+
+void Pool::release(void* p) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lk(mu_);
+  auto it = live_.find(p);
+  if (it == live_.end()) return;
+  Slab& sl = slabs_[it->second.first];
+  size_t off = (char*)p - sl.base, len = it->second.second;
+  used_ -= len;
+  live_.erase(it);
+  auto nx = sl.free_.lower_bound(off);
+  if (nx != sl.free_.end() && off + len == nx->first) {
+    len += nx->second;
+    nx = sl.free_.erase(nx);
+  }
+  if (nx != sl.free_.begin()) {
+    auto pv = std::prev(nx);
+    if (pv->first + pv->second == off) {
+      pv->second += len;
+      return;
+    }
+  }
+  sl.free_[off] = len;
+}
+
+Pool::~Pool() {
+  for (auto& s : slabs_) cudaFree(s.base);
+}
+
+// ------------------------------------------------------------------ hierarchy sizes
+// Same rule as the oracle: coarsen while both n-1 are even, the coarse grid keeps
+// unknowns in both directions and the current level has more than coarse_max unknowns.
+int count_levels(int nx, int ny, int periodic, int coarse_max, int* nxs, int* nys) {
+  int L = 1;
+  nxs[0] = nx;
+  nys[0] = ny;
+  while (L < kMaxLevels) {
+    if (coarse_unknowns(nx, ny, periodic) <= coarse_max) break;
+    if ((nx - 1) % 2 || (ny - 1) % 2) break;
+    const int nxc = (nx - 1) / 2 + 1, nyc = (ny - 1) / 2 + 1;
+    if (nxc < 3 || nyc < 3) break;
+    if (periodic && nyc - 1 < 2) break;
+    nx = nxc;
+    ny = nyc;
+    nxs[L] = nx;
+    nys[L] = ny;
+    ++L;
+  }
+  return L;
+}
+
+static int pitch_for(int nx) { return (nx + 31) & ~31; }
+
+}  // namespace mg
+
+using namespace mg;
+
+// ------------------------------------------------------------------ context
+extern "C" const char* mg_last_error(void) { return g_err; }
+
+extern "C" void mg_default_opts(mg_solve_opts* o) {
+  if (!o) return;
+  o->precision = MG_PREC_FP64;
+  o->outer = MG_OUTER_FCG;
+  o->smoother = MG_SMOOTH_GS4;
+  o->nu1 = 2;
+  o->nu2 = 2;
+  o->omega_j = 0.8;
+  o->rtol = 1e-10;
+  o->max_iters = 200;
+  o->coarse_max = 64;
+  o->warm_start = 0;
+}
+
+extern "C" mg_status mg_create(int device, size_t mem_budget, mg_ctx** out) {
+  if (!out) return set_error(MG_ERR_ARG, "mg_create: out is NULL");
+  *out = nullptr;
+  int n = 0;
+  CU(cudaGetDeviceCount(&n));
+  if (device < 0 || device >= n) return set_error(MG_ERR_ARG, "mg_create: no CUDA device %d", device);
+  CU(cudaSetDevice(device));
+  size_t fr = 0, tot = 0;
+  CU(cudaMemGetInfo(&fr, &tot));
+  mg_ctx* c = new mg_ctx();
+  c->device = device;
+  c->pool.budget_ = mem_budget ? mem_budget : (size_t)(0.9 * (double)fr);
+  if (cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->cap_stream2, cudaStreamNonBlocking) != cudaSuccess) {
+    delete c;
+    return set_error(MG_ERR_CUDA, "mg_create: stream creation failed");
+  }
+  c->stream = c->own_stream;
+  for (int k = 0; k < kBatchStreams; ++k) cudaStreamCreateWithFlags(&c->batch[k], cudaStreamNonBlocking);
+  *out = c;
+  return MG_OK;
+}
+
+extern "C" void mg_destroy(mg_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  cudaDeviceSynchronize();
+  for (int k = 0; k < kBatchStreams; ++k) cudaStreamDestroy(c->batch[k]);
+  cudaStreamDestroy(c->own_stream);
+  cudaStreamDestroy(c->cap_stream);
+  cudaStreamDestroy(c->cap_stream2);
+  delete c;
+}
+
+extern "C" mg_status mg_set_stream(mg_ctx* c, void* stream) {
+  if (!c) return set_error(MG_ERR_ARG, "mg_set_stream: ctx is NULL");
+  c->stream = stream ? (cudaStream_t)stream : c->own_stream;
+  return MG_OK;
+}
+
+extern "C" mg_status mg_mem_info(mg_ctx* c, size_t* used, size_t* budget) {
+  if (!c) return set_error(MG_ERR_ARG, "mg_mem_info: ctx is NULL");
+  if (used) *used = c->pool.used();
+  if (budget) *budget = c->pool.budget_;
+  return MG_OK;
+}
+
+// ------------------------------------------------------------------ problems
+namespace mg {
+
+template <typename T>
+static T* palloc(mg_problem* P, size_t count) {
+  void* p = P->ctx->pool.alloc(count * sizeof(T));
+  if (p) P->allocs.push_back(p);
+  return (T*)p;
+}
+
+static void problem_release(mg_problem* P) {
+  for (auto& kv : P->graphs) {
+    cudaGraphExecDestroy(kv.second.exec);
+    cudaGraphDestroy(kv.second.graph);
+  }
+  P->graphs.clear();
+  for (void* a : P->allocs) P->ctx->pool.release(a);
+  P->allocs.clear();
+  if (P->h_args) cudaFreeHost(P->h_args);
+  if (P->h_state) cudaFreeHost(P->h_state);
+  if (P->ev0) cudaEventDestroy(P->ev0);
+  if (P->ev1) cudaEventDestroy(P->ev1);
+}
+
+// Allocate every array of the hierarchy (FP64 levels, FP32 mirrors when mixed, the
+// finest-level solve vectors and the coarsest inverse).
+static mg_status problem_alloc(mg_problem* P, bool mixed) {
+  for (int l = 0; l < P->nlev; ++l) {
+    LevelMem& M = P->lev[l];
+    const int nx = P->nxs[l], ny = P->nys[l], nyr = rows_stored(ny, P->grid.periodic_y);
+    const int pt = pitch_for(nx);
+    const size_t n = (size_t)pt * nyr;
+    double* blk = palloc<double>(P, 9 * n);
+    if (!blk) return set_error(MG_ERR_OOM, "device memory budget exhausted (level %d)", l);
+    M.A = OpF64{nx, ny, P->grid.periodic_y, pt, blk, blk + n, blk + 2 * n, blk + 3 * n,
+                blk + 4 * n, blk + 5 * n};
+    M.x = blk + 6 * n;
+    M.b = blk + 7 * n;
+    M.t = blk + 8 * n;
+    if (mixed) {
+      float* f = palloc<float>(P, 9 * n);
+      if (!f) return set_error(MG_ERR_OOM, "device memory budget exhausted (FP32 level %d)", l);
+      M.A32 = OpF32{nx, ny, P->grid.periodic_y, pt, f, f + n, f + 2 * n, f + 3 * n, f + 4 * n,
+                    f + 5 * n};
+      M.x32 = f + 6 * n;
+      M.b32 = f + 7 * n;
+      M.t32 = f + 8 * n;
+    }
+    CU(cudaMemsetAsync(blk, 0, 9 * n * sizeof(double), P->ctx->stream));
+    if (mixed) CU(cudaMemsetAsync(M.A32.cE, 0, 9 * n * sizeof(float), P->ctx->stream));
+  }
+  const size_t n0 = (size_t)P->lev[0].A.pitch * rows_stored(P->grid.ny, P->grid.periodic_y);
+  double* v = palloc<double>(P, 5 * n0);
+  if (!v) return set_error(MG_ERR_OOM, "device memory budget exhausted (solve vectors)");
+  P->D = v;
+  P->r = v + n0;
+  P->z = v + 2 * n0;
+  P->p = v + 3 * n0;
+  P->q = v + 4 * n0;
+  CU(cudaMemsetAsync(v, 0, 5 * n0 * sizeof(double), P->ctx->stream));
+  const OpF64& C = P->lev[P->nlev - 1].A;
+  P->m = coarse_unknowns(C.nx, C.ny, C.periodic);
+  P->inv = palloc<double>(P, (size_t)P->m * P->m);
+  P->part = palloc<double>(P, 4 * kRedBlocks);
+  P->st = palloc<SolveState>(P, 1);
+  P->args = palloc<SolveArgs>(P, 1);
+  P->flags = palloc<int>(P, 4);
+  if (!P->inv || !P->part || !P->st || !P->args || !P->flags)
+    return set_error(MG_ERR_OOM, "device memory budget exhausted (solver state)");
+  CU(cudaMemsetAsync(P->st, 0, sizeof(SolveState), P->ctx->stream));
+  CU(cudaMallocHost(&P->h_args, sizeof(SolveArgs)));
+  CU(cudaMallocHost(&P->h_state, sizeof(SolveState)));
+  CU(cudaEventCreate(&P->ev0));
+  CU(cudaEventCreate(&P->ev1));
+  return MG_OK;
+}
+
+// Coefficients of the finest level from the map, then the Galerkin hierarchy and the
+// coarsest inverse.  Reads host or device inputs; synchronises once to check flags.
+static mg_status problem_build(mg_problem* P, const mg_map_desc* map, const double* eps_phys,
+                               mg_mem_kind mem) {
+  cudaStream_t s = P->ctx->stream;
+  const mg_grid_desc& g = P->grid;
+  const int nx = g.nx, ny = g.ny, nyr = rows_stored(ny, g.periodic_y);
+  const double hx = g.lx / (nx - 1), hy = g.ly / (ny - 1);
+  const size_t nn = (size_t)nx * nyr;
+  LevelMem& F = P->lev[0];
+  const int pt = F.A.pitch;
+  const size_t np = (size_t)pt * nyr;
+  CU(cudaEventRecord(P->ev0, s));
+  // temporaries: eps components in the fine level's scratch arrays (x, b, t), inputs
+  // staged in pitched layout in q / z / p
+  double *exx = F.x, *exy = F.b, *eyy = F.t;
+  const double* eps_d = nullptr;
+  const double *xp_d = nullptr, *yp_d = nullptr;
+  auto stage = [&](const double* src, double* dst) -> cudaError_t {
+    return cudaMemcpy2DAsync(dst, pt * sizeof(double), src, nx * sizeof(double), nx * sizeof(double),
+                             nyr, mem == MG_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                             s);
+  };
+  if (eps_phys) {
+    CU(stage(eps_phys, P->q));
+    eps_d = P->q;
+  }
+  if (map->kind == MG_MAP_GRID) {
+    CU(stage(map->xp, P->z));
+    CU(stage(map->yp, P->p));
+    xp_d = P->z;
+    yp_d = P->p;
+  }
+  (void)nn;
+  CU(cudaMemsetAsync(P->flags, 0, 4 * sizeof(int), s));
+  if (map->kind == MG_MAP_GRID) {
+    CU(launch_eps_grid(nx, ny, g.periodic_y, hx, hy, xp_d, yp_d, map->jump_x, map->jump_y, eps_d, pt,
+                       P->D, exx, exy, eyy, P->flags, s));
+  } else {
+    CU(launch_eps_analytic(map->kind, map->params, nx, ny, g.periodic_y, g.x0, g.y0, hx, hy, eps_d,
+                           pt, P->D, exx, exy, eyy, P->flags, s));
+  }
+  CU(launch_assemble(F.A, hx, hy, exx, exy, eyy, s));
+  for (int l = 1; l < P->nlev; ++l) CU(launch_galerkin(P->lev[l - 1].A, P->lev[l].A, s));
+  CU(launch_coarse_factor(P->lev[P->nlev - 1].A, P->inv, P->flags + 1, s));
+  if (P->mixed)
+    for (int l = 0; l < P->nlev; ++l) CU(launch_op_to_f32(P->lev[l].A, P->lev[l].A32, s));
+  // restore the scratch vectors used as staging
+  CU(cudaMemsetAsync(P->z, 0, 3 * np * sizeof(double), s));
+  CU(cudaEventRecord(P->ev1, s));
+  int hf[4];
+  CU(cudaMemcpyAsync(hf, P->flags, sizeof hf, cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, P->ev0, P->ev1);
+  P->setup_ms = ms;
+  if (hf[0]) return set_error(MG_ERR_MAP_FOLDED, "det J <= 0 at some node: the map folds");
+  if (hf[1]) return set_error(MG_ERR_NOT_SPD, "coarsest operator is not SPD (non-positive pivot)");
+  return MG_OK;
+}
+
+static mg_status check_grid(const mg_grid_desc* g, int coarse_max, int* nlev, int* nxs, int* nys) {
+  if (g->nx < 3 || g->ny < 3 || !(g->lx > 0) || !(g->ly > 0))
+    return set_error(MG_ERR_SIZE, "grid too small or empty domain (nx=%d ny=%d)", g->nx, g->ny);
+  if (g->periodic_y && (g->ny - 1) % 2)
+    return set_error(MG_ERR_SIZE, "periodic y needs an even number of rows (ny-1=%d)", g->ny - 1);
+  if ((size_t)g->nx * g->ny > ((size_t)1 << 31))
+    return set_error(MG_ERR_SIZE, "grid larger than 2^31 nodes");
+  if (coarse_max < 1 || coarse_max > kCoarseMax)
+    return set_error(MG_ERR_ARG, "coarse_max must be in [1, %d]", kCoarseMax);
+  *nlev = count_levels(g->nx, g->ny, g->periodic_y, coarse_max, nxs, nys);
+  const int L = *nlev - 1;
+  if (coarse_unknowns(nxs[L], nys[L], g->periodic_y) > kCoarseMax)
+    return set_error(MG_ERR_SIZE,
+                     "grid %dx%d: coarsest level %dx%d has more than %d unknowns; sides must be "
+                     "m*2^k+1 with a small m",
+                     g->nx, g->ny, nxs[L], nys[L], kCoarseMax);
+  return MG_OK;
+}
+
+static mg_status check_map(const mg_grid_desc* g, const mg_map_desc* m) {
+  if (!m) return set_error(MG_ERR_ARG, "map is NULL");
+  if (m->kind < MG_MAP_IDENTITY || m->kind > MG_MAP_GRID)
+    return set_error(MG_ERR_ARG, "unknown map kind %d", m->kind);
+  if (m->kind == MG_MAP_GRID && (!m->xp || !m->yp))
+    return set_error(MG_ERR_ARG, "MG_MAP_GRID needs xp and yp");
+  (void)g;
+  return MG_OK;
+}
+
+}  // namespace mg
+
+extern "C" mg_status mg_setup_transform(mg_ctx* ctx, const mg_grid_desc* grid,
+                                        const mg_map_desc* map, const double* eps_phys,
+                                        mg_mem_kind mem, const mg_solve_opts* opts,
+                                        mg_problem** out) {
+  if (!ctx || !grid || !out) return set_error(MG_ERR_ARG, "mg_setup_transform: NULL argument");
+  *out = nullptr;
+  mg_solve_opts o;
+  if (opts) o = *opts; else mg_default_opts(&o);
+  mg_status st = check_map(grid, map);
+  if (st) return st;
+  cudaSetDevice(ctx->device);
+  mg_problem* P = new mg_problem();
+  P->ctx = ctx;
+  P->grid = *grid;
+  P->coarse_max = o.coarse_max;
+  P->mixed = (o.precision == MG_PREC_MIXED);
+  st = check_grid(grid, o.coarse_max, &P->nlev, P->nxs, P->nys);
+  if (!st) st = problem_alloc(P, P->mixed);
+  if (!st) st = problem_build(P, map, eps_phys, mem);
+  if (st) {
+    char keep[512];
+    snprintf(keep, sizeof keep, "%s", g_err);
+    cudaStreamSynchronize(ctx->stream);
+    problem_release(P);
+    delete P;
+    return set_error(st, "%s", keep);
+  }
+  *out = P;
+  return MG_OK;
+}
+
+extern "C" mg_status mg_update_transform(mg_problem* P, const mg_map_desc* map,
+                                         const double* eps_phys, mg_mem_kind mem) {
+  if (!P) return set_error(MG_ERR_ARG, "mg_update_transform: problem is NULL");
+  mg_status st = check_map(&P->grid, map);
+  if (st) return st;
+  cudaSetDevice(P->ctx->device);
+  return problem_build(P, map, eps_phys, mem);
+}
+
+extern "C" void mg_problem_free(mg_problem* P) {
+  if (!P) return;
+  cudaSetDevice(P->ctx->device);
+  cudaStreamSynchronize(P->ctx->stream);
+  problem_release(P);
+  delete P;
+}
+
+extern "C" mg_status mg_problem_info(const mg_problem* P, int* levels, int* nx_out, int* ny_out) {
+  if (!P) return set_error(MG_ERR_ARG, "mg_problem_info: problem is NULL");
+  if (levels) *levels = P->nlev;
+  for (int l = 0; l < P->nlev; ++l) {
+    if (nx_out) nx_out[l] = P->nxs[l];
+    if (ny_out) ny_out[l] = P->nys[l];
+  }
+  return MG_OK;
+}
+
+// ------------------------------------------------------------------ solve graphs
+namespace mg {
+
+template <typename T>
+static mg_status emit_vcycle(mg_problem* P, bool f32, T* x0, const T* b0, const mg_solve_opts& o,
+                             const int* skip, cudaStream_t s) {
+  auto op = [&](int l) -> const Op<T>& {
+    if constexpr (sizeof(T) == 4) return P->lev[l].A32; else return P->lev[l].A;
+  };
+  auto X = [&](int l) -> T* {
+    if (l == 0) return x0;
+    if constexpr (sizeof(T) == 4) return P->lev[l].x32; else return P->lev[l].x;
+  };
+  auto B = [&](int l) -> const T* {
+    if (l == 0) return b0;
+    if constexpr (sizeof(T) == 4) return P->lev[l].b32; else return P->lev[l].b;
+  };
+  auto Bw = [&](int l) -> T* {
+    if constexpr (sizeof(T) == 4) return P->lev[l].b32; else return P->lev[l].b;
+  };
+  auto Tm = [&](int l) -> T* {
+    if constexpr (sizeof(T) == 4) return P->lev[l].t32; else return P->lev[l].t;
+  };
+  (void)f32;
+  const int L = P->nlev;
+  auto smooth = [&](int l, int sweeps, int rev) -> cudaError_t {
+    if (o.smoother == MG_SMOOTH_JACOBI)
+      return launch_jacobi(op(l), X(l), B(l), Tm(l), sweeps, o.omega_j, skip, s);
+    return launch_smooth(op(l), X(l), B(l), sweeps, rev, skip, s);
+  };
+  for (int l = 0; l < L - 1; ++l) {
+    CU(smooth(l, o.nu1, 0));
+    CU(launch_resid_restrict(op(l), X(l), B(l), Bw(l + 1), X(l + 1), op(l + 1).pitch, skip, s));
+  }
+  CU(launch_coarse_solve(op(L - 1), P->inv, B(L - 1), X(L - 1), skip, s));
+  for (int l = L - 2; l >= 0; --l) {
+    CU(launch_prolong_add(op(l), X(l), X(l + 1), op(l + 1).pitch, skip, s));
+    CU(smooth(l, o.nu2, 1));
+  }
+  return MG_OK;
+}
+
+// Body of one outer iteration.
+static mg_status emit_body(mg_problem* P, const mg_solve_opts& o, cudaGraphConditionalHandle h,
+                           int has_h, cudaStream_t s) {
+  LevelMem& F = P->lev[0];
+  const int* skip = &P->st->done;
+  const size_t n0 = (size_t)F.A.pitch * rows_stored(F.A.ny, F.A.periodic);
+  const bool mixed = (o.precision == MG_PREC_MIXED);
+  if (o.outer == MG_OUTER_VCYCLE) {
+    if (!mixed) {
+      CU(launch_resid_check(F.A, F.x, F.b, nullptr, P->st, P->part, h, has_h, s));
+      mg_status st = emit_vcycle<double>(P, false, F.x, F.b, o, skip, s);
+      if (st) return st;
+    } else {
+      CU(launch_resid_check(F.A, F.x, F.b, P->r, P->st, P->part, h, has_h, s));
+      CU(launch_r_to_f32(F.A, P->r, F.b32, F.A32.pitch, P->st, s));
+      CU(cudaMemsetAsync(F.x32, 0, n0 * sizeof(float), s));
+      mg_status st = emit_vcycle<float>(P, true, F.x32, F.b32, o, skip, s);
+      if (st) return st;
+      CU(launch_add_f32(F.A, F.x, F.x32, F.A32.pitch, P->st, s));
+    }
+    CU(launch_iter_inc(P->st, s));
+    return MG_OK;
+  }
+  // flexible CG preconditioned by one V-cycle
+  CU(launch_fcg_verify(F.A, F.x, F.b, P->r, P->st, P->part, h, has_h, s));
+  if (!mixed) {
+    CU(cudaMemsetAsync(P->z, 0, n0 * sizeof(double), s));
+    mg_status st = emit_vcycle<double>(P, false, P->z, P->r, o, skip, s);
+    if (st) return st;
+    CU(launch_fcg_zq<double>(F.A, P->z, F.A.pitch, P->q, P->st, P->part, s));
+    CU(launch_fcg_p<double>(F.A, P->z, F.A.pitch, P->p, P->st, s));
+  } else {
+    CU(launch_r_to_f32(F.A, P->r, F.b32, F.A32.pitch, P->st, s));
+    CU(cudaMemsetAsync(F.x32, 0, n0 * sizeof(float), s));
+    mg_status st = emit_vcycle<float>(P, true, F.x32, F.b32, o, skip, s);
+    if (st) return st;
+    CU(launch_fcg_zq<float>(F.A, F.x32, F.A32.pitch, P->q, P->st, P->part, s));
+    CU(launch_fcg_p<float>(F.A, F.x32, F.A32.pitch, P->p, P->st, s));
+  }
+  CU(launch_fcg_q(F.A, P->p, P->r, P->q, P->st, P->part, s));
+  CU(launch_fcg_update(F.A, F.x, P->r, P->p, P->q, P->st, P->part, h, has_h, s));
+  return MG_OK;
+}
+
+static uint64_t graph_key(const mg_solve_opts& o) {
+  uint64_t k = (uint64_t)o.precision | ((uint64_t)o.outer << 2) | ((uint64_t)o.smoother << 4) |
+               ((uint64_t)(o.nu1 & 255) << 8) | ((uint64_t)(o.nu2 & 255) << 16);
+  uint64_t w;
+  float om = (float)o.omega_j;
+  uint32_t ob;
+  memcpy(&ob, &om, 4);
+  w = ob;
+  return k ^ (w << 24);
+}
+
+// Whole solve as one graph: init -> initial residual (sets the condition) ->
+// WHILE(condition){ one outer iteration; the last kernel re-sets the condition } -> copy out.
+static mg_status build_graph(mg_problem* P, const mg_solve_opts& o, GraphEntry* ge) {
+  cudaStream_t cs = P->ctx->cap_stream, cs2 = P->ctx->cap_stream2;
+  LevelMem& F = P->lev[0];
+  const bool fcg = (o.outer == MG_OUTER_FCG);
+  CU(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  cudaGraph_t g = nullptr;
+  cudaStreamCaptureStatus cst;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  mg_status st = MG_OK;
+  cudaGraphConditionalHandle h = 0;
+  do {
+    if (cudaStreamGetCaptureInfo(cs, &cst, nullptr, &g, nullptr, nullptr, nullptr) != cudaSuccess) {
+      st = set_error(MG_ERR_CUDA, "capture info failed");
+      break;
+    }
+    if (cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
+      st = set_error(MG_ERR_CUDA, "conditional handle creation failed");
+      break;
+    }
+    if (launch_solve_init(F.A, P->args, P->D, F.x, F.b, P->st, cs) != cudaSuccess ||
+        launch_resid_init(F.A, F.x, F.b, fcg ? P->r : nullptr, P->st, P->part, h, 1, cs) !=
+            cudaSuccess) {
+      st = set_error(MG_ERR_CUDA, "capture of solve init failed");
+      break;
+    }
+    if (cudaStreamGetCaptureInfo(cs, &cst, nullptr, nullptr, &deps, nullptr, &ndeps) != cudaSuccess) {
+      st = set_error(MG_ERR_CUDA, "capture info failed");
+      break;
+    }
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cnode;
+    if (cudaGraphAddNode(&cnode, g, deps, nullptr, ndeps, &cp) != cudaSuccess) {
+      st = set_error(MG_ERR_CUDA, "adding the WHILE node failed");
+      break;
+    }
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    if (cudaStreamUpdateCaptureDependencies(cs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies) !=
+        cudaSuccess) {
+      st = set_error(MG_ERR_CUDA, "capture dependency update failed");
+      break;
+    }
+    if (cudaStreamBeginCaptureToGraph(cs2, body, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      st = set_error(MG_ERR_CUDA, "body capture failed to start");
+      break;
+    }
+    st = emit_body(P, o, h, 1, cs2);
+    if (!st && launch_loop_guard(P->st, h, cs2) != cudaSuccess)
+      st = set_error(MG_ERR_CUDA, "capture of the loop guard failed");
+    cudaGraph_t body_out = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(cs2, &body_out);
+    if (!st && e2 != cudaSuccess) st = set_error(MG_ERR_CUDA, "body capture failed: %s", cudaGetErrorString(e2));
+    if (st) break;
+    if (launch_copy_out(F.A, F.x, P->args, cs) != cudaSuccess) {
+      st = set_error(MG_ERR_CUDA, "capture of copy-out failed");
+      break;
+    }
+  } while (0);
+  cudaGraph_t gout = nullptr;
+  cudaError_t e = cudaStreamEndCapture(cs, &gout);
+  if (st) {
+    if (gout) cudaGraphDestroy(gout);
+    cudaGetLastError();
+    return st;
+  }
+  if (e != cudaSuccess) return set_error(MG_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+  cudaGraphExec_t ex;
+  e = cudaGraphInstantiate(&ex, gout, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(gout);
+    return set_error(MG_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+  }
+  ge->graph = gout;
+  ge->exec = ex;
+  return MG_OK;
+}
+
+static mg_status check_opts(const mg_problem* P, const mg_solve_opts& o) {
+  if (o.precision != MG_PREC_FP64 && o.precision != MG_PREC_MIXED)
+    return set_error(MG_ERR_ARG, "bad precision %d", o.precision);
+  if (o.precision == MG_PREC_MIXED && !P->mixed)
+    return set_error(MG_ERR_ARG, "mixed precision needs a problem set up with MG_PREC_MIXED");
+  if (o.outer != MG_OUTER_VCYCLE && o.outer != MG_OUTER_FCG)
+    return set_error(MG_ERR_ARG, "bad outer iteration %d", o.outer);
+  if (o.smoother != MG_SMOOTH_GS4 && o.smoother != MG_SMOOTH_JACOBI)
+    return set_error(MG_ERR_ARG, "bad smoother %d", o.smoother);
+  if (o.nu1 < 0 || o.nu2 < 0 || o.nu1 + o.nu2 == 0 || o.nu1 > 16 || o.nu2 > 16)
+    return set_error(MG_ERR_ARG, "bad smoothing counts %d, %d", o.nu1, o.nu2);
+  if (o.max_iters < 1 || !(o.rtol >= 0)) return set_error(MG_ERR_ARG, "bad rtol / max_iters");
+  if (o.coarse_max != P->coarse_max)
+    return set_error(MG_ERR_ARG, "coarse_max differs from the one the problem was set up with");
+  return MG_OK;
+}
+
+// Enqueue one solve on stream s (inputs already device-resident at the given pointers).
+mg_status enqueue_solve(mg_problem* P, const mg_solve_opts& o, const double* rho, const double* bc,
+                        const double* phi_in, double* phi_out, cudaStream_t s) {
+  const uint64_t key = graph_key(o);
+  auto it = P->graphs.find(key);
+  if (it == P->graphs.end()) {
+    GraphEntry ge;
+    mg_status st = build_graph(P, o, &ge);
+    if (st) return st;
+    it = P->graphs.emplace(key, ge).first;
+  }
+  SolveArgs* a = P->h_args;
+  a->rho = rho;
+  a->bc = bc;
+  a->phi_in = phi_in;
+  a->phi_out = phi_out;
+  a->user_pitch = P->grid.nx;
+  a->warm = o.warm_start ? 1 : 0;
+  a->max_iters = o.max_iters;
+  a->rtol = o.rtol;
+  a->n_unknowns = (long long)coarse_unknowns(P->grid.nx, P->grid.ny, P->grid.periodic_y);
+  CU(cudaMemcpyAsync(P->args, a, sizeof(SolveArgs), cudaMemcpyHostToDevice, s));
+  CU(cudaEventRecord(P->ev0, s));
+  CU(cudaGraphLaunch(it->second.exec, s));
+  CU(cudaEventRecord(P->ev1, s));
+  CU(cudaMemcpyAsync(P->h_state, P->st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+  return MG_OK;
+}
+
+mg_status finish_solve(mg_problem* P, mg_solve_stats* stats) {
+  const SolveState& S = *P->h_state;
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    stats->iters = S.it;
+    stats->levels = P->nlev;
+    stats->rel_residual = S.rel;
+    stats->setup_ms = P->setup_ms;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, P->ev0, P->ev1);
+    stats->solve_ms = ms;
+    const int n = std::min(S.hist_n, MG_HIST_MAX);
+    for (int k = 0; k < n; ++k) stats->hist[k] = S.hist[k];
+  }
+  if (S.status == 7) return set_error(MG_ERR_DIVERGED, "solve diverged (NaN/Inf residual)");
+  if (S.status == 6)
+    return set_error(MG_ERR_NOT_CONVERGED, "not converged after %d iterations (rel %.3e)", S.it, S.rel);
+  return MG_OK;
+}
+
+}  // namespace mg
+
+extern "C" mg_status mg_solve(mg_problem* P, const double* rho_phys, const double* bc, double* phi,
+                              mg_mem_kind mem, const mg_solve_opts* opts, mg_solve_stats* stats) {
+  if (!P || !rho_phys || !phi) return set_error(MG_ERR_ARG, "mg_solve: NULL argument");
+  mg_solve_opts o;
+  if (opts) o = *opts; else mg_default_opts(&o);
+  mg_status st = check_opts(P, o);
+  if (st) return st;
+  cudaSetDevice(P->ctx->device);
+  cudaStream_t s = P->ctx->stream;
+  const size_t n = (size_t)P->grid.nx * rows_stored(P->grid.ny, P->grid.periodic_y);
+  const double *rho = rho_phys, *bcd = bc, *pin = phi;
+  double* pout = phi;
+  if (mem == MG_MEM_HOST) {
+    if (!P->stage) {
+      P->stage = palloc<double>(P, 3 * n);
+      if (!P->stage) return set_error(MG_ERR_OOM, "device memory budget exhausted (staging)");
+    }
+    CU(cudaMemcpyAsync(P->stage, rho_phys, n * sizeof(double), cudaMemcpyHostToDevice, s));
+    if (bc) CU(cudaMemcpyAsync(P->stage + n, bc, n * sizeof(double), cudaMemcpyHostToDevice, s));
+    if (o.warm_start)
+      CU(cudaMemcpyAsync(P->stage + 2 * n, phi, n * sizeof(double), cudaMemcpyHostToDevice, s));
+    rho = P->stage;
+    bcd = bc ? P->stage + n : nullptr;
+    pin = P->stage + 2 * n;
+    pout = P->stage + 2 * n;
+  } else if (mem != MG_MEM_DEVICE) {
+    return set_error(MG_ERR_ARG, "bad memory kind");
+  }
+  st = enqueue_solve(P, o, rho, bcd, pin, pout, s);
+  if (st) return st;
+  if (mem == MG_MEM_HOST)
+    CU(cudaMemcpyAsync(phi, pout, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  return finish_solve(P, stats);
+}
+
+extern "C" mg_status mg_batch_solve(mg_ctx* ctx, int count, mg_problem* const* probs,
+                                    const double* const* rho, const double* const* bc,
+                                    double* const* phi, mg_mem_kind mem, const mg_solve_opts* opts,
+                                    mg_solve_stats* stats) {
+  if (!ctx || count < 0 || (count && (!probs || !rho || !phi)))
+    return set_error(MG_ERR_ARG, "mg_batch_solve: NULL argument");
+  mg_solve_opts o;
+  if (opts) o = *opts; else mg_default_opts(&o);
+  if (mem != MG_MEM_DEVICE && mem != MG_MEM_HOST) return set_error(MG_ERR_ARG, "bad memory kind");
+  cudaSetDevice(ctx->device);
+  return batch_solve_impl(ctx, count, probs, rho, bc, phi, mem, o, stats);
+}

@@ -152,14 +152,6 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ our arm
-def launches_per_step(levels, iters, mixed, nu1=2, nu2=2):
-    L = levels
-    setup = 1 + 2 + (L - 1) + 1 + (L if mixed else 0)
-    vcycle = (L - 1) * (4 * nu1 + 4 * nu2 + 2) + 1
-    body = 1 + vcycle + 4 + 1 + (1 if mixed else 0)
-    return setup + 2 + (iters + 1) * body + 1
-
-
 def measure_smoother(mg, torch, inst, reps=20):
     """Dominant FP64 kernel timed alone: one four-colour Gauss-Seidel sweep (4 launches)
     on the fine level of this workload, operator built by the library's own kernels."""
@@ -199,6 +191,71 @@ def measure_smoother(mg, torch, inst, reps=20):
             "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2.07 GHz (probe: 1.20 TFLOP/s at 1.99 GHz)"}
 
 
+def run_kernel_only(args):
+    """Run one library kernel `--reps` times on a sine-warp operator of side `--side`
+    (built by the library's own kernels) and print its mean CUDA-event time per launch;
+    used for profiling a single kernel at a chosen size."""
+    import ctypes as C
+    import torch
+    from paper_2602_01888_gb300 import mg
+    torch.cuda.set_device(0)
+    n = args.side
+    g = I.Grid(n, n)
+    pitch = (n + 31) // 32 * 32
+    f64 = args.kernel.endswith("64")
+    dt = torch.float64 if f64 else torch.float32
+    z = lambda d=torch.float64: torch.zeros((g.nyr, pitch), dtype=d, device="cuda")
+    D, exx, exy, eyy = z(), z(), z(), z()
+    folded = torch.zeros(1, dtype=torch.int32, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    prm = (C.c_double * 4)(0.1, 0.0, 0.0, 0.0)
+    mg.mgk("mgk_eps_analytic", 1, prm, n, n, 0, 0.0, 0.0, g.hx, g.hy, None, pitch, D.data_ptr(),
+           exx.data_ptr(), exy.data_ptr(), eyy.data_ptr(), folded.data_ptr(), s)
+    ops = [z() for _ in range(6)]
+    st = mg.op_struct(ops, n, n, False)
+    mg.mgk("mgk_assemble", C.byref(st), g.hx, g.hy, exx.data_ptr(), exy.data_ptr(), eyy.data_ptr(), s)
+    if not f64:
+        ops32 = [z(torch.float32) for _ in range(6)]
+        st32 = mg.op_struct(ops32, n, n, False, f32=True)
+        mg.mgk("mgk_op_to_f32", C.byref(st), C.byref(st32), s)
+        st = st32
+    x, b = z(dt), torch.randn((g.nyr, pitch), dtype=torch.float64, device="cuda").to(dt)
+    x2 = z(dt)
+    nc = (n - 1) // 2 + 1
+    pc = (nc + 31) // 32 * 32
+    bH = torch.zeros((nc, pc), dtype=dt, device="cuda")
+    sfx = "f64" if f64 else "f32"
+
+    def once():
+        if args.kernel.startswith("pipe"):
+            mg.mgk(f"mgk_smooth_pipe_{sfx}", C.byref(st), x.data_ptr(), x2.data_ptr(), b.data_ptr(), 0,
+                   None, 0, None, s)
+        elif args.kernel.startswith("fused"):
+            mg.mgk(f"mgk_smooth_fused_{sfx}", C.byref(st), x.data_ptr(), x2.data_ptr(), b.data_ptr(), 0,
+                   None, 0, s)
+        elif args.kernel.startswith("smooth"):
+            mg.mgk(f"mgk_smooth_{sfx}", C.byref(st), x.data_ptr(), b.data_ptr(), 1, 0, s)
+        elif args.kernel.startswith("restrict"):
+            mg.mgk(f"mgk_resid_restrict_{sfx}", C.byref(st), x.data_ptr(), b.data_ptr(), bH.data_ptr(), pc, s)
+        elif args.kernel.startswith("prolong"):
+            mg.mgk(f"mgk_prolong_add_{sfx}", C.byref(st), x.data_ptr(), bH.data_ptr(), pc, s)
+        else:
+            raise SystemExit(f"unknown kernel {args.kernel}")
+
+    for _ in range(3):
+        once()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(args.reps):
+        once()
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"kernel": args.kernel, "side": n, "reps": args.reps,
+                      "ms_per_call": e0.elapsed_time(e1) / args.reps}))
+    return 0
+
+
 def run_ours(args):
     import torch
     from paper_2602_01888_gb300 import mg
@@ -215,7 +272,7 @@ def run_ours(args):
     ctx.use_torch_stream()
     res = {}
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+    dev = lambda a: torch.from_numpy(np.array(a, dtype=np.float64)).cuda()
     xp_d, yp_d, eps_d, rho_d = dev(inst.map.xp), dev(inst.map.yp), dev(inst.eps_phys), dev(inst.rho_phys)
     phi_d = torch.zeros(g.shape, dtype=torch.float64, device="cuda")
     for prec in ("fp64", "mixed"):
@@ -283,13 +340,15 @@ def run_ours(args):
                        "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
             "mixed": {"value": mixed_value, "ms_per_step": 1e3 * rmx["tot"] / args.steps,
                       "iters": rmx["stats"].iters, "dtype": "f32 cycle in f64 refinement",
+                      "gpu_launches": args.steps * (rmx["stats"].kernel_launches
+                                                    + rmx["stats"].setup_kernel_launches),
                       "e2e": rmx["e2e"], "solve_ms": rmx["solve_ms"], "setup_ms": rmx["setup_ms"]},
             "iters": r64["stats"].iters, "levels": r64["levels"],
             "setup_ms": r64["setup_ms"], "solve_ms": r64["solve_ms"],
             "rel_residual": r64["stats"].rel_residual,
             "e2e": {"value": r64["e2e"], "unit": "unknowns/s", "h2d_bytes_per_step": 4 * n * 8,
                     "d2h_bytes_per_step": n * 8},
-            "gpu_launches": args.steps * launches_per_step(r64["levels"], r64["stats"].iters, False),
+            "gpu_launches": args.steps * (r64["stats"].kernel_launches + r64["stats"].setup_kernel_launches),
             "roofline": roof, "cpu_baseline": cpu, "clocks": r64["clocks"],
         }
         print(json.dumps(line))
@@ -305,7 +364,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="inclusion_1025", choices=["inclusion_1025", "sine_warp_129"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel-only", dest="kernel", default=None,
+                    help="smooth64|smooth32|fused64|fused32|pipe64|pipe32|restrict64|restrict32|prolong64|prolong32")
+    ap.add_argument("--side", type=int, default=2049)
+    ap.add_argument("--reps", type=int, default=5)
     args = ap.parse_args()
+    if args.kernel:
+        return run_kernel_only(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

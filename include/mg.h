@@ -111,6 +111,8 @@ typedef struct {
   double setup_ms;        /* coefficient build + coarsening of the problem */
   double solve_ms;        /* device time of the solve */
   double hist[MG_HIST_MAX]; /* relative residual before each iteration (iters + 1 entries) */
+  int kernel_launches;    /* kernels the solve launched on the device */
+  int setup_kernel_launches; /* kernels of the last coefficient build / coarsening */
 } mg_solve_stats;
 
 typedef struct mg_ctx mg_ctx;
@@ -136,8 +138,11 @@ mg_status mg_mem_info(mg_ctx *ctx, size_t *used, size_t *budget);
  * Build a resident problem: Jacobian of the map (analytic, or Eqs. 39-42 on the mapped
  * grid), tensor eps (Eqs. 10, 12-15) times the scalar eps' (eps_phys, NULL = 1, Eq. 10
  * with eps' = s I), fine-level 9-point operator, Galerkin coarse operators on every level
- * and the coarsest-level inverse.  With opts->precision == MG_PREC_MIXED the FP32 copies
- * of the hierarchy are built too (opts may be NULL for the defaults).
+ * and the coarsest-level inverse.  opts->precision fixes the precision of the hierarchy:
+ * MG_PREC_FP64 builds FP64 Galerkin operators; MG_PREC_MIXED keeps the finest operator in
+ * FP64 (for the outer residual) and builds the cycle's hierarchy in FP32 (Galerkin
+ * products in FP32, coarsest inverse in FP64).  Later solves must use the same precision.
+ * opts may be NULL for the defaults.
  * Errors: MG_ERR_SIZE, MG_ERR_ARG, MG_ERR_OOM, MG_ERR_MAP_FOLDED, MG_ERR_NOT_SPD, MG_ERR_CUDA.
  */
 mg_status mg_setup_transform(mg_ctx *ctx, const mg_grid_desc *grid, const mg_map_desc *map,

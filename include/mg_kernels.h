@@ -110,6 +110,43 @@ int mgk_coarse_solve_f64(const mgk_op_f64 *A, const double *inv, const double *b
 int mgk_coarse_solve_f32(const mgk_op_f32 *A, const double *inv, const float *b, float *x,
                          void *stream);
 
+/* One multigrid V(nu1, nu2) cycle (Sec. 3, Eqs. 19-24) on a caller-built hierarchy of
+ * nlev levels: ops[l] the level operators (ops[l+1] the coarsening of ops[l]), x[l], b[l]
+ * the iterate and right-hand side of each level, t[l] a scratch array of the same shape,
+ * inv the coarsest inverse from mgk_coarse_factor on ops[nlev-1].  Starts from the
+ * iterate in x[0] (coarse iterates start from zero) and leaves the result in x[0];
+ * smoother: 0 four-colour Gauss-Seidel (forward colours before the coarse-grid
+ * correction, reverse after), 1 weighted Jacobi (omega 0.8).  Same kernels as mg_solve. */
+int mgk_vcycle_f64(int nlev, const mgk_op_f64 *ops, double *const *x, double *const *b,
+                   double *const *t, const double *inv, int nu1, int nu2, int smoother,
+                   void *stream);
+int mgk_vcycle_f32(int nlev, const mgk_op_f32 *ops, float *const *x, float *const *b,
+                   float *const *t, const double *inv, int nu1, int nu2, int smoother,
+                   void *stream);
+
+/* Fused smoothing launch used inside the V-cycle: xout = mgk_fused_sweeps() four-colour
+ * Gauss-Seidel sweeps (Sec. 2.1, omega = 1) applied to xin, or to xin + I_H^h eH (Eq. 24)
+ * when eH is not NULL (coarse array of pitch pitch_c); reverse != 0 runs the colours
+ * backwards.  xin and xout must be different arrays (neighbouring tiles read xin while
+ * others write xout); Dirichlet nodes are copied from xin to xout. */
+int mgk_smooth_fused_f64(const mgk_op_f64 *A, const double *xin, double *xout, const double *b,
+                         int reverse, const double *eH, int pitch_c, void *stream);
+int mgk_smooth_fused_f32(const mgk_op_f32 *A, const float *xin, float *xout, const float *b,
+                         int reverse, const float *eH, int pitch_c, void *stream);
+/* Number of sweeps one fused launch performs (f32 != 0: FP32 instance). */
+int mgk_fused_sweeps(int f32);
+
+/* Persistent pipelined variant of mgk_smooth_fused_*: same result (mgk_pipe_sweeps() sweeps,
+ * optional prolongation-correction first), tiles staged by bulk asynchronous copies into
+ * two shared-memory stages.  Needs 16-byte aligned arrays and a pitch that keeps every row
+ * 16-byte aligned (else returns 1).  *err (device int, nullable) is set to 1 if a copy wait
+ * exceeds its bound, in which case the launch stops early. */
+int mgk_smooth_pipe_f64(const mgk_op_f64 *A, const double *xin, double *xout, const double *b,
+                        int reverse, const double *eH, int pitch_c, int *err, void *stream);
+int mgk_smooth_pipe_f32(const mgk_op_f32 *A, const float *xin, float *xout, const float *b,
+                        int reverse, const float *eH, int pitch_c, int *err, void *stream);
+int mgk_pipe_sweeps(int f32);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,6 +1,7 @@
 // Setup kernels: coefficient build (Eqs. 1, 10-15, 39-42), fine-level operator,
 // right-hand side (Eq. 11), Galerkin coarse operators (Sec. 3) and the coarsest-level
-// inverse.  All FP64; they run once per problem (or per geometry update).
+// inverse.  They run once per problem (or per geometry update); everything is FP64
+// except the Galerkin products of the mixed-precision hierarchy, which are FP32.
 #include "mg_common.cuh"
 #include "mg_kernels.h"
 #include "mg_launch.h"
@@ -16,9 +17,10 @@ __device__ __forceinline__ void store_eps(double a, double b, double c, double d
   const double det = a * d - b * c;
   if (!(det > 0.0)) atomicOr(folded, 1);
   D[k] = det;
-  exx[k] = s * (d * d + b * b) / det;   // Eq. 12
-  exy[k] = s * (-d * c - b * a) / det;  // Eq. 13 = Eq. 14
-  eyy[k] = s * (c * c + a * a) / det;   // Eq. 15
+  const double sd = s / det;            // one division per node
+  exx[k] = sd * (d * d + b * b);        // Eq. 12
+  exy[k] = sd * (-d * c - b * a);       // Eq. 13 = Eq. 14
+  eyy[k] = sd * (c * c + a * a);        // Eq. 15
 }
 
 __global__ void k_eps_analytic(int kind, double p0, double p1, double p2, double p3, int nx,
@@ -68,33 +70,34 @@ __global__ void k_eps_analytic(int kind, double p0, double p1, double p2, double
   store_eps(a, b, c, d, eps ? eps[k] : 1.0, k, D, exx, exy, eyy, folded);
 }
 
-// d/dx: central difference (Eqs. 39, 41), one-sided second order at the line ends.
+// d/dx: central difference (Eqs. 39, 41), one-sided second order at the line ends;
+// i2h = 1 / (2 hx).
 __device__ __forceinline__ double ddx(const double* __restrict__ f, size_t r, int i, int nx,
-                                      double hx) {
-  if (i == 0) return (-3.0 * f[r] + 4.0 * f[r + 1] - f[r + 2]) / (2.0 * hx);
-  if (i == nx - 1) return (3.0 * f[r + nx - 1] - 4.0 * f[r + nx - 2] + f[r + nx - 3]) / (2.0 * hx);
-  return (f[r + i + 1] - f[r + i - 1]) / (2.0 * hx);
+                                      double i2h) {
+  if (i == 0) return (-3.0 * f[r] + 4.0 * f[r + 1] - f[r + 2]) * i2h;
+  if (i == nx - 1) return (3.0 * f[r + nx - 1] - 4.0 * f[r + nx - 2] + f[r + nx - 3]) * i2h;
+  return (f[r + i + 1] - f[r + i - 1]) * i2h;
 }
 
-// d/dy (Eqs. 40, 42); a periodic line wraps and adds `jump` across the seam.
+// d/dy (Eqs. 40, 42); a periodic line wraps and adds `jump` across the seam; i2h = 1 / (2 hy).
 __device__ __forceinline__ double ddy(const double* __restrict__ f, int i, int j, int ny, int nyr,
-                                      int periodic, int pitch, double hy, double jump) {
+                                      int periodic, int pitch, double i2h, double jump) {
   if (periodic) {
     const double fp = (j + 1 >= nyr) ? f[(size_t)(j + 1 - nyr) * pitch + i] + jump
                                      : f[(size_t)(j + 1) * pitch + i];
     const double fm = (j - 1 < 0) ? f[(size_t)(j - 1 + nyr) * pitch + i] - jump
                                   : f[(size_t)(j - 1) * pitch + i];
-    return (fp - fm) / (2.0 * hy);
+    return (fp - fm) * i2h;
   }
   if (j == 0)
-    return (-3.0 * f[i] + 4.0 * f[(size_t)pitch + i] - f[2 * (size_t)pitch + i]) / (2.0 * hy);
+    return (-3.0 * f[i] + 4.0 * f[(size_t)pitch + i] - f[2 * (size_t)pitch + i]) * i2h;
   if (j == ny - 1)
     return (3.0 * f[(size_t)(ny - 1) * pitch + i] - 4.0 * f[(size_t)(ny - 2) * pitch + i] +
-            f[(size_t)(ny - 3) * pitch + i]) / (2.0 * hy);
-  return (f[(size_t)(j + 1) * pitch + i] - f[(size_t)(j - 1) * pitch + i]) / (2.0 * hy);
+            f[(size_t)(ny - 3) * pitch + i]) * i2h;
+  return (f[(size_t)(j + 1) * pitch + i] - f[(size_t)(j - 1) * pitch + i]) * i2h;
 }
 
-__global__ void k_eps_grid(int nx, int ny, int nyr, int periodic, double hx, double hy,
+__global__ void k_eps_grid(int nx, int ny, int nyr, int periodic, double i2hx, double i2hy,
                            const double* __restrict__ xp, const double* __restrict__ yp,
                            double jump_x, double jump_y, const double* __restrict__ eps,
                            int pitch, double* D, double* exx, double* exy, double* eyy,
@@ -103,10 +106,10 @@ __global__ void k_eps_grid(int nx, int ny, int nyr, int periodic, double hx, dou
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= nx || j >= nyr) return;
   const size_t r = (size_t)j * pitch, k = r + i;
-  const double a = ddx(xp, r, i, nx, hx);                                  // Eq. 39
-  const double b = ddy(xp, i, j, ny, nyr, periodic, pitch, hy, jump_x);    // Eq. 40
-  const double c = ddx(yp, r, i, nx, hx);                                  // Eq. 41
-  const double d = ddy(yp, i, j, ny, nyr, periodic, pitch, hy, jump_y);    // Eq. 42
+  const double a = ddx(xp, r, i, nx, i2hx);                                  // Eq. 39
+  const double b = ddy(xp, i, j, ny, nyr, periodic, pitch, i2hy, jump_x);    // Eq. 40
+  const double c = ddx(yp, r, i, nx, i2hx);                                  // Eq. 41
+  const double d = ddy(yp, i, j, ny, nyr, periodic, pitch, i2hy, jump_y);    // Eq. 42
   store_eps(a, b, c, d, eps ? eps[k] : 1.0, k, D, exx, exy, eyy, folded);
 }
 
@@ -170,10 +173,11 @@ __global__ void k_rhs(int nx, int ny, int nyr, int periodic, int pitch,
 }
 
 // Bilinear weight of a fine offset d from a coarse node (in fine units).
-__device__ __forceinline__ double pw(int d) { return d == 0 ? 1.0 : ((d == 1 || d == -1) ? 0.5 : 0.0); }
+__host__ __device__ constexpr double pw(int d) { return d == 0 ? 1.0 : ((d == 1 || d == -1) ? 0.5 : 0.0); }
 
-// A[(fi,fj),(fi+di,fj+dj)] through the symmetric storage of the fine level.
-__device__ __forceinline__ double fine_entry(const Lvl<double>& F, int fi, int fj, int di, int dj) {
+// A[(fi,fj),(fi+di,fj+dj)] through the symmetric storage of a level.
+template <typename T>
+__device__ __forceinline__ T fine_entry(const Lvl<T>& F, int fi, int fj, int di, int dj) {
   const size_t r0 = (size_t)fj * F.pitch, rd = (size_t)row_dn(fj, F.nyr) * F.pitch;
   if (dj == 0) {
     if (di == 0) return F.diag[r0 + fi];
@@ -189,51 +193,51 @@ __device__ __forceinline__ double fine_entry(const Lvl<double>& F, int fi, int f
 
 // A_H = (1/4) P^T A_h P: for each coarse unknown I, row(I, I+o) = (1/4) sum_k sum_l
 // P(k, I) A(k, l) P(l, I+o) over fine k in the 3x3 support of I and the 9 stencil
-// neighbours l of k.
-__global__ void k_galerkin(Lvl<double> F, int nxc, int nyc, int nyrc, int pitchc, double* cE,
-                           double* cN, double* cNE, double* cNW, double* diag, double* dinv) {
+// neighbours l of k.  Every loop is unrolled so the bilinear weights are constants and
+// only the (k, l, o) triples with non-zero weight remain (324 multiply-adds).
+template <typename T>
+__global__ void k_galerkin(Lvl<T> F, int nxc, int nyc, int nyrc, int pitchc, T* cE, T* cN, T* cNE,
+                           T* cNW, T* diag, T* dinv) {
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   const int J = blockIdx.y * blockDim.y + threadIdx.y;
   if (I >= nxc || J >= nyrc) return;
   const size_t K = (size_t)J * pitchc + I;
   const bool unk = (I >= 1 && I <= nxc - 2) && (F.periodic || (J >= 1 && J <= nyc - 2));
   if (!unk) {
-    cE[K] = cN[K] = cNE[K] = cNW[K] = 0.0;
-    diag[K] = dinv[K] = 1.0;
+    cE[K] = cN[K] = cNE[K] = cNW[K] = T(0);
+    diag[K] = dinv[K] = T(1);
     return;
   }
-  double row[3][3];
+  T row[3][3];
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
-    for (int b = 0; b < 3; ++b) row[a][b] = 0.0;
-#pragma unroll 1
+    for (int b = 0; b < 3; ++b) row[a][b] = T(0);
+#pragma unroll
   for (int kj = -1; kj <= 1; ++kj) {
     int fj = 2 * J + kj;
     if (fj < 0) fj += F.nyr;
     if (fj >= F.nyr) fj -= F.nyr;
-#pragma unroll 1
+#pragma unroll
     for (int ki = -1; ki <= 1; ++ki) {
       const int fi = 2 * I + ki;
-      const double wk = 0.25 * pw(ki) * pw(kj);
 #pragma unroll
       for (int lj = -1; lj <= 1; ++lj)
 #pragma unroll
         for (int li = -1; li <= 1; ++li) {
-          const double a = wk * fine_entry(F, fi, fj, li, lj);
-          const int dx = ki + li, dy = kj + lj;
+          const T a = fine_entry(F, fi, fj, li, lj);
 #pragma unroll
           for (int oj = -1; oj <= 1; ++oj)
 #pragma unroll
             for (int oi = -1; oi <= 1; ++oi) {
-              const double wl = pw(dx - 2 * oi) * pw(dy - 2 * oj);
-              if (wl != 0.0) row[oi + 1][oj + 1] += a * wl;
+              const double w = 0.25 * pw(ki) * pw(kj) * pw(ki + li - 2 * oi) * pw(kj + lj - 2 * oj);
+              if (w != 0.0) row[oi + 1][oj + 1] = fma((T)w, a, row[oi + 1][oj + 1]);
             }
         }
     }
   }
   diag[K] = row[1][1];
-  dinv[K] = 1.0 / row[1][1];
+  dinv[K] = T(1) / row[1][1];
   cE[K] = row[2][1];
   cN[K] = row[1][2];
   cNE[K] = row[2][2];
@@ -257,16 +261,18 @@ __global__ void k_op_to_f32(int nx, int nyr, int ps, int pd, const double* __res
   b5[d] = (float)a5[s];
 }
 
-// Dense matrix of the coarsest level's unknowns, inverted in place by Gauss-Jordan
-// elimination (SPD: no pivoting).  One CTA of kCoarseThreads threads.
-__global__ void __launch_bounds__(kCoarseThreads) k_coarse_factor(Lvl<double> L, double* M,
-                                                                  int* status) {
-  __shared__ double col[kCoarseMax];
+// Dense matrix of the coarsest level's unknowns, inverted by Gauss-Jordan elimination
+// (SPD: no pivoting) in one CTA.  The matrix lives in shared memory when it fits
+// (m <= kCoarseSmemM), else in the output array.
+__global__ void __launch_bounds__(kCoarseThreads) k_coarse_factor(Lvl<double> L, double* out,
+                                                                        int* status) {
+  extern __shared__ __align__(16) double smat[];
   __shared__ double rowk[kCoarseMax];
   const int ux = L.nx - 2;
   const int uy = L.periodic ? L.nyr : L.ny - 2;
   const int m = ux * uy;
   const int j0 = L.periodic ? 0 : 1;
+  double* M = (m <= kCoarseSmemM) ? smat : out;
   for (int e = threadIdx.x; e < m * m; e += blockDim.x) M[e] = 0.0;
   __syncthreads();
   for (int p = threadIdx.x; p < m; p += blockDim.x) {
@@ -284,6 +290,8 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse_factor(Lvl<double> L,
       }
   }
   __syncthreads();
+  // Gauss-Jordan: at step k every thread owns whole rows and updates them against the
+  // scaled pivot row, which all threads read from shared memory.
   for (int k = 0; k < m; ++k) {
     const double piv = M[(size_t)k * m + k];
     if (!(piv > 0.0)) {
@@ -291,22 +299,21 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse_factor(Lvl<double> L,
       return;  // uniform: every thread read the same pivot
     }
     const double ip = 1.0 / piv;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) col[i] = M[(size_t)i * m + k];
+    for (int jj = threadIdx.x; jj < m; jj += blockDim.x) rowk[jj] = (jj == k) ? ip : M[(size_t)k * m + jj] * ip;
     __syncthreads();
-    for (int jj = threadIdx.x; jj < m; jj += blockDim.x) {
-      const double v = (jj == k) ? ip : M[(size_t)k * m + jj] * ip;
-      rowk[jj] = v;
-      M[(size_t)k * m + jj] = v;
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-      const int i = e / m, jj = e % m;
-      if (i == k) continue;
-      const double f = col[i];
-      M[e] = (jj == k) ? -f * ip : M[e] - f * rowk[jj];
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      double* Mi = M + (size_t)i * m;
+      if (i == k) {
+        for (int jj = 0; jj < m; ++jj) Mi[jj] = rowk[jj];
+        continue;
+      }
+      const double f = Mi[k];
+      for (int jj = 0; jj < m; ++jj) Mi[jj] = (jj == k) ? -f * ip : fma(-f, rowk[jj], Mi[jj]);
     }
     __syncthreads();
   }
+  if (M != out)
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) out[e] = M[e];
   if (threadIdx.x == 0) *status = 0;
 }
 
@@ -330,7 +337,7 @@ cudaError_t launch_eps_grid(int nx, int ny, int periodic, double hx, double hy, 
                             cudaStream_t s) {
   const int nyr = rows_stored(ny, periodic);
   dim3 b(32, 8);
-  k_eps_grid<<<grid2(nx, nyr, b), b, 0, s>>>(nx, ny, nyr, periodic, hx, hy, xp, yp, jx, jy, eps,
+  k_eps_grid<<<grid2(nx, nyr, b), b, 0, s>>>(nx, ny, nyr, periodic, 0.5 / hx, 0.5 / hy, xp, yp, jx, jy, eps,
                                              pitch, D, exx, exy, eyy, folded);
   return cudaGetLastError();
 }
@@ -356,11 +363,39 @@ cudaError_t launch_rhs(const OpF64& A, const double* rho, int rho_pitch, const d
   return cudaGetLastError();
 }
 
-cudaError_t launch_galerkin(const OpF64& F, const OpF64& C, cudaStream_t s) {
+template <typename T>
+cudaError_t launch_galerkin(const Op<T>& F, const Op<T>& C, cudaStream_t s) {
   const int nyrc = rows_stored(C.ny, C.periodic);
   dim3 b(32, 4);
-  k_galerkin<<<grid2(C.nx, nyrc, b), b, 0, s>>>(lvl_of(F), C.nx, C.ny, nyrc, C.pitch, C.cE, C.cN,
-                                                C.cNE, C.cNW, C.diag, C.dinv);
+  k_galerkin<T><<<grid2(C.nx, nyrc, b), b, 0, s>>>(lvl_of(F), C.nx, C.ny, nyrc, C.pitch, C.cE, C.cN,
+                                                   C.cNE, C.cNW, C.diag, C.dinv);
+  return cudaGetLastError();
+}
+template cudaError_t launch_galerkin<double>(const OpF64&, const OpF64&, cudaStream_t);
+template cudaError_t launch_galerkin<float>(const OpF32&, const OpF32&, cudaStream_t);
+
+// Coarsest operator in FP64 from an FP32 level (mixed path: its hierarchy is FP32).
+__global__ void k_op_to_f64(int nx, int nyr, int ps, int pd, const float* __restrict__ a0,
+                            const float* __restrict__ a1, const float* __restrict__ a2,
+                            const float* __restrict__ a3, const float* __restrict__ a4, double* b0,
+                            double* b1, double* b2, double* b3, double* b4, double* b5) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= nx || j >= nyr) return;
+  const size_t s = (size_t)j * ps + i, d = (size_t)j * pd + i;
+  b0[d] = a0[s];
+  b1[d] = a1[s];
+  b2[d] = a2[s];
+  b3[d] = a3[s];
+  b4[d] = a4[s];
+  b5[d] = 1.0 / (double)a4[s];
+}
+
+cudaError_t launch_op_to_f64(const OpF32& A, const OpF64& B, cudaStream_t s) {
+  const int nyr = rows_stored(A.ny, A.periodic);
+  dim3 b(32, 8);
+  k_op_to_f64<<<grid2(A.nx, nyr, b), b, 0, s>>>(A.nx, nyr, A.pitch, B.pitch, A.cE, A.cN, A.cNE, A.cNW,
+                                                A.diag, B.cE, B.cN, B.cNE, B.cNW, B.diag, B.dinv);
   return cudaGetLastError();
 }
 
@@ -374,7 +409,16 @@ cudaError_t launch_op_to_f32(const OpF64& A, const OpF32& B, cudaStream_t s) {
 }
 
 cudaError_t launch_coarse_factor(const OpF64& A, double* inv, int* status, cudaStream_t s) {
-  k_coarse_factor<<<1, kCoarseThreads, 0, s>>>(lvl_of(A), inv, status);
+  const int m = coarse_unknowns(A.nx, A.ny, A.periodic);
+  const size_t sm = (m <= kCoarseSmemM) ? (size_t)m * m * sizeof(double) : 0;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_coarse_factor, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(kCoarseSmemM * kCoarseSmemM * sizeof(double)));
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_coarse_factor<<<1, kCoarseThreads, sm, s>>>(lvl_of(A), inv, status);
   return cudaGetLastError();
 }
 
@@ -429,8 +473,8 @@ extern "C" int mgk_galerkin(const mgk_op_f64* fine, const mgk_op_f64* coarse, vo
       coarse->nx != (fine->nx - 1) / 2 + 1 || coarse->ny != (fine->ny - 1) / 2 + 1 ||
       coarse->periodic != fine->periodic)
     return 1;
-  return launch_galerkin(op_from(*fine), op_from(*coarse), (cudaStream_t)stream) == cudaSuccess
-             ? 0 : 4;
+  return launch_galerkin<double>(op_from(*fine), op_from(*coarse), (cudaStream_t)stream) ==
+                 cudaSuccess ? 0 : 4;
 }
 
 extern "C" int mgk_op_to_f32(const mgk_op_f64* src, const mgk_op_f32* dst, void* stream) {

@@ -167,10 +167,11 @@ __global__ void __launch_bounds__(kNT) k_resid_check(Lvl<double> L, const double
 // b32 = fp32(r * scale) (scale: power of two from the last decision).
 __global__ void __launch_bounds__(kNT) k_r_to_f32(Lvl<double> L, const double* __restrict__ r,
                                                   float* __restrict__ b32, int pitch32,
-                                                  const SolveState* __restrict__ st) {
+                                                  SolveState* st) {
   if (st->done) return;
   const double sc = st->scale;
   NODE_LOOP(L) { b32[(size_t)j * pitch32 + i] = (float)(r[(size_t)j * L.pitch + i] * sc); }
+  if (bid() == 0 && threadIdx.x == 0) st->inv_scale_r32 = st->inv_scale;
 }
 
 // Plain-cycle refinement step: x += inv_scale * e32 at unknowns; iteration counter.
@@ -178,7 +179,7 @@ __global__ void __launch_bounds__(kNT) k_add_f32(Lvl<double> L, double* __restri
                                                  const float* __restrict__ e32, int pitch32,
                                                  SolveState* st) {
   if (st->done) return;
-  const double is = st->inv_scale;
+  const double is = st->inv_scale_r32;
   NODE_LOOP(L) {
     if (is_unknown(L, i, j)) x[(size_t)j * L.pitch + i] += is * (double)e32[(size_t)j * pitch32 + i];
   }
@@ -212,7 +213,7 @@ __global__ void __launch_bounds__(kNT) k_fcg_zq(Lvl<double> L, const TZ* __restr
   }
   __shared__ double sh[kNT / 32];
   __shared__ int flag;
-  const double is = (sizeof(TZ) == 4) ? st->inv_scale : 1.0;
+  const double is = (sizeof(TZ) == 4) ? st->inv_scale_r32 : 1.0;
   double s = 0.0;
   NODE_LOOP(L) {
     if (is_unknown(L, i, j)) s += (is * (double)z[(size_t)j * zp + i]) * q[(size_t)j * L.pitch + i];
@@ -228,38 +229,43 @@ __global__ void __launch_bounds__(kNT) k_fcg_zq(Lvl<double> L, const TZ* __restr
   }
 }
 
+// p = z + beta p_old and q = A p computed as q = A z + beta q_old (q_old = A p_old), so
+// the stencil only reads z and every other array is updated elementwise in place;
+// partial sums of p.q and p.r; the last block sets alpha = (p.r) / (p.q).
 template <typename TZ>
-__global__ void __launch_bounds__(kNT) k_fcg_p(Lvl<double> L, const TZ* __restrict__ z, int zp,
-                                               double* __restrict__ p, const SolveState* st) {
-  if (st->done) return;
-  const double is = (sizeof(TZ) == 4) ? st->inv_scale : 1.0;
-  const double beta = st->beta;
-  const bool first = (st->it == 0);
-  NODE_LOOP(L) {
-    if (!is_unknown(L, i, j)) continue;
-    const size_t k = (size_t)j * L.pitch + i;
-    const double zz = is * (double)z[(size_t)j * zp + i];
-    p[k] = first ? zz : fma(beta, p[k], zz);
-  }
-}
-
-__global__ void __launch_bounds__(kNT) k_fcg_q(Lvl<double> L, const double* __restrict__ p,
-                                               const double* __restrict__ r,
-                                               double* __restrict__ q, SolveState* st,
-                                               double* part) {
+__global__ void __launch_bounds__(kNT) k_fcg_pq(Lvl<double> L, const TZ* __restrict__ z, int zp,
+                                                double* __restrict__ p, double* __restrict__ q,
+                                                const double* __restrict__ r, SolveState* st,
+                                                double* part) {
   if (st->done) return;
   __shared__ double sh[kNT / 32];
   __shared__ int flag;
+  const double is = (sizeof(TZ) == 4) ? st->inv_scale_r32 : 1.0;
+  const double beta = st->beta;
+  const bool first = (st->it == 0);
   double spq = 0.0, spr = 0.0;
   NODE_LOOP(L) {
+    if (!is_unknown(L, i, j)) continue;
     const size_t k = (size_t)j * L.pitch + i;
-    double qv = 0.0;
-    if (is_unknown(L, i, j)) {
-      qv = fma(L.diag[k], p[k], offdiag(L, p, i, j));
-      spq += p[k] * qv;
-      spr += p[k] * r[k];
-    }
-    q[k] = qv;
+    const int jd = row_dn(j, L.nyr), ju = row_up(j, L.nyr);
+    const size_t r0 = (size_t)j * zp, rd = (size_t)jd * zp, ru = (size_t)ju * zp;
+    const size_t c0 = (size_t)j * L.pitch, cd = (size_t)jd * L.pitch;
+    double az = L.cE[c0 + i] * (double)z[r0 + i + 1];
+    az = fma(L.cE[c0 + i - 1], (double)z[r0 + i - 1], az);
+    az = fma(L.cN[c0 + i], (double)z[ru + i], az);
+    az = fma(L.cN[cd + i], (double)z[rd + i], az);
+    az = fma(L.cNE[c0 + i], (double)z[ru + i + 1], az);
+    az = fma(L.cNE[cd + i - 1], (double)z[rd + i - 1], az);
+    az = fma(L.cNW[c0 + i], (double)z[ru + i - 1], az);
+    az = fma(L.cNW[cd + i + 1], (double)z[rd + i + 1], az);
+    az = fma(L.diag[k], (double)z[r0 + i], az);
+    const double zz = is * (double)z[r0 + i];
+    const double pn = first ? zz : fma(beta, p[k], zz);
+    const double qn = first ? is * az : fma(beta, q[k], is * az);
+    p[k] = pn;
+    q[k] = qn;
+    spq = fma(pn, qn, spq);
+    spr = fma(pn, r[k], spr);
   }
   const double a0 = block_sum<kNT>(spq, sh);
   const double a1 = block_sum<kNT>(spr, sh);
@@ -279,16 +285,70 @@ __global__ void __launch_bounds__(kNT) k_fcg_q(Lvl<double> L, const double* __re
   }
 }
 
+// Split form for an FP32 z (the fused form would widen nine FP32 neighbours per node on
+// the FP64 pipe): p = inv_scale z + beta p elementwise, then q = A p with the FP64 stencil.
+__global__ void __launch_bounds__(kNT) k_fcg_p32(Lvl<double> L, const float* __restrict__ z, int zp,
+                                                 double* __restrict__ p, const SolveState* st) {
+  if (st->done) return;
+  const double is = st->inv_scale_r32;
+  const double beta = st->beta;
+  const bool first = (st->it == 0);
+  NODE_LOOP(L) {
+    if (!is_unknown(L, i, j)) continue;
+    const size_t k = (size_t)j * L.pitch + i;
+    const double zz = is * (double)z[(size_t)j * zp + i];
+    p[k] = first ? zz : fma(beta, p[k], zz);
+  }
+}
+
+__global__ void __launch_bounds__(kNT) k_fcg_q(Lvl<double> L, const double* __restrict__ p,
+                                               const double* __restrict__ r,
+                                               double* __restrict__ q, SolveState* st,
+                                               double* part) {
+  if (st->done) return;
+  __shared__ double sh[kNT / 32];
+  __shared__ int flag;
+  double spq = 0.0, spr = 0.0;
+  NODE_LOOP(L) {
+    if (!is_unknown(L, i, j)) continue;
+    const size_t k = (size_t)j * L.pitch + i;
+    const double qv = fma(L.diag[k], p[k], offdiag(L, p, i, j));
+    q[k] = qv;
+    spq = fma(p[k], qv, spq);
+    spr = fma(p[k], r[k], spr);
+  }
+  const double a0 = block_sum<kNT>(spq, sh);
+  const double a1 = block_sum<kNT>(spr, sh);
+  if (threadIdx.x == 0) {
+    part[bid()] = a0;
+    part[nblocks() + bid()] = a1;
+  }
+  if (last_block_arrival(&st->ticket[3], nblocks(), &flag)) {
+    const double pq = reduce_partials<kNT>(part, nblocks(), sh);
+    const double pr = reduce_partials<kNT>(part + nblocks(), nblocks(), sh);
+    if (threadIdx.x == 0) {
+      st->pq = pq;
+      st->pr = pr;
+      st->alpha = (pq != 0.0) ? pr / pq : 0.0;
+      st->pq_old = pq;
+    }
+  }
+}
+
+// x += alpha p; r -= alpha q; ||r||^2; and, for the mixed path, the next cycle's
+// right-hand side r32 = fp32(r * scale) with the current power-of-two scale.
 __global__ void __launch_bounds__(kNT) k_fcg_update(Lvl<double> L, double* __restrict__ x,
                                                     double* __restrict__ r,
                                                     const double* __restrict__ p,
-                                                    const double* __restrict__ q, SolveState* st,
-                                                    double* part, cudaGraphConditionalHandle h,
-                                                    int has_h) {
+                                                    const double* __restrict__ q,
+                                                    float* __restrict__ r32, int p32,
+                                                    SolveState* st, double* part,
+                                                    cudaGraphConditionalHandle h, int has_h) {
   if (st->done) return;
   __shared__ double sh[kNT / 32];
   __shared__ int flag;
   const double alpha = st->alpha;
+  const double sc = st->scale;
   double s = 0.0;
   NODE_LOOP(L) {
     if (!is_unknown(L, i, j)) continue;
@@ -296,7 +356,8 @@ __global__ void __launch_bounds__(kNT) k_fcg_update(Lvl<double> L, double* __res
     x[k] = fma(alpha, p[k], x[k]);
     const double rv = fma(-alpha, q[k], r[k]);
     r[k] = rv;
-    s += rv * rv;
+    if (r32) r32[(size_t)j * p32 + i] = (float)(rv * sc);
+    s = fma(rv, rv, s);
   }
   const double a0 = block_sum<kNT>(s, sh);
   if (threadIdx.x == 0) part[bid()] = a0;
@@ -304,6 +365,7 @@ __global__ void __launch_bounds__(kNT) k_fcg_update(Lvl<double> L, double* __res
     const double rr = reduce_partials<kNT>(part, nblocks(), sh);
     if (threadIdx.x == 0) {
       st->it += 1;
+      if (r32) st->inv_scale_r32 = 1.0 / sc;
       decide(st, rr, h, has_h, 1);
     }
   }
@@ -313,12 +375,14 @@ __global__ void __launch_bounds__(kNT) k_fcg_update(Lvl<double> L, double* __res
 // the solve stops only if the true residual meets rtol, else CG continues from it.
 __global__ void __launch_bounds__(kNT) k_fcg_verify(Lvl<double> L, const double* __restrict__ x,
                                                     const double* __restrict__ b,
-                                                    double* __restrict__ r, SolveState* st,
-                                                    double* part, cudaGraphConditionalHandle h,
-                                                    int has_h) {
+                                                    double* __restrict__ r,
+                                                    float* __restrict__ r32, int p32,
+                                                    SolveState* st, double* part,
+                                                    cudaGraphConditionalHandle h, int has_h) {
   if (st->done || !st->verify) return;
   __shared__ double sh[kNT / 32];
   __shared__ int flag;
+  const double sc = st->scale;
   double s = 0.0;
   NODE_LOOP(L) {
     const size_t k = (size_t)j * L.pitch + i;
@@ -328,6 +392,7 @@ __global__ void __launch_bounds__(kNT) k_fcg_verify(Lvl<double> L, const double*
       s += rv * rv;
     }
     r[k] = rv;
+    if (r32) r32[(size_t)j * p32 + i] = (float)(rv * sc);
   }
   const double a0 = block_sum<kNT>(s, sh);
   if (threadIdx.x == 0) part[bid()] = a0;
@@ -335,6 +400,7 @@ __global__ void __launch_bounds__(kNT) k_fcg_verify(Lvl<double> L, const double*
     const double rr = reduce_partials<kNT>(part, nblocks(), sh);
     if (threadIdx.x == 0) {
       st->verify = 0;
+      if (r32) st->inv_scale_r32 = 1.0 / sc;
       decide(st, rr, h, has_h, 0);
     }
   }
@@ -380,7 +446,7 @@ cudaError_t launch_resid_check(const OpF64& A, const double* x, const double* b,
   CHK();
 }
 cudaError_t launch_r_to_f32(const OpF64& A, const double* r, float* b32, int pitch32,
-                            const SolveState* st, cudaStream_t s) {
+                            SolveState* st, cudaStream_t s) {
   const Lvl<double> L = lvl_of(A);
   k_r_to_f32<<<red_grid(L.nx, L.nyr), kNT, 0, s>>>(L, r, b32, pitch32, st);
   CHK();
@@ -406,39 +472,39 @@ cudaError_t launch_fcg_zq(const OpF64& A, const TZ* z, int zp, const double* q, 
   k_fcg_zq<TZ><<<red_grid(L.nx, L.nyr), kNT, 0, s>>>(L, z, zp, q, st, part);
   CHK();
 }
-template <typename TZ>
-cudaError_t launch_fcg_p(const OpF64& A, const TZ* z, int zp, double* p, const SolveState* st,
-                         cudaStream_t s) {
-  const Lvl<double> L = lvl_of(A);
-  k_fcg_p<TZ><<<red_grid(L.nx, L.nyr), kNT, 0, s>>>(L, z, zp, p, st);
-  CHK();
-}
 template cudaError_t launch_fcg_zq<double>(const OpF64&, const double*, int, const double*,
                                            SolveState*, double*, cudaStream_t);
 template cudaError_t launch_fcg_zq<float>(const OpF64&, const float*, int, const double*,
                                           SolveState*, double*, cudaStream_t);
-template cudaError_t launch_fcg_p<double>(const OpF64&, const double*, int, double*,
-                                          const SolveState*, cudaStream_t);
-template cudaError_t launch_fcg_p<float>(const OpF64&, const float*, int, double*,
-                                         const SolveState*, cudaStream_t);
-cudaError_t launch_fcg_q(const OpF64& A, const double* p, const double* r, double* q,
-                         SolveState* st, double* part, cudaStream_t s) {
+template <typename TZ>
+cudaError_t launch_fcg_pq(const OpF64& A, const TZ* z, int zp, double* p, double* q, const double* r,
+                          SolveState* st, double* part, cudaStream_t s) {
   const Lvl<double> L = lvl_of(A);
+  k_fcg_pq<TZ><<<red_grid(L.nx, L.nyr), kNT, 0, s>>>(L, z, zp, p, q, r, st, part);
+  CHK();
+}
+template cudaError_t launch_fcg_pq<double>(const OpF64&, const double*, int, double*, double*,
+                                           const double*, SolveState*, double*, cudaStream_t);
+template <>
+cudaError_t launch_fcg_pq<float>(const OpF64& A, const float* z, int zp, double* p, double* q,
+                                 const double* r, SolveState* st, double* part, cudaStream_t s) {
+  const Lvl<double> L = lvl_of(A);
+  k_fcg_p32<<<red_grid(L.nx, L.nyr), kNT, 0, s>>>(L, z, zp, p, st);
   k_fcg_q<<<red_grid(L.nx, L.nyr), kNT, 0, s>>>(L, p, r, q, st, part);
   CHK();
 }
 cudaError_t launch_fcg_update(const OpF64& A, double* x, double* r, const double* p,
-                              const double* q, SolveState* st, double* part,
+                              const double* q, float* r32, int p32, SolveState* st, double* part,
                               cudaGraphConditionalHandle h, int has_h, cudaStream_t s) {
   const Lvl<double> L = lvl_of(A);
-  k_fcg_update<<<red_grid(L.nx, L.nyr), kNT, 0, s>>>(L, x, r, p, q, st, part, h, has_h);
+  k_fcg_update<<<red_grid(L.nx, L.nyr), kNT, 0, s>>>(L, x, r, p, q, r32, p32, st, part, h, has_h);
   CHK();
 }
 cudaError_t launch_fcg_verify(const OpF64& A, const double* x, const double* b, double* r,
-                              SolveState* st, double* part, cudaGraphConditionalHandle h,
-                              int has_h, cudaStream_t s) {
+                              float* r32, int p32, SolveState* st, double* part,
+                              cudaGraphConditionalHandle h, int has_h, cudaStream_t s) {
   const Lvl<double> L = lvl_of(A);
-  k_fcg_verify<<<red_grid(L.nx, L.nyr), kNT, 0, s>>>(L, x, b, r, st, part, h, has_h);
+  k_fcg_verify<<<red_grid(L.nx, L.nyr), kNT, 0, s>>>(L, x, b, r, r32, p32, st, part, h, has_h);
   CHK();
 }
 cudaError_t launch_copy_out(const OpF64& A, const double* x, const SolveArgs* a, cudaStream_t s) {

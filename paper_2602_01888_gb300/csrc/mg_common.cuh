@@ -67,6 +67,7 @@ struct SolveState {
   double alpha, beta;
   double scale;       // power-of-two scaling of r before the FP32 cycle (mixed)
   double inv_scale;
+  double inv_scale_r32;  // 1/scale of the r32 the current FP32 cycle started from
   double rtol;
   int it;             // iterations done
   int max_iters;

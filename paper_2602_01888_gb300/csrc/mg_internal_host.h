@@ -51,6 +51,8 @@ struct LevelMem {
 struct GraphEntry {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  int fixed_kernels = 0;  // kernel nodes outside the loop
+  int body_kernels = 0;   // kernel nodes of one loop pass
 };
 
 }  // namespace mg
@@ -78,8 +80,11 @@ struct mg_problem {
   double* stage = nullptr;  // device copies of host inputs/outputs (3 node arrays)
   mg::SolveArgs* h_args = nullptr;
   mg::SolveState* h_state = nullptr;
+  int* h_flags = nullptr;  // folded, coarse status, kernel wait timeout
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   double setup_ms = 0.0;
+  int setup_kernels = 0;
+  int last_fixed_kernels = 0, last_body_kernels = 0;
   std::map<uint64_t, mg::GraphEntry> graphs;
   std::vector<void*> allocs;
 };

@@ -8,7 +8,9 @@
 namespace mg {
 
 constexpr int kCoarseMax = 256;      // unknowns of the coarsest level (dense inverse)
-constexpr int kCoarseThreads = 256;  // threads of the single-CTA coarsest kernels
+constexpr int kCoarseThreads = 256;  // threads of the single-CTA coarsest solve
+constexpr int kCoarseFactorThreads = 1024;
+constexpr int kCoarseSmemM = 128;    // coarsest inverses up to this order are formed in shared memory
 constexpr int kRRX = 16, kRRY = 16;  // coarse tile of the residual + restriction kernel
 
 template <typename T>
@@ -60,7 +62,9 @@ cudaError_t launch_assemble(const OpF64& A, double hx, double hy, const double* 
                             const double* exy, const double* eyy, cudaStream_t s);
 cudaError_t launch_rhs(const OpF64& A, const double* rho, int rho_pitch, const double* D, double* b,
                        cudaStream_t s);
-cudaError_t launch_galerkin(const OpF64& F, const OpF64& C, cudaStream_t s);
+template <typename T>
+cudaError_t launch_galerkin(const Op<T>& F, const Op<T>& C, cudaStream_t s);
+cudaError_t launch_op_to_f64(const OpF32& A, const OpF64& B, cudaStream_t s);
 cudaError_t launch_op_to_f32(const OpF64& A, const OpF32& B, cudaStream_t s);
 cudaError_t launch_coarse_factor(const OpF64& A, double* inv, int* status, cudaStream_t s);
 

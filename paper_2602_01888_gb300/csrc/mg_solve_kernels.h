@@ -34,7 +34,7 @@ cudaError_t launch_resid_check(const OpF64& A, const double* x, const double* b,
                                SolveState* st, double* part, cudaGraphConditionalHandle h,
                                int has_h, cudaStream_t s);
 cudaError_t launch_r_to_f32(const OpF64& A, const double* r, float* b32, int pitch32,
-                            const SolveState* st, cudaStream_t s);
+                            SolveState* st, cudaStream_t s);
 cudaError_t launch_add_f32(const OpF64& A, double* x, const float* e32, int pitch32,
                            SolveState* st, cudaStream_t s);
 cudaError_t launch_iter_inc(SolveState* st, cudaStream_t s);
@@ -43,16 +43,14 @@ template <typename TZ>
 cudaError_t launch_fcg_zq(const OpF64& A, const TZ* z, int zp, const double* q, SolveState* st,
                           double* part, cudaStream_t s);
 template <typename TZ>
-cudaError_t launch_fcg_p(const OpF64& A, const TZ* z, int zp, double* p, const SolveState* st,
-                         cudaStream_t s);
-cudaError_t launch_fcg_q(const OpF64& A, const double* p, const double* r, double* q,
-                         SolveState* st, double* part, cudaStream_t s);
+cudaError_t launch_fcg_pq(const OpF64& A, const TZ* z, int zp, double* p, double* q, const double* r,
+                          SolveState* st, double* part, cudaStream_t s);
 cudaError_t launch_fcg_update(const OpF64& A, double* x, double* r, const double* p,
-                              const double* q, SolveState* st, double* part,
+                              const double* q, float* r32, int p32, SolveState* st, double* part,
                               cudaGraphConditionalHandle h, int has_h, cudaStream_t s);
 cudaError_t launch_fcg_verify(const OpF64& A, const double* x, const double* b, double* r,
-                              SolveState* st, double* part, cudaGraphConditionalHandle h,
-                              int has_h, cudaStream_t s);
+                              float* r32, int p32, SolveState* st, double* part,
+                              cudaGraphConditionalHandle h, int has_h, cudaStream_t s);
 cudaError_t launch_copy_out(const OpF64& A, const double* x, const SolveArgs* a, cudaStream_t s);
 
 }  // namespace mg

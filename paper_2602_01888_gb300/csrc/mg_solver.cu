@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -16,6 +17,7 @@
 #include "mg_launch.h"
 #include "mg_solve_kernels.h"
 #include "mg_internal_host.h"
+#include "mg_vcycle.h"
 
 namespace mg {
 
@@ -223,6 +225,7 @@ static void problem_release(mg_problem* P) {
   P->allocs.clear();
   if (P->h_args) cudaFreeHost(P->h_args);
   if (P->h_state) cudaFreeHost(P->h_state);
+  if (P->h_flags) cudaFreeHost(P->h_flags);
   if (P->ev0) cudaEventDestroy(P->ev0);
   if (P->ev1) cudaEventDestroy(P->ev1);
 }
@@ -275,6 +278,7 @@ static mg_status problem_alloc(mg_problem* P, bool mixed) {
   CU(cudaMemsetAsync(P->st, 0, sizeof(SolveState), P->ctx->stream));
   CU(cudaMallocHost(&P->h_args, sizeof(SolveArgs)));
   CU(cudaMallocHost(&P->h_state, sizeof(SolveState)));
+  CU(cudaMallocHost(&P->h_flags, 4 * sizeof(int)));
   CU(cudaEventCreate(&P->ev0));
   CU(cudaEventCreate(&P->ev1));
   return MG_OK;
@@ -323,10 +327,17 @@ static mg_status problem_build(mg_problem* P, const mg_map_desc* map, const doub
                            pt, P->D, exx, exy, eyy, P->flags, s));
   }
   CU(launch_assemble(F.A, hx, hy, exx, exy, eyy, s));
-  for (int l = 1; l < P->nlev; ++l) CU(launch_galerkin(P->lev[l - 1].A, P->lev[l].A, s));
+  if (!P->mixed) {
+    for (int l = 1; l < P->nlev; ++l) CU(launch_galerkin<double>(P->lev[l - 1].A, P->lev[l].A, s));
+  } else {
+    // the FP32 cycle only needs FP32 coarse operators: Galerkin products in FP32, and the
+    // coarsest one widened to FP64 for its dense inverse
+    CU(launch_op_to_f32(F.A, F.A32, s));
+    for (int l = 1; l < P->nlev; ++l) CU(launch_galerkin<float>(P->lev[l - 1].A32, P->lev[l].A32, s));
+    if (P->nlev > 1) CU(launch_op_to_f64(P->lev[P->nlev - 1].A32, P->lev[P->nlev - 1].A, s));
+  }
   CU(launch_coarse_factor(P->lev[P->nlev - 1].A, P->inv, P->flags + 1, s));
-  if (P->mixed)
-    for (int l = 0; l < P->nlev; ++l) CU(launch_op_to_f32(P->lev[l].A, P->lev[l].A32, s));
+  P->setup_kernels = 1 + 2 + (P->mixed ? 1 + (P->nlev - 1) + (P->nlev > 1 ? 1 : 0) : P->nlev - 1) + 1;
   // restore the scratch vectors used as staging
   CU(cudaMemsetAsync(P->z, 0, 3 * np * sizeof(double), s));
   CU(cudaEventRecord(P->ev1, s));
@@ -433,42 +444,37 @@ extern "C" mg_status mg_problem_info(const mg_problem* P, int* levels, int* nx_o
 // ------------------------------------------------------------------ solve graphs
 namespace mg {
 
+// Level table of the problem for one cycle in precision T; level 0 uses (x0, b0) and the
+// level's scratch array as its ping-pong partner.
 template <typename T>
-static mg_status emit_vcycle(mg_problem* P, bool f32, T* x0, const T* b0, const mg_solve_opts& o,
-                             const int* skip, cudaStream_t s) {
-  auto op = [&](int l) -> const Op<T>& {
-    if constexpr (sizeof(T) == 4) return P->lev[l].A32; else return P->lev[l].A;
-  };
-  auto X = [&](int l) -> T* {
-    if (l == 0) return x0;
-    if constexpr (sizeof(T) == 4) return P->lev[l].x32; else return P->lev[l].x;
-  };
-  auto B = [&](int l) -> const T* {
-    if (l == 0) return b0;
-    if constexpr (sizeof(T) == 4) return P->lev[l].b32; else return P->lev[l].b;
-  };
-  auto Bw = [&](int l) -> T* {
-    if constexpr (sizeof(T) == 4) return P->lev[l].b32; else return P->lev[l].b;
-  };
-  auto Tm = [&](int l) -> T* {
-    if constexpr (sizeof(T) == 4) return P->lev[l].t32; else return P->lev[l].t;
-  };
-  (void)f32;
-  const int L = P->nlev;
-  auto smooth = [&](int l, int sweeps, int rev) -> cudaError_t {
-    if (o.smoother == MG_SMOOTH_JACOBI)
-      return launch_jacobi(op(l), X(l), B(l), Tm(l), sweeps, o.omega_j, skip, s);
-    return launch_smooth(op(l), X(l), B(l), sweeps, rev, skip, s);
-  };
-  for (int l = 0; l < L - 1; ++l) {
-    CU(smooth(l, o.nu1, 0));
-    CU(launch_resid_restrict(op(l), X(l), B(l), Bw(l + 1), X(l + 1), op(l + 1).pitch, skip, s));
+static void level_table(mg_problem* P, T* x0, T* b0, VLevels<T>* V) {
+  V->L = P->nlev;
+  V->inv = P->inv;
+  for (int l = 0; l < P->nlev; ++l) {
+    LevelMem& M = P->lev[l];
+    if constexpr (sizeof(T) == 4) {
+      V->A[l] = M.A32;
+      V->x[l] = M.x32;
+      V->b[l] = M.b32;
+      V->t[l] = M.t32;
+    } else {
+      V->A[l] = M.A;
+      V->x[l] = M.x;
+      V->b[l] = M.b;
+      V->t[l] = M.t;
+    }
   }
-  CU(launch_coarse_solve(op(L - 1), P->inv, B(L - 1), X(L - 1), skip, s));
-  for (int l = L - 2; l >= 0; --l) {
-    CU(launch_prolong_add(op(l), X(l), X(l + 1), op(l + 1).pitch, skip, s));
-    CU(smooth(l, o.nu2, 1));
-  }
+  V->x[0] = x0;
+  V->b[0] = b0;
+  V->err = P->flags + 2;
+}
+
+template <typename T>
+static mg_status emit_vcycle_on(mg_problem* P, T* x0, T* b0, const mg_solve_opts& o,
+                                const int* skip, cudaStream_t s, T** result) {
+  VLevels<T> V;
+  level_table<T>(P, x0, b0, &V);
+  CU(emit_vcycle<T>(V, o.smoother, o.nu1, o.nu2, o.omega_j, skip, s, result));
   return MG_OK;
 }
 
@@ -479,40 +485,43 @@ static mg_status emit_body(mg_problem* P, const mg_solve_opts& o, cudaGraphCondi
   const int* skip = &P->st->done;
   const size_t n0 = (size_t)F.A.pitch * rows_stored(F.A.ny, F.A.periodic);
   const bool mixed = (o.precision == MG_PREC_MIXED);
+  mg_status st;
   if (o.outer == MG_OUTER_VCYCLE) {
     if (!mixed) {
       CU(launch_resid_check(F.A, F.x, F.b, nullptr, P->st, P->part, h, has_h, s));
-      mg_status st = emit_vcycle<double>(P, false, F.x, F.b, o, skip, s);
-      if (st) return st;
+      double* res = nullptr;
+      if ((st = emit_vcycle_on<double>(P, F.x, F.b, o, skip, s, &res))) return st;
+      if (res != F.x) CU(cudaMemcpyAsync(F.x, res, n0 * sizeof(double), cudaMemcpyDeviceToDevice, s));
     } else {
       CU(launch_resid_check(F.A, F.x, F.b, P->r, P->st, P->part, h, has_h, s));
       CU(launch_r_to_f32(F.A, P->r, F.b32, F.A32.pitch, P->st, s));
       CU(cudaMemsetAsync(F.x32, 0, n0 * sizeof(float), s));
-      mg_status st = emit_vcycle<float>(P, true, F.x32, F.b32, o, skip, s);
-      if (st) return st;
-      CU(launch_add_f32(F.A, F.x, F.x32, F.A32.pitch, P->st, s));
+      float* res = nullptr;
+      if ((st = emit_vcycle_on<float>(P, F.x32, F.b32, o, skip, s, &res))) return st;
+      CU(launch_add_f32(F.A, F.x, res, F.A32.pitch, P->st, s));
     }
     CU(launch_iter_inc(P->st, s));
     return MG_OK;
   }
-  // flexible CG preconditioned by one V-cycle
-  CU(launch_fcg_verify(F.A, F.x, F.b, P->r, P->st, P->part, h, has_h, s));
+  // flexible CG preconditioned by one V-cycle; for the mixed path the cycle's right-hand
+  // side r32 was written by the previous update (or the initialisation / verification)
+  CU(launch_fcg_verify(F.A, F.x, F.b, P->r, mixed ? F.b32 : nullptr, F.A32.pitch, P->st, P->part, h,
+                       has_h, s));
   if (!mixed) {
     CU(cudaMemsetAsync(P->z, 0, n0 * sizeof(double), s));
-    mg_status st = emit_vcycle<double>(P, false, P->z, P->r, o, skip, s);
-    if (st) return st;
-    CU(launch_fcg_zq<double>(F.A, P->z, F.A.pitch, P->q, P->st, P->part, s));
-    CU(launch_fcg_p<double>(F.A, P->z, F.A.pitch, P->p, P->st, s));
+    double* res = nullptr;
+    if ((st = emit_vcycle_on<double>(P, P->z, P->r, o, skip, s, &res))) return st;
+    CU(launch_fcg_zq<double>(F.A, res, F.A.pitch, P->q, P->st, P->part, s));
+    CU(launch_fcg_pq<double>(F.A, res, F.A.pitch, P->p, P->q, P->r, P->st, P->part, s));
   } else {
-    CU(launch_r_to_f32(F.A, P->r, F.b32, F.A32.pitch, P->st, s));
     CU(cudaMemsetAsync(F.x32, 0, n0 * sizeof(float), s));
-    mg_status st = emit_vcycle<float>(P, true, F.x32, F.b32, o, skip, s);
-    if (st) return st;
-    CU(launch_fcg_zq<float>(F.A, F.x32, F.A32.pitch, P->q, P->st, P->part, s));
-    CU(launch_fcg_p<float>(F.A, F.x32, F.A32.pitch, P->p, P->st, s));
+    float* res = nullptr;
+    if ((st = emit_vcycle_on<float>(P, F.x32, F.b32, o, skip, s, &res))) return st;
+    CU(launch_fcg_zq<float>(F.A, res, F.A32.pitch, P->q, P->st, P->part, s));
+    CU(launch_fcg_pq<float>(F.A, res, F.A32.pitch, P->p, P->q, P->r, P->st, P->part, s));
   }
-  CU(launch_fcg_q(F.A, P->p, P->r, P->q, P->st, P->part, s));
-  CU(launch_fcg_update(F.A, F.x, P->r, P->p, P->q, P->st, P->part, h, has_h, s));
+  CU(launch_fcg_update(F.A, F.x, P->r, P->p, P->q, mixed ? F.b32 : nullptr, F.A32.pitch, P->st,
+                       P->part, h, has_h, s));
   return MG_OK;
 }
 
@@ -539,6 +548,7 @@ static mg_status build_graph(mg_problem* P, const mg_solve_opts& o, GraphEntry* 
   const cudaGraphNode_t* deps = nullptr;
   size_t ndeps = 0;
   mg_status st = MG_OK;
+  int body_kernel_count = 0;
   cudaGraphConditionalHandle h = 0;
   do {
     if (cudaStreamGetCaptureInfo(cs, &cst, nullptr, &g, nullptr, nullptr, nullptr) != cudaSuccess) {
@@ -551,7 +561,9 @@ static mg_status build_graph(mg_problem* P, const mg_solve_opts& o, GraphEntry* 
     }
     if (launch_solve_init(F.A, P->args, P->D, F.x, F.b, P->st, cs) != cudaSuccess ||
         launch_resid_init(F.A, F.x, F.b, fcg ? P->r : nullptr, P->st, P->part, h, 1, cs) !=
-            cudaSuccess) {
+            cudaSuccess ||
+        (fcg && o.precision == MG_PREC_MIXED &&
+         launch_r_to_f32(F.A, P->r, F.b32, F.A32.pitch, P->st, cs) != cudaSuccess)) {
       st = set_error(MG_ERR_CUDA, "capture of solve init failed");
       break;
     }
@@ -587,6 +599,17 @@ static mg_status build_graph(mg_problem* P, const mg_solve_opts& o, GraphEntry* 
     cudaError_t e2 = cudaStreamEndCapture(cs2, &body_out);
     if (!st && e2 != cudaSuccess) st = set_error(MG_ERR_CUDA, "body capture failed: %s", cudaGetErrorString(e2));
     if (st) break;
+    {
+      size_t n = 0;
+      cudaGraphGetNodes(body, nullptr, &n);
+      std::vector<cudaGraphNode_t> nodes(n);
+      if (n) cudaGraphGetNodes(body, nodes.data(), &n);
+      for (size_t q = 0; q < n; ++q) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nodes[q], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel)
+          ++body_kernel_count;
+      }
+    }
     if (launch_copy_out(F.A, F.x, P->args, cs) != cudaSuccess) {
       st = set_error(MG_ERR_CUDA, "capture of copy-out failed");
       break;
@@ -600,6 +623,20 @@ static mg_status build_graph(mg_problem* P, const mg_solve_opts& o, GraphEntry* 
     return st;
   }
   if (e != cudaSuccess) return set_error(MG_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+  auto kernel_nodes = [](cudaGraph_t g) {
+    size_t n = 0;
+    cudaGraphGetNodes(g, nullptr, &n);
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (n) cudaGraphGetNodes(g, nodes.data(), &n);
+    int k = 0;
+    for (size_t q = 0; q < n; ++q) {
+      cudaGraphNodeType t;
+      if (cudaGraphNodeGetType(nodes[q], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+    }
+    return k;
+  };
+  ge->fixed_kernels = kernel_nodes(gout);
+  ge->body_kernels = body_kernel_count;
   cudaGraphExec_t ex;
   e = cudaGraphInstantiate(&ex, gout, 0);
   if (e != cudaSuccess) {
@@ -614,8 +651,8 @@ static mg_status build_graph(mg_problem* P, const mg_solve_opts& o, GraphEntry* 
 static mg_status check_opts(const mg_problem* P, const mg_solve_opts& o) {
   if (o.precision != MG_PREC_FP64 && o.precision != MG_PREC_MIXED)
     return set_error(MG_ERR_ARG, "bad precision %d", o.precision);
-  if (o.precision == MG_PREC_MIXED && !P->mixed)
-    return set_error(MG_ERR_ARG, "mixed precision needs a problem set up with MG_PREC_MIXED");
+  if ((o.precision == MG_PREC_MIXED) != (P->mixed != 0))
+    return set_error(MG_ERR_ARG, "solve precision differs from the precision the problem was set up with");
   if (o.outer != MG_OUTER_VCYCLE && o.outer != MG_OUTER_FCG)
     return set_error(MG_ERR_ARG, "bad outer iteration %d", o.outer);
   if (o.smoother != MG_SMOOTH_GS4 && o.smoother != MG_SMOOTH_JACOBI)
@@ -628,12 +665,48 @@ static mg_status check_opts(const mg_problem* P, const mg_solve_opts& o) {
   return MG_OK;
 }
 
+// Host-driven loop (MG_SOLVE_LOOP=host): the same kernels in the same order launched
+// directly on the stream, with one stream synchronisation per outer iteration to read
+// the convergence flag.  Used by per-kernel profilers, which do not support kernels
+// inside graphs with conditional nodes.
+static bool host_loop_mode() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = getenv("MG_SOLVE_LOOP");
+    v = (e && strcmp(e, "host") == 0) ? 1 : 0;
+  }
+  return v == 1;
+}
+
+static mg_status run_host_loop(mg_problem* P, const mg_solve_opts& o, cudaStream_t s) {
+  LevelMem& F = P->lev[0];
+  const bool fcg = (o.outer == MG_OUTER_FCG);
+  CU(launch_solve_init(F.A, P->args, P->D, F.x, F.b, P->st, s));
+  CU(launch_resid_init(F.A, F.x, F.b, fcg ? P->r : nullptr, P->st, P->part, 0, 0, s));
+  if (fcg && o.precision == MG_PREC_MIXED)
+    CU(launch_r_to_f32(F.A, P->r, F.b32, F.A32.pitch, P->st, s));
+  P->last_fixed_kernels = 3 + ((fcg && o.precision == MG_PREC_MIXED) ? 1 : 0);
+  P->last_body_kernels = 0;
+  for (int pass = 0; pass < 2 * o.max_iters + 8; ++pass) {
+    int done = 0;
+    CU(cudaMemcpyAsync(&done, &P->st->done, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    if (done) break;
+    mg_status st = emit_body(P, o, 0, 0, s);
+    if (st) return st;
+    P->last_fixed_kernels += 0;
+  }
+  CU(launch_copy_out(F.A, F.x, P->args, s));
+  return MG_OK;
+}
+
 // Enqueue one solve on stream s (inputs already device-resident at the given pointers).
 mg_status enqueue_solve(mg_problem* P, const mg_solve_opts& o, const double* rho, const double* bc,
                         const double* phi_in, double* phi_out, cudaStream_t s) {
+  const bool host_loop = host_loop_mode();
   const uint64_t key = graph_key(o);
   auto it = P->graphs.find(key);
-  if (it == P->graphs.end()) {
+  if (!host_loop && it == P->graphs.end()) {
     GraphEntry ge;
     mg_status st = build_graph(P, o, &ge);
     if (st) return st;
@@ -651,14 +724,24 @@ mg_status enqueue_solve(mg_problem* P, const mg_solve_opts& o, const double* rho
   a->n_unknowns = (long long)coarse_unknowns(P->grid.nx, P->grid.ny, P->grid.periodic_y);
   CU(cudaMemcpyAsync(P->args, a, sizeof(SolveArgs), cudaMemcpyHostToDevice, s));
   CU(cudaEventRecord(P->ev0, s));
-  CU(cudaGraphLaunch(it->second.exec, s));
+  if (host_loop) {
+    mg_status st = run_host_loop(P, o, s);
+    if (st) return st;
+  } else {
+    CU(cudaGraphLaunch(it->second.exec, s));
+    P->last_fixed_kernels = it->second.fixed_kernels;
+    P->last_body_kernels = it->second.body_kernels;
+  }
   CU(cudaEventRecord(P->ev1, s));
   CU(cudaMemcpyAsync(P->h_state, P->st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+  CU(cudaMemcpyAsync(P->h_flags, P->flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
   return MG_OK;
 }
 
 mg_status finish_solve(mg_problem* P, mg_solve_stats* stats) {
   const SolveState& S = *P->h_state;
+  if (P->h_flags[2])
+    return set_error(MG_ERR_TIMEOUT, "a bounded wait inside a smoothing kernel gave up");
   if (stats) {
     memset(stats, 0, sizeof(*stats));
     stats->iters = S.it;
@@ -670,6 +753,8 @@ mg_status finish_solve(mg_problem* P, mg_solve_stats* stats) {
     stats->solve_ms = ms;
     const int n = std::min(S.hist_n, MG_HIST_MAX);
     for (int k = 0; k < n; ++k) stats->hist[k] = S.hist[k];
+    stats->kernel_launches = P->last_fixed_kernels + S.guard * P->last_body_kernels;
+    stats->setup_kernel_launches = P->setup_kernels;
   }
   if (S.status == 7) return set_error(MG_ERR_DIVERGED, "solve diverged (NaN/Inf residual)");
   if (S.status == 6)

@@ -1,0 +1,253 @@
+// One multigrid V(nu1, nu2) cycle (Sec. 3, Eqs. 19-24) enqueued on a stream:
+// levels above the tail threshold use the fused tile smoother (NS sweeps per launch,
+// ping-pong iterates) and the fused residual + full-weighting restriction; the levels
+// at and below it run in one single-CTA tail kernel that ends with the coarsest dense
+// solve.  The weighted-Jacobi smoother uses the per-sweep kernels on every level.
+#include <cstdlib>
+#include <cstring>
+
+#include "mg.h"
+#include "mg_fused.h"
+#include "mg_internal_host.h"
+#include "mg_kernels.h"
+#include "mg_launch.h"
+#include "mg_pipe.h"
+#include "mg_vcycle.h"
+
+namespace mg {
+
+template <typename T>
+static int default_tail_nodes() {
+  // One SM runs the tail, so its phases are limited by one SM's issue rate (and, in FP64,
+  // by its 2 FMA/clk): only the smallest levels go there; in FP64 just the coarsest.
+  return sizeof(T) == 8 ? 0 : 400;
+}
+
+template <typename T>
+int tail_nodes() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = getenv(sizeof(T) == 8 ? "MG_TAIL_NODES_F64" : "MG_TAIL_NODES_F32");
+    v = e ? atoi(e) : default_tail_nodes<T>();
+  }
+  return v;
+}
+
+// Levels with more nodes than this use the per-colour smoothing kernels (four launches
+// a sweep); smaller levels above the tail use the fused tile kernel.
+template <typename T>
+int colour_nodes() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = getenv(sizeof(T) == 8 ? "MG_COLOUR_NODES_F64" : "MG_COLOUR_NODES_F32");
+    v = e ? atoi(e) : 40000;
+  }
+  return v;
+}
+
+template <typename T>
+cudaError_t emit_vcycle(const VLevels<T>& V, int smoother, int nu1, int nu2, double omega,
+                        const int* skip, cudaStream_t s, T** result) {
+  const int L = V.L;
+  T* cur[kMaxLevels];
+  T* alt[kMaxLevels];
+  for (int l = 0; l < L; ++l) {
+    cur[l] = V.x[l];
+    alt[l] = V.t[l];
+  }
+  cudaError_t e;
+  if (smoother == MG_SMOOTH_JACOBI) {
+    for (int l = 0; l < L - 1; ++l) {
+      if ((e = launch_jacobi(V.A[l], cur[l], V.b[l], alt[l], nu1, omega, skip, s))) return e;
+      if ((e = launch_resid_restrict(V.A[l], cur[l], V.b[l], V.b[l + 1], cur[l + 1],
+                                     V.A[l + 1].pitch, skip, s)))
+        return e;
+    }
+    if ((e = launch_coarse_solve(V.A[L - 1], V.inv, V.b[L - 1], cur[L - 1], skip, s))) return e;
+    for (int l = L - 2; l >= 0; --l) {
+      if ((e = launch_prolong_add(V.A[l], cur[l], cur[l + 1], V.A[l + 1].pitch, skip, s))) return e;
+      if ((e = launch_jacobi(V.A[l], cur[l], V.b[l], alt[l], nu2, omega, skip, s))) return e;
+    }
+    *result = cur[0];
+    return cudaSuccess;
+  }
+  // first level handled by the tail kernel
+  // the tail starts at the first level that is small enough and whose levels fit in
+  // the tail kernel's shared memory
+  int t = L - 1;
+  const int thr = tail_nodes<T>();
+  for (int l = 0; l < L; ++l) {
+    const long long nodes = (long long)V.A[l].nx * rows_stored(V.A[l].ny, V.A[l].periodic);
+    size_t bytes = 0;
+    for (int q = l; q < L; ++q)
+      bytes += (size_t)9 * sizeof(T) * V.A[q].nx * rows_stored(V.A[q].ny, V.A[q].periodic);
+    if ((nodes <= thr || l == L - 1) && L - l <= kMaxTail && bytes <= kTailSmemMax) {
+      t = l;
+      break;
+    }
+  }
+  const int NS = fused_sweeps<T>();
+  const long long cthr = colour_nodes<T>();
+  auto smooth = [&](int l, int sweeps, int rev, const T* eH) -> cudaError_t {
+    cudaError_t err;
+    const long long nodes = (long long)V.A[l].nx * rows_stored(V.A[l].ny, V.A[l].periodic);
+    const int nyr = rows_stored(V.A[l].ny, V.A[l].periodic);
+    // large FP32 levels: pipelined fused kernel
+    if (sizeof(T) == 4 && nodes > cthr && sweeps % pipe_sweeps<T>() == 0 && nyr >= 64 &&
+        V.A[l].nx >= 160 && V.A[l].pitch % 4 == 0) {
+      for (int k = 0; k < sweeps / pipe_sweeps<T>(); ++k) {
+        err = launch_smooth_pipe<T>(V.A[l], cur[l], alt[l], V.b[l], rev, k == 0 ? eH : nullptr,
+                                    eH ? V.A[l + 1].pitch : 0, skip, V.err, s);
+        if (err) return err;
+        T* tmp = cur[l];
+        cur[l] = alt[l];
+        alt[l] = tmp;
+      }
+      return cudaSuccess;
+    }
+    if (sweeps % NS != 0 || nodes > cthr) {  // per-colour kernels, in place
+      if (eH && (err = launch_prolong_add(V.A[l], cur[l], eH, V.A[l + 1].pitch, skip, s))) return err;
+      return launch_smooth(V.A[l], cur[l], V.b[l], sweeps, rev, skip, s);
+    }
+    for (int k = 0; k < sweeps / NS; ++k) {
+      err = launch_smooth_fused(V.A[l], cur[l], alt[l], V.b[l], rev, k == 0 ? eH : nullptr,
+                                eH ? V.A[l + 1].pitch : 0, skip, s);
+      if (err) return err;
+      T* tmp = cur[l];
+      cur[l] = alt[l];
+      alt[l] = tmp;
+    }
+    if (sweeps == 0 && eH)
+      return launch_prolong_add(V.A[l], cur[l], eH, V.A[l + 1].pitch, skip, s);
+    return cudaSuccess;
+  };
+  for (int l = 0; l < t; ++l) {
+    if ((e = smooth(l, nu1, 0, nullptr))) return e;
+    if ((e = launch_resid_restrict(V.A[l], cur[l], V.b[l], V.b[l + 1], cur[l + 1], V.A[l + 1].pitch,
+                                   skip, s)))
+      return e;
+  }
+  {
+    TailArgs<T> ta;
+    memset(&ta, 0, sizeof ta);
+    ta.nlev = L - t;
+    ta.nu1 = nu1;
+    ta.nu2 = nu2;
+    ta.inv = V.inv;
+    for (int l = t; l < L; ++l) {
+      ta.lv[l - t].L = lvl_of(V.A[l]);
+      ta.lv[l - t].x = cur[l];
+      ta.lv[l - t].b = V.b[l];
+      ta.lv[l - t].t = alt[l];
+    }
+    if ((e = launch_tail(ta, skip, s))) return e;
+  }
+  for (int l = t - 1; l >= 0; --l)
+    if ((e = smooth(l, nu2, 1, cur[l + 1]))) return e;
+  *result = cur[0];
+  return cudaSuccess;
+}
+
+template int tail_nodes<double>();
+template int tail_nodes<float>();
+template cudaError_t emit_vcycle<double>(const VLevels<double>&, int, int, int, double, const int*,
+                                         cudaStream_t, double**);
+template cudaError_t emit_vcycle<float>(const VLevels<float>&, int, int, int, double, const int*,
+                                        cudaStream_t, float**);
+
+}  // namespace mg
+
+using namespace mg;
+
+template <typename T, typename OPK>
+static int vcycle_abi(int nlev, const OPK* ops, T* const* x, T* const* b, T* const* t,
+                      const double* inv, int nu1, int nu2, int smoother, void* stream) {
+  if (nlev < 1 || nlev > kMaxLevels || !ops || !x || !b || !t || !inv || nu1 < 0 || nu2 < 0 ||
+      nu1 + nu2 == 0)
+    return 1;
+  VLevels<T> V;
+  V.L = nlev;
+  V.inv = inv;
+  for (int l = 0; l < nlev; ++l) {
+    const OPK& o = ops[l];
+    if (o.nx < 3 || o.ny < 3 || o.pitch < o.nx || !x[l] || !b[l] || !t[l]) return 1;
+    if (l > 0 && (o.nx != (ops[l - 1].nx - 1) / 2 + 1 || o.ny != (ops[l - 1].ny - 1) / 2 + 1))
+      return 1;
+    V.A[l] = op_from(o);
+    V.x[l] = x[l];
+    V.b[l] = b[l];
+    V.t[l] = t[l];
+  }
+  if (coarse_unknowns(ops[nlev - 1].nx, ops[nlev - 1].ny, ops[nlev - 1].periodic) > kCoarseMax) return 1;
+  cudaStream_t s = (cudaStream_t)stream;
+  T* res = nullptr;
+  if (emit_vcycle<T>(V, smoother, nu1, nu2, 0.8, nullptr, s, &res) != cudaSuccess) return 4;
+  if (res != x[0]) {
+    const size_t bytes = (size_t)ops[0].pitch * rows_stored(ops[0].ny, ops[0].periodic) * sizeof(T);
+    if (cudaMemcpyAsync(x[0], res, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return 4;
+  }
+  return 0;
+}
+
+extern "C" int mgk_vcycle_f64(int nlev, const mgk_op_f64* ops, double* const* x, double* const* b,
+                              double* const* t, const double* inv, int nu1, int nu2, int smoother,
+                              void* stream) {
+  return vcycle_abi<double>(nlev, ops, x, b, t, inv, nu1, nu2, smoother, stream);
+}
+
+extern "C" int mgk_vcycle_f32(int nlev, const mgk_op_f32* ops, float* const* x, float* const* b,
+                              float* const* t, const double* inv, int nu1, int nu2, int smoother,
+                              void* stream) {
+  return vcycle_abi<float>(nlev, ops, x, b, t, inv, nu1, nu2, smoother, stream);
+}
+
+// Single fused smoothing launch on caller memory (testing and profiling).
+template <typename T, typename OPK>
+static int fused_abi(const OPK* A, const T* xin, T* xout, const T* b, int rev, const T* eH,
+                     int pitch_c, void* stream) {
+  if (!A || A->nx < 3 || A->ny < 3 || A->pitch < A->nx || !xin || !xout || !b || xin == xout)
+    return 1;
+  if (eH && ((A->nx - 1) % 2 || (A->ny - 1) % 2 || pitch_c < (A->nx - 1) / 2 + 1)) return 1;
+  return launch_smooth_fused<T>(op_from(*A), xin, xout, b, rev, eH, pitch_c, nullptr,
+                                (cudaStream_t)stream) == cudaSuccess ? 0 : 4;
+}
+
+extern "C" int mgk_smooth_fused_f64(const mgk_op_f64* A, const double* xin, double* xout,
+                                    const double* b, int reverse, const double* eH, int pitch_c,
+                                    void* stream) {
+  return fused_abi<double>(A, xin, xout, b, reverse, eH, pitch_c, stream);
+}
+
+extern "C" int mgk_smooth_fused_f32(const mgk_op_f32* A, const float* xin, float* xout,
+                                    const float* b, int reverse, const float* eH, int pitch_c,
+                                    void* stream) {
+  return fused_abi<float>(A, xin, xout, b, reverse, eH, pitch_c, stream);
+}
+
+extern "C" int mgk_fused_sweeps(int f32) { return f32 ? fused_sweeps<float>() : fused_sweeps<double>(); }
+
+template <typename T, typename OPK>
+static int pipe_abi(const OPK* A, const T* xin, T* xout, const T* b, int rev, const T* eH,
+                    int pitch_c, int* err, void* stream) {
+  if (!A || A->nx < 3 || A->ny < 3 || A->pitch < A->nx || !xin || !xout || !b || xin == xout)
+    return 1;
+  if (eH && ((A->nx - 1) % 2 || (A->ny - 1) % 2 || pitch_c < (A->nx - 1) / 2 + 1)) return 1;
+  const cudaError_t e = launch_smooth_pipe<T>(op_from(*A), xin, xout, b, rev, eH, pitch_c, nullptr,
+                                              err, (cudaStream_t)stream);
+  if (e == cudaErrorInvalidValue) return 1;
+  return e == cudaSuccess ? 0 : 4;
+}
+
+extern "C" int mgk_smooth_pipe_f64(const mgk_op_f64* A, const double* xin, double* xout,
+                                   const double* b, int reverse, const double* eH, int pitch_c,
+                                   int* err, void* stream) {
+  return pipe_abi<double>(A, xin, xout, b, reverse, eH, pitch_c, err, stream);
+}
+
+extern "C" int mgk_smooth_pipe_f32(const mgk_op_f32* A, const float* xin, float* xout,
+                                   const float* b, int reverse, const float* eH, int pitch_c,
+                                   int* err, void* stream) {
+  return pipe_abi<float>(A, xin, xout, b, reverse, eH, pitch_c, err, stream);
+}
+
+extern "C" int mgk_pipe_sweeps(int f32) { return f32 ? pipe_sweeps<float>() : pipe_sweeps<double>(); }

@@ -54,7 +54,8 @@ class mg_solve_opts(C.Structure):
 class mg_solve_stats(C.Structure):
     _fields_ = [("iters", C.c_int), ("levels", C.c_int), ("rel_residual", C.c_double),
                 ("setup_ms", C.c_double), ("solve_ms", C.c_double),
-                ("hist", C.c_double * MG_HIST_MAX)]
+                ("hist", C.c_double * MG_HIST_MAX), ("kernel_launches", C.c_int),
+                ("setup_kernel_launches", C.c_int)]
 
     def history(self):
         return np.array(self.hist[: min(self.iters + 1, MG_HIST_MAX)])
@@ -139,6 +140,22 @@ _SIGS = {
                               C.c_void_p], C.c_int),
     "mgk_coarse_solve_f32": ([C.POINTER(mgk_op_f32), C.c_void_p, C.c_void_p, C.c_void_p,
                               C.c_void_p], C.c_int),
+    "mgk_smooth_fused_f64": ([C.POINTER(mgk_op_f64), C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                              C.c_void_p, C.c_int, C.c_void_p], C.c_int),
+    "mgk_smooth_fused_f32": ([C.POINTER(mgk_op_f32), C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                              C.c_void_p, C.c_int, C.c_void_p], C.c_int),
+    "mgk_fused_sweeps": ([C.c_int], C.c_int),
+    "mgk_smooth_pipe_f64": ([C.POINTER(mgk_op_f64), C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                             C.c_void_p, C.c_int, C.c_void_p, C.c_void_p], C.c_int),
+    "mgk_smooth_pipe_f32": ([C.POINTER(mgk_op_f32), C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                             C.c_void_p, C.c_int, C.c_void_p, C.c_void_p], C.c_int),
+    "mgk_pipe_sweeps": ([C.c_int], C.c_int),
+    "mgk_vcycle_f64": ([C.c_int, C.POINTER(mgk_op_f64), C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                        C.POINTER(C.c_void_p), C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p],
+                       C.c_int),
+    "mgk_vcycle_f32": ([C.c_int, C.POINTER(mgk_op_f32), C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                        C.POINTER(C.c_void_p), C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p],
+                       C.c_int),
 }
 
 _lib = None

@@ -52,7 +52,7 @@ def test_struct_layouts_match_header(libmg):
     assert ctypes.sizeof(libmg.mg_grid_desc) == 48
     assert ctypes.sizeof(libmg.mg_map_desc) == 4 + 4 + 32 + 16 + 16
     assert ctypes.sizeof(libmg.mg_solve_opts) == 5 * 4 + 4 + 16 + 12 + 4
-    assert ctypes.sizeof(libmg.mg_solve_stats) == 8 + 3 * 8 + 256 * 8
+    assert ctypes.sizeof(libmg.mg_solve_stats) == 8 + 3 * 8 + 256 * 8 + 8
 
 
 def test_no_oracle_on_the_product_path():

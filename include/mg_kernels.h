@@ -14,6 +14,8 @@
 #ifndef MG_KERNELS_H_
 #define MG_KERNELS_H_
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -146,6 +148,20 @@ int mgk_smooth_pipe_f64(const mgk_op_f64 *A, const double *xin, double *xout, co
 int mgk_smooth_pipe_f32(const mgk_op_f32 *A, const float *xin, float *xout, const float *b,
                         int reverse, const float *eH, int pitch_c, int *err, void *stream);
 int mgk_pipe_sweeps(int f32);
+
+/* Weighted-Jacobi sweeps exactly as mgk_jacobi_f64, for callers that cannot allocate
+ * device memory when they call it (a latency-critical loop where cudaMalloc/cudaFree would
+ * synchronise the device, or an application whose device memory all belongs to another
+ * allocator).  The paper has no counterpart: this is a deployment variant.  Instead of the
+ * caller's tmp array it uses one fixed device array of mgk_jacobi_f64_static_capacity()
+ * doubles (8 MiB) that every device loading the library keeps until the process exits.
+ * Returns 2 (message in mg_last_error) when pitch * rows exceeds that capacity.  The first
+ * call on a device looks up the array's device address, so make it before capturing any
+ * stream.  All calls on a device share the array and it keeps the last call's contents;
+ * calls that overlap on the GPU race on it. */
+int mgk_jacobi_f64_static(const mgk_op_f64 *A, double *phi, const double *b, int sweeps,
+                          double omega, void *stream);
+size_t mgk_jacobi_f64_static_capacity(void);
 
 #ifdef __cplusplus
 }

@@ -31,13 +31,24 @@ from paper_2602_01888_gb300 import inputs as I  # noqa: E402
 METRIC = "unknowns solved/sec to 1e-9 rel. error (FP64 vs mixed, 1 GB300)"
 RTOL = 1e-9
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # 2 FP64 FMA/clk/SM x 152 SMs x 2.07 GHz
+HBM_PEAK_GBS = 6681.2
+
+# Single-instance workloads: (builder, precisions with the headline first, outer iteration,
+# rtol giving an error <= 1e-9 against the FP64 oracle (checked by the GPU tests), builder of
+# the bounded CPU sample).
+WORKLOADS = {
+    "inclusion_1025": (lambda: I.config2(1025), ("fp64", "mixed"), "fcg", 1e-9,
+                       lambda: I.config2(1025)),
+    "sine_warp_129": (lambda: I.config1(129), ("fp64", "mixed"), "vcycle", 1e-10,
+                      lambda: I.config1(129)),
+    "annulus_8193": (lambda: I.config3(8193), ("mixed", "fp64"), "fcg", 6e-10,
+                     lambda: I.config3(1025)),
+}
 
 
 def workload(name: str):
-    if name == "inclusion_1025":
-        return I.config2(1025)
-    if name == "sine_warp_129":
-        return I.config1(129)
+    if name in WORKLOADS:
+        return WORKLOADS[name][0]()
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -114,11 +125,11 @@ def allmax(dist, v):
 
 
 # ------------------------------------------------------------------ reference arm (oracle)
-def oracle_solve_seconds(inst):
+def oracle_solve_seconds(inst, rtol=RTOL):
     import oracle as O
     t0 = time.perf_counter()
     P = O.prepare(inst)
-    phi, it, hist = O.pcg_solve(P.A, P.b, P.phi0, rtol=RTOL, max_iters=400)
+    phi, it, hist = O.pcg_solve(P.A, P.b, P.phi0, rtol=rtol, max_iters=400)
     return time.perf_counter() - t0, it
 
 
@@ -128,22 +139,27 @@ def run_reference(args):
         return 0
     import oracle as O
     O.build()
-    side = 1025 if (args.steps + args.warmup) <= 16 else 513
-    inst = workload(args.workload) if side == 1025 else I.inclusion_instance(513, 0.25, 10.0, 2)
+    _, _, outer, rtol, sample_builder = WORKLOADS[args.workload]
+    if args.workload == "inclusion_1025" and (args.steps + args.warmup) > 16:
+        inst, sample = (I.inclusion_instance(513, 0.25, 10.0, 2),
+                        "inclusion recipe at 513^2 per step (1/4 of the unknowns), same rtol")
+    else:
+        inst = sample_builder()
+        sample = (f"full {args.workload} workload per step" if inst.grid.unknowns ==
+                  workload(args.workload).grid.unknowns else
+                  f"{args.workload} recipe at {inst.grid.nx}^2 per step, same rtol")
     U = inst.grid.unknowns
     for _ in range(args.warmup):
-        oracle_solve_seconds(inst)
+        oracle_solve_seconds(inst, rtol)
     tot = 0.0
     for _ in range(args.steps):
-        dt, it = oracle_solve_seconds(inst)
+        dt, it = oracle_solve_seconds(inst, rtol)
         tot += dt
     v = U * args.steps / tot
-    sample = (f"full {args.workload} workload per step" if side == 1025 else
-              "inclusion recipe at 513^2 per step (1/4 of the unknowns), same rtol")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "unknowns/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": args.workload, "rtol": RTOL},
+            "data": "synthetic", "config": {"workload": args.workload, "rtol": rtol},
             "cpu_baseline": {"value": v, "unit": "unknowns/s", "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": v, "unit": "unknowns/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -152,42 +168,69 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ our arm
-def measure_smoother(mg, torch, inst, reps=20):
-    """Dominant FP64 kernel timed alone: one four-colour Gauss-Seidel sweep (4 launches)
-    on the fine level of this workload, operator built by the library's own kernels."""
+def measure_smoother(mg, torch, inst, prec, reps=20):
+    """Dominant kernel of the level-0 smoothing timed alone with CUDA events: one
+    four-colour Gauss-Seidel sweep (4 launches of k_gs_colour) on this workload's finest
+    level, operator built by the library's own kernels.  FP64: flop-bound (18 flop per
+    updated unknown); FP32: bytes-bound (algorithmic 32 B per node and sweep: iterate read
+    and written, b, four couplings, 1/diag)."""
     import ctypes as C
     g = inst.grid
     pitch = (g.nx + 31) // 32 * 32
-    dev = lambda a=None: (torch.zeros((g.nyr, pitch), dtype=torch.float64, device="cuda") if a is None
-                          else torch.nn.functional.pad(torch.from_numpy(np.array(a)).cuda(),
-                                                       (0, pitch - g.nx)))
-    xp, yp, eps = dev(inst.map.xp), dev(inst.map.yp), dev(inst.eps_phys)
-    D, exx, exy, eyy = dev(), dev(), dev(), dev()
+    f32 = prec == "mixed"
+    z = lambda d=torch.float64: torch.zeros((g.nyr, pitch), dtype=d, device="cuda")
+    pad = lambda a: torch.nn.functional.pad(torch.from_numpy(np.array(a, dtype=np.float64)).cuda(),
+                                            (0, pitch - g.nx))
+    D, exx, exy, eyy = z(), z(), z(), z()
     folded = torch.zeros(1, dtype=torch.int32, device="cuda")
     s = torch.cuda.current_stream().cuda_stream
-    mg.mgk("mgk_eps_grid", g.nx, g.ny, 0, g.hx, g.hy, xp.data_ptr(), yp.data_ptr(), 0.0, 0.0,
-           eps.data_ptr(), pitch, D.data_ptr(), exx.data_ptr(), exy.data_ptr(), eyy.data_ptr(),
-           folded.data_ptr(), s)
-    ops = [dev() for _ in range(6)]
-    st = mg.op_struct(ops, g.nx, g.ny, False)
+    eps = pad(inst.eps_phys) if inst.eps_phys is not None else None
+    if inst.map.kind == "grid":
+        xp, yp = pad(inst.map.xp), pad(inst.map.yp)
+        mg.mgk("mgk_eps_grid", g.nx, g.ny, int(g.periodic_y), g.hx, g.hy, xp.data_ptr(), yp.data_ptr(),
+               0.0, 0.0, eps.data_ptr() if eps is not None else None, pitch, D.data_ptr(),
+               exx.data_ptr(), exy.data_ptr(), eyy.data_ptr(), folded.data_ptr(), s)
+    else:
+        prm = (C.c_double * 4)(*(list(inst.map.params) + [0.0] * 4)[:4])
+        mg.mgk("mgk_eps_analytic", mg.MAP_CODES[inst.map.kind], prm, g.nx, g.ny, int(g.periodic_y),
+               g.x0, g.y0, g.hx, g.hy, eps.data_ptr() if eps is not None else None, pitch,
+               D.data_ptr(), exx.data_ptr(), exy.data_ptr(), eyy.data_ptr(), folded.data_ptr(), s)
+    ops = [z() for _ in range(6)]
+    st = mg.op_struct(ops, g.nx, g.ny, g.periodic_y)
     mg.mgk("mgk_assemble", C.byref(st), g.hx, g.hy, exx.data_ptr(), exy.data_ptr(), eyy.data_ptr(), s)
-    x = dev()
-    b = torch.randn((g.nyr, pitch), dtype=torch.float64, device="cuda")
+    dt = torch.float32 if f32 else torch.float64
+    if f32:
+        ops32 = [z(torch.float32) for _ in range(6)]
+        st32 = mg.op_struct(ops32, g.nx, g.ny, g.periodic_y, f32=True)
+        mg.mgk("mgk_op_to_f32", C.byref(st), C.byref(st32), s)
+        st, name = st32, "mgk_smooth_f32"
+    else:
+        name = "mgk_smooth_f64"
+    del D, exx, exy, eyy
+    x = z(dt)
+    b = torch.randn((g.nyr, pitch), dtype=torch.float64, device="cuda").to(dt)
     for _ in range(3):
-        mg.mgk("mgk_smooth_f64", C.byref(st), x.data_ptr(), b.data_ptr(), 1, 0, s)
+        mg.mgk(name, C.byref(st), x.data_ptr(), b.data_ptr(), 1, 0, s)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record()
     for _ in range(reps):
-        mg.mgk("mgk_smooth_f64", C.byref(st), x.data_ptr(), b.data_ptr(), 1, 0, s)
+        mg.mgk(name, C.byref(st), x.data_ptr(), b.data_ptr(), 1, 0, s)
     e1.record()
     torch.cuda.synchronize()
     per_launch_s = e0.elapsed_time(e1) * 1e-3 / (reps * 4)
+    kern = "k_gs_colour<float>" if f32 else "k_gs_colour<double>"
+    if f32:
+        bytes_per_launch = 32.0 * g.nx * g.nyr / 4  # a sweep's algorithmic bytes over its 4 launches
+        ach = bytes_per_launch / per_launch_s / 1e9
+        return {"bound": "hbm", "achieved": ach, "peak": HBM_PEAK_GBS, "unit": "GB/s",
+                "frac": ach / HBM_PEAK_GBS, "traffic": None, "kernel": kern,
+                "launch_us": per_launch_s * 1e6, "peak_source": "measured copy (MEASURED_PEAKS.json)"}
     flops_per_launch = g.unknowns / 4 * 18.0  # 8 FMA + subtract + scale per updated unknown
     achieved = flops_per_launch / per_launch_s / 1e12
     return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-            "kernel": "k_gs_colour<double>", "launch_us": per_launch_s * 1e6,
+            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": kern,
+            "launch_us": per_launch_s * 1e6,
             "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2.07 GHz (probe: 1.20 TFLOP/s at 1.99 GHz)"}
 
 
@@ -264,6 +307,7 @@ def run_ours(args):
     dist = dist_init(ws)
     torch.cuda.set_device(local)
     mg.lib()
+    _, precisions, outer, rtol, sample_builder = WORKLOADS[args.workload]
     inst = workload(args.workload)
     g = inst.grid
     U = g.unknowns
@@ -272,22 +316,28 @@ def run_ours(args):
     ctx.use_torch_stream()
     res = {}
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    dev = lambda a: torch.from_numpy(np.array(a, dtype=np.float64)).cuda()
-    xp_d, yp_d, eps_d, rho_d = dev(inst.map.xp), dev(inst.map.yp), dev(inst.eps_phys), dev(inst.rho_phys)
+    dev = lambda a: None if a is None else torch.from_numpy(np.array(a, dtype=np.float64)).cuda()
+    grid_map = inst.map.kind == "grid"
+    xp_d = dev(inst.map.xp) if grid_map else None
+    yp_d = dev(inst.map.yp) if grid_map else None
+    eps_d, rho_d, bc_d = dev(inst.eps_phys), dev(inst.rho_phys), dev(inst.bc)
     phi_d = torch.zeros(g.shape, dtype=torch.float64, device="cuda")
-    for prec in ("fp64", "mixed"):
-        opts = mg.make_opts(prec, "fcg", rtol=RTOL, max_iters=400)
+    n_in = 1 + (2 if grid_map else 0) + (1 if inst.eps_phys is not None else 0) + \
+        (1 if inst.bc is not None else 0)
+    for prec in precisions:
+        opts = mg.make_opts(prec, outer, rtol=rtol, max_iters=400)
         prob = mg.Problem(ctx, inst, opts, device_inputs=True)
 
         def step():
             mg.mg_update_transform(prob.h, g, inst.map, eps_d, xp_d, yp_d)
-            return mg.mg_solve(prob.h, rho_d, None, phi_d, opts)
+            return mg.mg_solve(prob.h, rho_d, bc_d, phi_d, opts)
 
         for _ in range(args.warmup):
             st = step()
         torch.cuda.synchronize()
         barrier(dist)
-        sampler = ClockSampler(local) if (prec == "fp64" and rank == 0) else None
+        headline = prec == precisions[0]
+        sampler = ClockSampler(local) if (headline and rank == 0) else None
         if sampler:
             sampler.start()
         times = []
@@ -303,54 +353,61 @@ def run_ours(args):
         clocks = sampler.stop() if sampler else None
         tot = allmax(dist, float(sum(times)))
         barrier(dist)
-        # end to end through the public API with host buffers (pinned)
-        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).pin_memory().numpy()
-        xp_h, yp_h, eps_h, rho_h = pin(inst.map.xp), pin(inst.map.yp), pin(inst.eps_phys), pin(inst.rho_phys)
+        # end to end through the public API with host (pinned) buffers
+        pin = lambda a: None if a is None else \
+            torch.from_numpy(np.array(a, dtype=np.float64)).pin_memory().numpy()
+        xp_h = pin(inst.map.xp) if grid_map else None
+        yp_h = pin(inst.map.yp) if grid_map else None
+        eps_h, rho_h, bc_h = pin(inst.eps_phys), pin(inst.rho_phys), pin(inst.bc)
         phi_h = torch.zeros(g.shape, dtype=torch.float64).pin_memory().numpy()
         e2e_steps = max(1, min(args.steps, 5))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
             mg.mg_update_transform(prob.h, g, inst.map, eps_h, xp_h, yp_h)
-            mg.mg_solve(prob.h, rho_h, None, phi_h, opts)
+            mg.mg_solve(prob.h, rho_h, bc_h, phi_h, opts)
         e2e_t = allmax(dist, time.perf_counter() - t0)
         res[prec] = {"tot": tot, "times": times, "stats": st, "clocks": clocks,
                      "e2e": ws * U * e2e_steps / e2e_t, "levels": len(prob.levels()),
                      "setup_ms": st.setup_ms, "solve_ms": st.solve_ms}
         prob.close()
-    roof = measure_smoother(mg, torch, inst) if rank == 0 else None
+    del flush
+    roof = measure_smoother(mg, torch, inst, precisions[0]) if rank == 0 else None
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         import oracle as O
         O.build()
-        dt, it = oracle_solve_seconds(inst)
-        cpu = {"value": U / dt, "unit": "unknowns/s", "cores": 1, "kind": "oracle",
-               "sample": f"one full {args.workload} solve (coefficients + PCG to rtol {RTOL}), 1 thread"}
+        sample = sample_builder()
+        dt, it = oracle_solve_seconds(sample, rtol)
+        cpu = {"value": sample.grid.unknowns / dt, "unit": "unknowns/s", "cores": 1, "kind": "oracle",
+               "sample": (f"one {sample.grid.nx}^2 solve of the {args.workload} recipe (coefficients + "
+                          f"MG-preconditioned CG to rtol {rtol}), 1 thread")}
     if rank == 0:
-        r64, rmx = res["fp64"], res["mixed"]
-        value = ws * U * args.steps / r64["tot"]
-        mixed_value = ws * U * args.steps / rmx["tot"]
+        h, others = precisions[0], precisions[1:]
+        rh = res[h]
+        value = ws * U * args.steps / rh["tot"]
         line = {
             "metric": METRIC, "value": value, "unit": "unknowns/s", "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * r64["tot"] / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
-            "config": {"workload": args.workload, "precision": "fp64", "outer": "fcg+vcycle(2,2)",
-                       "rtol": RTOL, "unknowns": U, "l2": "flushed between steps (512 MB write)",
+            "warmup": args.warmup, "ms_per_step": 1e3 * rh["tot"] / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if h == "fp64" else "f32 cycle in f64 refinement", "data": "synthetic",
+            "config": {"workload": args.workload, "precision": h, "outer": f"{outer}+vcycle(2,2)",
+                       "rtol": rtol, "unknowns": U, "l2": "flushed between steps (512 MB write)",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
-            "mixed": {"value": mixed_value, "ms_per_step": 1e3 * rmx["tot"] / args.steps,
-                      "iters": rmx["stats"].iters, "dtype": "f32 cycle in f64 refinement",
-                      "gpu_launches": args.steps * (rmx["stats"].kernel_launches
-                                                    + rmx["stats"].setup_kernel_launches),
-                      "e2e": rmx["e2e"], "solve_ms": rmx["solve_ms"], "setup_ms": rmx["setup_ms"]},
-            "iters": r64["stats"].iters, "levels": r64["levels"],
-            "setup_ms": r64["setup_ms"], "solve_ms": r64["solve_ms"],
-            "rel_residual": r64["stats"].rel_residual,
-            "e2e": {"value": r64["e2e"], "unit": "unknowns/s", "h2d_bytes_per_step": 4 * n * 8,
+            "iters": rh["stats"].iters, "levels": rh["levels"], "setup_ms": rh["setup_ms"],
+            "solve_ms": rh["solve_ms"], "rel_residual": rh["stats"].rel_residual,
+            "e2e": {"value": rh["e2e"], "unit": "unknowns/s", "h2d_bytes_per_step": n_in * n * 8,
                     "d2h_bytes_per_step": n * 8},
-            "gpu_launches": args.steps * (r64["stats"].kernel_launches + r64["stats"].setup_kernel_launches),
-            "roofline": roof, "cpu_baseline": cpu, "clocks": r64["clocks"],
+            "gpu_launches": args.steps * (rh["stats"].kernel_launches + rh["stats"].setup_kernel_launches),
+            "roofline": roof, "cpu_baseline": cpu, "clocks": rh["clocks"],
         }
+        for o in others:
+            ro = res[o]
+            line[o] = {"value": ws * U * args.steps / ro["tot"], "ms_per_step": 1e3 * ro["tot"] / args.steps,
+                       "iters": ro["stats"].iters, "e2e": ro["e2e"], "solve_ms": ro["solve_ms"],
+                       "setup_ms": ro["setup_ms"], "rel_residual": ro["stats"].rel_residual,
+                       "gpu_launches": args.steps * (ro["stats"].kernel_launches
+                                                     + ro["stats"].setup_kernel_launches)}
         print(json.dumps(line))
     ctx.close()
     return 0
@@ -362,7 +419,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="inclusion_1025", choices=["inclusion_1025", "sine_warp_129"])
+    ap.add_argument("--workload", default="inclusion_1025", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel-only", dest="kernel", default=None,
                     help="smooth64|smooth32|fused64|fused32|pipe64|pipe32|restrict64|restrict32|prolong64|prolong32")

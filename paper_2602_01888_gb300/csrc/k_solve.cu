@@ -15,6 +15,7 @@
 namespace mg {
 
 constexpr int kNT = 256;
+constexpr int kMaxVerifyFail = 4;
 
 #define NODE_LOOP(L)                                                            \
   for (int j = blockIdx.y; j < (L).nyr; j += gridDim.y)                         \
@@ -80,6 +81,7 @@ __global__ void __launch_bounds__(kNT) k_solve_init(Lvl<double> L, const SolveAr
     st->hist_n = 0;
     st->verify = 0;
     st->guard = 0;
+    st->verify_fail = 0;
     st->rtol = a->rtol;
     st->max_iters = a->max_iters;
     st->beta = 0.0;
@@ -402,8 +404,25 @@ __global__ void __launch_bounds__(kNT) k_fcg_verify(Lvl<double> L, const double*
       st->verify = 0;
       if (r32) st->inv_scale_r32 = 1.0 / sc;
       decide(st, rr, h, has_h, 0);
+      // the recursive residual keeps meeting rtol but the true one does not: the true
+      // residual has reached its rounding floor above rtol; stop (not converged)
+      if (!st->done && ++st->verify_fail >= kMaxVerifyFail) {
+        st->done = 1;
+        st->status = 6;
+        if (has_h) cudaGraphSetConditional(h, 0u);
+      }
     }
   }
+}
+
+// Batch epilogue: block k copies instance k's solve state and flags into contiguous arrays.
+__global__ void k_gather_states(SolveState* const* __restrict__ src, int* const* __restrict__ srcflags,
+                                SolveState* dst, int* dflags) {
+  const int k = blockIdx.x;
+  const unsigned long long* a = reinterpret_cast<const unsigned long long*>(src[k]);
+  unsigned long long* d = reinterpret_cast<unsigned long long*>(dst + k);
+  for (size_t w = threadIdx.x; w < sizeof(SolveState) / 8; w += blockDim.x) d[w] = a[w];
+  if (threadIdx.x < 4) dflags[4 * k + threadIdx.x] = srcflags[k][threadIdx.x];
 }
 
 // phi_out (caller layout) = x at every node.
@@ -505,6 +524,11 @@ cudaError_t launch_fcg_verify(const OpF64& A, const double* x, const double* b, 
                               cudaGraphConditionalHandle h, int has_h, cudaStream_t s) {
   const Lvl<double> L = lvl_of(A);
   k_fcg_verify<<<red_grid(L.nx, L.nyr), kNT, 0, s>>>(L, x, b, r, r32, p32, st, part, h, has_h);
+  CHK();
+}
+cudaError_t launch_gather_states(SolveState* const* src, int* const* srcflags, SolveState* dst,
+                                 int* dflags, int count, cudaStream_t s) {
+  k_gather_states<<<count, 128, 0, s>>>(src, srcflags, dst, dflags);
   CHK();
 }
 cudaError_t launch_copy_out(const OpF64& A, const double* x, const SolveArgs* a, cudaStream_t s) {

@@ -76,10 +76,13 @@ struct SolveState {
   int hist_n;
   int verify;         // recursive residual met rtol: recompute the true one next
   int guard;          // body passes; bounds the device-driven loop whatever happens
+  int verify_fail;    // true-residual checks that did not meet rtol
   long long n_unknowns;  // for the rms used by the FP32 scaling
   unsigned int ticket[8];  // arrival counters of the last-block reductions
   double hist[256];
 };
+
+static_assert(sizeof(SolveState) % 8 == 0, "SolveState is copied as 8-byte words");
 
 // ---- deterministic block reduction -------------------------------------------------
 // Sums v over the block in a fixed order (warp shuffle tree, then warps in order).

@@ -4,6 +4,7 @@
 
 #include <cstdint>
 #include <map>
+#include <string>
 #include <mutex>
 #include <unordered_map>
 #include <vector>
@@ -57,9 +58,28 @@ struct GraphEntry {
 
 }  // namespace mg
 
+namespace mg {
+// A captured batch: the graph over a fixed list of problems and its argument / state arrays.
+struct BatchEntry {
+  std::vector<mg_problem*> probs;
+  GraphEntry ge;
+  std::vector<int> fixed, body;  // kernel nodes per instance outside / inside its loop
+  SolveArgs* d_args = nullptr;
+  SolveArgs* h_args = nullptr;
+  SolveState* d_states = nullptr;
+  SolveState* h_states = nullptr;
+  int* d_flags = nullptr;
+  int* h_flags = nullptr;
+  SolveState** d_src = nullptr;
+  int** d_srcflags = nullptr;
+  std::vector<void*> allocs;
+};
+}  // namespace mg
+
 struct mg_ctx {
   int device = 0;
   mg::Pool pool;
+  std::map<std::string, mg::BatchEntry*> batches;
   cudaStream_t stream = nullptr, own_stream = nullptr, cap_stream = nullptr, cap_stream2 = nullptr;
   cudaStream_t batch[mg::kBatchStreams] = {};
 };
@@ -93,6 +113,15 @@ namespace mg {
 mg_status enqueue_solve(mg_problem* P, const mg_solve_opts& o, const double* rho, const double* bc,
                         const double* phi_in, double* phi_out, cudaStream_t s);
 mg_status finish_solve(mg_problem* P, mg_solve_stats* stats);
+mg_status finish_from(mg_problem* P, const SolveState& S, const int* flags, mg_solve_stats* stats,
+                      double solve_ms);
+mg_status build_batch_graph(mg_ctx* ctx, mg_problem* const* probs, int count, const mg_solve_opts& o,
+                            SolveArgs* d_args, SolveState* const* d_src, int* const* d_srcflags,
+                            SolveState* d_states, int* d_flags, GraphEntry* ge,
+                            std::vector<int>* fixed, std::vector<int>* body);
+void batch_cache_clear(mg_ctx* ctx);
+uint64_t graph_key(const mg_solve_opts& o);
+mg_status check_opts(const mg_problem* P, const mg_solve_opts& o);
 mg_status batch_solve_impl(mg_ctx* ctx, int count, mg_problem* const* probs,
                            const double* const* rho, const double* const* bc, double* const* phi,
                            mg_mem_kind mem, const mg_solve_opts& o, mg_solve_stats* stats);

@@ -51,6 +51,8 @@ cudaError_t launch_fcg_update(const OpF64& A, double* x, double* r, const double
 cudaError_t launch_fcg_verify(const OpF64& A, const double* x, const double* b, double* r,
                               float* r32, int p32, SolveState* st, double* part,
                               cudaGraphConditionalHandle h, int has_h, cudaStream_t s);
+cudaError_t launch_gather_states(SolveState* const* src, int* const* srcflags, SolveState* dst,
+                                 int* dflags, int count, cudaStream_t s);
 cudaError_t launch_copy_out(const OpF64& A, const double* x, const SolveArgs* a, cudaStream_t s);
 
 }  // namespace mg

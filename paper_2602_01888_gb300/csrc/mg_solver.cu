@@ -185,6 +185,7 @@ extern "C" void mg_destroy(mg_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);
   cudaDeviceSynchronize();
+  batch_cache_clear(c);
   for (int k = 0; k < kBatchStreams; ++k) cudaStreamDestroy(c->batch[k]);
   cudaStreamDestroy(c->own_stream);
   cudaStreamDestroy(c->cap_stream);
@@ -427,6 +428,7 @@ extern "C" void mg_problem_free(mg_problem* P) {
   if (!P) return;
   cudaSetDevice(P->ctx->device);
   cudaStreamSynchronize(P->ctx->stream);
+  batch_cache_clear(P->ctx);  // captured batches reference the problem's arrays
   problem_release(P);
   delete P;
 }
@@ -525,7 +527,7 @@ static mg_status emit_body(mg_problem* P, const mg_solve_opts& o, cudaGraphCondi
   return MG_OK;
 }
 
-static uint64_t graph_key(const mg_solve_opts& o) {
+uint64_t graph_key(const mg_solve_opts& o) {
   uint64_t k = (uint64_t)o.precision | ((uint64_t)o.outer << 2) | ((uint64_t)o.smoother << 4) |
                ((uint64_t)(o.nu1 & 255) << 8) | ((uint64_t)(o.nu2 & 255) << 16);
   uint64_t w;
@@ -536,85 +538,81 @@ static uint64_t graph_key(const mg_solve_opts& o) {
   return k ^ (w << 24);
 }
 
-// Whole solve as one graph: init -> initial residual (sets the condition) ->
-// WHILE(condition){ one outer iteration; the last kernel re-sets the condition } -> copy out.
-static mg_status build_graph(mg_problem* P, const mg_solve_opts& o, GraphEntry* ge) {
-  cudaStream_t cs = P->ctx->cap_stream, cs2 = P->ctx->cap_stream2;
+// One solve captured into the graph g that stream cs is capturing: init -> initial
+// residual (sets the condition) -> WHILE(condition){ one outer iteration; the last kernel
+// re-sets the condition } -> copy out.  `args` is the device argument block the kernels
+// read; the loop body is captured on cs2.  Counts the kernel nodes it adds.
+static mg_status capture_solve_chain(mg_problem* P, const mg_solve_opts& o, SolveArgs* args,
+                                     cudaStream_t cs, cudaStream_t cs2, cudaGraph_t g,
+                                     int* fixed_kernels, int* body_kernels) {
   LevelMem& F = P->lev[0];
   const bool fcg = (o.outer == MG_OUTER_FCG);
-  CU(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-  cudaGraph_t g = nullptr;
+  const bool r32 = fcg && o.precision == MG_PREC_MIXED;
   cudaStreamCaptureStatus cst;
   const cudaGraphNode_t* deps = nullptr;
   size_t ndeps = 0;
-  mg_status st = MG_OK;
-  int body_kernel_count = 0;
   cudaGraphConditionalHandle h = 0;
-  do {
-    if (cudaStreamGetCaptureInfo(cs, &cst, nullptr, &g, nullptr, nullptr, nullptr) != cudaSuccess) {
-      st = set_error(MG_ERR_CUDA, "capture info failed");
-      break;
+  if (cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) != cudaSuccess)
+    return set_error(MG_ERR_CUDA, "conditional handle creation failed");
+  if (launch_solve_init(F.A, args, P->D, F.x, F.b, P->st, cs) != cudaSuccess ||
+      launch_resid_init(F.A, F.x, F.b, fcg ? P->r : nullptr, P->st, P->part, h, 1, cs) !=
+          cudaSuccess ||
+      (r32 && launch_r_to_f32(F.A, P->r, F.b32, F.A32.pitch, P->st, cs) != cudaSuccess))
+    return set_error(MG_ERR_CUDA, "capture of solve init failed");
+  *fixed_kernels = 3 + (r32 ? 1 : 0);
+  if (cudaStreamGetCaptureInfo(cs, &cst, nullptr, nullptr, &deps, nullptr, &ndeps) != cudaSuccess)
+    return set_error(MG_ERR_CUDA, "capture info failed");
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cnode;
+  if (cudaGraphAddNode(&cnode, g, deps, nullptr, ndeps, &cp) != cudaSuccess)
+    return set_error(MG_ERR_CUDA, "adding the WHILE node failed");
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  if (cudaStreamUpdateCaptureDependencies(cs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies) !=
+      cudaSuccess)
+    return set_error(MG_ERR_CUDA, "capture dependency update failed");
+  if (cudaStreamBeginCaptureToGraph(cs2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+      cudaSuccess)
+    return set_error(MG_ERR_CUDA, "body capture failed to start");
+  mg_status st = emit_body(P, o, h, 1, cs2);
+  if (!st && launch_loop_guard(P->st, h, cs2) != cudaSuccess)
+    st = set_error(MG_ERR_CUDA, "capture of the loop guard failed");
+  cudaGraph_t body_out = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(cs2, &body_out);
+  if (!st && e2 != cudaSuccess)
+    st = set_error(MG_ERR_CUDA, "body capture failed: %s", cudaGetErrorString(e2));
+  if (st) return st;
+  *body_kernels = 0;
+  {
+    size_t n = 0;
+    cudaGraphGetNodes(body, nullptr, &n);
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (n) cudaGraphGetNodes(body, nodes.data(), &n);
+    for (size_t q = 0; q < n; ++q) {
+      cudaGraphNodeType t;
+      if (cudaGraphNodeGetType(nodes[q], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel)
+        ++*body_kernels;
     }
-    if (cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
-      st = set_error(MG_ERR_CUDA, "conditional handle creation failed");
-      break;
-    }
-    if (launch_solve_init(F.A, P->args, P->D, F.x, F.b, P->st, cs) != cudaSuccess ||
-        launch_resid_init(F.A, F.x, F.b, fcg ? P->r : nullptr, P->st, P->part, h, 1, cs) !=
-            cudaSuccess ||
-        (fcg && o.precision == MG_PREC_MIXED &&
-         launch_r_to_f32(F.A, P->r, F.b32, F.A32.pitch, P->st, cs) != cudaSuccess)) {
-      st = set_error(MG_ERR_CUDA, "capture of solve init failed");
-      break;
-    }
-    if (cudaStreamGetCaptureInfo(cs, &cst, nullptr, nullptr, &deps, nullptr, &ndeps) != cudaSuccess) {
-      st = set_error(MG_ERR_CUDA, "capture info failed");
-      break;
-    }
-    cudaGraphNodeParams cp = {};
-    cp.type = cudaGraphNodeTypeConditional;
-    cp.conditional.handle = h;
-    cp.conditional.type = cudaGraphCondTypeWhile;
-    cp.conditional.size = 1;
-    cudaGraphNode_t cnode;
-    if (cudaGraphAddNode(&cnode, g, deps, nullptr, ndeps, &cp) != cudaSuccess) {
-      st = set_error(MG_ERR_CUDA, "adding the WHILE node failed");
-      break;
-    }
-    cudaGraph_t body = cp.conditional.phGraph_out[0];
-    if (cudaStreamUpdateCaptureDependencies(cs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies) !=
-        cudaSuccess) {
-      st = set_error(MG_ERR_CUDA, "capture dependency update failed");
-      break;
-    }
-    if (cudaStreamBeginCaptureToGraph(cs2, body, nullptr, nullptr, 0,
-                                      cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-      st = set_error(MG_ERR_CUDA, "body capture failed to start");
-      break;
-    }
-    st = emit_body(P, o, h, 1, cs2);
-    if (!st && launch_loop_guard(P->st, h, cs2) != cudaSuccess)
-      st = set_error(MG_ERR_CUDA, "capture of the loop guard failed");
-    cudaGraph_t body_out = nullptr;
-    cudaError_t e2 = cudaStreamEndCapture(cs2, &body_out);
-    if (!st && e2 != cudaSuccess) st = set_error(MG_ERR_CUDA, "body capture failed: %s", cudaGetErrorString(e2));
-    if (st) break;
-    {
-      size_t n = 0;
-      cudaGraphGetNodes(body, nullptr, &n);
-      std::vector<cudaGraphNode_t> nodes(n);
-      if (n) cudaGraphGetNodes(body, nodes.data(), &n);
-      for (size_t q = 0; q < n; ++q) {
-        cudaGraphNodeType t;
-        if (cudaGraphNodeGetType(nodes[q], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel)
-          ++body_kernel_count;
-      }
-    }
-    if (launch_copy_out(F.A, F.x, P->args, cs) != cudaSuccess) {
-      st = set_error(MG_ERR_CUDA, "capture of copy-out failed");
-      break;
-    }
-  } while (0);
+  }
+  if (launch_copy_out(F.A, F.x, args, cs) != cudaSuccess)
+    return set_error(MG_ERR_CUDA, "capture of copy-out failed");
+  *fixed_kernels += 1;
+  return MG_OK;
+}
+
+static mg_status build_graph(mg_problem* P, const mg_solve_opts& o, GraphEntry* ge) {
+  cudaStream_t cs = P->ctx->cap_stream, cs2 = P->ctx->cap_stream2;
+  CU(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  cudaGraph_t g = nullptr;
+  cudaStreamCaptureStatus cst;
+  mg_status st = MG_OK;
+  int fixed = 0, body = 0;
+  if (cudaStreamGetCaptureInfo(cs, &cst, nullptr, &g, nullptr, nullptr, nullptr) != cudaSuccess)
+    st = set_error(MG_ERR_CUDA, "capture info failed");
+  if (!st) st = capture_solve_chain(P, o, P->args, cs, cs2, g, &fixed, &body);
   cudaGraph_t gout = nullptr;
   cudaError_t e = cudaStreamEndCapture(cs, &gout);
   if (st) {
@@ -623,20 +621,8 @@ static mg_status build_graph(mg_problem* P, const mg_solve_opts& o, GraphEntry* 
     return st;
   }
   if (e != cudaSuccess) return set_error(MG_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
-  auto kernel_nodes = [](cudaGraph_t g) {
-    size_t n = 0;
-    cudaGraphGetNodes(g, nullptr, &n);
-    std::vector<cudaGraphNode_t> nodes(n);
-    if (n) cudaGraphGetNodes(g, nodes.data(), &n);
-    int k = 0;
-    for (size_t q = 0; q < n; ++q) {
-      cudaGraphNodeType t;
-      if (cudaGraphNodeGetType(nodes[q], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
-    }
-    return k;
-  };
-  ge->fixed_kernels = kernel_nodes(gout);
-  ge->body_kernels = body_kernel_count;
+  ge->fixed_kernels = fixed;
+  ge->body_kernels = body;
   cudaGraphExec_t ex;
   e = cudaGraphInstantiate(&ex, gout, 0);
   if (e != cudaSuccess) {
@@ -648,7 +634,80 @@ static mg_status build_graph(mg_problem* P, const mg_solve_opts& o, GraphEntry* 
   return MG_OK;
 }
 
-static mg_status check_opts(const mg_problem* P, const mg_solve_opts& o) {
+// The whole batch as one graph: an empty root node, then for every instance its own
+// solve chain as an independent branch (they run concurrently), then one kernel that
+// gathers every instance's solve state and flags into contiguous arrays.
+mg_status build_batch_graph(mg_ctx* ctx, mg_problem* const* probs, int count, const mg_solve_opts& o,
+                            SolveArgs* d_args, SolveState* const* d_src, int* const* d_srcflags,
+                            SolveState* d_states, int* d_flags, GraphEntry* ge,
+                            std::vector<int>* fixed, std::vector<int>* body) {
+  cudaStream_t cs = ctx->cap_stream, cs2 = ctx->cap_stream2;
+  CU(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  cudaGraph_t g = nullptr;
+  cudaStreamCaptureStatus cst;
+  mg_status st = MG_OK;
+  std::vector<cudaGraphNode_t> leaves;
+  fixed->assign(count, 0);
+  body->assign(count, 0);
+  do {
+    if (cudaStreamGetCaptureInfo(cs, &cst, nullptr, &g, nullptr, nullptr, nullptr) != cudaSuccess) {
+      st = set_error(MG_ERR_CUDA, "capture info failed");
+      break;
+    }
+    cudaGraphNode_t root;
+    cudaGraphNodeParams ep = {};
+    ep.type = cudaGraphNodeTypeEmpty;
+    if (cudaGraphAddNode(&root, g, nullptr, nullptr, 0, &ep) != cudaSuccess) {
+      st = set_error(MG_ERR_CUDA, "adding the batch root node failed");
+      break;
+    }
+    for (int k = 0; k < count && !st; ++k) {
+      if (cudaStreamUpdateCaptureDependencies(cs, &root, nullptr, 1, cudaStreamSetCaptureDependencies) !=
+          cudaSuccess) {
+        st = set_error(MG_ERR_CUDA, "capture dependency update failed");
+        break;
+      }
+      st = capture_solve_chain(probs[k], o, d_args + k, cs, cs2, g, &(*fixed)[k], &(*body)[k]);
+      if (st) break;
+      const cudaGraphNode_t* deps = nullptr;
+      size_t nd = 0;
+      if (cudaStreamGetCaptureInfo(cs, &cst, nullptr, nullptr, &deps, nullptr, &nd) != cudaSuccess) {
+        st = set_error(MG_ERR_CUDA, "capture info failed");
+        break;
+      }
+      for (size_t q = 0; q < nd; ++q) leaves.push_back(deps[q]);
+    }
+    if (st) break;
+    if (cudaStreamUpdateCaptureDependencies(cs, leaves.data(), nullptr, leaves.size(),
+                                            cudaStreamSetCaptureDependencies) != cudaSuccess) {
+      st = set_error(MG_ERR_CUDA, "capture join failed");
+      break;
+    }
+    if (launch_gather_states(d_src, d_srcflags, d_states, d_flags, count, cs) != cudaSuccess) {
+      st = set_error(MG_ERR_CUDA, "capture of the state gather failed");
+      break;
+    }
+  } while (0);
+  cudaGraph_t gout = nullptr;
+  cudaError_t e = cudaStreamEndCapture(cs, &gout);
+  if (st) {
+    if (gout) cudaGraphDestroy(gout);
+    cudaGetLastError();
+    return st;
+  }
+  if (e != cudaSuccess) return set_error(MG_ERR_CUDA, "batch graph capture failed: %s", cudaGetErrorString(e));
+  cudaGraphExec_t ex;
+  e = cudaGraphInstantiate(&ex, gout, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(gout);
+    return set_error(MG_ERR_CUDA, "batch graph instantiation failed: %s", cudaGetErrorString(e));
+  }
+  ge->graph = gout;
+  ge->exec = ex;
+  return MG_OK;
+}
+
+mg_status check_opts(const mg_problem* P, const mg_solve_opts& o) {
   if (o.precision != MG_PREC_FP64 && o.precision != MG_PREC_MIXED)
     return set_error(MG_ERR_ARG, "bad precision %d", o.precision);
   if ((o.precision == MG_PREC_MIXED) != (P->mixed != 0))
@@ -739,18 +798,27 @@ mg_status enqueue_solve(mg_problem* P, const mg_solve_opts& o, const double* rho
 }
 
 mg_status finish_solve(mg_problem* P, mg_solve_stats* stats) {
-  const SolveState& S = *P->h_state;
-  if (P->h_flags[2])
-    return set_error(MG_ERR_TIMEOUT, "a bounded wait inside a smoothing kernel gave up");
+  return finish_from(P, *P->h_state, P->h_flags, stats, -1.0);
+}
+
+// Stats and status of a finished solve from its copied-back state; solve_ms < 0: time it
+// from the problem's own events.
+mg_status finish_from(mg_problem* P, const SolveState& S, const int* flags, mg_solve_stats* stats,
+                      double solve_ms) {
+  if (flags[2]) return set_error(MG_ERR_TIMEOUT, "a bounded wait inside a smoothing kernel gave up");
   if (stats) {
     memset(stats, 0, sizeof(*stats));
     stats->iters = S.it;
     stats->levels = P->nlev;
     stats->rel_residual = S.rel;
     stats->setup_ms = P->setup_ms;
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, P->ev0, P->ev1);
-    stats->solve_ms = ms;
+    if (solve_ms < 0) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, P->ev0, P->ev1);
+      stats->solve_ms = ms;
+    } else {
+      stats->solve_ms = solve_ms;
+    }
     const int n = std::min(S.hist_n, MG_HIST_MAX);
     for (int k = 0; k < n; ++k) stats->hist[k] = S.hist[k];
     stats->kernel_launches = P->last_fixed_kernels + S.guard * P->last_body_kernels;

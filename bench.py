@@ -413,13 +413,289 @@ def run_ours(args):
     return 0
 
 
+# ------------------------------------------------------------------ batched workload
+BATCH_COUNT = 512
+BATCH_RTOL = 1e-9  # oracle check on the largest-ratio instances of each size: error <= 1e-10
+
+
+def _d64(torch, a):
+    return None if a is None else torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def run_batch(args):
+    """512 independent inclusion instances (sides uniform over {65,129,257,513}, radius
+    U[0.1,0.35], eps' ratio U[1,50], 16 blobs each).  One step = the coefficient build and
+    hierarchy of every instance (one mg_batch_update_transform) + one mg_batch_solve of all 512 (one
+    graph launch).  Reported for the mixed path (headline), the FP64 path, and the plain FP64
+    solver run instance by instance (mg_update_transform + mg_solve per instance)."""
+    ws, rank, local = dist_env()
+    specs = I.config4_specs(BATCH_COUNT, seed0=4000 + BATCH_COUNT * rank)
+    I.prefetch_inclusion_grids([(n, r) for n, r, _, _ in specs])  # spawn pool, before CUDA
+    import torch
+    from paper_2602_01888_gb300 import mg
+
+    dist = dist_init(ws)
+    torch.cuda.set_device(local)
+    mg.lib()
+    insts = [I.inclusion_instance(n, r, e, sd) for n, r, e, sd in specs]
+    U = sum(x.grid.unknowns for x in insts)
+    nodes = sum(x.grid.nx * x.grid.nyr for x in insts)
+    ctx = mg.Context(local)
+    ctx.use_torch_stream()
+    dev = [dict(xp=_d64(torch, x.map.xp), yp=_d64(torch, x.map.yp), eps=_d64(torch, x.eps_phys),
+                rho=_d64(torch, x.rho_phys), phi=torch.zeros(x.grid.shape, dtype=torch.float64, device="cuda"))
+           for x in insts]
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    res = {}
+    for prec in ("mixed", "fp64"):
+        opts = mg.make_opts(prec, "fcg", rtol=BATCH_RTOL, max_iters=400)
+        probs = [mg.Problem(ctx, x, opts, device_inputs=True) for x in insts]
+        hs = [p.h for p in probs]
+        rhos = [d["rho"] for d in dev]
+        phis = [d["phi"] for d in dev]
+
+        maps = [x.map for x in insts]
+        eps_l, xp_l, yp_l = ([d[k] for d in dev] for k in ("eps", "xp", "yp"))
+
+        def setup_all():
+            mg.mg_batch_update_transform(ctx.h, hs, maps, eps_l, xp_l, yp_l)
+
+        def step():
+            setup_all()
+            return mg.mg_batch_solve(ctx.h, hs, rhos, None, phis, opts)
+
+        for _ in range(args.warmup):
+            stats = step()
+        torch.cuda.synchronize()
+        barrier(dist)
+        sampler = ClockSampler(local) if (prec == "mixed" and rank == 0) else None
+        if sampler:
+            sampler.start()
+        times, solve_t = [], []
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            torch.cuda.synchronize()
+            e0.record()
+            setup_all()
+            e1.record()
+            stats = mg.mg_batch_solve(ctx.h, hs, rhos, None, phis, opts)
+            e2.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e2) * 1e-3)
+            solve_t.append(e1.elapsed_time(e2) * 1e-3)
+        clocks = sampler.stop() if sampler else None
+        tot = allmax(dist, float(sum(times)))
+        r = {"tot": tot, "solve": allmax(dist, float(sum(solve_t))), "clocks": clocks,
+             "iters": [s.iters for s in stats], "rel": max(s.rel_residual for s in stats),
+             "launches": sum(s.kernel_launches + s.setup_kernel_launches for s in stats)}
+        # the plain solver, one instance after another (same resident problems)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for p, x, d in zip(probs, insts, dev):
+            mg.mg_update_transform(p.h, x.grid, x.map, d["eps"], d["xp"], d["yp"])
+            mg.mg_solve(p.h, d["rho"], None, d["phi"], opts)
+        e1.record()
+        torch.cuda.synchronize()
+        r["sequential_s"] = allmax(dist, e0.elapsed_time(e1) * 1e-3)
+        if prec == "mixed":
+            # end to end with host buffers: inputs read from pinned host memory, results written back
+            pin = lambda a: None if a is None else \
+                torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).pin_memory().numpy()
+            host = [dict(xp=pin(x.map.xp), yp=pin(x.map.yp), eps=pin(x.eps_phys), rho=pin(x.rho_phys),
+                         phi=torch.zeros(x.grid.shape, dtype=torch.float64).pin_memory().numpy())
+                    for x in insts]
+            e2e_steps = max(1, min(args.steps, 3))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(e2e_steps):
+                mg.mg_batch_update_transform(ctx.h, hs, maps, [h["eps"] for h in host],
+                                             [h["xp"] for h in host], [h["yp"] for h in host])
+                mg.mg_batch_solve(ctx.h, hs, [h["rho"] for h in host], None, [h["phi"] for h in host], opts)
+            r["e2e"] = ws * U * e2e_steps / allmax(dist, time.perf_counter() - t0)
+            del host
+        res[prec] = r
+        for p in probs:
+            p.close()
+    del flush
+    roof = None
+    if rank == 0:
+        big = max(insts, key=lambda x: x.grid.nx)
+        roof = measure_smoother(mg, torch, big, "mixed")
+        roof["note"] = f"k_gs_colour<float> on one {big.grid.nx}^2 instance (L2-resident at this size)"
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle as O
+        O.build()
+        sample = [x for x in insts if x.grid.nx == 257][:2]
+        t = 0.0
+        for x in sample:
+            dt, _ = oracle_solve_seconds(x, BATCH_RTOL)
+            t += dt
+        cpu = {"value": sum(x.grid.unknowns for x in sample) / t, "unit": "unknowns/s", "cores": 1,
+               "kind": "oracle", "sample": f"{len(sample)} of the 257^2 instances solved one by one "
+                                           f"(coefficients + MG-preconditioned CG to rtol {BATCH_RTOL}), 1 thread"}
+    if rank == 0:
+        rm, rf = res["mixed"], res["fp64"]
+        line = {
+            "metric": METRIC, "value": ws * U * args.steps / rm["tot"], "unit": "unknowns/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * rm["tot"] / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 cycle in f64 refinement", "data": "synthetic",
+            "config": {"workload": "batch512", "instances": BATCH_COUNT, "sides": [65, 129, 257, 513],
+                       "precision": "mixed", "outer": "fcg+vcycle(2,2)", "rtol": BATCH_RTOL, "unknowns": U,
+                       "l2": "flushed between steps (512 MB write)",
+                       "parallelism": f"{BATCH_COUNT} instances per GPU x{ws}" if ws > 1 else "1 GPU"},
+            "solve_ms": 1e3 * rm["solve"] / args.steps,
+            "iters": {"min": min(rm["iters"]), "max": max(rm["iters"]), "mean": float(np.mean(rm["iters"]))},
+            "rel_residual_max": rm["rel"],
+            "fp64_batched": {"value": ws * U * args.steps / rf["tot"], "ms_per_step": 1e3 * rf["tot"] / args.steps,
+                             "solve_ms": 1e3 * rf["solve"] / args.steps, "iters_max": max(rf["iters"])},
+            "fp64_sequential": {"value": ws * U / rf["sequential_s"], "ms_per_step": 1e3 * rf["sequential_s"]},
+            "mixed_sequential": {"value": ws * U / rm["sequential_s"], "ms_per_step": 1e3 * rm["sequential_s"]},
+            "e2e": {"value": rm["e2e"], "unit": "unknowns/s", "h2d_bytes_per_step": 4 * 8 * nodes,
+                    "d2h_bytes_per_step": 8 * nodes},
+            "gpu_launches": args.steps * rm["launches"],
+            "roofline": roof, "cpu_baseline": cpu, "clocks": rm["clocks"],
+        }
+        print(json.dumps(line))
+    ctx.close()
+    return 0
+
+
+# ------------------------------------------------------------------ serving workload
+SERVE_RTOL = 5e-10
+
+
+def _serve_requests(stream):
+    """(arrival, grid, map, rho, eps, unknowns) per request; sources come from the
+    pre-drawn cache, eps' from the request's own ratio."""
+    out = []
+    for t, n, r, ratio, seed in stream:
+        xp, yp, i0, rs = I.inclusion_grid(n, r)
+        out.append((t, I.Grid(n, n), I.MapSpec("grid", (), xp, yp), I.cached_source(n, i0, seed),
+                    (n, i0, ratio), (n - 2) ** 2))
+    return out
+
+
+def _serve_pass(mg, ctx, reqs, arrivals, inflight, mem_budget):
+    """Submit reqs at the given arrival offsets (None: all at once), collect every result,
+    return the server's report and the client-side wall time."""
+    import collections
+    srv = mg.mg_server_start(ctx.h, max_inflight=inflight, mem_budget=mem_budget)
+    tickets = collections.deque()
+
+    def collect(tk):
+        st, _ = mg.mg_serve_poll(srv, tk, 600_000, None)
+        if st:
+            raise RuntimeError(f"mg_serve_poll: status {st}: {mg.mg_last_error()}")
+
+    eps_cache = {}
+    opts = mg.make_opts("mixed", "fcg", rtol=SERVE_RTOL, max_iters=400)
+    t0 = time.perf_counter()
+    for k, (_, grid, mp, rho, epsk, _) in enumerate(reqs):
+        if arrivals is not None:
+            dt = arrivals[k] - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+        eps = eps_cache.get(epsk)
+        if eps is None:
+            eps = I.inclusion_eps(epsk[0], epsk[1], epsk[2])
+            if len(eps_cache) < 64:
+                eps_cache[epsk] = eps
+        while True:
+            st, tk = mg.mg_serve_submit(srv, grid, mp, rho, eps_phys=eps, opts=opts)
+            if st != mg.MG_ERR_BUSY or not tickets:
+                break
+            collect(tickets.popleft())  # staging full: take the oldest result first
+        if st:
+            raise RuntimeError(f"mg_serve_submit: status {st}: {mg.mg_last_error()}")
+        tickets.append(tk)
+    while tickets:
+        collect(tickets.popleft())
+    wall = time.perf_counter() - t0
+    rep = mg.mg_server_stop(srv)
+    return rep, wall
+
+
+def run_serve(args):
+    """Poisson-arrival request stream (sides log-uniform in [129, 2049] snapped to m 2^k + 1,
+    inclusion geometry from a catalogue of radii, eps' ratio U[1,50]), solved by the
+    library's request server.  First a saturation pass (every request submitted at once)
+    measures throughput; then open-loop passes at fractions of that rate measure p50/p99
+    submit-to-result latency."""
+    ws, rank, local = dist_env()
+    count = args.requests
+    stream = I.config5_stream(count, seed=5 + 1000 * rank, rate=1.0, side_range=(129, args.serve_max_side))
+    warm_stream = I.config5_stream(min(64, count), seed=99, rate=1.0, side_range=(129, 513))
+    I.prefetch_inclusion_grids([(n, r) for _, n, r, _, _ in stream + warm_stream], sources=2, seed=5)
+    import torch
+    from paper_2602_01888_gb300 import mg
+
+    dist = dist_init(ws)
+    torch.cuda.set_device(local)
+    mg.lib()
+    ctx = mg.Context(local)
+    reqs = _serve_requests(stream)
+    U = sum(q[5] for q in reqs)
+    warm = _serve_requests(warm_stream)
+    _serve_pass(mg, ctx, warm, None, args.inflight, 0)
+    barrier(dist)
+    sampler = ClockSampler(local) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    rep, wall = _serve_pass(mg, ctx, reqs, None, args.inflight, 0)
+    clocks = sampler.stop() if sampler else None
+    wall = allmax(dist, wall)
+    sat_rps = count / wall
+    lat = []
+    base = np.array([q[0] for q in stream])
+    for frac in args.serve_loads:
+        rate = frac * sat_rps
+        arr = base / rate  # the same exponential gaps rescaled to the target rate
+        r2, w2 = _serve_pass(mg, ctx, reqs, arr, args.inflight, 0)
+        lat.append({"load": frac, "rate_rps": rate, "p50_ms": r2.p50_ms, "p99_ms": r2.p99_ms,
+                    "max_ms": r2.max_ms, "unknowns_per_s": U / w2, "completed": r2.completed,
+                    "failed": r2.failed, "mean_inflight": r2.mean_batch, "reused": r2.reused,
+                    "evicted": r2.evicted})
+    if rank == 0:
+        bytes_in = sum(8 * q[1].nx * q[1].nyr * 4 for q in reqs)
+        bytes_out = sum(8 * q[1].nx * q[1].nyr for q in reqs)
+        line = {
+            "metric": METRIC, "value": ws * U / wall, "unit": "unknowns/s", "n_gpus": ws, "steps": 1,
+            "warmup": 1, "ms_per_step": 1e3 * wall, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 cycle in f64 refinement", "data": "synthetic",
+            "config": {"workload": "serve", "requests": count,
+                       "sides": f"log-uniform [129,{args.serve_max_side}] snapped to m*2^k+1",
+                       "radii": list(I.SERVE_RADII), "rtol": SERVE_RTOL, "inflight_slots": args.inflight,
+                       "unknowns": U, "l2": "inputs of consecutive requests exceed L2 in aggregate"},
+            "saturated": {"requests_per_s": sat_rps, "p50_ms": rep.p50_ms, "p99_ms": rep.p99_ms,
+                          "completed": rep.completed, "failed": rep.failed, "mean_inflight": rep.mean_batch,
+                          "reused": rep.reused, "evicted": rep.evicted},
+            "latency": lat,
+            "e2e": {"value": ws * U / wall, "unit": "unknowns/s", "h2d_bytes_per_step": bytes_in,
+                    "d2h_bytes_per_step": bytes_out},
+            "gpu_launches": None, "roofline": None, "cpu_baseline": None, "clocks": clocks,
+        }
+        print(json.dumps(line))
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="inclusion_1025", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="inclusion_1025",
+                    choices=sorted(WORKLOADS) + ["batch512", "serve"])
+    ap.add_argument("--requests", type=int, default=2000, help="serve: requests per pass")
+    ap.add_argument("--inflight", type=int, default=16, help="serve: concurrent request slots")
+    ap.add_argument("--serve-max-side", type=int, default=2049, help="serve: largest grid side")
+    ap.add_argument("--serve-loads", type=float, nargs="*", default=[0.5, 0.8, 0.95],
+                    help="serve: open-loop arrival rates as fractions of the saturated rate")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel-only", dest="kernel", default=None,
                     help="smooth64|smooth32|fused64|fused32|pipe64|pipe32|restrict64|restrict32|prolong64|prolong32")
@@ -432,6 +708,10 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch512":
+        return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_ours(args)
 
 

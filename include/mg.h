@@ -152,6 +152,19 @@ mg_status mg_setup_transform(mg_ctx *ctx, const mg_grid_desc *grid, const mg_map
  * same grid (no allocation).  Same errors as mg_setup_transform. */
 mg_status mg_update_transform(mg_problem *prob, const mg_map_desc *map, const double *eps_phys,
                               mg_mem_kind mem);
+/*
+ * mg_update_transform for `count` problems of one context with a single synchronisation:
+ * the coefficient builds of different problems run concurrently on the context's batch
+ * streams.  maps / eps_phys (nullable array; its entries nullable) are indexed like probs;
+ * every array has the memory kind `mem`.  statuses (nullable, count entries) receives each
+ * instance's outcome (MG_OK, MG_ERR_MAP_FOLDED, MG_ERR_NOT_SPD, ...); the return value is
+ * MG_OK or the first failing instance's status.  Argument errors (NULL problem, a problem of
+ * another context, a map that does not fit its grid) are detected before any work starts.
+ * This entry point has no counterpart in the paper: it batches the per-problem setup.
+ */
+mg_status mg_batch_update_transform(mg_ctx *ctx, int count, mg_problem *const *probs,
+                                    const mg_map_desc *maps, const double *const *eps_phys,
+                                    mg_mem_kind mem, mg_status *statuses);
 void mg_problem_free(mg_problem *prob);
 /* Levels and per-level sizes (nx_out/ny_out: arrays of at least 24 ints, nullable). */
 mg_status mg_problem_info(const mg_problem *prob, int *levels, int *nx_out, int *ny_out);
@@ -184,9 +197,12 @@ typedef struct {
   int max_inflight;       /* requests resident on the device at once */
   int queue_capacity;     /* pending requests; beyond it mg_serve_submit returns MG_ERR_BUSY */
   size_t mem_budget;      /* device bytes for resident hierarchies (0 = the context's budget) */
+  size_t host_budget;     /* page-locked host bytes for the arrays of submitted, not yet polled
+                             requests (0 = 8 GiB); when full, mg_serve_submit returns MG_ERR_BUSY */
 } mg_server_opts;
 
-/* A request: everything is copied in at submit time (host memory). */
+/* A request: everything is copied in at submit time (host memory), into page-locked
+ * buffers owned by the server until the ticket is polled. */
 typedef struct {
   mg_grid_desc grid;
   mg_map_desc map;          /* xp/yp host arrays for MG_MAP_GRID */
@@ -200,8 +216,10 @@ typedef struct {
   uint64_t completed, failed;
   double wall_s, unknowns_per_s;
   double p50_ms, p99_ms, max_ms;  /* submit -> result latency */
-  double mean_batch;              /* mean requests advanced per device tick */
+  double mean_batch;              /* mean requests in flight per scheduler tick */
   int ticks;
+  uint64_t reused;                /* requests served by an already resident hierarchy */
+  uint64_t evicted;               /* idle hierarchies freed to make room */
 } mg_serve_report;
 
 mg_status mg_server_start(mg_ctx *ctx, const mg_server_opts *opts, mg_server **out);

@@ -28,6 +28,7 @@ class Pool {
   size_t used() const { return used_; }
   ~Pool();
   size_t budget_ = 0;
+  bool pinned_ = false;  // slabs of page-locked host memory instead of device memory
 
  private:
   struct Slab {
@@ -101,7 +102,8 @@ struct mg_problem {
   mg::SolveArgs* h_args = nullptr;
   mg::SolveState* h_state = nullptr;
   int* h_flags = nullptr;  // folded, coarse status, kernel wait timeout
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;    // around the last solve
+  cudaEvent_t evb0 = nullptr, evb1 = nullptr;  // around the last coefficient build
   double setup_ms = 0.0;
   int setup_kernels = 0;
   int last_fixed_kernels = 0, last_body_kernels = 0;
@@ -110,6 +112,12 @@ struct mg_problem {
 };
 
 namespace mg {
+mg_status problem_create(mg_ctx* ctx, const mg_grid_desc* grid, const mg_solve_opts& o,
+                         mg_problem** out);
+mg_status check_map(const mg_grid_desc* g, const mg_map_desc* m);
+mg_status problem_enqueue_build(mg_problem* P, const mg_map_desc* map, const double* eps_phys,
+                                mg_mem_kind mem, cudaStream_t s);
+mg_status problem_check_build(mg_problem* P);
 mg_status enqueue_solve(mg_problem* P, const mg_solve_opts& o, const double* rho, const double* bc,
                         const double* phi_in, double* phi_out, cudaStream_t s);
 mg_status finish_solve(mg_problem* P, mg_solve_stats* stats);

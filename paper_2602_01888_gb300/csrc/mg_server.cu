@@ -1,16 +1,21 @@
 // Request server: a scheduler thread admits submitted solves while in-flight slots and
-// the device-memory budget allow, builds each request's resident hierarchy, runs its
-// captured solve graph on a slot stream (so requests that arrive while others are on
-// the GPU overlap with them), retires finished requests and records submit-to-result
-// latency.  A request's result does not depend on what else is in flight: it runs the
-// same graph as mg_solve.
+// the device-memory budget allow, gives each a resident hierarchy (reusing an idle one of
+// the same grid when there is one), enqueues the coefficient build and the captured solve
+// graph on a slot stream (so requests that arrive while others are on the GPU overlap with
+// them), retires finished requests and records submit-to-result latency.  A request's
+// result does not depend on what else is in flight or on which resident hierarchy it got:
+// it runs the same kernels and graph as mg_setup_transform + mg_solve.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
+#include <cstdio>
 #include <deque>
+#include <iterator>
+#include <list>
+#include <string>
 #include <memory>
 #include <mutex>
 #include <thread>
@@ -29,8 +34,9 @@ struct Request {
   mg_grid_desc grid{};
   mg_map_desc map{};
   mg_solve_opts opts{};
-  std::vector<double> xp, yp, eps, rho, bc, phi;
-  bool has_eps = false, has_bc = false;
+  // page-locked arrays (nullptr when absent), carved from one block of the host pool
+  double *xp = nullptr, *yp = nullptr, *eps = nullptr, *rho = nullptr, *bc = nullptr, *phi = nullptr;
+  void* block = nullptr;
   Clock::time_point t_submit, t_done;
   mg_problem* prob = nullptr;
   int slot = -1;
@@ -51,7 +57,9 @@ struct Server {
   std::vector<cudaStream_t> slots;
   std::vector<int> slot_free;
   std::vector<double> lat_ms;
-  uint64_t next_ticket = 1, completed = 0, failed = 0;
+  Pool host;  // page-locked request buffers
+  std::list<std::pair<std::string, mg_problem*>> idle;  // resident, least recently used first
+  uint64_t next_ticket = 1, completed = 0, failed = 0, reused = 0, evicted = 0;
   double unknowns_done = 0.0;
   long long batch_sum = 0;
   int ticks = 0;
@@ -65,24 +73,61 @@ static size_t nodes_of(const mg_grid_desc& g) {
   return (size_t)g.nx * (size_t)(g.periodic_y ? g.ny - 1 : g.ny);
 }
 
+// Problems whose hierarchy fits a request of the same grid and options are kept resident
+// after their request retires and are reused (coefficients rebuilt in place, captured
+// solve graph replayed).  Idle ones are freed, least recently used first, only when a new
+// hierarchy does not fit the memory budget.
+static std::string shape_key(const mg_grid_desc& g, const mg_solve_opts& o) {
+  char k[256];
+  snprintf(k, sizeof k, "%d:%d:%d:%.17g:%.17g:%.17g:%.17g:%d:%d:%d", g.nx, g.ny, g.periodic_y, g.x0,
+           g.y0, g.lx, g.ly, (int)o.precision, o.coarse_max, (int)o.outer);
+  return k;
+}
+
+static mg_problem* take_idle(Server* S, const std::string& key) {
+  for (auto it = S->idle.rbegin(); it != S->idle.rend(); ++it)
+    if (it->first == key) {
+      mg_problem* P = it->second;
+      S->idle.erase(std::next(it).base());
+      S->reused++;
+      return P;
+    }
+  return nullptr;
+}
+
+static bool evict_idle(Server* S) {
+  if (S->idle.empty()) return false;
+  mg_problem_free(S->idle.front().second);
+  S->idle.pop_front();
+  S->evicted++;
+  return true;
+}
+
+// Resident problem for R: an idle one of the same shape, else a new allocation (evicting
+// idle problems while the budget is exhausted).  MG_ERR_OOM: nothing fits right now.
+static mg_status acquire_problem(Server* S, Request* R, mg_problem** out) {
+  const std::string key = shape_key(R->grid, R->opts);
+  *out = take_idle(S, key);
+  if (*out) return MG_OK;
+  while (true) {
+    mg_status st = problem_create(S->ctx, &R->grid, R->opts, out);
+    if (st != MG_ERR_OOM || !evict_idle(S)) return st;
+  }
+}
+
 // Admit, launch, retire; runs on the scheduler thread.
 static void server_loop(Server* S) {
   cudaSetDevice(S->ctx->device);
   std::unique_lock<std::mutex> lk(S->mu);
   while (true) {
-    // admission
+    // admission: coefficient build and solve go onto the request's slot stream back to
+    // back; the scheduler does not wait for either
     bool progressed = false;
     while (!S->pending.empty() && !S->slot_free.empty()) {
       auto R = S->pending.front();
       lk.unlock();
-      mg_map_desc m = R->map;
-      if (m.kind == MG_MAP_GRID) {
-        m.xp = R->xp.data();
-        m.yp = R->yp.data();
-      }
       mg_problem* P = nullptr;
-      mg_status st = mg_setup_transform(S->ctx, &R->grid, &m, R->has_eps ? R->eps.data() : nullptr,
-                                        MG_MEM_HOST, &R->opts, &P);
+      mg_status st = acquire_problem(S, R.get(), &P);
       lk.lock();
       if (st == MG_ERR_OOM && !S->inflight.empty()) break;  // wait for memory to free up
       S->pending.pop_front();
@@ -105,16 +150,22 @@ static void server_loop(Server* S) {
         P->stage = (double*)S->ctx->pool.alloc(3 * n * sizeof(double));
         if (P->stage) P->allocs.push_back(P->stage);
       }
-      st = P->stage ? MG_OK : MG_ERR_OOM;
+      st = P->stage ? MG_OK : set_error(MG_ERR_OOM, "server: no memory for the staging arrays");
       if (!st) {
-        cudaMemcpyAsync(P->stage, R->rho.data(), n * sizeof(double), cudaMemcpyHostToDevice, s);
-        if (R->has_bc)
-          cudaMemcpyAsync(P->stage + n, R->bc.data(), n * sizeof(double), cudaMemcpyHostToDevice, s);
+        mg_map_desc m = R->map;
+        m.xp = R->xp;
+        m.yp = R->yp;
+        st = problem_enqueue_build(P, &m, R->eps, MG_MEM_HOST, s);
+      }
+      if (!st) {
+        cudaMemcpyAsync(P->stage, R->rho, n * sizeof(double), cudaMemcpyHostToDevice, s);
+        if (R->bc) cudaMemcpyAsync(P->stage + n, R->bc, n * sizeof(double), cudaMemcpyHostToDevice, s);
         R->opts.warm_start = 0;
-        st = enqueue_solve(P, R->opts, P->stage, R->has_bc ? P->stage + n : nullptr, P->stage + 2 * n,
+        st = enqueue_solve(P, R->opts, P->stage, R->bc ? P->stage + n : nullptr, P->stage + 2 * n,
                            P->stage + 2 * n, s);
       }
       if (!st) {
+        cudaMemcpyAsync(R->phi, P->stage + 2 * n, n * sizeof(double), cudaMemcpyDeviceToHost, s);
         cudaEventCreateWithFlags(&R->done_ev, cudaEventDisableTiming);
         cudaEventRecord(R->done_ev, s);
       }
@@ -125,7 +176,10 @@ static void server_loop(Server* S) {
         R->t_done = Clock::now();
         S->failed++;
         S->slot_free.push_back(R->slot);
-        mg_problem_free(R->prob);
+        lk.unlock();
+        cudaStreamSynchronize(s);
+        mg_problem_free(R->prob);  // its state is unknown after a failed enqueue
+        lk.lock();
         R->prob = nullptr;
         S->cv_done.notify_all();
         continue;
@@ -144,16 +198,12 @@ static void server_loop(Server* S) {
         continue;
       }
       mg_problem* P = R->prob;
-      const size_t n = nodes_of(R->grid);
       lk.unlock();
-      R->phi.resize(n);
-      cudaStream_t s = S->slots[R->slot];
-      cudaMemcpyAsync(R->phi.data(), P->stage + 2 * n, n * sizeof(double), cudaMemcpyDeviceToHost, s);
-      cudaStreamSynchronize(s);
-      mg_status st = finish_solve(P, &R->stats);
-      mg_problem_free(P);
+      mg_status st = problem_check_build(P);
+      if (!st) st = finish_solve(P, &R->stats);
       cudaEventDestroy(R->done_ev);
       lk.lock();
+      S->idle.emplace_back(shape_key(R->grid, R->opts), P);  // stays resident for reuse
       R->prob = nullptr;
       R->status = st;
       R->finished = true;
@@ -179,6 +229,9 @@ static void server_loop(Server* S) {
       }
     }
   }
+  lk.unlock();
+  for (auto& kv : S->idle) mg_problem_free(kv.second);
+  S->idle.clear();
 }
 
 }  // namespace mg
@@ -199,6 +252,8 @@ extern "C" mg_status mg_server_start(mg_ctx* ctx, const mg_server_opts* opts, mg
   S->opts.max_inflight = std::min(S->opts.max_inflight, 64);
   if (S->opts.queue_capacity <= 0) S->opts.queue_capacity = 1 << 16;
   if (S->opts.mem_budget && S->opts.mem_budget < ctx->pool.budget_) ctx->pool.budget_ = S->opts.mem_budget;
+  S->host.pinned_ = true;
+  S->host.budget_ = S->opts.host_budget ? S->opts.host_budget : ((size_t)8 << 30);
   cudaSetDevice(ctx->device);
   for (int k = 0; k < S->opts.max_inflight; ++k) {
     cudaStream_t s;
@@ -221,31 +276,40 @@ extern "C" mg_status mg_serve_submit(mg_server* h, const mg_request* rq, uint64_
   Server* S = &h->s;
   const mg_grid_desc& g = rq->grid;
   if (g.nx < 3 || g.ny < 3) return set_error(MG_ERR_SIZE, "mg_serve_submit: grid too small");
-  if (rq->map.kind == MG_MAP_GRID && (!rq->map.xp || !rq->map.yp))
-    return set_error(MG_ERR_ARG, "mg_serve_submit: MG_MAP_GRID needs xp and yp");
+  mg_status cm = check_map(&g, &rq->map);
+  if (cm) return cm;
   auto R = std::make_shared<Request>();
   R->grid = g;
   R->map = rq->map;
   R->opts = rq->opts;
   const size_t n = nodes_of(g);
-  R->rho.assign(rq->rho_phys, rq->rho_phys + n);
-  if (rq->bc) {
-    R->bc.assign(rq->bc, rq->bc + n);
-    R->has_bc = true;
-  }
-  if (rq->eps_phys) {
-    R->eps.assign(rq->eps_phys, rq->eps_phys + n);
-    R->has_eps = true;
-  }
-  if (rq->map.kind == MG_MAP_GRID) {
-    R->xp.assign(rq->map.xp, rq->map.xp + n);
-    R->yp.assign(rq->map.yp, rq->map.yp + n);
+  const bool grid_map = rq->map.kind == MG_MAP_GRID;
+  const size_t arrays = 2 + (rq->bc ? 1 : 0) + (rq->eps_phys ? 1 : 0) + (grid_map ? 2 : 0);
+  R->block = S->host.alloc(arrays * n * sizeof(double));
+  if (!R->block)
+    return set_error(MG_ERR_BUSY, "mg_serve_submit: host staging budget full (poll finished tickets)");
+  double* cur = (double*)R->block;
+  auto take = [&](const double* src) {
+    double* d = cur;
+    cur += n;
+    if (src) memcpy(d, src, n * sizeof(double));
+    return d;
+  };
+  R->rho = take(rq->rho_phys);
+  R->phi = take(nullptr);
+  if (rq->bc) R->bc = take(rq->bc);
+  if (rq->eps_phys) R->eps = take(rq->eps_phys);
+  if (grid_map) {
+    R->xp = take(rq->map.xp);
+    R->yp = take(rq->map.yp);
   }
   R->map.xp = R->map.yp = nullptr;
   std::lock_guard<std::mutex> lk(S->mu);
-  if (S->stopping) return set_error(MG_ERR_BUSY, "mg_serve_submit: server is stopping");
-  if ((int)S->pending.size() >= S->opts.queue_capacity)
+  if (S->stopping || (int)S->pending.size() >= S->opts.queue_capacity) {
+    S->host.release(R->block);
+    if (S->stopping) return set_error(MG_ERR_BUSY, "mg_serve_submit: server is stopping");
     return set_error(MG_ERR_BUSY, "mg_serve_submit: queue full (%d pending)", (int)S->pending.size());
+  }
   R->ticket = S->next_ticket++;
   R->t_submit = Clock::now();
   S->pending.push_back(R);
@@ -267,10 +331,13 @@ extern "C" mg_status mg_serve_poll(mg_server* h, uint64_t ticket, int timeout_ms
     S->cv_done.wait_for(lk, std::chrono::milliseconds(std::max(timeout_ms, 0)), [&] { return R->finished; });
     if (!R->finished) return set_error(MG_ERR_TIMEOUT, "mg_serve_poll: ticket %llu not done", (unsigned long long)ticket);
   }
-  if (phi_out && !R->phi.empty()) memcpy(phi_out, R->phi.data(), R->phi.size() * sizeof(double));
+  S->by_ticket.erase(it);
+  lk.unlock();
+  if (phi_out && R->status == MG_OK) memcpy(phi_out, R->phi, nodes_of(R->grid) * sizeof(double));
   if (stats) *stats = R->stats;
   mg_status st = R->status;
-  S->by_ticket.erase(it);
+  S->host.release(R->block);
+  R->block = nullptr;
   if (st) return set_error(st, "mg_serve_poll: request %llu failed (status %d)", (unsigned long long)ticket, (int)st);
   return MG_OK;
 }
@@ -302,6 +369,8 @@ extern "C" mg_status mg_server_stop(mg_server* h, mg_serve_report* rep) {
     rep->max_ms = l.empty() ? 0.0 : l.back();
     rep->ticks = S->ticks;
     rep->mean_batch = S->ticks ? (double)S->batch_sum / S->ticks : 0.0;
+    rep->reused = S->reused;
+    rep->evicted = S->evicted;
   }
   for (auto s : S->slots) cudaStreamDestroy(s);
   delete h;

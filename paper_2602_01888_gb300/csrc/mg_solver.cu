@@ -40,8 +40,9 @@ mg_status set_error(mg_status s, const char* fmt, ...) {
   } while (0)
 
 // ------------------------------------------------------------------ memory pool
-// Slabs of device memory obtained with cudaMalloc; best-fit ranges inside them,
-// coalesced on release; total slab bytes capped by the context's budget.
+// Slabs of device memory obtained with cudaMalloc (or page-locked host memory from
+// cudaMallocHost); best-fit ranges inside them, coalesced on release; total slab bytes
+// capped by the budget.
 void* Pool::alloc(size_t n) {
   std::lock_guard<std::mutex> lk(mu_);
   n = (n + 255) & ~size_t(255);
@@ -70,7 +71,7 @@ void* Pool::alloc(size_t n) {
     if (reserved_ + want > budget_) want = n;
     if (reserved_ + want > budget_) return nullptr;
     void* base = nullptr;
-    if (cudaMalloc(&base, want) != cudaSuccess) {
+    if ((pinned_ ? cudaMallocHost(&base, want) : cudaMalloc(&base, want)) != cudaSuccess) {
       cudaGetLastError();
       return nullptr;
     }
@@ -109,7 +110,10 @@ void Pool::release(void* p) {
 }
 
 Pool::~Pool() {
-  for (auto& s : slabs_) cudaFree(s.base);
+  for (auto& s : slabs_) {
+    if (pinned_) cudaFreeHost(s.base);
+    else cudaFree(s.base);
+  }
 }
 
 // ------------------------------------------------------------------ hierarchy sizes
@@ -229,6 +233,8 @@ static void problem_release(mg_problem* P) {
   if (P->h_flags) cudaFreeHost(P->h_flags);
   if (P->ev0) cudaEventDestroy(P->ev0);
   if (P->ev1) cudaEventDestroy(P->ev1);
+  if (P->evb0) cudaEventDestroy(P->evb0);
+  if (P->evb1) cudaEventDestroy(P->evb1);
 }
 
 // Allocate every array of the hierarchy (FP64 levels, FP32 mirrors when mixed, the
@@ -282,14 +288,16 @@ static mg_status problem_alloc(mg_problem* P, bool mixed) {
   CU(cudaMallocHost(&P->h_flags, 4 * sizeof(int)));
   CU(cudaEventCreate(&P->ev0));
   CU(cudaEventCreate(&P->ev1));
+  CU(cudaEventCreate(&P->evb0));
+  CU(cudaEventCreate(&P->evb1));
   return MG_OK;
 }
 
 // Coefficients of the finest level from the map, then the Galerkin hierarchy and the
-// coarsest inverse.  Reads host or device inputs; synchronises once to check flags.
-static mg_status problem_build(mg_problem* P, const mg_map_desc* map, const double* eps_phys,
-                               mg_mem_kind mem) {
-  cudaStream_t s = P->ctx->stream;
+// coarsest inverse, enqueued on stream s.  Reads host or device inputs.  The map and SPD
+// flags land in P->h_flags; problem_check_build reads them once s has been synchronised.
+mg_status problem_enqueue_build(mg_problem* P, const mg_map_desc* map, const double* eps_phys,
+                                mg_mem_kind mem, cudaStream_t s) {
   const mg_grid_desc& g = P->grid;
   const int nx = g.nx, ny = g.ny, nyr = rows_stored(ny, g.periodic_y);
   const double hx = g.lx / (nx - 1), hy = g.ly / (ny - 1);
@@ -297,7 +305,7 @@ static mg_status problem_build(mg_problem* P, const mg_map_desc* map, const doub
   LevelMem& F = P->lev[0];
   const int pt = F.A.pitch;
   const size_t np = (size_t)pt * nyr;
-  CU(cudaEventRecord(P->ev0, s));
+  CU(cudaEventRecord(P->evb0, s));
   // temporaries: eps components in the fine level's scratch arrays (x, b, t), inputs
   // staged in pitched layout in q / z / p
   double *exx = F.x, *exy = F.b, *eyy = F.t;
@@ -341,16 +349,29 @@ static mg_status problem_build(mg_problem* P, const mg_map_desc* map, const doub
   P->setup_kernels = 1 + 2 + (P->mixed ? 1 + (P->nlev - 1) + (P->nlev > 1 ? 1 : 0) : P->nlev - 1) + 1;
   // restore the scratch vectors used as staging
   CU(cudaMemsetAsync(P->z, 0, 3 * np * sizeof(double), s));
-  CU(cudaEventRecord(P->ev1, s));
-  int hf[4];
-  CU(cudaMemcpyAsync(hf, P->flags, sizeof hf, cudaMemcpyDeviceToHost, s));
-  CU(cudaStreamSynchronize(s));
-  float ms = 0.f;
-  cudaEventElapsedTime(&ms, P->ev0, P->ev1);
-  P->setup_ms = ms;
-  if (hf[0]) return set_error(MG_ERR_MAP_FOLDED, "det J <= 0 at some node: the map folds");
-  if (hf[1]) return set_error(MG_ERR_NOT_SPD, "coarsest operator is not SPD (non-positive pivot)");
+  CU(cudaEventRecord(P->evb1, s));
+  CU(cudaMemcpyAsync(P->h_flags, P->flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
   return MG_OK;
+}
+
+// Outcome of an enqueued build; the build's stream must have been synchronised.  The
+// flags stay valid after a solve on the same stream (solves do not touch them).
+mg_status problem_check_build(mg_problem* P) {
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, P->evb0, P->evb1);
+  P->setup_ms = ms;
+  if (P->h_flags[0]) return set_error(MG_ERR_MAP_FOLDED, "det J <= 0 at some node: the map folds");
+  if (P->h_flags[1]) return set_error(MG_ERR_NOT_SPD, "coarsest operator is not SPD (non-positive pivot)");
+  return MG_OK;
+}
+
+static mg_status problem_build(mg_problem* P, const mg_map_desc* map, const double* eps_phys,
+                               mg_mem_kind mem) {
+  cudaStream_t s = P->ctx->stream;
+  mg_status st = problem_enqueue_build(P, map, eps_phys, mem, s);
+  if (st) return st;
+  CU(cudaStreamSynchronize(s));
+  return problem_check_build(P);
 }
 
 static mg_status check_grid(const mg_grid_desc* g, int coarse_max, int* nlev, int* nxs, int* nys) {
@@ -372,7 +393,7 @@ static mg_status check_grid(const mg_grid_desc* g, int coarse_max, int* nlev, in
   return MG_OK;
 }
 
-static mg_status check_map(const mg_grid_desc* g, const mg_map_desc* m) {
+mg_status check_map(const mg_grid_desc* g, const mg_map_desc* m) {
   if (!m) return set_error(MG_ERR_ARG, "map is NULL");
   if (m->kind < MG_MAP_IDENTITY || m->kind > MG_MAP_GRID)
     return set_error(MG_ERR_ARG, "unknown map kind %d", m->kind);
@@ -382,6 +403,34 @@ static mg_status check_map(const mg_grid_desc* g, const mg_map_desc* m) {
   return MG_OK;
 }
 
+}  // namespace mg
+
+namespace mg {
+// A problem with its hierarchy allocated (zeroed) but no coefficients yet.
+mg_status problem_create(mg_ctx* ctx, const mg_grid_desc* grid, const mg_solve_opts& o,
+                         mg_problem** out) {
+  *out = nullptr;
+  cudaSetDevice(ctx->device);
+  mg_problem* P = new mg_problem();
+  P->ctx = ctx;
+  P->grid = *grid;
+  P->coarse_max = o.coarse_max;
+  P->mixed = (o.precision == MG_PREC_MIXED);
+  mg_status st = check_grid(grid, o.coarse_max, &P->nlev, P->nxs, P->nys);
+  if (!st) st = problem_alloc(P, P->mixed);
+  if (!st && cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+    st = set_error(MG_ERR_CUDA, "problem_create: %s", cudaGetErrorString(cudaGetLastError()));
+  if (st) {
+    char keep[512];
+    snprintf(keep, sizeof keep, "%s", g_err);
+    cudaStreamSynchronize(ctx->stream);
+    problem_release(P);
+    delete P;
+    return set_error(st, "%s", keep);
+  }
+  *out = P;
+  return MG_OK;
+}
 }  // namespace mg
 
 extern "C" mg_status mg_setup_transform(mg_ctx* ctx, const mg_grid_desc* grid,
@@ -394,15 +443,10 @@ extern "C" mg_status mg_setup_transform(mg_ctx* ctx, const mg_grid_desc* grid,
   if (opts) o = *opts; else mg_default_opts(&o);
   mg_status st = check_map(grid, map);
   if (st) return st;
-  cudaSetDevice(ctx->device);
-  mg_problem* P = new mg_problem();
-  P->ctx = ctx;
-  P->grid = *grid;
-  P->coarse_max = o.coarse_max;
-  P->mixed = (o.precision == MG_PREC_MIXED);
-  st = check_grid(grid, o.coarse_max, &P->nlev, P->nxs, P->nys);
-  if (!st) st = problem_alloc(P, P->mixed);
-  if (!st) st = problem_build(P, map, eps_phys, mem);
+  mg_problem* P = nullptr;
+  st = problem_create(ctx, grid, o, &P);
+  if (st) return st;
+  st = problem_build(P, map, eps_phys, mem);
   if (st) {
     char keep[512];
     snprintf(keep, sizeof keep, "%s", g_err);
@@ -422,6 +466,61 @@ extern "C" mg_status mg_update_transform(mg_problem* P, const mg_map_desc* map,
   if (st) return st;
   cudaSetDevice(P->ctx->device);
   return problem_build(P, map, eps_phys, mem);
+}
+
+extern "C" mg_status mg_batch_update_transform(mg_ctx* ctx, int count, mg_problem* const* probs,
+                                               const mg_map_desc* maps, const double* const* eps_phys,
+                                               mg_mem_kind mem, mg_status* statuses) {
+  if (!ctx || count < 0 || (count > 0 && (!probs || !maps)))
+    return set_error(MG_ERR_ARG, "mg_batch_update_transform: NULL argument");
+  for (int k = 0; k < count; ++k) {
+    if (!probs[k] || probs[k]->ctx != ctx)
+      return set_error(MG_ERR_ARG, "mg_batch_update_transform: problem %d is NULL or from another context", k);
+    mg_status st = check_map(&probs[k]->grid, &maps[k]);
+    if (st) return st;
+  }
+  if (count == 0) return MG_OK;
+  cudaSetDevice(ctx->device);
+  // fork: instance k builds on batch stream k mod kBatchStreams, after the work already
+  // queued on the context stream; join back onto the context stream
+  cudaEvent_t fork = nullptr, join[kBatchStreams] = {};
+  mg_status st = MG_OK;
+  auto cleanup = [&]() {
+    if (fork) cudaEventDestroy(fork);
+    for (auto& e : join)
+      if (e) cudaEventDestroy(e);
+  };
+  if (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventRecord(fork, ctx->stream) != cudaSuccess) {
+    cleanup();
+    return set_error(MG_ERR_CUDA, "mg_batch_update_transform: event setup failed");
+  }
+  const int ns = std::min(count, kBatchStreams);
+  for (int b = 0; b < ns; ++b) {
+    if (cudaEventCreateWithFlags(&join[b], cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamWaitEvent(ctx->batch[b], fork, 0) != cudaSuccess) {
+      cleanup();
+      return set_error(MG_ERR_CUDA, "mg_batch_update_transform: event setup failed");
+    }
+  }
+  std::vector<mg_status> enq(count, MG_OK);
+  for (int k = 0; k < count; ++k)
+    enq[k] = problem_enqueue_build(probs[k], &maps[k], eps_phys ? eps_phys[k] : nullptr, mem,
+                                   ctx->batch[k % kBatchStreams]);
+  for (int b = 0; b < ns; ++b) {
+    cudaEventRecord(join[b], ctx->batch[b]);
+    cudaStreamWaitEvent(ctx->stream, join[b], 0);
+  }
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  cleanup();
+  if (e != cudaSuccess) return set_error(MG_ERR_CUDA, "mg_batch_update_transform: %s", cudaGetErrorString(e));
+  for (int k = 0; k < count; ++k) {
+    mg_status sk = enq[k] ? enq[k] : problem_check_build(probs[k]);
+    if (statuses) statuses[k] = sk;
+    if (sk && !st) st = sk;
+  }
+  if (st) return set_error(st, "mg_batch_update_transform: at least one instance failed (first status %d)", (int)st);
+  return MG_OK;
 }
 
 extern "C" void mg_problem_free(mg_problem* P) {

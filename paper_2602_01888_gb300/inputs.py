@@ -331,33 +331,45 @@ def inclusion_grid(n: int, r: float):
 
 
 def _grid_job(args):
-    n, i0 = args
+    n, i0, nsrc, seed = args
     xp, yp = _inclusion_grid_cached(n, i0)
-    return n, i0, np.array(xp), np.array(yp)
+    src = [gaussian_blobs(xp, yp, np.random.default_rng(seed + 7919 * v)) for v in range(nsrc)]
+    return n, i0, np.array(xp), np.array(yp), src
 
 
-def prefetch_inclusion_grids(pairs, workers: int = 0):
+def prefetch_inclusion_grids(pairs, workers: int = 0, sources: int = 0, seed: int = 0):
     """Generate the mapped grids of many (side, radius) pairs in parallel worker
-    processes (started with 'spawn') and seed the in-process cache with them."""
+    processes (started with 'spawn') and seed the in-process cache with them.  With
+    sources > 0 also draw that many seeded 16-blob sources per grid (served by
+    ``cached_source``).  Call it from a script's main guard."""
     import concurrent.futures as cf
     import multiprocessing as mp
     import os
 
     jobs = sorted({(n, snap_ring(n, r)) for n, r in pairs})
-    todo = [j for j in jobs if j not in _SEEDED]
+    todo = [j for j in jobs if j not in _SEEDED or len(_SOURCES.get(j, ())) < sources]
     if not todo:
         return
     workers = workers or max(1, min(16, (os.cpu_count() or 2) - 1))
-    # largest first: they dominate the wall time
-    todo.sort(key=lambda j: -j[0])
+    todo.sort(key=lambda j: -j[0])  # largest first: they dominate the wall time
+    args = [(n, i0, sources, seed + 1009 * n + i0) for n, i0 in todo]
     with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
-        for n, i0, xp, yp in ex.map(_grid_job, todo):
+        for n, i0, xp, yp, src in ex.map(_grid_job, args):
             xp.setflags(write=False)
             yp.setflags(write=False)
             _SEEDED[(n, i0)] = (xp, yp)
+            if sources:
+                _SOURCES[(n, i0)] = src
+
+
+def cached_source(n: int, i0: int, variant: int) -> np.ndarray:
+    """One of the pre-drawn sources of grid (n, i0) (see prefetch_inclusion_grids)."""
+    src = _SOURCES[(n, i0)]
+    return src[variant % len(src)]
 
 
 _SEEDED: dict = {}
+_SOURCES: dict = {}
 
 
 def inclusion_eps(n: int, i0: int, ratio: float) -> np.ndarray:

@@ -71,7 +71,8 @@ class mgk_op_f32(C.Structure):
 
 
 class mg_server_opts(C.Structure):
-    _fields_ = [("max_inflight", C.c_int), ("queue_capacity", C.c_int), ("mem_budget", C.c_size_t)]
+    _fields_ = [("max_inflight", C.c_int), ("queue_capacity", C.c_int), ("mem_budget", C.c_size_t),
+                ("host_budget", C.c_size_t)]
 
 
 class mg_request(C.Structure):
@@ -82,7 +83,8 @@ class mg_request(C.Structure):
 class mg_serve_report(C.Structure):
     _fields_ = [("completed", C.c_uint64), ("failed", C.c_uint64), ("wall_s", C.c_double),
                 ("unknowns_per_s", C.c_double), ("p50_ms", C.c_double), ("p99_ms", C.c_double),
-                ("max_ms", C.c_double), ("mean_batch", C.c_double), ("ticks", C.c_int)]
+                ("max_ms", C.c_double), ("mean_batch", C.c_double), ("ticks", C.c_int),
+                ("reused", C.c_uint64), ("evicted", C.c_uint64)]
 
 
 _SIGS = {
@@ -95,6 +97,8 @@ _SIGS = {
     "mg_setup_transform": ([C.c_void_p, C.POINTER(mg_grid_desc), C.POINTER(mg_map_desc), C.c_void_p,
                             C.c_int, C.POINTER(mg_solve_opts), C.POINTER(C.c_void_p)], C.c_int),
     "mg_update_transform": ([C.c_void_p, C.POINTER(mg_map_desc), C.c_void_p, C.c_int], C.c_int),
+    "mg_batch_update_transform": ([C.c_void_p, C.c_int, C.POINTER(C.c_void_p), C.POINTER(mg_map_desc),
+                                   C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_int)], C.c_int),
     "mg_problem_free": ([C.c_void_p], None),
     "mg_problem_info": ([C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)],
                         C.c_int),
@@ -302,6 +306,31 @@ def mg_update_transform(prob: int, grid, mapspec, eps_phys=None, xp=None, yp=Non
     _check(lib().mg_update_transform(prob, C.byref(m), _ptr(eps_phys), mem), "mg_update_transform")
 
 
+def mg_batch_update_transform(ctx: int, probs: Sequence[int], mapspecs, eps=None, xps=None, yps=None,
+                              raise_on_error: bool = True):
+    """mg_update_transform for many problems with one synchronisation.  Returns the
+    per-instance statuses."""
+    n = len(probs)
+    xps = xps if xps is not None else [None] * n
+    yps = yps if yps is not None else [None] * n
+    arrs = []
+    maps = (mg_map_desc * max(n, 1))()
+    for k, ms in enumerate(mapspecs):
+        xp, yp = xps[k], yps[k]
+        if ms.kind == "grid" and xp is None:
+            xp, yp = np.ascontiguousarray(ms.xp), np.ascontiguousarray(ms.yp)
+        maps[k] = map_desc(ms, xp, yp)
+        arrs += [xp, yp]
+    mem = _mem_kind(*arrs, *([e for e in eps if e is not None] if eps is not None else []))
+    P = (C.c_void_p * max(n, 1))(*probs)
+    E = (C.c_void_p * max(n, 1))(*[_ptr(e) for e in eps]) if eps is not None else None
+    stats = (C.c_int * max(n, 1))()
+    st = lib().mg_batch_update_transform(ctx, n, P, maps, E, mem, stats)
+    if raise_on_error:
+        _check(st, "mg_batch_update_transform")
+    return [stats[k] for k in range(n)]
+
+
 def mg_problem_free(prob: int):
     lib().mg_problem_free(prob)
 
@@ -341,8 +370,8 @@ def mg_batch_solve(ctx: int, probs: Sequence[int], rhos, bcs, phis,
     return list(stats)[:n]
 
 
-def mg_server_start(ctx: int, max_inflight=16, queue_capacity=65536, mem_budget=0) -> int:
-    o = mg_server_opts(max_inflight, queue_capacity, mem_budget)
+def mg_server_start(ctx: int, max_inflight=16, queue_capacity=65536, mem_budget=0, host_budget=0) -> int:
+    o = mg_server_opts(max_inflight, queue_capacity, mem_budget, host_budget)
     h = C.c_void_p()
     _check(lib().mg_server_start(ctx, C.byref(o), C.byref(h)), "mg_server_start")
     return h.value

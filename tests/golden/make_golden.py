@@ -30,17 +30,26 @@ def main(case):
     # PCG is not monotone in the 2-norm: on the largest grids the residual grows for the first
     # few iterations, so the stagnation window must be wider than that transient.
     phi, it, hist = O.pcg_solve(P.A, P.b, P.phi0, rtol=0.0, max_iters=400, stagnate=10)
-    t2 = time.time()
+    # Plain CG stalls where its recursively updated residual parts from b - A phi (here near
+    # 2.5e-9 relative at 8193^2).  One step of defect correction recovers what the iteration
+    # lost: solve A e = b - A phi by the same method from zero and add e.
     g = inst.grid
+    r = O.residual(P.A, phi, P.b)
+    rel1 = float(np.linalg.norm(r[g.interior_mask()]) / np.linalg.norm(P.b[g.interior_mask()]))
+    e, it2, _ = O.pcg_solve(P.A, r, np.zeros_like(phi), rtol=0.0, max_iters=400, stagnate=10)
+    phi = phi + e
+    r = O.residual(P.A, phi, P.b)
+    rel2 = float(np.linalg.norm(r[g.interior_mask()]) / np.linalg.norm(P.b[g.interior_mask()]))
+    t2 = time.time()
     rng = np.random.default_rng(SEED)
     ii = rng.integers(1, g.nx - 1, N_SAMPLES)
     jj = rng.integers(0, g.nyr, N_SAMPLES)
     out = os.path.join(os.path.dirname(os.path.abspath(__file__)), f"{case}_samples.npz")
-    np.savez_compressed(out, i=ii, j=jj, phi=phi[jj, ii], iterations=it, final_rel_residual=hist[it],
-                        best_rel_residual=float(np.min(hist[: it + 1])),
+    np.savez_compressed(out, i=ii, j=jj, phi=phi[jj, ii], iterations=it, correction_iterations=it2,
+                        rel_residual_before_correction=rel1, final_rel_residual=rel2,
                         phi_l2=float(np.linalg.norm(phi[g.interior_mask()])),
                         prepare_s=t1 - t0, solve_s=t2 - t1)
-    print(f"{case}: {it} oracle iterations, final rel residual {hist[-1]:.3e}, "
+    print(f"{case}: {it} + {it2} oracle iterations, rel residual {rel1:.3e} -> {rel2:.3e}, "
           f"prepare {t1 - t0:.1f}s, solve {t2 - t1:.1f}s -> {out}")
 
 

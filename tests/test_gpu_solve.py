@@ -184,3 +184,56 @@ def test_full_size_inclusion_1025(libmg, oracle, ctx):
         err = _err(oracle, inst, phi, ref)
         assert err <= tol, (prec, err, st.iters)
         prob.close()
+
+
+def test_server_reuses_resident_hierarchies_with_identical_results(libmg, ctx):
+    """Twelve requests over three grid sides through two slots: later requests run on
+    hierarchies left resident by earlier ones (coefficients rebuilt in place) and still
+    return exactly what a fresh mg_setup_transform + mg_solve returns."""
+    sides = [65, 129, 97, 65, 129, 97, 129, 65, 97, 65, 129, 97]
+    specs = [(n, 0.12 + 0.02 * k, 2.0 + 3.0 * k, 100 + k) for k, n in enumerate(sides)]
+    insts = [I.inclusion_instance(*s) for s in specs]
+    opts = libmg.make_opts("mixed", "fcg", rtol=1e-10)
+    alone = []
+    for inst in insts:
+        p = libmg.Problem(ctx, inst, opts)
+        alone.append(p.solve()[0])
+        p.close()
+    srv = libmg.mg_server_start(ctx.h, max_inflight=2)
+    tickets = []
+    for inst in insts:
+        st, t = libmg.mg_serve_submit(srv, inst.grid, inst.map, np.ascontiguousarray(inst.rho_phys),
+                                      None, np.ascontiguousarray(inst.eps_phys), opts)
+        assert st == 0
+        tickets.append(t)
+    for inst, t, a in zip(insts, tickets, alone):
+        out = np.zeros(inst.grid.shape)
+        st, _ = libmg.mg_serve_poll(srv, t, 60000, out)
+        assert st == 0
+        assert np.array_equal(out, a), inst.name
+    rep = libmg.mg_server_stop(srv)
+    assert rep.completed == len(insts) and rep.failed == 0
+    assert rep.reused >= len(insts) - 2 * 3
+
+
+def test_server_host_staging_budget_gives_busy_then_recovers(libmg, ctx):
+    """Submitted arrays live in page-locked staging until their ticket is polled; a full
+    staging budget makes mg_serve_submit return MG_ERR_BUSY, and polling frees room."""
+    insts = [I.inclusion_instance(65, 0.2, 3.0 + k, 300 + k) for k in range(3)]
+    one = 6 * 65 * 65 * 8  # rho, phi, eps, xp, yp and rounding slack
+    opts = libmg.make_opts("mixed", "fcg", rtol=1e-10)
+    srv = libmg.mg_server_start(ctx.h, max_inflight=2, host_budget=2 * one + 4096)
+    sub = lambda x: libmg.mg_serve_submit(srv, x.grid, x.map, np.ascontiguousarray(x.rho_phys), None,
+                                          np.ascontiguousarray(x.eps_phys), opts)
+    st0, t0 = sub(insts[0])
+    st1, t1 = sub(insts[1])
+    st2, _ = sub(insts[2])
+    assert (st0, st1, st2) == (0, 0, libmg.MG_ERR_BUSY)
+    out = np.zeros(insts[0].grid.shape)
+    assert libmg.mg_serve_poll(srv, t0, 60000, out)[0] == 0
+    st2, t2 = sub(insts[2])
+    assert st2 == 0
+    for t in (t1, t2):
+        assert libmg.mg_serve_poll(srv, t, 60000, None)[0] == 0
+    rep = libmg.mg_server_stop(srv)
+    assert rep.completed == 3 and rep.failed == 0

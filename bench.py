@@ -32,6 +32,10 @@ METRIC = "unknowns solved/sec to 1e-9 rel. error (FP64 vs mixed, 1 GB300)"
 RTOL = 1e-9
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # 2 FP64 FMA/clk/SM x 152 SMs x 2.07 GHz
 HBM_PEAK_GBS = 6681.2
+# DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture, keyed
+# by (kernel, side); cold-cache figures (profiles/gs_colour_f64_1025.md).  Null for any
+# kernel or size not captured since its last change.
+PROFILED_TRAFFIC = {("k_gs_colour<double>", 1025): (46.06e6 + 46.35e6 + 46.26e6 + 11.5e3) / 3}
 
 # Single-instance workloads: (builder, precisions with the headline first, outer iteration,
 # rtol giving an error <= 1e-9 against the FP64 oracle (checked by the GPU tests), builder of
@@ -224,12 +228,12 @@ def measure_smoother(mg, torch, inst, prec, reps=20):
         bytes_per_launch = 32.0 * g.nx * g.nyr / 4  # a sweep's algorithmic bytes over its 4 launches
         ach = bytes_per_launch / per_launch_s / 1e9
         return {"bound": "hbm", "achieved": ach, "peak": HBM_PEAK_GBS, "unit": "GB/s",
-                "frac": ach / HBM_PEAK_GBS, "traffic": None, "kernel": kern,
+                "frac": ach / HBM_PEAK_GBS, "traffic": PROFILED_TRAFFIC.get((kern, g.nx)), "kernel": kern,
                 "launch_us": per_launch_s * 1e6, "peak_source": "measured copy (MEASURED_PEAKS.json)"}
     flops_per_launch = g.unknowns / 4 * 18.0  # 8 FMA + subtract + scale per updated unknown
     achieved = flops_per_launch / per_launch_s / 1e12
     return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": kern,
+            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": PROFILED_TRAFFIC.get((kern, g.nx)), "kernel": kern,
             "launch_us": per_launch_s * 1e6,
             "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2.07 GHz (probe: 1.20 TFLOP/s at 1.99 GHz)"}
 
@@ -565,7 +569,7 @@ def run_batch(args):
 
 
 # ------------------------------------------------------------------ serving workload
-SERVE_RTOL = 5e-10
+SERVE_RTOL = 1e-9
 
 
 def _serve_requests(stream):
@@ -585,10 +589,13 @@ def _serve_pass(mg, ctx, reqs, arrivals, inflight, mem_budget):
     import collections
     srv = mg.mg_server_start(ctx.h, max_inflight=inflight, mem_budget=mem_budget)
     tickets = collections.deque()
+    unconverged = []
 
     def collect(tk):
         st, _ = mg.mg_serve_poll(srv, tk, 600_000, None)
-        if st:
+        if st == mg.MG_ERR_NOT_CONVERGED:
+            unconverged.append(tk)  # best iterate returned; counted in the report
+        elif st:
             raise RuntimeError(f"mg_serve_poll: status {st}: {mg.mg_last_error()}")
 
     eps_cache = {}
@@ -616,6 +623,7 @@ def _serve_pass(mg, ctx, reqs, arrivals, inflight, mem_budget):
         collect(tickets.popleft())
     wall = time.perf_counter() - t0
     rep = mg.mg_server_stop(srv)
+    rep.not_converged = len(unconverged)
     return rep, wall
 
 
@@ -657,7 +665,8 @@ def run_serve(args):
         r2, w2 = _serve_pass(mg, ctx, reqs, arr, args.inflight, 0)
         lat.append({"load": frac, "rate_rps": rate, "p50_ms": r2.p50_ms, "p99_ms": r2.p99_ms,
                     "max_ms": r2.max_ms, "unknowns_per_s": U / w2, "completed": r2.completed,
-                    "failed": r2.failed, "mean_inflight": r2.mean_batch, "reused": r2.reused,
+                    "failed": r2.failed, "not_converged": r2.not_converged,
+                    "mean_inflight": r2.mean_batch, "reused": r2.reused,
                     "evicted": r2.evicted})
     if rank == 0:
         bytes_in = sum(8 * q[1].nx * q[1].nyr * 4 for q in reqs)
@@ -671,7 +680,8 @@ def run_serve(args):
                        "radii": list(I.SERVE_RADII), "rtol": SERVE_RTOL, "inflight_slots": args.inflight,
                        "unknowns": U, "l2": "inputs of consecutive requests exceed L2 in aggregate"},
             "saturated": {"requests_per_s": sat_rps, "p50_ms": rep.p50_ms, "p99_ms": rep.p99_ms,
-                          "completed": rep.completed, "failed": rep.failed, "mean_inflight": rep.mean_batch,
+                          "completed": rep.completed, "failed": rep.failed,
+                          "not_converged": rep.not_converged, "mean_inflight": rep.mean_batch,
                           "reused": rep.reused, "evicted": rep.evicted},
             "latency": lat,
             "e2e": {"value": ws * U / wall, "unit": "unknowns/s", "h2d_bytes_per_step": bytes_in,

@@ -836,15 +836,14 @@ static bool host_loop_mode() {
   return v == 1;
 }
 
-static mg_status run_host_loop(mg_problem* P, const mg_solve_opts& o, cudaStream_t s) {
+static mg_status run_host_loop(mg_problem* P, const mg_solve_opts& o, cudaStream_t s, int* passes) {
   LevelMem& F = P->lev[0];
   const bool fcg = (o.outer == MG_OUTER_FCG);
   CU(launch_solve_init(F.A, P->args, P->D, F.x, F.b, P->st, s));
   CU(launch_resid_init(F.A, F.x, F.b, fcg ? P->r : nullptr, P->st, P->part, 0, 0, s));
   if (fcg && o.precision == MG_PREC_MIXED)
     CU(launch_r_to_f32(F.A, P->r, F.b32, F.A32.pitch, P->st, s));
-  P->last_fixed_kernels = 3 + ((fcg && o.precision == MG_PREC_MIXED) ? 1 : 0);
-  P->last_body_kernels = 0;
+  *passes = 0;
   for (int pass = 0; pass < 2 * o.max_iters + 8; ++pass) {
     int done = 0;
     CU(cudaMemcpyAsync(&done, &P->st->done, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -852,7 +851,7 @@ static mg_status run_host_loop(mg_problem* P, const mg_solve_opts& o, cudaStream
     if (done) break;
     mg_status st = emit_body(P, o, 0, 0, s);
     if (st) return st;
-    P->last_fixed_kernels += 0;
+    ++*passes;
   }
   CU(launch_copy_out(F.A, F.x, P->args, s));
   return MG_OK;
@@ -864,7 +863,7 @@ mg_status enqueue_solve(mg_problem* P, const mg_solve_opts& o, const double* rho
   const bool host_loop = host_loop_mode();
   const uint64_t key = graph_key(o);
   auto it = P->graphs.find(key);
-  if (!host_loop && it == P->graphs.end()) {
+  if (it == P->graphs.end()) {  // also built in host-loop mode, for its kernel counts
     GraphEntry ge;
     mg_status st = build_graph(P, o, &ge);
     if (st) return st;
@@ -883,8 +882,12 @@ mg_status enqueue_solve(mg_problem* P, const mg_solve_opts& o, const double* rho
   CU(cudaMemcpyAsync(P->args, a, sizeof(SolveArgs), cudaMemcpyHostToDevice, s));
   CU(cudaEventRecord(P->ev0, s));
   if (host_loop) {
-    mg_status st = run_host_loop(P, o, s);
+    int passes = 0;
+    mg_status st = run_host_loop(P, o, s, &passes);
     if (st) return st;
+    // the graph's loop body also holds the loop guard, which the host loop replaces
+    P->last_fixed_kernels = it->second.fixed_kernels + passes * (it->second.body_kernels - 1);
+    P->last_body_kernels = 0;
   } else {
     CU(cudaGraphLaunch(it->second.exec, s));
     P->last_fixed_kernels = it->second.fixed_kernels;

@@ -274,7 +274,10 @@ def run_kernel_only(args):
     sfx = "f64" if f64 else "f32"
 
     def once():
-        if args.kernel.startswith("pipe"):
+        if args.kernel.startswith("march"):
+            mg.mgk("mgk_smooth_march_f32", C.byref(st), x.data_ptr(), x2.data_ptr(), b.data_ptr(), 0,
+                   None, 0, s)
+        elif args.kernel.startswith("pipe"):
             mg.mgk(f"mgk_smooth_pipe_{sfx}", C.byref(st), x.data_ptr(), x2.data_ptr(), b.data_ptr(), 0,
                    None, 0, None, s)
         elif args.kernel.startswith("fused"):
@@ -708,7 +711,7 @@ def main():
                     help="serve: open-loop arrival rates as fractions of the saturated rate")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel-only", dest="kernel", default=None,
-                    help="smooth64|smooth32|fused64|fused32|pipe64|pipe32|restrict64|restrict32|prolong64|prolong32")
+                    help="smooth64|smooth32|fused64|fused32|pipe64|pipe32|march32|restrict64|restrict32|prolong64|prolong32")
     ap.add_argument("--side", type=int, default=2049)
     ap.add_argument("--reps", type=int, default=5)
     args = ap.parse_args()

@@ -149,6 +149,17 @@ int mgk_smooth_pipe_f32(const mgk_op_f32 *A, const float *xin, float *xout, cons
                         int reverse, const float *eH, int pitch_c, int *err, void *stream);
 int mgk_pipe_sweeps(int f32);
 
+/* Row-marching variant for large FP32 levels: xout = mgk_march_sweeps() four-colour
+ * Gauss-Seidel sweeps (Sec. 2.1, omega = 1; reverse = 1 reverses the colour order) of
+ * xin [+ P eH] (Eq. 24) in one pass over the level.  Each CTA streams a strip of columns
+ * upward through a ring of rows in shared memory, so every array is read about once.
+ * Same result as mgk_smooth_fused_f32 up to FP32 rounding order (identical operations in
+ * the same order per node).  Needs xin != xout, 16-byte aligned arrays and a pitch that
+ * keeps rows 16-byte aligned (else returns 1); 4 on a CUDA error. */
+int mgk_smooth_march_f32(const mgk_op_f32 *A, const float *xin, float *xout, const float *b,
+                         int reverse, const float *eH, int pitch_c, void *stream);
+int mgk_march_sweeps(void);
+
 /* Weighted-Jacobi sweeps exactly as mgk_jacobi_f64, for callers that cannot allocate
  * device memory when they call it (a latency-critical loop where cudaMalloc/cudaFree would
  * synchronise the device, or an application whose device memory all belongs to another

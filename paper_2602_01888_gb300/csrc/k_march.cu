@@ -1,0 +1,415 @@
+// Row-marching temporally blocked smoother: NS four-colour Gauss-Seidel sweeps (Sec. 2.1,
+// omega = 1) in one pass over the level, with an optional prolongation-correction
+// (Eq. 24) of the iterate as it is read.
+//
+// Each CTA owns a strip of W = C - 2 HX columns and a segment of S rows.  It streams the
+// rows of the strip plus a halo of HX columns and HY = 4 NS rows on each side from the
+// bottom up through a ring of R rows in shared memory (all seven arrays: iterate, b, E,
+// N, NE, NW couplings, 1/diag).  Each ring row is stored de-interleaved (even columns,
+// then odd columns) so that the nodes of one colour and their neighbours are unit-stride.
+//
+// Phase ph (0 <= ph < 4 NS, colour ph mod 4, or reversed) runs on local row s - 2 ph at
+// step s.  Lagging consecutive phases by two rows makes the phases of one step touch
+// disjoint row triples: phase ph at row q reads rows q-1..q+1, which by then hold
+// exactly the state after phase ph-1 there (phase ph-1 ran on row q+1 one step earlier,
+// on row q-1 three steps earlier) and that phase ph+1 has not yet overwritten (it reaches
+// row q-1 one step later).  So a step needs one barrier, and at each step only the
+// phases whose colour lives on rows of the step's parity do work, 2 NS of them, one
+// thread group each.  As in a tile of the same halo, phase ph updates only rows and
+// columns at distance > ph from the loaded edge; after 4 NS phases the owned rows and
+// columns hold exactly the result of NS sequential sweeps.
+//
+// The threads of a CTA have one role each, in whole warps: compute threads run the
+// phases; loader threads request rows D steps ahead with asynchronous 16-byte copies into
+// a small staging ring (a barrier does not wait for these, unlike for plain loads, so the
+// copies stay in flight across steps) and de-interleave a landed row into the main ring;
+// writer threads copy finished owned rows out.  The iterate is read from xin and written
+// to xout (halos of neighbouring CTAs overlap).
+#include <cstdint>
+#include <type_traits>
+
+#include "mg_common.cuh"
+#include "mg_launch.h"
+#include "mg_march.h"
+
+namespace mg {
+
+template <typename T, int NS>
+struct MarchGeom;
+
+// FP32: 256 loaded columns (128 per parity).  1024 threads in three roles: 512 compute
+// threads (4 active phases x 128 nodes), 448 loaders (one 16-byte chunk of each of the 7
+// arrays' rows) and 64 writers (60 of them copy the owned 240 columns of a finished row).
+template <>
+struct MarchGeom<float, 2> {
+  static constexpr int C = 256, HX = 8, W = C - 2 * HX, HY = 8, R = 20, D = 6, NPT = 1;
+  static constexpr int THREADS = 1024;
+};
+
+template <typename T, int NS>
+struct MarchLayout {
+  using G = MarchGeom<T, NS>;
+  static constexpr int M = G::C / 2;              // nodes per parity half
+  static constexpr int VEC = 16 / sizeof(T);      // elements per 16-byte chunk
+  static constexpr int CHUNKS = G::C / VEC;       // chunks per array row
+  static constexpr int NPT = G::NPT;              // nodes per compute thread (m + k M/NPT)
+  static constexpr int COMPUTE = 2 * NS * M / NPT;  // compute threads of the active phases
+  static constexpr int LOADERS = 7 * CHUNKS;      // threads moving one row of all arrays
+  static constexpr int WRITERS = G::W / VEC;      // threads writing one owned row
+  static constexpr int ROW = 7 * G::C;            // elements of one ring row
+  static constexpr int RAWS = G::D + 1;           // staging slots: rows in flight + the landed one
+  // coarse values of the correction per x-loader thread and staging slot: two coarse rows
+  // of VEC/2 + 1 values
+  static constexpr int ESTAGE = 2 * (VEC / 2 + 1);
+  static constexpr size_t smem_elems =
+      (size_t)G::R * ROW + (size_t)RAWS * ROW + (size_t)RAWS * CHUNKS * ESTAGE;
+  static constexpr size_t smem_bytes = smem_elems * sizeof(T);
+  static_assert(COMPUTE + LOADERS + WRITERS <= G::THREADS, "one role per thread");
+  static_assert(COMPUTE % 32 == 0 && LOADERS % 32 == 0, "roles are whole warps");
+  static_assert(G::HY == 4 * NS && G::HX >= 4 * NS, "halo must cover the dependency cone");
+  static_assert((G::HX * sizeof(T)) % 16 == 0, "strip start must stay 16-byte aligned");
+  // rows touched at step s: s - 2 (4 NS - 1) - 2 (written out) .. s + 2 (de-interleaved)
+  static_assert(G::R >= 2 * (4 * NS - 1) + 5, "ring must hold the live rows");
+  static_assert(sizeof(T) == 4, "de-interleave of 16-byte chunks assumes FP32");
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Asynchronous global-to-shared copy of 4 or 16 bytes (zero-filled when src_bytes is 0).
+// Unlike a plain load it does not hold up the next barrier: its completion is awaited
+// with cp.async.wait_group, so copies stay in flight across steps.
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_addr(dst)), "l"(src),
+               "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_addr(dst)), "l"(src),
+               "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Dynamic shared memory of the kernel, indexed by element offsets (32-bit addressing).
+extern __shared__ __align__(16) float march_smem[];
+
+// Per-thread constants of one phase parity: which phase the thread's group runs on steps
+// of that parity and where its node and the node's left/right neighbours sit in a ring row.
+struct MarchLane {
+  int ph;                // phase index
+  int own, left, right;  // element offsets in a ring row (parity half * M + index)
+  int qlo, qhi;          // local rows the phase may update (halo shrink, grid rows)
+  bool col_ok;           // column inside the shrinking halo and an interior grid column
+};
+
+template <typename T, int NS>
+__global__ void __launch_bounds__(MarchGeom<T, NS>::THREADS, 1)
+    k_smooth_march(Lvl<T> L, const T* __restrict__ xin, T* __restrict__ xout,
+                   const T* __restrict__ b, int rev, const T* __restrict__ eH, int pitchc,
+                   int nyrc, int S, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  using G = MarchGeom<T, NS>;
+  using Y = MarchLayout<T, NS>;
+  constexpr int C = G::C, HX = G::HX, W = G::W, HY = G::HY, D = G::D, M = Y::M, VEC = Y::VEC;
+  constexpr int R = G::R, ROW = Y::ROW, RAWS = Y::RAWS;
+  constexpr int LAG = 2 * (4 * NS - 1);  // rows between phase 0 and the last phase
+  T* const sm = march_smem;  // ring at 0, staging rows at RAW0, coarse staging at EST0
+  constexpr int RAW0 = R * ROW, EST0 = RAW0 + RAWS * ROW;
+  T* const raw = sm + RAW0;
+  T* const estage = sm + EST0;
+
+  const int t = threadIdx.x;
+  const int X0 = blockIdx.x * W, Y0 = blockIdx.y * S;
+  const int Seff = min(S, L.nyr - Y0);
+  const int Q = Seff + 2 * HY;  // loaded rows, local q <-> global row jb + q
+  const int jb = Y0 - HY;       // global row of local row 0 (before periodic wrap)
+  const int xl0 = X0 - HX;      // global column of local column 0 (even)
+  const int p = L.pitch;
+  auto wrapR = [](int x) { return x < 0 ? x + R : (x >= R ? x - R : x); };
+
+  const bool computer = t < Y::COMPUTE;
+  const int lt = t - Y::COMPUTE;
+  const bool loader = lt >= 0 && lt < Y::LOADERS;
+  const int wt = t - Y::COMPUTE - Y::LOADERS;
+  const bool writer = wt >= 0 && wt < Y::WRITERS;
+
+  // ---- loader role: array la, chunk lc (VEC consecutive columns) of every row
+  const int la = loader ? lt / Y::CHUNKS : 0, lc = loader ? lt % Y::CHUNKS : 0;
+  const T* const lsrc = la == 0 ? xin : la == 1 ? b : la == 2 ? L.cE : la == 3 ? L.cN
+                       : la == 4 ? L.cNE : la == 5 ? L.cNW : L.dinv;
+  const int lcol = xl0 + lc * VEC;  // first global column of the chunk
+  const bool lcol_ok = lcol >= 0 && lcol + VEC <= p;
+  const int raw_off = la * C + lc * VEC;        // chunk in a staging row
+  const int put_off = la * C + lc * (VEC / 2);  // first even column in a ring row
+  const bool corr = loader && la == 0 && eH != nullptr;
+  T* const ed0 = estage + lc * Y::ESTAGE;        // + slot * CHUNKS * ESTAGE
+
+  // global row of local row q (wrapped on a periodic level), -1 outside a non-periodic grid
+  auto grow = [&](int q) -> int {
+    const int j = jb + q;
+    if (L.periodic) return j < 0 ? j + L.nyr : (j >= L.nyr ? j - L.nyr : j);
+    return (j >= 0 && j < L.nyr) ? j : -1;
+  };
+  // request local row q into staging slot rs, committed as one copy group
+  auto issue = [&](int q, int rs) {
+    if (loader && q < Q) {
+      const int j = grow(q);
+      const bool ok = lcol_ok && j >= 0;
+      cp_async16(raw + rs * ROW + raw_off, ok ? lsrc + (size_t)j * p + lcol : lsrc, ok ? 16 : 0);
+      if (corr) {
+        // coarse rows J = j >> 1 and the next one (wrapped when periodic), columns I0 ..
+        const int J = j >> 1;
+        int Jp = J + 1;
+        if (Jp == nyrc) Jp = L.periodic ? 0 : -1;
+        const int I0 = lcol >> 1;
+        T* ed = ed0 + rs * Y::CHUNKS * Y::ESTAGE;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          const int JJ = k ? Jp : J;
+#pragma unroll
+          for (int v = 0; v <= VEC / 2; ++v) {
+            const bool ev = j >= 0 && JJ >= 0 && I0 + v >= 0 && I0 + v < pitchc;
+            cp_async4(ed + k * (VEC / 2 + 1) + v, ev ? eH + (size_t)JJ * pitchc + I0 + v : eH,
+                      ev ? (int)sizeof(T) : 0);
+          }
+        }
+      }
+    }
+    cp_async_commit();
+  };
+  // the landed local row q (staging slot rs) into ring slot sr, de-interleaved; the
+  // x-loader adds P eH (bilinear, Eq. 24) to the unknowns of its chunk on the way, from
+  // coarse values its own copies brought
+  auto settle = [&](int q, int rs, int sr) {
+    if (!loader || q >= Q) return;
+    float4 v = *reinterpret_cast<const float4*>(raw + rs * ROW + raw_off);
+    if (corr) {
+      const int j = grow(q);
+      if (j >= 0) {
+        const T* ed = ed0 + rs * Y::CHUNKS * Y::ESTAGE;
+        T e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = lcol + u;
+          if (!is_unknown(L, i, j)) continue;
+          const int w = u >> 1;  // (i >> 1) - I0
+          const T a0 = ed[w], a1 = ed[w + 1], c0 = ed[VEC / 2 + 1 + w], c1 = ed[VEC / 2 + 2 + w];
+          T add;
+          if (!(i & 1) && !(j & 1)) add = a0;
+          else if ((i & 1) && !(j & 1)) add = T(0.5) * (a0 + a1);
+          else if (!(i & 1)) add = T(0.5) * (a0 + c0);
+          else add = T(0.25) * ((a0 + a1) + (c0 + c1));
+          e[u] += add;
+        }
+        v = make_float4(e[0], e[1], e[2], e[3]);
+      }
+    }
+    T* row = sm + sr * ROW + put_off;
+    *reinterpret_cast<float2*>(row) = make_float2(v.x, v.z);      // even columns
+    *reinterpret_cast<float2*>(row + M) = make_float2(v.y, v.w);  // odd columns
+  };
+
+  // ---- compute role: group grp runs phase 2 grp + parity on node m of a parity half
+  constexpr int MH = M / Y::NPT;  // compute threads per phase group
+  const int grp = computer ? t / MH : 0, m = computer ? t % MH : 0;
+  // rows a phase may touch: global unknown rows (all rows when periodic)
+  const int qrow_lo = L.periodic ? 0 : 1 - jb, qrow_hi = L.periodic ? Q : L.ny - 2 - jb;
+  // node mm of a parity half (mm = m or m + MH) for phase parity par
+  auto lane = [&](int par, int mm) {
+    MarchLane z;
+    z.ph = 2 * grp + par;
+    const int c = rev ? 3 - (z.ph & 3) : (z.ph & 3);
+    const int ci = colour_ci(c);
+    const int i = 2 * mm + ci;  // local column; its global column xl0 + i has parity ci
+    const int h = ci, o = 1 - ci;
+    z.own = h * M + mm;
+    z.left = o * M + mm - 1 + ci;
+    z.right = o * M + mm + ci;
+    z.col_ok = computer && i >= 1 + z.ph && i <= C - 2 - z.ph && xl0 + i >= 1 && xl0 + i <= L.nx - 2;
+    z.qlo = max(1 + z.ph, qrow_lo);
+    z.qhi = min(Q - 2 - z.ph, qrow_hi);
+    return z;
+  };
+  // lanes of the steps with s even and s odd (the phase parity is that of s + rev), for
+  // each of the thread's nodes
+  MarchLane l_even[Y::NPT], l_odd[Y::NPT];
+#pragma unroll
+  for (int k = 0; k < Y::NPT; ++k) {
+    l_even[k] = lane(rev & 1, m + k * MH);
+    l_odd[k] = lane((rev & 1) ^ 1, m + k * MH);
+  }
+
+  // ---- writer role: chunk wt of the owned columns of a finished row
+  const int wl = HX + wt * VEC;  // even local column of the chunk
+  const int wcol = xl0 + wl;
+  T* const wdst = xout + wcol;
+
+  // prologue: rows 0 and 1 settled, rows 2 .. D + 1 in flight (row r stages in slot r mod
+  // RAWS; RAWS = D + 1 slots hold the D rows in flight and the one being settled)
+  issue(0, 0);
+  issue(1, 1);
+  cp_async_wait<0>();
+  settle(0, 0, 0);
+  settle(1, 1, 1);
+#pragma unroll 1
+  for (int q = 2; q < D + 2; ++q) issue(q, q % RAWS);
+  __syncthreads();
+
+  const int last_step = HY + Seff - 1 + LAG + 2;  // the last owned row is written at this step
+  int sbase = 0;     // s mod R at the start of each unrolled block
+  int rsn = 2 % RAWS;  // staging slot of row s + 2
+#pragma unroll 1
+  for (int s0 = 0; s0 <= last_step; s0 += 2) {
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int s = s0 + u;
+      // phase ph of the thread's group on local row s - 2 ph, for each of its nodes (they
+      // share the phase, hence the row and the ring slots)
+      {
+        const MarchLane* zz = u ? l_odd : l_even;
+        const MarchLane& za = zz[0];
+        const int q = s - 2 * za.ph;
+        if (q >= za.qlo && q <= za.qhi) {
+          const int sq = wrapR(sbase + u - 2 * za.ph);
+          const int iR = sq * ROW;  // ring rows q, q + 1, q - 1; arrays at offsets a * C
+          const int iU = (sq + 1 == R ? 0 : sq + 1) * ROW;
+          const int iD = (sq == 0 ? R - 1 : sq - 1) * ROW;
+          auto update = [&](const MarchLane& z) {
+            const int ow = z.own, lf = z.left, rt = z.right;
+            const T* r0 = sm + iR;
+            const T* ru = sm + iU;
+            const T* rd = sm + iD;
+            T acc = r0[2 * C + ow] * r0[rt];
+            acc = fma(r0[2 * C + lf], r0[lf], acc);
+            acc = fma(r0[3 * C + ow], ru[ow], acc);
+            acc = fma(rd[3 * C + ow], rd[ow], acc);
+            acc = fma(r0[4 * C + ow], ru[rt], acc);
+            acc = fma(rd[4 * C + lf], rd[lf], acc);
+            acc = fma(r0[5 * C + ow], ru[lf], acc);
+            acc = fma(rd[5 * C + rt], rd[rt], acc);
+            return (r0[C + ow] - acc) * r0[6 * C + ow];
+          };
+          T v[Y::NPT];
+#pragma unroll
+          for (int k = 0; k < Y::NPT; ++k) v[k] = zz[k].col_ok ? update(zz[k]) : T(0);
+#pragma unroll
+          for (int k = 0; k < Y::NPT; ++k)
+            if (zz[k].col_ok) sm[iR + zz[k].own] = v[k];
+        }
+      }
+      // write-out: local row s - LAG - 2 is final (its last phase ran at step s - 2 at the
+      // latest); owned rows never wrap
+      if (writer) {
+        const int qo = s - LAG - 2;
+        if (qo >= HY && qo < HY + Seff) {
+          const T* xr = sm + wrapR(sbase + u - LAG - 2) * ROW;
+          const float2 ev = *reinterpret_cast<const float2*>(xr + wl / 2);
+          const float2 od = *reinterpret_cast<const float2*>(xr + M + wl / 2);
+          T* dst = wdst + (size_t)(jb + qo) * p;
+          if (wcol + VEC <= L.nx) {
+            *reinterpret_cast<float4*>(dst) = make_float4(ev.x, od.x, ev.y, od.y);
+          } else {
+            const T e[4] = {ev.x, od.x, ev.y, od.y};
+#pragma unroll
+            for (int v = 0; v < 4; ++v)
+              if (wcol + v < L.nx) dst[v] = e[v];
+          }
+        }
+      }
+      // loaders: request row s + 2 + D into the staging slot that row s + 1 left, then
+      // settle row s + 2 (requested D steps ago) into its ring slot, which last held row
+      // s + 2 - R, no longer read
+      {
+        const int rs_new = rsn == 0 ? RAWS - 1 : rsn - 1;  // slot of row s + 1
+        issue(s + 2 + D, rs_new);
+        cp_async_wait<D>();
+        settle(s + 2, rsn, wrapR(sbase + u + 2));
+        rsn = rsn + 1 == RAWS ? 0 : rsn + 1;
+      }
+      __syncthreads();
+    }
+    sbase = wrapR(sbase + 2);
+  }
+}
+
+template <typename T>
+struct MarchCfg;
+template <>
+struct MarchCfg<float> {
+  static constexpr int NS = 2;
+};
+
+template <typename T>
+int march_sweeps() {
+  return MarchCfg<T>::NS;
+}
+
+template <typename T>
+int march_strip_width() {
+  return MarchGeom<T, MarchCfg<T>::NS>::W;
+}
+
+template <typename T>
+cudaError_t launch_smooth_march(const Op<T>& A, const T* xin, T* xout, const T* b, int rev,
+                                const T* eH, int pitch_c, const int* skip, cudaStream_t s) {
+  constexpr int NS = MarchCfg<T>::NS;
+  using G = MarchGeom<T, NS>;
+  using Y = MarchLayout<T, NS>;
+  if (A.pitch % Y::VEC != 0) return cudaErrorInvalidValue;
+  if (((uintptr_t)xin | (uintptr_t)xout | (uintptr_t)b | (uintptr_t)A.cE | (uintptr_t)A.cN |
+       (uintptr_t)A.cNE | (uintptr_t)A.cNW | (uintptr_t)A.dinv) % 16 != 0)
+    return cudaErrorInvalidValue;
+  if (xin == xout) return cudaErrorInvalidValue;
+  auto kern = k_smooth_march<T, NS>;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)Y::smem_bytes);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  }
+  const Lvl<T> L = lvl_of(A);
+  const int strips = (L.nx + G::W - 1) / G::W;
+  // segment height S (even, so that local and global row parities agree): the choice with
+  // the least estimated time, counting the redundant halo rows of each segment and the
+  // idle SMs of a partly filled last wave (one resident CTA per SM)
+  int S = 0;
+  double best = 1e300;
+  for (int segs = 1; segs <= 256; ++segs) {
+    int s2 = (L.nyr + segs - 1) / segs;
+    s2 = (s2 + 1) & ~1;
+    if (s2 < 4 * G::HY && segs > 1) break;
+    const int n = (L.nyr + s2 - 1) / s2;
+    const int waves = (strips * n + nsm - 1) / nsm;
+    const double cost = (double)waves * (s2 + 2 * G::HY + 2 * (4 * NS - 1));
+    if (cost < best) {
+      best = cost;
+      S = s2;
+    }
+  }
+  const int segs = (L.nyr + S - 1) / S;
+  const int nyc = (A.ny - 1) / 2 + 1;
+  kern<<<dim3(strips, segs), G::THREADS, Y::smem_bytes, s>>>(
+      L, xin, xout, b, rev, eH, pitch_c, eH ? rows_stored(nyc, A.periodic) : 0, S, skip);
+  return cudaGetLastError();
+}
+
+template int march_sweeps<float>();
+template int march_strip_width<float>();
+template cudaError_t launch_smooth_march<float>(const Op<float>&, const float*, float*,
+                                                const float*, int, const float*, int, const int*,
+                                                cudaStream_t);
+
+}  // namespace mg

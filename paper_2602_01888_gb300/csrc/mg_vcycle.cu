@@ -1,8 +1,11 @@
-// One multigrid V(nu1, nu2) cycle (Sec. 3, Eqs. 19-24) enqueued on a stream:
-// levels above the tail threshold use the fused tile smoother (NS sweeps per launch,
-// ping-pong iterates) and the fused residual + full-weighting restriction; the levels
-// at and below it run in one single-CTA tail kernel that ends with the coarsest dense
-// solve.  The weighted-Jacobi smoother uses the per-sweep kernels on every level.
+// One multigrid V(nu1, nu2) cycle (Sec. 3, Eqs. 19-24) enqueued on a stream.  Smoothing
+// per level, by size: the largest FP32 levels use the row-marching kernel (two sweeps a
+// pass), other large FP32 levels the pipelined tile kernel, large FP64 levels the
+// per-colour kernels, mid-size levels the fused tile kernel (NS sweeps per launch,
+// ping-pong iterates); the residual is fused with full-weighting restriction; the levels
+// at and below the tail threshold run in one single-CTA tail kernel that ends with the
+// coarsest dense solve.  The weighted-Jacobi smoother uses the per-sweep kernels on every
+// level.
 #include <cstdlib>
 #include <cstring>
 
@@ -12,6 +15,7 @@
 #include "mg_kernels.h"
 #include "mg_launch.h"
 #include "mg_pipe.h"
+#include "mg_march.h"
 #include "mg_vcycle.h"
 
 namespace mg {
@@ -41,6 +45,17 @@ int colour_nodes() {
   if (v < 0) {
     const char* e = getenv(sizeof(T) == 8 ? "MG_COLOUR_NODES_F64" : "MG_COLOUR_NODES_F32");
     v = e ? atoi(e) : 40000;
+  }
+  return v;
+}
+
+// FP32 levels with at least this many nodes use the row-marching smoother (two sweeps a
+// pass); below it the grid has too few strips and segments to fill the GPU.
+inline long long march_nodes() {
+  static long long v = -1;
+  if (v < 0) {
+    const char* e = getenv("MG_MARCH_NODES");
+    v = e ? atoll(e) : 2000000;
   }
   return v;
 }
@@ -92,6 +107,21 @@ cudaError_t emit_vcycle(const VLevels<T>& V, int smoother, int nu1, int nu2, dou
     cudaError_t err;
     const long long nodes = (long long)V.A[l].nx * rows_stored(V.A[l].ny, V.A[l].periodic);
     const int nyr = rows_stored(V.A[l].ny, V.A[l].periodic);
+    // the largest FP32 levels: row-marching kernel
+    if constexpr (sizeof(T) == 4) {
+      const int ms = march_sweeps<float>();
+      if (nodes >= march_nodes() && sweeps % ms == 0 && V.A[l].pitch % 4 == 0) {
+        for (int k = 0; k < sweeps / ms; ++k) {
+          err = launch_smooth_march<float>(V.A[l], cur[l], alt[l], V.b[l], rev, k == 0 ? eH : nullptr,
+                                           eH ? V.A[l + 1].pitch : 0, skip, s);
+          if (err) return err;
+          T* tmp = cur[l];
+          cur[l] = alt[l];
+          alt[l] = tmp;
+        }
+        return cudaSuccess;
+      }
+    }
     // large FP32 levels: pipelined fused kernel
     if (sizeof(T) == 4 && nodes > cthr && sweeps % pipe_sweeps<T>() == 0 && nyr >= 64 &&
         V.A[l].nx >= 160 && V.A[l].pitch % 4 == 0) {
@@ -251,3 +281,17 @@ extern "C" int mgk_smooth_pipe_f32(const mgk_op_f32* A, const float* xin, float*
 }
 
 extern "C" int mgk_pipe_sweeps(int f32) { return f32 ? pipe_sweeps<float>() : pipe_sweeps<double>(); }
+
+extern "C" int mgk_smooth_march_f32(const mgk_op_f32* A, const float* xin, float* xout, const float* b,
+                                    int reverse, const float* eH, int pitch_c, void* stream) {
+  if (!A || A->nx < 3 || A->ny < 3 || A->pitch < A->nx || !xin || !xout || !b || xin == xout)
+    return 1;
+  if (A->periodic && (A->ny - 1) % 2) return 1;
+  if (eH && ((A->nx - 1) % 2 || (A->ny - 1) % 2 || pitch_c < (A->nx - 1) / 2 + 1)) return 1;
+  const cudaError_t e = launch_smooth_march<float>(op_from(*A), xin, xout, b, reverse, eH, pitch_c,
+                                                   nullptr, (cudaStream_t)stream);
+  if (e == cudaErrorInvalidValue) return 1;
+  return e == cudaSuccess ? 0 : 4;
+}
+
+extern "C" int mgk_march_sweeps(void) { return march_sweeps<float>(); }

@@ -154,6 +154,9 @@ _SIGS = {
     "mgk_smooth_pipe_f32": ([C.POINTER(mgk_op_f32), C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                              C.c_void_p, C.c_int, C.c_void_p, C.c_void_p], C.c_int),
     "mgk_pipe_sweeps": ([C.c_int], C.c_int),
+    "mgk_smooth_march_f32": ([C.POINTER(mgk_op_f32), C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                              C.c_void_p, C.c_int, C.c_void_p], C.c_int),
+    "mgk_march_sweeps": ([], C.c_int),
     "mgk_jacobi_f64_static": ([C.POINTER(mgk_op_f64), C.c_void_p, C.c_void_p, C.c_int, C.c_double,
                                C.c_void_p], C.c_int),
     "mgk_jacobi_f64_static_capacity": ([], C.c_size_t),

@@ -82,3 +82,26 @@ def test_annulus_full_size_sampled_residuals(libmg, oracle, ctx, cuda):
     assert worst <= RTOL * r0, (worst, RTOL * r0)
     # and the solution is not trivially small: it carries the source's scale
     assert np.abs(phi_h).max() > 1e-6
+
+
+def test_annulus_full_size_matches_oracle_golden(libmg, ctx, cuda):
+    """8193^2 annulus, mixed path at the benchmark's rtol, against the oracle's phi* at 4096
+    seeded sample nodes (tests/golden/annulus_8193_samples.npz, written by
+    tests/golden/make_golden.py from the oracle alone): relative L2 error over the samples
+    within the 1e-9 target."""
+    import os
+    torch = cuda
+    gold = np.load(os.path.join(os.path.dirname(__file__), "golden", "annulus_8193_samples.npz"))
+    inst = I.config3(8193)
+    g = inst.grid
+    prob = libmg.Problem(ctx, inst, libmg.make_opts("mixed", "fcg", rtol=RTOL, max_iters=400))
+    rho = torch.from_numpy(np.ascontiguousarray(inst.rho_phys)).cuda()
+    phi = torch.zeros(g.shape, dtype=torch.float64, device="cuda")
+    _, st = prob.solve(rho=rho, phi=phi)
+    jj = torch.from_numpy(gold["j"]).cuda()
+    ii = torch.from_numpy(gold["i"]).cuda()
+    got = phi[jj, ii].cpu().numpy()
+    prob.close()
+    ref = gold["phi"]
+    err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert err <= 1e-9, (err, st.iters, st.rel_residual)

@@ -126,8 +126,9 @@ PIPE_CASES = {
 @pytest.mark.parametrize("rev", [0, 1])
 @pytest.mark.parametrize("prolong", [False, True])
 def test_pipelined_and_tile_smoothers_match_oracle(libmg, oracle, cuda, case, prec, rev, prolong):
-    """k_smooth_pipe and k_smooth_fused (one launch each) against the oracle's sweeps,
-    with and without the fused prolongation-correction; rows padded to a 32-multiple pitch."""
+    """k_smooth_pipe, k_smooth_fused and (FP32) k_smooth_march, one launch each, against the
+    oracle's sweeps, with and without the fused prolongation-correction; rows padded to a
+    32-multiple pitch."""
     torch = cuda
     inst = PIPE_CASES[case]()
     P = oracle.prepare(inst)
@@ -158,15 +159,19 @@ def test_pipelined_and_tile_smoothers_match_oracle(libmg, oracle, cuda, case, pr
         pytest.skip("odd grid: no coarse level")
     stream = torch.cuda.current_stream().cuda_stream
     err = torch.zeros(1, dtype=torch.int32, device="cuda")
-    for kind in ("pipe", "fused"):
-        sweeps = libmg.lib().mgk_pipe_sweeps(int(prec == "f32")) if kind == "pipe" else \
-            libmg.lib().mgk_fused_sweeps(int(prec == "f32"))
+    kinds = ("pipe", "fused", "march") if prec == "f32" else ("pipe", "fused")
+    for kind in kinds:
+        sweeps = {"pipe": lambda: libmg.lib().mgk_pipe_sweeps(int(prec == "f32")),
+                  "fused": lambda: libmg.lib().mgk_fused_sweeps(int(prec == "f32")),
+                  "march": lambda: libmg.lib().mgk_march_sweeps()}[kind]()
         ref = oracle.smooth(P.A, start, b, sweeps=sweeps, reverse=bool(rev))
         xin, xout, b_d = padded(phi0), torch.zeros((g.nyr, pitch), dtype=dt, device="cuda"), padded(b)
         args = [C.byref(st), xin.data_ptr(), xout.data_ptr(), b_d.data_ptr(), rev,
                 eH_d.data_ptr() if eH_d is not None else None, pc]
         if kind == "pipe":
             libmg.mgk(f"mgk_smooth_pipe_{prec}", *args, err.data_ptr(), stream)
+        elif kind == "march":
+            libmg.mgk("mgk_smooth_march_f32", *args, stream)
         else:
             libmg.mgk(f"mgk_smooth_fused_{prec}", *args, stream)
         torch.cuda.synchronize()
@@ -174,3 +179,46 @@ def test_pipelined_and_tile_smoothers_match_oracle(libmg, oracle, cuda, case, pr
         got = xout[:, : g.nx].double().cpu().numpy()
         e = np.abs(got - ref).max() / np.abs(ref).max()
         assert e < (1e-13 if prec == "f64" else 1e-5), (kind, case, prec, rev, prolong, e)
+
+
+MARCH_CASES = {
+    "annulus_1025": lambda: I.annulus_log(1025),
+    "sine_1537x769": lambda: I.Instance("s", I.Grid(1537, 769, 0.0, 0.0, 2.0, 1.0),
+                                        I.MapSpec("sine_warp", (0.06,)), np.ones((769, 1537))),
+    "ragged_483x131": lambda: I.Instance("g", I.Grid(483, 131, 0.0, 0.0, 1.0, 0.27),
+                                         I.MapSpec("affine", (1.0, 0.2, -0.15, 1.1)),
+                                         np.ones((131, 483))),
+}
+
+
+@pytest.mark.parametrize("case", list(MARCH_CASES))
+@pytest.mark.parametrize("rev", [0, 1])
+def test_march_smoother_multi_strip_matches_oracle(libmg, oracle, cuda, case, rev):
+    """The row-marching FP32 smoother on grids of several strips and segments (and the
+    periodic seam of the annulus) against the oracle's sweeps; every node of xout written."""
+    torch = cuda
+    inst = MARCH_CASES[case]()
+    P = oracle.prepare(inst)
+    g = inst.grid
+    pitch = (g.nx + 31) // 32 * 32
+    rng = np.random.default_rng(43)
+    phi0 = rng.standard_normal(g.shape)
+    b = rng.standard_normal(g.shape) * np.abs(P.A.diag).max()
+
+    def padded(a):
+        t = torch.zeros((g.nyr, pitch), dtype=torch.float32, device="cuda")
+        t[:, : g.nx] = torch.from_numpy(np.array(a)).to("cuda", torch.float32)
+        return t
+
+    ops = [padded(a) for a in (P.A.cE, P.A.cN, P.A.cNE, P.A.cNW, P.A.diag, 1.0 / P.A.diag)]
+    st = libmg.op_struct(ops, g.nx, g.ny, g.periodic_y, f32=True)
+    ref = oracle.smooth(P.A, phi0, b, sweeps=libmg.lib().mgk_march_sweeps(), reverse=bool(rev))
+    xin, b_d = padded(phi0), padded(b)
+    xout = torch.full((g.nyr, pitch), float("nan"), dtype=torch.float32, device="cuda")
+    libmg.mgk("mgk_smooth_march_f32", C.byref(st), xin.data_ptr(), xout.data_ptr(), b_d.data_ptr(), rev,
+              None, 0, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    got = xout[:, : g.nx].double().cpu().numpy()
+    assert np.isfinite(got).all()
+    e = np.abs(got - ref).max() / np.abs(ref).max()
+    assert e < 1e-5, (case, rev, e)

@@ -14,7 +14,7 @@ MIXED_TOL = 1e-9
 
 def _ref(oracle, inst):
     P = oracle.prepare(inst)
-    phi, it, hist = oracle.pcg_solve(P.A, P.b, P.phi0, rtol=0.0, max_iters=400, stagnate=3)
+    phi, it, hist = oracle.pcg_solve(P.A, P.b, P.phi0, rtol=0.0, max_iters=400, stagnate=10)
     return phi
 
 
@@ -175,11 +175,12 @@ def test_server_results_equal_mg_solve_bitwise(libmg, ctx):
 
 def test_full_size_inclusion_1025(libmg, oracle, ctx):
     """The 1025^2 inclusion workload at the settings the benchmark uses (FP64 and mixed,
-    flexible CG, rtol 1e-9): error against the oracle's phi* within the 1e-9 target."""
+    flexible CG, residual tolerance 3e-8): error against the oracle's phi* within a tenth
+    of the 1e-9 target."""
     inst = I.config2(1025)
     ref = _ref(oracle, inst)
-    for prec, tol in (("fp64", 1e-9), ("mixed", 1e-9)):
-        prob = libmg.Problem(ctx, inst, libmg.make_opts(prec, "fcg", rtol=1e-9))
+    for prec, tol in (("fp64", 1e-10), ("mixed", 1e-10)):
+        prob = libmg.Problem(ctx, inst, libmg.make_opts(prec, "fcg", rtol=3e-8))
         phi, st = prob.solve()
         err = _err(oracle, inst, phi, ref)
         assert err <= tol, (prec, err, st.iters)

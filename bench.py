@@ -300,8 +300,10 @@ def run_kernel_only(args):
 
     def once():
         if args.kernel.startswith("march"):
+            # "march32p": with the coarse-grid correction fused (post-smoothing form)
+            corr = args.kernel.startswith("march32p")
             mg.mgk("mgk_smooth_march_f32", C.byref(st), x.data_ptr(), x2.data_ptr(), b.data_ptr(), 0,
-                   None, 0, s)
+                   bH.data_ptr() if corr else None, pc if corr else 0, s)
         elif args.kernel.startswith("pipe"):
             mg.mgk(f"mgk_smooth_pipe_{sfx}", C.byref(st), x.data_ptr(), x2.data_ptr(), b.data_ptr(), 0,
                    None, 0, None, s)
@@ -736,7 +738,8 @@ def main():
                     help="serve: open-loop arrival rates as fractions of the saturated rate")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel-only", dest="kernel", default=None,
-                    help="smooth64|smooth32|fused64|fused32|pipe64|pipe32|march32|restrict64|restrict32|prolong64|prolong32")
+                    help="smooth64|smooth32|fused64|fused32|pipe64|pipe32|march32|march32p|restrict64|restrict32|"
+                         "prolong64|prolong32")
     ap.add_argument("--side", type=int, default=2049)
     ap.add_argument("--reps", type=int, default=5)
     args = ap.parse_args()

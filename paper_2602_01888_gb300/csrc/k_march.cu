@@ -43,7 +43,7 @@ struct MarchGeom;
 template <>
 struct MarchGeom<float, 2> {
   static constexpr int C = 256, HX = 8, W = C - 2 * HX, HY = 8, R = 20, D = 6, NPT = 1;
-  static constexpr int THREADS = 1024;
+  static constexpr int THREADS = 1024, CTAS_PER_SM = 1;
 };
 
 template <typename T, int NS>
@@ -58,11 +58,12 @@ struct MarchLayout {
   static constexpr int WRITERS = G::W / VEC;      // threads writing one owned row
   static constexpr int ROW = 7 * G::C;            // elements of one ring row
   static constexpr int RAWS = G::D + 1;           // staging slots: rows in flight + the landed one
-  // coarse values of the correction per x-loader thread and staging slot: two coarse rows
-  // of VEC/2 + 1 values
-  static constexpr int ESTAGE = 2 * (VEC / 2 + 1);
+  // coarse correction staged per staging slot: the two coarse rows a fine row interpolates
+  // from, CW values each (the strip's C/2 + 1 coarse columns, rounded up to whole chunks)
+  static constexpr int CW = G::C / 2 + VEC, CCHUNKS = 2 * CW / VEC;
+  static constexpr int ESTAGE = 2 * CW;
   static constexpr size_t smem_elems =
-      (size_t)G::R * ROW + (size_t)RAWS * ROW + (size_t)RAWS * CHUNKS * ESTAGE;
+      (size_t)G::R * ROW + (size_t)RAWS * ROW + (size_t)RAWS * ESTAGE;
   static constexpr size_t smem_bytes = smem_elems * sizeof(T);
   static_assert(COMPUTE + LOADERS + WRITERS <= G::THREADS, "one role per thread");
   static_assert(COMPUTE % 32 == 0 && LOADERS % 32 == 0, "roles are whole warps");
@@ -109,7 +110,7 @@ struct MarchLane {
 };
 
 template <typename T, int NS>
-__global__ void __launch_bounds__(MarchGeom<T, NS>::THREADS, 1)
+__global__ void __launch_bounds__(MarchGeom<T, NS>::THREADS, MarchGeom<T, NS>::CTAS_PER_SM)
     k_smooth_march(Lvl<T> L, const T* __restrict__ xin, T* __restrict__ xout,
                    const T* __restrict__ b, int rev, const T* __restrict__ eH, int pitchc,
                    int nyrc, int S, const int* __restrict__ skip) {
@@ -148,7 +149,7 @@ __global__ void __launch_bounds__(MarchGeom<T, NS>::THREADS, 1)
   const int raw_off = la * C + lc * VEC;        // chunk in a staging row
   const int put_off = la * C + lc * (VEC / 2);  // first even column in a ring row
   const bool corr = loader && la == 0 && eH != nullptr;
-  T* const ed0 = estage + lc * Y::ESTAGE;        // + slot * CHUNKS * ESTAGE
+  const int I0b = xl0 >> 1;  // global coarse column of coarse staging column 0 (multiple of 4)
 
   // global row of local row q (wrapped on a periodic level), -1 outside a non-periodic grid
   auto grow = [&](int q) -> int {
@@ -163,51 +164,49 @@ __global__ void __launch_bounds__(MarchGeom<T, NS>::THREADS, 1)
       const bool ok = lcol_ok && j >= 0;
       cp_async16(raw + rs * ROW + raw_off, ok ? lsrc + (size_t)j * p + lcol : lsrc, ok ? 16 : 0);
       if (corr) {
-        // coarse rows J = j >> 1 and the next one (wrapped when periodic), columns I0 ..
+        // coarse rows J = j >> 1 and the next one (wrapped when periodic) over the strip's
+        // coarse columns, in 16-byte chunks shared out among the x-loader threads
         const int J = j >> 1;
         int Jp = J + 1;
         if (Jp == nyrc) Jp = L.periodic ? 0 : -1;
-        const int I0 = lcol >> 1;
-        T* ed = ed0 + rs * Y::CHUNKS * Y::ESTAGE;
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-          const int JJ = k ? Jp : J;
-#pragma unroll
-          for (int v = 0; v <= VEC / 2; ++v) {
-            const bool ev = j >= 0 && JJ >= 0 && I0 + v >= 0 && I0 + v < pitchc;
-            cp_async4(ed + k * (VEC / 2 + 1) + v, ev ? eH + (size_t)JJ * pitchc + I0 + v : eH,
-                      ev ? (int)sizeof(T) : 0);
-          }
+        T* ed = estage + rs * Y::ESTAGE;
+        for (int c = lc; c < Y::CCHUNKS; c += Y::CHUNKS) {
+          const int k = c / (Y::CW / VEC), cc = c % (Y::CW / VEC);
+          const int JJ = k ? Jp : J, I = I0b + cc * VEC;
+          const bool ev = j >= 0 && JJ >= 0 && I >= 0 && I + VEC <= pitchc;
+          cp_async16(ed + k * Y::CW + cc * VEC, ev ? eH + (size_t)JJ * pitchc + I : eH, ev ? 16 : 0);
         }
       }
     }
     cp_async_commit();
   };
   // the landed local row q (staging slot rs) into ring slot sr, de-interleaved; the
-  // x-loader adds P eH (bilinear, Eq. 24) to the unknowns of its chunk on the way, from
-  // coarse values its own copies brought
+  // x-loader adds P eH (bilinear, Eq. 24) to its chunk on the way.  The coarse correction
+  // is zero on the coarse boundary ring, so P eH vanishes at every fine node that is not an
+  // unknown and needs no mask.  The coarse rows were brought by the x-loaders' copies of
+  // the same group, so the whole x-loader warp pair waits for them (named barrier 1).
   auto settle = [&](int q, int rs, int sr) {
     if (!loader || q >= Q) return;
     float4 v = *reinterpret_cast<const float4*>(raw + rs * ROW + raw_off);
     if (corr) {
+      asm volatile("bar.sync 1, %0;" ::"n"(Y::CHUNKS) : "memory");
       const int j = grow(q);
       if (j >= 0) {
-        const T* ed = ed0 + rs * Y::CHUNKS * Y::ESTAGE;
-        T e[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int i = lcol + u;
-          if (!is_unknown(L, i, j)) continue;
-          const int w = u >> 1;  // (i >> 1) - I0
-          const T a0 = ed[w], a1 = ed[w + 1], c0 = ed[VEC / 2 + 1 + w], c1 = ed[VEC / 2 + 2 + w];
-          T add;
-          if (!(i & 1) && !(j & 1)) add = a0;
-          else if ((i & 1) && !(j & 1)) add = T(0.5) * (a0 + a1);
-          else if (!(i & 1)) add = T(0.5) * (a0 + c0);
-          else add = T(0.25) * ((a0 + a1) + (c0 + c1));
-          e[u] += add;
+        // local coarse columns 2 lc .. 2 lc + 2 of rows J (a) and J + 1 (c)
+        const T* ed = estage + rs * Y::ESTAGE + 2 * lc;
+        const T a0 = ed[0], a1 = ed[1], a2 = ed[2];
+        if (!(j & 1)) {
+          v.x += a0;
+          v.y += T(0.5) * (a0 + a1);
+          v.z += a1;
+          v.w += T(0.5) * (a1 + a2);
+        } else {
+          const T c0 = ed[Y::CW], c1 = ed[Y::CW + 1], c2 = ed[Y::CW + 2];
+          v.x += T(0.5) * (a0 + c0);
+          v.y += T(0.25) * ((a0 + a1) + (c0 + c1));
+          v.z += T(0.5) * (a1 + c1);
+          v.w += T(0.25) * ((a1 + a2) + (c1 + c2));
         }
-        v = make_float4(e[0], e[1], e[2], e[3]);
       }
     }
     T* row = sm + sr * ROW + put_off;
@@ -363,8 +362,9 @@ cudaError_t launch_smooth_march(const Op<T>& A, const T* xin, T* xout, const T* 
   using Y = MarchLayout<T, NS>;
   if (A.pitch % Y::VEC != 0) return cudaErrorInvalidValue;
   if (((uintptr_t)xin | (uintptr_t)xout | (uintptr_t)b | (uintptr_t)A.cE | (uintptr_t)A.cN |
-       (uintptr_t)A.cNE | (uintptr_t)A.cNW | (uintptr_t)A.dinv) % 16 != 0)
+       (uintptr_t)A.cNE | (uintptr_t)A.cNW | (uintptr_t)A.dinv | (uintptr_t)eH) % 16 != 0)
     return cudaErrorInvalidValue;
+  if (eH && pitch_c % Y::VEC != 0) return cudaErrorInvalidValue;
   if (xin == xout) return cudaErrorInvalidValue;
   auto kern = k_smooth_march<T, NS>;
   static bool attr = false;
@@ -384,7 +384,7 @@ cudaError_t launch_smooth_march(const Op<T>& A, const T* xin, T* xout, const T* 
   const int strips = (L.nx + G::W - 1) / G::W;
   // segment height S (even, so that local and global row parities agree): the choice with
   // the least estimated time, counting the redundant halo rows of each segment and the
-  // idle SMs of a partly filled last wave (one resident CTA per SM)
+  // idle SMs of a partly filled last wave (CTAS_PER_SM resident CTAs per SM)
   int S = 0;
   double best = 1e300;
   for (int segs = 1; segs <= 256; ++segs) {
@@ -392,7 +392,8 @@ cudaError_t launch_smooth_march(const Op<T>& A, const T* xin, T* xout, const T* 
     s2 = (s2 + 1) & ~1;
     if (s2 < 4 * G::HY && segs > 1) break;
     const int n = (L.nyr + s2 - 1) / s2;
-    const int waves = (strips * n + nsm - 1) / nsm;
+    const int slots = nsm * G::CTAS_PER_SM;
+    const int waves = (strips * n + slots - 1) / slots;
     const double cost = (double)waves * (s2 + 2 * G::HY + 2 * (4 * NS - 1));
     if (cost < best) {
       best = cost;

@@ -27,6 +27,21 @@ __device__ __forceinline__ unsigned bid() { return blockIdx.y * gridDim.x + bloc
 // Convergence decision, run by one thread of the last block.
 // recursive != 0: rr comes from the recursively updated CG residual; meeting rtol then
 // only requests a check of the true residual (residual replacement) in the next pass.
+// Scaling between the FP64 residual and the FP32 cycle by a power of two s (the factor
+// that brings the residual's rms to [1, 2)).  Multiplying by s in FP32 on the FP32 side of
+// the conversion is exact and gives the same value as multiplying in FP64, except for
+// entries so far below the rms that they leave the FP32 normal range on one side of the
+// conversion (more than 2^60 below it while |log2 s| <= 60), far under FP32 resolution of
+// the vector.  It keeps the multiply off the FP64 pipe (GB300 runs FP64 at 1/62 of the
+// FP32 rate).
+__device__ __forceinline__ bool pow2_fits_f32(double s) { return s >= 0x1p-60 && s <= 0x1p60; }
+__device__ __forceinline__ float to_f32_scaled(double v, double s, bool f32ok) {
+  return f32ok ? (float)v * (float)s : (float)(v * s);
+}
+__device__ __forceinline__ double from_f32_scaled(float v, double s, bool f32ok) {
+  return f32ok ? (double)(v * (float)s) : s * (double)v;
+}
+
 __device__ void decide(SolveState* st, double rr, cudaGraphConditionalHandle h, int has_h,
                        int recursive = 0) {
   const double rel = sqrt(rr) / st->r0;
@@ -172,7 +187,8 @@ __global__ void __launch_bounds__(kNT) k_r_to_f32(Lvl<double> L, const double* _
                                                   SolveState* st) {
   if (st->done) return;
   const double sc = st->scale;
-  NODE_LOOP(L) { b32[(size_t)j * pitch32 + i] = (float)(r[(size_t)j * L.pitch + i] * sc); }
+  const bool f32ok = pow2_fits_f32(sc);
+  NODE_LOOP(L) { b32[(size_t)j * pitch32 + i] = to_f32_scaled(r[(size_t)j * L.pitch + i], sc, f32ok); }
   if (bid() == 0 && threadIdx.x == 0) st->inv_scale_r32 = st->inv_scale;
 }
 
@@ -182,8 +198,10 @@ __global__ void __launch_bounds__(kNT) k_add_f32(Lvl<double> L, double* __restri
                                                  SolveState* st) {
   if (st->done) return;
   const double is = st->inv_scale_r32;
+  const bool f32ok = pow2_fits_f32(is);
   NODE_LOOP(L) {
-    if (is_unknown(L, i, j)) x[(size_t)j * L.pitch + i] += is * (double)e32[(size_t)j * pitch32 + i];
+    if (is_unknown(L, i, j))
+      x[(size_t)j * L.pitch + i] += from_f32_scaled(e32[(size_t)j * pitch32 + i], is, f32ok);
   }
 }
 
@@ -216,9 +234,13 @@ __global__ void __launch_bounds__(kNT) k_fcg_zq(Lvl<double> L, const TZ* __restr
   __shared__ double sh[kNT / 32];
   __shared__ int flag;
   const double is = (sizeof(TZ) == 4) ? st->inv_scale_r32 : 1.0;
+  const bool f32ok = pow2_fits_f32(is);
   double s = 0.0;
   NODE_LOOP(L) {
-    if (is_unknown(L, i, j)) s += (is * (double)z[(size_t)j * zp + i]) * q[(size_t)j * L.pitch + i];
+    if (is_unknown(L, i, j))
+      s += (sizeof(TZ) == 4 ? from_f32_scaled((float)z[(size_t)j * zp + i], is, f32ok)
+                            : (double)z[(size_t)j * zp + i]) *
+           q[(size_t)j * L.pitch + i];
   }
   const double a0 = block_sum<kNT>(s, sh);
   if (threadIdx.x == 0) part[bid()] = a0;
@@ -293,12 +315,13 @@ __global__ void __launch_bounds__(kNT) k_fcg_p32(Lvl<double> L, const float* __r
                                                  double* __restrict__ p, const SolveState* st) {
   if (st->done) return;
   const double is = st->inv_scale_r32;
+  const bool f32ok = pow2_fits_f32(is);
   const double beta = st->beta;
   const bool first = (st->it == 0);
   NODE_LOOP(L) {
     if (!is_unknown(L, i, j)) continue;
     const size_t k = (size_t)j * L.pitch + i;
-    const double zz = is * (double)z[(size_t)j * zp + i];
+    const double zz = from_f32_scaled(z[(size_t)j * zp + i], is, f32ok);
     p[k] = first ? zz : fma(beta, p[k], zz);
   }
 }
@@ -351,6 +374,7 @@ __global__ void __launch_bounds__(kNT) k_fcg_update(Lvl<double> L, double* __res
   __shared__ int flag;
   const double alpha = st->alpha;
   const double sc = st->scale;
+  const bool f32ok = pow2_fits_f32(sc);
   double s = 0.0;
   NODE_LOOP(L) {
     if (!is_unknown(L, i, j)) continue;
@@ -358,7 +382,7 @@ __global__ void __launch_bounds__(kNT) k_fcg_update(Lvl<double> L, double* __res
     x[k] = fma(alpha, p[k], x[k]);
     const double rv = fma(-alpha, q[k], r[k]);
     r[k] = rv;
-    if (r32) r32[(size_t)j * p32 + i] = (float)(rv * sc);
+    if (r32) r32[(size_t)j * p32 + i] = to_f32_scaled(rv, sc, f32ok);
     s = fma(rv, rv, s);
   }
   const double a0 = block_sum<kNT>(s, sh);
@@ -385,6 +409,7 @@ __global__ void __launch_bounds__(kNT) k_fcg_verify(Lvl<double> L, const double*
   __shared__ double sh[kNT / 32];
   __shared__ int flag;
   const double sc = st->scale;
+  const bool f32ok = pow2_fits_f32(sc);
   double s = 0.0;
   NODE_LOOP(L) {
     const size_t k = (size_t)j * L.pitch + i;
@@ -394,7 +419,7 @@ __global__ void __launch_bounds__(kNT) k_fcg_verify(Lvl<double> L, const double*
       s += rv * rv;
     }
     r[k] = rv;
-    if (r32) r32[(size_t)j * p32 + i] = (float)(rv * sc);
+    if (r32) r32[(size_t)j * p32 + i] = to_f32_scaled(rv, sc, f32ok);
   }
   const double a0 = block_sum<kNT>(s, sh);
   if (threadIdx.x == 0) part[bid()] = a0;

@@ -263,6 +263,35 @@ def measure_smoother(mg, torch, inst, prec, reps=20):
             "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2.07 GHz (probe: 1.20 TFLOP/s at 1.99 GHz)"}
 
 
+def measure_grid_generation(mg, torch, ctx, n, r, cpu=False):
+    """Numerical grid generation of the inclusion workload's mapped grid (Sec. 4.2) on the
+    GPU (mg_harmonic_grid: x' and y', device arrays, FCG to rtol 1e-13), timed with CUDA
+    events after one warm-up; with cpu=True also the numpy multigrid that generates the
+    workload inputs, for comparison."""
+    i0 = I.snap_ring(n, r)
+    ring, xp0, yp0 = I.inclusion_ring_data(n, i0)
+    g = I.Grid(n, n)
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    fx, xi, yi = d(ring.astype(np.uint8)), d(xp0), d(yp0)
+    xo, yo = torch.empty_like(xi), torch.empty_like(yi)
+    st = mg.mg_harmonic_grid(ctx.h, g, fx, xi, yi, xo, yo, rtol=1e-13)
+    torch.cuda.synchronize()
+    reps = 3
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        st = mg.mg_harmonic_grid(ctx.h, g, fx, xi, yi, xo, yo, rtol=1e-13)
+    e1.record()
+    torch.cuda.synchronize()
+    out = {"side": n, "gpu_ms": e0.elapsed_time(e1) / reps, "iters": [s.iters for s in st],
+           "rel_residual": max(s.rel_residual for s in st)}
+    if cpu:
+        t0 = time.perf_counter()
+        I._inclusion_grid_cached.__wrapped__(n, i0)
+        out["cpu_numpy_s"] = time.perf_counter() - t0
+    return out
+
+
 def run_kernel_only(args):
     """Run one library kernel `--reps` times on a sine-warp operator of side `--side`
     (built by the library's own kernels) and print its mean CUDA-event time per launch;
@@ -407,6 +436,9 @@ def run_ours(args):
         prob.close()
     del flush
     roof = measure_smoother(mg, torch, inst, precisions[0]) if rank == 0 else None
+    gridgen = None
+    if rank == 0 and grid_map and "r" in inst.meta:
+        gridgen = measure_grid_generation(mg, torch, ctx, g.nx, inst.meta["r"], cpu=not args.no_cpu_baseline)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         import oracle as O
@@ -435,6 +467,8 @@ def run_ours(args):
             "gpu_launches": args.steps * (rh["stats"].kernel_launches + rh["stats"].setup_kernel_launches),
             "roofline": roof, "cpu_baseline": cpu, "clocks": rh["clocks"],
         }
+        if gridgen:
+            line["grid_generation"] = gridgen
         for o in others:
             ro = res[o]
             line[o] = {"value": ws * U * args.steps / ro["tot"], "ms_per_step": 1e3 * ro["tot"] / args.steps,

@@ -190,6 +190,23 @@ mg_status mg_batch_solve(mg_ctx *ctx, int count, mg_problem *const *probs,
                          double *const *phi, mg_mem_kind mem, const mg_solve_opts *opts,
                          mg_solve_stats *stats);
 
+/*
+ * Numerical grid generation (Sec. 4.2, Eqs. 36-37): discrete-harmonic physical coordinates
+ * x'(x, y), y'(x, y) on the computational grid `grid`, with Dirichlet data on the outer
+ * boundary ring and at the interior nodes where fixed[] != 0 (for instance the ring of an
+ * immersed body carrying the Eq. 44 boundary map).  fixed (1 byte per node), xp, yp (node
+ * arrays, row-major, i fastest) have the memory kind `mem`; xp/yp hold the Dirichlet data at
+ * the outer ring and at fixed nodes and the initial guess elsewhere.  xp_out / yp_out
+ * (caller-owned, same kind) receive the solution at every node.  The 5-point Laplacian is
+ * solved to the relative residual rtol by the library's FP64 multigrid-preconditioned CG,
+ * with every coupling to a fixed interior node moved to the right-hand side.  stats
+ * (nullable) receives 2 entries (x', y').  Errors: MG_ERR_ARG, MG_ERR_SIZE, MG_ERR_OOM,
+ * MG_ERR_NOT_CONVERGED, MG_ERR_CUDA.
+ */
+mg_status mg_harmonic_grid(mg_ctx *ctx, const mg_grid_desc *grid, const unsigned char *fixed,
+                           const double *xp, const double *yp, double *xp_out, double *yp_out,
+                           mg_mem_kind mem, double rtol, mg_solve_stats *stats);
+
 /* ------------------------------------------------------------------ serving */
 typedef struct mg_server mg_server;
 

@@ -79,6 +79,7 @@ def lib():
             "orc_dense_solve": [i, i, i, D, D, D, D, D, D, D],
             "orc_paper_sor": [i, i, d, d, D, D, D, D, D, d, d, i],
             "orc_pcg_solve": [i, i, i, D, D, D, D, D, D, D, i, i, i, d, i, d, i, i, D],
+            "orc_mask_dirichlet": [i, i, i, D, D, D, D, D, ctypes.POINTER(ctypes.c_ubyte), D, D],
             "orc_hier_free": [ctypes.c_void_p],
             "orc_hier_vcycle": [ctypes.c_void_p, D, D],
         }
@@ -90,6 +91,7 @@ def lib():
         h.orc_hier_create.restype = ctypes.c_void_p
         h.orc_hier_free.restype = None
         h.orc_hier_vcycle.restype = None
+        h.orc_mask_dirichlet.restype = None
         _handle = h
     return _handle
 
@@ -335,6 +337,34 @@ def solve_instance(inst, rtol=1e-14, max_cycles=200, stagnate=3, **kw):
 
 
 # ---------------------------------------------------------------- error norms
+def mask_dirichlet(A: Operator, fixed, v):
+    """Operator and right-hand side with Dirichlet values v at the unknowns where fixed is
+    set (Sec. 4.2 grid generation with an internal boundary); returns (A', b)."""
+    B = Operator(A.nx, A.ny, A.periodic, *[a.copy() for a in A.arrays()])
+    fx = np.ascontiguousarray(np.asarray(fixed, dtype=np.uint8))
+    b = np.zeros(B.cE.shape)
+    lib().orc_mask_dirichlet(B.nx, B.ny, int(B.periodic), *[_p(a) for a in B.arrays()],
+                             fx.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)), _p(_f64(v)), _p(b))
+    return B, b
+
+
+def harmonic_grid(grid, fixed, xp, yp, rtol=0.0, max_iters=400, stagnate=10):
+    """Numerical grid generation (Sec. 4.2, Eqs. 36-37): x' and y' discrete-harmonic for the
+    identity map's operator (the 5-point Laplacian, eps = I), Dirichlet data on the outer
+    ring and at the fixed unknowns, solved by the oracle's MG-PCG from the given arrays
+    (rtol 0: to FP64 stagnation).  Returns (xp', yp', iterations)."""
+    ones = np.ones(grid.shape)
+    A = assemble(grid, ones, np.zeros(grid.shape), ones)
+    out, its = [], []
+    for v in (xp, yp):
+        B, b = mask_dirichlet(A, fixed, v)
+        phi, it, _ = pcg_solve(B, b, np.array(v, dtype=np.float64), rtol=rtol, max_iters=max_iters,
+                               stagnate=stagnate)
+        out.append(phi)
+        its.append(it)
+    return out[0], out[1], its
+
+
 def error_norms(exact, numerical):
     """(L_inf, L_2, L_1) over all N^2 nodes, Eqs. 25-27."""
     d = np.abs(np.asarray(exact) - np.asarray(numerical))

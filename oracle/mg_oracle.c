@@ -965,3 +965,69 @@ int orc_pcg_solve(int nx, int ny, int periodic, const double *cE, const double *
   orc_hier_free(H);
   return it;
 }
+
+/* ------------------------------------------------------------------------------------
+ * Numerical grid generation with internal Dirichlet nodes (Sec. 4.2, Eqs. 36-37).
+ * The coordinate x' (or y') is discrete-harmonic for the operator given (the identity
+ * map's 5-point Laplacian) at every free unknown; at unknowns with fixed[k] != 0 it equals
+ * v[k].  Rewrites the system so that the solver can treat every unknown alike: b[k] = v[k]
+ * and row k = e_k at fixed unknowns; at free unknowns b[k] = -(sum over fixed unknown
+ * neighbours m of A_km v[m]); every matrix entry between a fixed unknown and any other
+ * node is set to zero (the matrix stays symmetric).  Boundary-ring couplings of free nodes
+ * are kept: the ring carries its own Dirichlet values in phi.
+ * ------------------------------------------------------------------------------------ */
+void orc_mask_dirichlet(int nx, int ny, int periodic, double *cE, double *cN, double *cNE,
+                        double *cNW, double *diag, const unsigned char *fixed, const double *v,
+                        double *b) {
+  const int nyr = periodic ? ny - 1 : ny;
+  /* neighbour offsets and where the coupling to it is stored: (di, dj, array, storing node) */
+  for (int j = 0; j < nyr; ++j)
+    for (int i = 0; i < nx; ++i) {
+      const size_t k = (size_t)i + (size_t)nx * j;
+      b[k] = 0.0;
+      if (!is_interior(i, j, nx, ny, periodic)) continue;
+      if (fixed[k]) {
+        b[k] = v[k];
+        continue;
+      }
+      double s = 0.0;
+      for (int dj = -1; dj <= 1; ++dj)
+        for (int di = -1; di <= 1; ++di) {
+          if (di == 0 && dj == 0) continue;
+          int jj = j + dj, ii = i + di;
+          if (periodic) jj = (jj + nyr) % nyr;
+          if (!is_interior(ii, jj, nx, ny, periodic)) continue;
+          const size_t m = (size_t)ii + (size_t)nx * jj;
+          if (!fixed[m]) continue;
+          /* the entry A_km: stored at k for E, N, NE, NW; at m for W, S, SW, SE */
+          double c;
+          if (dj == 0) c = (di > 0) ? cE[k] : cE[m];
+          else if (di == 0) c = (dj > 0) ? cN[k] : cN[m];
+          else if (di == dj) c = (dj > 0) ? cNE[k] : cNE[m];
+          else c = (dj > 0) ? cNW[k] : cNW[m];
+          s += c * v[m];
+        }
+      b[k] = -s;
+    }
+  /* remove every entry that touches a fixed unknown; identity rows there */
+  for (int j = 0; j < nyr; ++j)
+    for (int i = 0; i < nx; ++i) {
+      const size_t k = (size_t)i + (size_t)nx * j;
+      const int kf = is_interior(i, j, nx, ny, periodic) && fixed[k];
+      int ju = j + 1;
+      int has_up = 1;
+      if (ju == nyr) {
+        if (periodic) ju = 0;
+        else has_up = 0;
+      }
+      const size_t ke = k + 1, kn = (size_t)i + (size_t)nx * ju;
+      if (i + 1 < nx && (kf || (is_interior(i + 1, j, nx, ny, periodic) && fixed[ke]))) cE[k] = 0.0;
+      if (has_up) {
+        if (kf || (is_interior(i, ju, nx, ny, periodic) && fixed[kn])) cN[k] = 0.0;
+        if (i + 1 < nx && (kf || (is_interior(i + 1, ju, nx, ny, periodic) && fixed[kn + 1])))
+          cNE[k] = 0.0;
+        if (i >= 1 && (kf || (is_interior(i - 1, ju, nx, ny, periodic) && fixed[kn - 1]))) cNW[k] = 0.0;
+      }
+      if (kf) diag[k] = 1.0;
+    }
+}

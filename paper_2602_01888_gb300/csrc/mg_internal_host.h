@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <functional>
 #include <map>
 #include <string>
 #include <mutex>
@@ -115,8 +116,10 @@ namespace mg {
 mg_status problem_create(mg_ctx* ctx, const mg_grid_desc* grid, const mg_solve_opts& o,
                          mg_problem** out);
 mg_status check_map(const mg_grid_desc* g, const mg_map_desc* m);
+// Work enqueued between the assembly of the finest operator and its coarsening.
+using FineHook = std::function<mg_status(mg_problem*, cudaStream_t)>;
 mg_status problem_enqueue_build(mg_problem* P, const mg_map_desc* map, const double* eps_phys,
-                                mg_mem_kind mem, cudaStream_t s);
+                                mg_mem_kind mem, cudaStream_t s, const FineHook* hook = nullptr);
 mg_status problem_check_build(mg_problem* P);
 mg_status enqueue_solve(mg_problem* P, const mg_solve_opts& o, const double* rho, const double* bc,
                         const double* phi_in, double* phi_out, cudaStream_t s);

@@ -297,7 +297,7 @@ static mg_status problem_alloc(mg_problem* P, bool mixed) {
 // coarsest inverse, enqueued on stream s.  Reads host or device inputs.  The map and SPD
 // flags land in P->h_flags; problem_check_build reads them once s has been synchronised.
 mg_status problem_enqueue_build(mg_problem* P, const mg_map_desc* map, const double* eps_phys,
-                                mg_mem_kind mem, cudaStream_t s) {
+                                mg_mem_kind mem, cudaStream_t s, const FineHook* hook) {
   const mg_grid_desc& g = P->grid;
   const int nx = g.nx, ny = g.ny, nyr = rows_stored(ny, g.periodic_y);
   const double hx = g.lx / (nx - 1), hy = g.ly / (ny - 1);
@@ -336,6 +336,10 @@ mg_status problem_enqueue_build(mg_problem* P, const mg_map_desc* map, const dou
                            pt, P->D, exx, exy, eyy, P->flags, s));
   }
   CU(launch_assemble(F.A, hx, hy, exx, exy, eyy, s));
+  if (hook && *hook) {  // a caller's change of the finest operator before coarsening
+    mg_status hs = (*hook)(P, s);
+    if (hs) return hs;
+  }
   if (!P->mixed) {
     for (int l = 1; l < P->nlev; ++l) CU(launch_galerkin<double>(P->lev[l - 1].A, P->lev[l].A, s));
   } else {

@@ -270,15 +270,16 @@ def _eq44_boundary(u, v, b):
     return xp, yp
 
 
-@lru_cache(maxsize=64)
-def _inclusion_grid_cached(n: int, i0: int):
+def inclusion_ring_data(n: int, i0: int):
+    """Dirichlet data of the inclusion grid: the ring of the inner square [i0, n-1-i0]^2
+    carries the Eq. 44 square-to-circle map, the outer boundary the identity.  Returns the
+    ring mask and x', y' arrays holding the identity everywhere except on the ring (the
+    initial guess of the harmonic solve)."""
     grid = Grid(n, n)
     x, y = grid.coords()
     xp, yp = x.copy(), y.copy()
-    fixed = np.zeros(grid.shape, dtype=bool)
-    fixed[0, :] = fixed[-1, :] = fixed[:, 0] = fixed[:, -1] = True
     i1 = n - 1 - i0
-    ring = np.zeros_like(fixed)
+    ring = np.zeros(grid.shape, dtype=bool)
     ring[i0:i1 + 1, i0] = ring[i0:i1 + 1, i1] = True
     ring[i0, i0:i1 + 1] = ring[i1, i0:i1 + 1] = True
     b = (i1 - i0) / 2 * grid.hx
@@ -286,7 +287,15 @@ def _inclusion_grid_cached(n: int, i0: int):
     bx, by = _eq44_boundary(x[ring] - c, y[ring] - c, b)
     xp[ring] = c + bx
     yp[ring] = c + by
-    fixed |= ring
+    return ring, xp, yp
+
+
+@lru_cache(maxsize=64)
+def _inclusion_grid_cached(n: int, i0: int):
+    grid = Grid(n, n)
+    ring, xp, yp = inclusion_ring_data(n, i0)
+    fixed = ring.copy()
+    fixed[0, :] = fixed[-1, :] = fixed[:, 0] = fixed[:, -1] = True
     # first guess: the identity outside the ring, the same square-to-disc boundary
     # data scaled inwards inside it (any guess converges; this one saves cycles)
     depth = _harmonic_depth(n, i0)

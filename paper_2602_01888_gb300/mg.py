@@ -107,6 +107,8 @@ _SIGS = {
     "mg_batch_solve": ([C.c_void_p, C.c_int, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
                         C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int,
                         C.POINTER(mg_solve_opts), C.POINTER(mg_solve_stats)], C.c_int),
+    "mg_harmonic_grid": ([C.c_void_p, C.POINTER(mg_grid_desc), C.c_void_p, C.c_void_p, C.c_void_p,
+                          C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.POINTER(mg_solve_stats)], C.c_int),
     "mg_server_start": ([C.c_void_p, C.POINTER(mg_server_opts), C.POINTER(C.c_void_p)], C.c_int),
     "mg_serve_submit": ([C.c_void_p, C.POINTER(mg_request), C.POINTER(C.c_uint64)], C.c_int),
     "mg_serve_poll": ([C.c_void_p, C.c_uint64, C.c_int, C.c_void_p, C.POINTER(mg_solve_stats)],
@@ -371,6 +373,21 @@ def mg_batch_solve(ctx: int, probs: Sequence[int], rhos, bcs, phis,
     _check(lib().mg_batch_solve(ctx, n, P, R, B, X, mem, C.byref(opts) if opts is not None else None,
                                 stats), "mg_batch_solve")
     return list(stats)[:n]
+
+
+def mg_harmonic_grid(ctx: int, grid, fixed, xp, yp, xp_out, yp_out, rtol: float = 1e-12):
+    """Discrete-harmonic x', y' (Sec. 4.2) with Dirichlet data on the outer ring and where
+    `fixed` (uint8 node array) is nonzero.  numpy arrays (host) or CUDA tensors (device).
+    Returns the two solves' statistics."""
+    mem = _mem_kind(xp, yp, xp_out, yp_out)
+    for a, nm in ((xp, "xp"), (yp, "yp"), (xp_out, "xp_out"), (yp_out, "yp_out")):
+        _check_array(a, grid.shape, nm)
+    if tuple(fixed.shape) != tuple(grid.shape):
+        raise ValueError("fixed: wrong shape")
+    stats = (mg_solve_stats * 2)()
+    _check(lib().mg_harmonic_grid(ctx, C.byref(grid_desc(grid)), _ptr(fixed), _ptr(xp), _ptr(yp),
+                                  _ptr(xp_out), _ptr(yp_out), mem, rtol, stats), "mg_harmonic_grid")
+    return list(stats)
 
 
 def mg_server_start(ctx: int, max_inflight=16, queue_capacity=65536, mem_budget=0, host_budget=0) -> int:

@@ -290,3 +290,49 @@ def test_inclusion_grid_boundary_data_and_positivity(oracle):
     assert np.abs(lap[free]).max() < 1e-12
     P = oracle.prepare(inst)
     assert P.status == 0 and P.D.min() > 0
+
+
+# ---------------------------------------------------------------- grid generation (Sec. 4.2)
+def _affine(x, y):
+    return 1.3 * x + 0.4 * y + 0.1, -0.2 * x + 0.9 * y - 0.05
+
+
+def test_harmonic_grid_reproduces_affine_maps_with_internal_dirichlet_nodes(oracle):
+    """Affine functions are discrete-harmonic for the 5-point Laplacian: with affine data on
+    the outer ring and at scattered fixed interior nodes, the generated grid is that map
+    at every node (and the fixed nodes keep their values)."""
+    g = I.Grid(33, 29, 0.0, 0.0, 1.0, 0.875)
+    x, y = g.coords()
+    ax, ay = _affine(x, y)
+    rng = np.random.default_rng(5)
+    fixed = (rng.random(g.shape) < 0.05) & g.interior_mask()
+    fixed[10, 5:20] = True  # a wall of fixed nodes
+    xp0 = np.where(fixed | ~g.interior_mask(), ax, 0.0)
+    yp0 = np.where(fixed | ~g.interior_mask(), ay, 0.0)
+    xo, yo, _ = oracle.harmonic_grid(g, fixed, xp0, yp0)
+    assert np.abs(xo - ax).max() < 1e-12 and np.abs(yo - ay).max() < 1e-12
+
+
+def test_harmonic_grid_matches_the_independent_masked_multigrid_of_the_inputs(oracle):
+    """The inclusion grid (ring carrying the Eq. 44 map) from the oracle's masked operator
+    and MG-PCG against the numpy red-black multigrid that generates the workloads' grids."""
+    n = 65
+    i0 = I.snap_ring(n, 0.25)
+    xref, yref = I._inclusion_grid_cached(n, i0)
+    g = I.Grid(n, n)
+    fixed, xp0, yp0 = I.inclusion_ring_data(n, i0)
+    xo, yo, _ = oracle.harmonic_grid(g, fixed, xp0, yp0)
+    assert np.abs(xo - xref).max() < 1e-11 and np.abs(yo - yref).max() < 1e-11
+
+
+def test_harmonic_grid_obeys_the_discrete_maximum_principle(oracle):
+    g = I.Grid(41, 41)
+    rng = np.random.default_rng(9)
+    data = rng.standard_normal(g.shape)
+    fixed = np.zeros(g.shape, dtype=bool)
+    fixed[20, 20] = True
+    v = np.where(fixed | ~g.interior_mask(), data, 0.0)
+    xo, _, _ = oracle.harmonic_grid(g, fixed, v, v)
+    lo, hi = data[fixed | ~g.interior_mask()].min(), data[fixed | ~g.interior_mask()].max()
+    assert xo.min() >= lo - 1e-12 and xo.max() <= hi + 1e-12
+    assert xo[20, 20] == data[20, 20]

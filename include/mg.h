@@ -128,6 +128,8 @@ void mg_default_opts(mg_solve_opts *opts);
 /* Create a context on CUDA device `device` with a device-memory budget (bytes, 0 = 90% of
  * free memory).  The context owns a memory pool and a stream (replace with mg_set_stream). */
 mg_status mg_create(int device, size_t mem_budget_bytes, mg_ctx **out);
+/* Waits for the device, then frees every problem of the context that is still alive and
+ * the context itself; handles of those problems must not be used afterwards. */
 void mg_destroy(mg_ctx *ctx);
 /* Run all later work of the context on `stream` (a cudaStream_t; NULL = the context's own). */
 mg_status mg_set_stream(mg_ctx *ctx, void *stream);

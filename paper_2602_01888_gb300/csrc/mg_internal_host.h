@@ -5,6 +5,7 @@
 #include <cstdint>
 #include <functional>
 #include <map>
+#include <set>
 #include <string>
 #include <mutex>
 #include <unordered_map>
@@ -81,6 +82,8 @@ struct BatchEntry {
 struct mg_ctx {
   int device = 0;
   mg::Pool pool;
+  std::set<mg_problem*> problems;  // live problems, freed by mg_destroy if still there
+  std::mutex problems_mu;          // the server's scheduler thread creates problems too
   std::map<std::string, mg::BatchEntry*> batches;
   cudaStream_t stream = nullptr, own_stream = nullptr, cap_stream = nullptr, cap_stream2 = nullptr;
   cudaStream_t batch[mg::kBatchStreams] = {};

@@ -190,6 +190,13 @@ extern "C" void mg_destroy(mg_ctx* c) {
   cudaSetDevice(c->device);
   cudaDeviceSynchronize();
   batch_cache_clear(c);
+  // problems the caller did not free: their memory belongs to this context's pool
+  std::vector<mg_problem*> left;
+  {
+    std::lock_guard<std::mutex> lk(c->problems_mu);
+    left.assign(c->problems.begin(), c->problems.end());
+  }
+  for (mg_problem* P : left) mg_problem_free(P);
   for (int k = 0; k < kBatchStreams; ++k) cudaStreamDestroy(c->batch[k]);
   cudaStreamDestroy(c->own_stream);
   cudaStreamDestroy(c->cap_stream);
@@ -432,6 +439,10 @@ mg_status problem_create(mg_ctx* ctx, const mg_grid_desc* grid, const mg_solve_o
     delete P;
     return set_error(st, "%s", keep);
   }
+  {
+    std::lock_guard<std::mutex> lk(ctx->problems_mu);
+    ctx->problems.insert(P);
+  }
   *out = P;
   return MG_OK;
 }
@@ -532,6 +543,10 @@ extern "C" void mg_problem_free(mg_problem* P) {
   cudaSetDevice(P->ctx->device);
   cudaStreamSynchronize(P->ctx->stream);
   batch_cache_clear(P->ctx);  // captured batches reference the problem's arrays
+  {
+    std::lock_guard<std::mutex> lk(P->ctx->problems_mu);
+    P->ctx->problems.erase(P);
+  }
   problem_release(P);
   delete P;
 }

@@ -453,8 +453,13 @@ def mgk(name: str, *args):
 
 # ------------------------------------------------------------------ convenience classes
 class Context:
+    """A library context.  Problems made on it are closed before it is (a problem must not
+    outlive its context: its memory belongs to the context's pool)."""
+
     def __init__(self, device: int = 0, mem_budget: int = 0):
+        import weakref
         self.h = mg_create(device, mem_budget)
+        self._problems = weakref.WeakSet()
 
     def use_torch_stream(self):
         mg_set_stream(self.h, _stream())
@@ -464,6 +469,8 @@ class Context:
 
     def close(self):
         if self.h:
+            for p in list(self._problems):
+                p.close()
             mg_destroy(self.h)
             self.h = None
 
@@ -491,6 +498,7 @@ class Problem:
             yp = None if yp is None else torch.from_numpy(np.array(yp)).cuda()
             eps = None if eps is None else torch.from_numpy(eps).cuda()
         self.h = mg_setup_transform(ctx.h, inst.grid, inst.map, eps, self.opts, xp, yp)
+        ctx._problems.add(self)
 
     def levels(self):
         return mg_problem_info(self.h)
@@ -510,7 +518,8 @@ class Problem:
 
     def close(self):
         if self.h:
-            mg_problem_free(self.h)
+            if self.ctx.h:  # a destroyed context has already released the problem
+                mg_problem_free(self.h)
             self.h = None
 
     def __del__(self):

@@ -37,7 +37,10 @@ HBM_PEAK_GBS = 6681.2
 # by (kernel, side); cold-cache figures (profiles/gs_colour_f64_1025.md).  Null for any
 # kernel or size not captured since its last change.
 MARCH_NODES = 2000000  # FP32 levels of at least this many nodes are smoothed by the marching kernel
-PROFILED_TRAFFIC = {("k_gs_colour<double>", 1025): (46.06e6 + 46.35e6 + 46.26e6 + 11.5e3) / 3}
+PROFILED_TRAFFIC = {("k_gs_colour<double>", 1025): (46.06e6 + 46.35e6 + 46.26e6 + 11.5e3) / 3,
+                    # captured at 4097^2 (profiles/march_f32_4097.md), scaled by the node count
+                    ("k_smooth_march<float,2>", 8193): (486.628e6 + 55.349e6) * (8193 / 4097) ** 2,
+                    ("k_smooth_march<float,2>", 4097): 486.628e6 + 55.349e6}
 
 # Single-instance workloads: (builder, precisions with the headline first, outer iteration,
 # residual tolerance, builder of the bounded CPU sample).  Each tolerance is calibrated so

@@ -365,6 +365,17 @@ def run_kernel_only(args):
     return 0
 
 
+def autotune(mg, ctx, max_side, enabled):
+    """Time the smoother families per level size on this GPU (mg_autotune) before the
+    problems are set up; returns {precision: {side: chosen family}} for the bench line."""
+    if not enabled:
+        return None
+    out = {}
+    for prec, side, _, choice in mg.mg_autotune(ctx.h, max(33, max_side)):
+        out.setdefault(prec, {})[str(side)] = choice
+    return out
+
+
 def run_ours(args):
     import torch
     from paper_2602_01888_gb300 import mg
@@ -380,6 +391,7 @@ def run_ours(args):
     n = g.nx * g.nyr
     ctx = mg.Context(local)
     ctx.use_torch_stream()
+    tuned = autotune(mg, ctx, max(g.nx, g.ny), not args.no_autotune)
     res = {}
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     dev = lambda a: None if a is None else torch.from_numpy(np.array(a, dtype=np.float64)).cuda()
@@ -472,6 +484,7 @@ def run_ours(args):
         }
         if gridgen:
             line["grid_generation"] = gridgen
+        line["autotune"] = tuned
         for o in others:
             ro = res[o]
             line[o] = {"value": ws * U * args.steps / ro["tot"], "ms_per_step": 1e3 * ro["tot"] / args.steps,
@@ -513,6 +526,7 @@ def run_batch(args):
     nodes = sum(x.grid.nx * x.grid.nyr for x in insts)
     ctx = mg.Context(local)
     ctx.use_torch_stream()
+    tuned = autotune(mg, ctx, 513, not args.no_autotune)
     dev = [dict(xp=_d64(torch, x.map.xp), yp=_d64(torch, x.map.yp), eps=_d64(torch, x.eps_phys),
                 rho=_d64(torch, x.rho_phys), phi=torch.zeros(x.grid.shape, dtype=torch.float64, device="cuda"))
            for x in insts]
@@ -628,7 +642,7 @@ def run_batch(args):
             "e2e": {"value": rm["e2e"], "unit": "unknowns/s", "h2d_bytes_per_step": 4 * 8 * nodes,
                     "d2h_bytes_per_step": 8 * nodes},
             "gpu_launches": args.steps * rm["launches"],
-            "roofline": roof, "cpu_baseline": cpu, "clocks": rm["clocks"],
+            "roofline": roof, "cpu_baseline": cpu, "clocks": rm["clocks"], "autotune": tuned,
         }
         print(json.dumps(line))
     ctx.close()
@@ -712,6 +726,7 @@ def run_serve(args):
     torch.cuda.set_device(local)
     mg.lib()
     ctx = mg.Context(local)
+    tuned = autotune(mg, ctx, args.serve_max_side, not args.no_autotune)
     reqs = _serve_requests(stream)
     U = sum(q[5] for q in reqs)
     warm = _serve_requests(warm_stream)
@@ -754,6 +769,7 @@ def run_serve(args):
             "e2e": {"value": ws * U / wall, "unit": "unknowns/s", "h2d_bytes_per_step": bytes_in,
                     "d2h_bytes_per_step": bytes_out},
             "gpu_launches": None, "roofline": None, "cpu_baseline": None, "clocks": clocks,
+            "autotune": tuned,
         }
         print(json.dumps(line))
     ctx.close()
@@ -774,6 +790,8 @@ def main():
     ap.add_argument("--serve-loads", type=float, nargs="*", default=[0.5, 0.8, 0.95],
                     help="serve: open-loop arrival rates as fractions of the saturated rate")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the size-threshold smoother choice instead of timing the families")
     ap.add_argument("--kernel-only", dest="kernel", default=None,
                     help="smooth64|smooth32|fused64|fused32|pipe64|pipe32|march32|march32p|restrict64|restrict32|"
                          "prolong64|prolong32")

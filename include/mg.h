@@ -209,6 +209,32 @@ mg_status mg_harmonic_grid(mg_ctx *ctx, const mg_grid_desc *grid, const unsigned
                            const double *xp, const double *yp, double *xp_out, double *yp_out,
                            mg_mem_kind mem, double rtol, mg_solve_stats *stats);
 
+/*
+ * Autotuner of the smoother per level size (project addition; the paper has a single
+ * sequential smoother).  For square levels of sides 33, 65, ..., up to max_side, in FP64 and
+ * FP32, it times two Gauss-Seidel sweeps (Sec. 2.1) with each kernel family that can run at
+ * that size -- per-colour kernels, fused shared-memory tiles, pipelined tiles, row marching
+ * (FP32) -- on a sine-warp operator built by the library, and records the fastest.  Every
+ * solve graph captured on the context afterwards takes, at each level, the choice of the
+ * tuned size nearest in node count (the families compute the same values, so results do not
+ * change); graphs captured before are dropped.  Call it when no solve or server is running
+ * on the context.  report (nullable) receives per (precision, side) the times in ms of the
+ * families in the order colour, fused, pipelined, marching (-1: cannot run) and the choice
+ * (1-4 in that order).
+ */
+#define MG_TUNE_MAX 32
+typedef struct {
+  int precision; /* MG_PREC_FP64 or MG_PREC_MIXED (the FP32 cycle) */
+  int side;
+  float ms[4];
+  int choice;
+} mg_tune_entry;
+typedef struct {
+  int count;
+  mg_tune_entry entry[MG_TUNE_MAX];
+} mg_tune_report;
+mg_status mg_autotune(mg_ctx *ctx, int max_side, mg_tune_report *report);
+
 /* ------------------------------------------------------------------ serving */
 typedef struct mg_server mg_server;
 

@@ -14,6 +14,7 @@
 #include "mg.h"
 #include "mg_launch.h"
 #include "mg_solve_kernels.h"
+#include "mg_vcycle.h"
 
 namespace mg {
 
@@ -87,6 +88,8 @@ struct mg_ctx {
   std::map<std::string, mg::BatchEntry*> batches;
   cudaStream_t stream = nullptr, own_stream = nullptr, cap_stream = nullptr, cap_stream2 = nullptr;
   cudaStream_t batch[mg::kBatchStreams] = {};
+  mg::SmoothPolicy pol[2];  // measured smoother choice: [0] FP64, [1] FP32 (mg_autotune)
+  int tuned = 0;
 };
 
 struct mg_problem {

@@ -587,6 +587,7 @@ static void level_table(mg_problem* P, T* x0, T* b0, VLevels<T>* V) {
   V->x[0] = x0;
   V->b[0] = b0;
   V->err = P->flags + 2;
+  V->pol = P->ctx->tuned ? &P->ctx->pol[sizeof(T) == 4 ? 1 : 0] : nullptr;
 }
 
 template <typename T>

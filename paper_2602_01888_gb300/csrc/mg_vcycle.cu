@@ -6,6 +6,7 @@
 // at and below the tail threshold run in one single-CTA tail kernel that ends with the
 // coarsest dense solve.  The weighted-Jacobi smoother uses the per-sweep kernels on every
 // level.
+#include <cmath>
 #include <cstdlib>
 #include <cstring>
 
@@ -60,6 +61,20 @@ inline long long march_nodes() {
   return v;
 }
 
+int SmoothPolicy::lookup(long long nodes) const {
+  if (n <= 0 || nodes <= 0) return SK_DEFAULT;
+  int best = 0;
+  double bd = 1e300;
+  for (int k = 0; k < n; ++k) {
+    const double d = fabs(log((double)nodes) - 2.0 * log((double)side[k]));
+    if (d < bd) {
+      bd = d;
+      best = k;
+    }
+  }
+  return kind[best];
+}
+
 template <typename T>
 cudaError_t emit_vcycle(const VLevels<T>& V, int smoother, int nu1, int nu2, double omega,
                         const int* skip, cudaStream_t s, T** result) {
@@ -107,48 +122,67 @@ cudaError_t emit_vcycle(const VLevels<T>& V, int smoother, int nu1, int nu2, dou
     cudaError_t err;
     const long long nodes = (long long)V.A[l].nx * rows_stored(V.A[l].ny, V.A[l].periodic);
     const int nyr = rows_stored(V.A[l].ny, V.A[l].periodic);
-    // the largest FP32 levels: row-marching kernel
-    if constexpr (sizeof(T) == 4) {
-      const int ms = march_sweeps<float>();
-      if (nodes >= march_nodes() && sweeps % ms == 0 && V.A[l].pitch % 4 == 0) {
-        for (int k = 0; k < sweeps / ms; ++k) {
+    const int pc = eH ? V.A[l + 1].pitch : 0;
+    // which families can run this level with this many sweeps
+    const bool can_march = sizeof(T) == 4 && sweeps % march_sweeps<float>() == 0 && sweeps > 0 &&
+                           V.A[l].pitch % 4 == 0 && nyr >= 128;
+    const bool can_pipe = sweeps % pipe_sweeps<T>() == 0 && sweeps > 0 && nyr >= 64 && V.A[l].nx >= 160 &&
+                          V.A[l].pitch % (16 / (int)sizeof(T)) == 0 &&
+                          (!V.A[l].periodic || nyr % (32 / (int)sizeof(T)) == 0);
+    const bool can_fused = sweeps % NS == 0 && sweeps > 0;
+    // size-threshold rule
+    int kind;
+    if (sizeof(T) == 4 && nodes >= march_nodes() && sweeps % march_sweeps<float>() == 0 && sweeps > 0 &&
+        V.A[l].pitch % 4 == 0)
+      kind = SK_MARCH;
+    else if (sizeof(T) == 4 && nodes > cthr && can_pipe)
+      kind = SK_PIPE;
+    else if (sweeps % NS != 0 || nodes > cthr)
+      kind = SK_COLOUR;
+    else
+      kind = SK_FUSED;
+    // measured choice, where it can run
+    if (V.pol) {
+      const int k = V.pol->lookup(nodes);
+      if ((k == SK_MARCH && can_march) || (k == SK_PIPE && can_pipe) || (k == SK_FUSED && can_fused) ||
+          k == SK_COLOUR)
+        kind = k;
+    }
+    auto swap_cur = [&]() {
+      T* tmp = cur[l];
+      cur[l] = alt[l];
+      alt[l] = tmp;
+    };
+    if (kind == SK_MARCH) {
+      if constexpr (sizeof(T) == 4) {
+        for (int k = 0; k < sweeps / march_sweeps<float>(); ++k) {
           err = launch_smooth_march<float>(V.A[l], cur[l], alt[l], V.b[l], rev, k == 0 ? eH : nullptr,
-                                           eH ? V.A[l + 1].pitch : 0, skip, s);
+                                           pc, skip, s);
           if (err) return err;
-          T* tmp = cur[l];
-          cur[l] = alt[l];
-          alt[l] = tmp;
+          swap_cur();
         }
         return cudaSuccess;
       }
     }
-    // large FP32 levels: pipelined fused kernel
-    if (sizeof(T) == 4 && nodes > cthr && sweeps % pipe_sweeps<T>() == 0 && nyr >= 64 &&
-        V.A[l].nx >= 160 && V.A[l].pitch % 4 == 0) {
+    if (kind == SK_PIPE) {
       for (int k = 0; k < sweeps / pipe_sweeps<T>(); ++k) {
-        err = launch_smooth_pipe<T>(V.A[l], cur[l], alt[l], V.b[l], rev, k == 0 ? eH : nullptr,
-                                    eH ? V.A[l + 1].pitch : 0, skip, V.err, s);
+        err = launch_smooth_pipe<T>(V.A[l], cur[l], alt[l], V.b[l], rev, k == 0 ? eH : nullptr, pc, skip,
+                                    V.err, s);
         if (err) return err;
-        T* tmp = cur[l];
-        cur[l] = alt[l];
-        alt[l] = tmp;
+        swap_cur();
       }
       return cudaSuccess;
     }
-    if (sweeps % NS != 0 || nodes > cthr) {  // per-colour kernels, in place
-      if (eH && (err = launch_prolong_add(V.A[l], cur[l], eH, V.A[l + 1].pitch, skip, s))) return err;
+    if (kind == SK_COLOUR || (kind == SK_MARCH && sizeof(T) == 8)) {  // per-colour kernels, in place
+      if (eH && (err = launch_prolong_add(V.A[l], cur[l], eH, pc, skip, s))) return err;
       return launch_smooth(V.A[l], cur[l], V.b[l], sweeps, rev, skip, s);
     }
     for (int k = 0; k < sweeps / NS; ++k) {
-      err = launch_smooth_fused(V.A[l], cur[l], alt[l], V.b[l], rev, k == 0 ? eH : nullptr,
-                                eH ? V.A[l + 1].pitch : 0, skip, s);
+      err = launch_smooth_fused(V.A[l], cur[l], alt[l], V.b[l], rev, k == 0 ? eH : nullptr, pc, skip, s);
       if (err) return err;
-      T* tmp = cur[l];
-      cur[l] = alt[l];
-      alt[l] = tmp;
+      swap_cur();
     }
-    if (sweeps == 0 && eH)
-      return launch_prolong_add(V.A[l], cur[l], eH, V.A[l + 1].pitch, skip, s);
+    if (sweeps == 0 && eH) return launch_prolong_add(V.A[l], cur[l], eH, pc, skip, s);
     return cudaSuccess;
   };
   for (int l = 0; l < t; ++l) {

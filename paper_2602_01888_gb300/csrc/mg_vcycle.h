@@ -8,6 +8,21 @@ namespace mg {
 
 constexpr int kMaxVLevels = 24;
 
+// Smoother family for a level: the per-colour kernels (four launches a sweep), the fused
+// tile kernel, the pipelined tile kernel, the row-marching kernel (FP32).
+enum SmoothKind : int { SK_DEFAULT = 0, SK_COLOUR = 1, SK_FUSED = 2, SK_PIPE = 3, SK_MARCH = 4 };
+
+// Measured choice of smoother family by level size (filled by mg_autotune): entry k says
+// that square levels of side[k] smooth fastest with kind[k].  A level takes the choice of the
+// entry nearest to it in node count (log scale); kinds that cannot run on a level fall back
+// to the size-threshold rule.
+struct SmoothPolicy {
+  int n = 0;
+  int side[16] = {};
+  int kind[16] = {};
+  int lookup(long long nodes) const;
+};
+
 // A hierarchy as seen by one cycle: level l operator, iterate x, right-hand side b and a
 // second iterate array t (ping-pong partner / residual scratch); inv = coarsest inverse.
 template <typename T>
@@ -19,6 +34,7 @@ struct VLevels {
   T* t[kMaxVLevels];
   const double* inv = nullptr;
   int* err = nullptr;  // device flag set when a bounded wait of a kernel gives up
+  const SmoothPolicy* pol = nullptr;  // measured smoother choice (nullable)
 };
 
 // Enqueue one V(nu1, nu2) cycle starting from the iterate in V.x[0]; *result receives the

@@ -80,6 +80,17 @@ class mg_request(C.Structure):
                 ("rho_phys", C.c_void_p), ("bc", C.c_void_p), ("opts", mg_solve_opts)]
 
 
+class mg_tune_entry(C.Structure):
+    _fields_ = [("precision", C.c_int), ("side", C.c_int), ("ms", C.c_float * 4), ("choice", C.c_int)]
+
+
+class mg_tune_report(C.Structure):
+    _fields_ = [("count", C.c_int), ("entry", mg_tune_entry * 32)]
+
+
+SMOOTHER_FAMILIES = {1: "colour", 2: "fused", 3: "pipelined", 4: "marching"}
+
+
 class mg_serve_report(C.Structure):
     _fields_ = [("completed", C.c_uint64), ("failed", C.c_uint64), ("wall_s", C.c_double),
                 ("unknowns_per_s", C.c_double), ("p50_ms", C.c_double), ("p99_ms", C.c_double),
@@ -109,6 +120,7 @@ _SIGS = {
                         C.POINTER(mg_solve_opts), C.POINTER(mg_solve_stats)], C.c_int),
     "mg_harmonic_grid": ([C.c_void_p, C.POINTER(mg_grid_desc), C.c_void_p, C.c_void_p, C.c_void_p,
                           C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.POINTER(mg_solve_stats)], C.c_int),
+    "mg_autotune": ([C.c_void_p, C.c_int, C.POINTER(mg_tune_report)], C.c_int),
     "mg_server_start": ([C.c_void_p, C.POINTER(mg_server_opts), C.POINTER(C.c_void_p)], C.c_int),
     "mg_serve_submit": ([C.c_void_p, C.POINTER(mg_request), C.POINTER(C.c_uint64)], C.c_int),
     "mg_serve_poll": ([C.c_void_p, C.c_uint64, C.c_int, C.c_void_p, C.POINTER(mg_solve_stats)],
@@ -388,6 +400,20 @@ def mg_harmonic_grid(ctx: int, grid, fixed, xp, yp, xp_out, yp_out, rtol: float 
     _check(lib().mg_harmonic_grid(ctx, C.byref(grid_desc(grid)), _ptr(fixed), _ptr(xp), _ptr(yp),
                                   _ptr(xp_out), _ptr(yp_out), mem, rtol, stats), "mg_harmonic_grid")
     return list(stats)
+
+
+def mg_autotune(ctx: int, max_side: int = 2049):
+    """Time the smoother families per level size and make the fastest the context's choice.
+    Returns [(precision, side, {family: ms}, chosen family)]."""
+    r = mg_tune_report()
+    _check(lib().mg_autotune(ctx, max_side, C.byref(r)), "mg_autotune")
+    out = []
+    for k in range(r.count):
+        e = r.entry[k]
+        ms = {SMOOTHER_FAMILIES[f + 1]: float(e.ms[f]) for f in range(4) if e.ms[f] > 0}
+        out.append(("mixed" if e.precision == MG_PREC_MIXED else "fp64", e.side, ms,
+                    SMOOTHER_FAMILIES.get(e.choice, "default")))
+    return out
 
 
 def mg_server_start(ctx: int, max_inflight=16, queue_capacity=65536, mem_budget=0, host_budget=0) -> int:

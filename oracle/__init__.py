@@ -39,6 +39,7 @@ _handle = None
 
 SMOOTHER_GS4 = 0
 SMOOTHER_JACOBI = 1
+SMOOTHER_XLINE = 2  # zebra x-line Gauss-Seidel
 DEFAULT_COARSE_MAX = 64
 
 
@@ -79,6 +80,7 @@ def lib():
             "orc_dense_solve": [i, i, i, D, D, D, D, D, D, D],
             "orc_paper_sor": [i, i, d, d, D, D, D, D, D, d, d, i],
             "orc_pcg_solve": [i, i, i, D, D, D, D, D, D, D, i, i, i, d, i, d, i, i, D],
+            "orc_line_rows": [i, i, i, D, D, D, D, D, D, D, i],
             "orc_mask_dirichlet": [i, i, i, D, D, D, D, D, ctypes.POINTER(ctypes.c_ubyte), D, D],
             "orc_hier_free": [ctypes.c_void_p],
             "orc_hier_vcycle": [ctypes.c_void_p, D, D],
@@ -209,6 +211,13 @@ def residual(A: Operator, phi, b):
 def smooth(A: Operator, phi, b, sweeps=1, reverse=False, smoother=SMOOTHER_GS4, omega_j=0.8):
     out = _f64(phi).copy()
     lib().orc_smooth(*A._args(), _p(out), _p(_f64(b)), smoother, sweeps, int(reverse), omega_j)
+    return out
+
+
+def line_rows(A: Operator, phi, b, parity):
+    """One half-sweep of zebra x-line Gauss-Seidel on the rows j with j mod 2 == parity."""
+    out = _f64(phi).copy()
+    lib().orc_line_rows(*A._args(), _p(out), _p(_f64(b)), parity)
     return out
 
 

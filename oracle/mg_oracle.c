@@ -328,6 +328,52 @@ static void jacobi(const op_t *A, double *phi, const double *b, double *tmp, int
   }
 }
 
+/* One half-sweep of x-line Gauss-Seidel in zebra order: every row j of parity par
+ * (j mod 2 == par) is solved as a whole.  On that row the couplings to its own unknowns
+ * (W and E) stay in a tridiagonal system; the couplings to the rows above and below (N, S
+ * and the four diagonals) and to the row's two Dirichlet end nodes go to the right-hand
+ * side with the current values of those nodes.  Rows of one parity share no coupling, so
+ * they can be solved in any order.  The tridiagonal system is solved by the Thomas
+ * algorithm (forward elimination, back substitution). */
+static void line_rows(const op_t *A, double *phi, const double *b, int par) {
+  const int nx = A->nx, N = nx - 2;
+  if (N < 1) return;
+  double *cp = (double *)calloc((size_t)N, sizeof(double));
+  double *dp = (double *)calloc((size_t)N, sizeof(double));
+  for (int j = par; j < A->nyr; j += 2) {
+    if (!is_interior(1, j, nx, A->ny, A->periodic)) continue;
+    const int ju = A->periodic ? wrapj(j + 1, A->nyr) : j + 1;
+    const int jd = A->periodic ? wrapj(j - 1, A->nyr) : j - 1;
+    const size_t r0 = (size_t)nx * j, ru = (size_t)nx * ju, rd = (size_t)nx * jd;
+    for (int t = 0; t < N; ++t) {
+      const int i = t + 1;
+      const size_t k = r0 + i;
+      /* couplings leaving the row: N, S, NE, SW, NW, SE, and the Dirichlet ends */
+      double off = A->cN[k] * phi[ru + i] + A->cN[rd + i] * phi[rd + i];
+      off += A->cNE[k] * phi[ru + i + 1] + A->cNE[rd + i - 1] * phi[rd + i - 1];
+      off += A->cNW[k] * phi[ru + i - 1] + A->cNW[rd + i + 1] * phi[rd + i + 1];
+      if (i == 1) off += A->cE[r0] * phi[r0];
+      if (i == nx - 2) off += A->cE[k] * phi[k + 1];
+      const double rhs = b[k] - off;
+      const double sub = (i - 1 >= 1) ? A->cE[k - 1] : 0.0;
+      const double sup = (i + 1 <= nx - 2) ? A->cE[k] : 0.0;
+      const double m = (t == 0) ? A->diag[k] : A->diag[k] - sub * cp[t - 1];
+      cp[t] = sup / m;
+      dp[t] = (t == 0) ? rhs / m : (rhs - sub * dp[t - 1]) / m;
+    }
+    phi[r0 + N] = dp[N - 1];
+    for (int t = N - 2; t >= 0; --t) phi[r0 + t + 1] = dp[t] - cp[t] * phi[r0 + t + 2];
+  }
+  free(cp);
+  free(dp);
+}
+
+/* sweeps of zebra x-line Gauss-Seidel: rows of parity 0 then 1 (reverse: 1 then 0). */
+static void xline(const op_t *A, double *phi, const double *b, int sweeps, int reverse) {
+  for (int s = 0; s < sweeps; ++s)
+    for (int h = 0; h < 2; ++h) line_rows(A, phi, b, reverse ? 1 - h : h);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Grid transfers                                                              */
 /* ------------------------------------------------------------------------ */
@@ -624,6 +670,7 @@ static void smooth(hier_t *H, int l, int sweeps, int reverse) {
   op_t A = op_of(H, l);
   level_t *L = &H->lev[l];
   if (H->smoother == 1) jacobi(&A, L->phi, L->b, L->r, sweeps, H->omega_j);
+  else if (H->smoother == 2) xline(&A, L->phi, L->b, sweeps, reverse);
   else gs4(&A, L->phi, L->b, sweeps, reverse);
 }
 
@@ -737,9 +784,20 @@ int orc_smooth(int nx, int ny, int periodic, const double *cE, const double *cN,
     double *tmp = xcalloc((size_t)nx * A.nyr);
     jacobi(&A, phi, b, tmp, sweeps, omega_j);
     free(tmp);
+  } else if (smoother == 2) {
+    xline(&A, phi, b, sweeps, reverse);
   } else {
     gs4(&A, phi, b, sweeps, reverse);
   }
+  return ORC_OK;
+}
+
+/* One half-sweep of zebra x-line Gauss-Seidel on the rows of parity par only. */
+int orc_line_rows(int nx, int ny, int periodic, const double *cE, const double *cN,
+                  const double *cNE, const double *cNW, const double *diag, double *phi,
+                  const double *b, int par) {
+  op_t A = {nx, ny, periodic ? ny - 1 : ny, periodic, cE, cN, cNE, cNW, diag};
+  line_rows(&A, phi, b, par);
   return ORC_OK;
 }
 

@@ -336,3 +336,59 @@ def test_harmonic_grid_obeys_the_discrete_maximum_principle(oracle):
     lo, hi = data[fixed | ~g.interior_mask()].min(), data[fixed | ~g.interior_mask()].max()
     assert xo.min() >= lo - 1e-12 and xo.max() <= hi + 1e-12
     assert xo[20, 20] == data[20, 20]
+
+
+# ---------------------------------------------------------------- x-line smoothing
+def _rows_residual(oracle, A, phi, b, parity):
+    r = oracle.residual(A, phi, b)
+    rows = np.zeros(r.shape, dtype=bool)
+    rows[parity::2, :] = True
+    return np.abs(r[rows]).max(), np.abs(r[~rows]).max()
+
+
+@pytest.mark.parametrize("case", ["sine", "annulus", "inclusion"])
+@pytest.mark.parametrize("parity", [0, 1])
+def test_line_half_sweep_zeroes_the_residual_on_its_rows(oracle, case, parity):
+    """A line half-sweep solves every row of its parity exactly: afterwards the residual
+    vanishes (to rounding) on those rows, for 9-point operators (sine warp, inclusion) and
+    a periodic one (annulus), and not on the other rows."""
+    inst = {"sine": lambda: I.config1(33), "annulus": lambda: I.annulus_log(33),
+            "inclusion": lambda: I.inclusion_instance(65, 0.25, 10.0, 3)}[case]()
+    P = oracle.prepare(inst)
+    rng = np.random.default_rng(3)
+    phi0 = P.phi0 + rng.standard_normal(P.phi0.shape) * inst.grid.interior_mask()
+    phi = oracle.line_rows(P.A, phi0, P.b, parity)
+    on, off = _rows_residual(oracle, P.A, phi, P.b, parity)
+    scale = np.abs(P.A.diag).max() * np.abs(phi).max()
+    assert on < 1e-12 * scale and off > 1e-6 * scale, (on, off, scale)
+    # Dirichlet ring untouched, the other parity's rows untouched
+    keep = ~inst.grid.interior_mask()
+    other = np.zeros_like(keep)
+    other[1 - parity::2, :] = True
+    assert np.array_equal(phi[keep | other], phi0[keep | other])
+
+
+def test_line_smoothing_of_decoupled_rows_is_an_exact_solve(oracle):
+    """With every coupling between rows removed the rows are independent one-dimensional
+    problems; one zebra sweep solves them exactly (compared with numpy's dense solve)."""
+    inst = I.config1(17)
+    P = oracle.prepare(inst)
+    A = oracle.Operator(P.A.nx, P.A.ny, P.A.periodic, P.A.cE.copy(), np.zeros_like(P.A.cN),
+                        np.zeros_like(P.A.cNE), np.zeros_like(P.A.cNW), P.A.diag.copy())
+    b = np.random.default_rng(8).standard_normal(P.b.shape) * inst.grid.interior_mask()
+    phi = oracle.smooth(A, np.zeros_like(b), b, sweeps=1, smoother=oracle.SMOOTHER_XLINE)
+    for j in range(1, A.ny - 1):
+        N = A.nx - 2
+        M = np.diag(A.diag[j, 1:-1]) + np.diag(A.cE[j, 1:-2], 1) + np.diag(A.cE[j, 1:-2], -1)
+        assert np.allclose(phi[j, 1:-1], np.linalg.solve(M, b[j, 1:-1]), rtol=1e-12, atol=1e-14)
+
+
+def test_line_smoothing_makes_the_annulus_cycle_robust(oracle):
+    """On the anisotropic annulus (strong coupling along x) the x-line V(1,1) preconditioner
+    needs a handful of CG iterations where the point smoother needs over twenty."""
+    inst = I.config3(257)
+    P = oracle.prepare(inst)
+    _, it_pt, _ = oracle.pcg_solve(P.A, P.b, P.phi0, rtol=1e-8, max_iters=200, nu1=1, nu2=1)
+    _, it_ln, _ = oracle.pcg_solve(P.A, P.b, P.phi0, rtol=1e-8, max_iters=200, nu1=1, nu2=1,
+                                   smoother=oracle.SMOOTHER_XLINE)
+    assert it_ln <= 8 and it_pt >= 3 * it_ln, (it_ln, it_pt)

@@ -180,7 +180,7 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ our arm
-def measure_smoother(mg, torch, inst, prec, reps=20):
+def measure_smoother(mg, torch, inst, prec, reps=20, smoother="gs4"):
     """Dominant kernel of the level-0 smoothing timed alone with CUDA events on this
     workload's finest level, operator built by the library's own kernels: one four-colour
     Gauss-Seidel sweep (4 launches of k_gs_colour), or on FP32 levels of at least
@@ -222,6 +222,8 @@ def measure_smoother(mg, torch, inst, prec, reps=20):
     del D, exx, exy, eyy
     x = z(dt)
     b = torch.randn((g.nyr, pitch), dtype=torch.float64, device="cuda").to(dt)
+    if smoother == "xline":
+        return _measure_line(mg, torch, g, st, x, b, f32, s, reps)
     march = f32 and g.nx * g.nyr >= MARCH_NODES
     x2 = z(dt) if march else None
 
@@ -264,6 +266,39 @@ def measure_smoother(mg, torch, inst, prec, reps=20):
             "frac": achieved / FP64_PEAK_TFLOPS, "traffic": PROFILED_TRAFFIC.get((kern, g.nx)), "kernel": kern,
             "launch_us": per_launch_s * 1e6,
             "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2.07 GHz (probe: 1.20 TFLOP/s at 1.99 GHz)"}
+
+
+def _measure_line(mg, torch, g, st, x, b, f32, s, reps):
+    """Zebra x-line sweep (two launches of k_line_zebra, one per row parity) on the finest
+    level.  Bytes-bound; algorithmic bytes per node and sweep: 14 elements (the N, NE, NW
+    couplings of every row, read once per half-sweep as own or lower row: 6; the iterate
+    read once and written once: 2; b: 1; the five cyclic-reduction factor arrays: 5)."""
+    import ctypes as C
+    tag = "f32" if f32 else "f64"
+    esz = 4 if f32 else 8
+    n = mg.lib().mgk_line_factor_elems(g.nx, g.ny, int(g.periodic_y))
+    f = torch.zeros(n, dtype=torch.float32 if f32 else torch.float64, device="cuda")
+    mg.mgk(f"mgk_line_factor_{tag}", C.byref(st), f.data_ptr(), s)
+
+    def once():
+        mg.mgk(f"mgk_line_smooth_{tag}", C.byref(st), f.data_ptr(), x.data_ptr(), b.data_ptr(), 1, 0, s)
+
+    for _ in range(3):
+        once()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        once()
+    e1.record()
+    torch.cuda.synchronize()
+    per_launch_s = e0.elapsed_time(e1) * 1e-3 / (reps * 2)
+    kern = f"k_line_zebra<{'float' if f32 else 'double'}>"
+    bytes_per_launch = 14.0 * esz * g.nx * g.nyr / 2
+    ach = bytes_per_launch / per_launch_s / 1e9
+    return {"bound": "hbm", "achieved": ach, "peak": HBM_PEAK_GBS, "unit": "GB/s",
+            "frac": ach / HBM_PEAK_GBS, "traffic": PROFILED_TRAFFIC.get((kern, g.nx)), "kernel": kern,
+            "launch_us": per_launch_s * 1e6, "peak_source": "measured copy (MEASURED_PEAKS.json)"}
 
 
 def measure_grid_generation(mg, torch, ctx, n, r, cpu=False):
@@ -403,7 +438,8 @@ def run_ours(args):
     n_in = 1 + (2 if grid_map else 0) + (1 if inst.eps_phys is not None else 0) + \
         (1 if inst.bc is not None else 0)
     for prec in precisions:
-        opts = mg.make_opts(prec, outer, rtol=rtol, max_iters=400)
+        opts = mg.make_opts(prec, outer, rtol=rtol, max_iters=400, smoother=args.smoother,
+                            nu1=args.nu[0], nu2=args.nu[1])
         prob = mg.Problem(ctx, inst, opts, device_inputs=True)
 
         def step():
@@ -450,7 +486,7 @@ def run_ours(args):
                      "setup_ms": st.setup_ms, "solve_ms": st.solve_ms}
         prob.close()
     del flush
-    roof = measure_smoother(mg, torch, inst, precisions[0]) if rank == 0 else None
+    roof = measure_smoother(mg, torch, inst, precisions[0], smoother=args.smoother) if rank == 0 else None
     gridgen = None
     if rank == 0 and grid_map and "r" in inst.meta:
         gridgen = measure_grid_generation(mg, torch, ctx, g.nx, inst.meta["r"], cpu=not args.no_cpu_baseline)
@@ -472,7 +508,8 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": 1e3 * rh["tot"] / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if h == "fp64" else "f32 cycle in f64 refinement", "data": "synthetic",
-            "config": {"workload": args.workload, "precision": h, "outer": f"{outer}+vcycle(2,2)",
+            "config": {"workload": args.workload, "precision": h,
+                       "outer": f"{outer}+vcycle({args.nu[0]},{args.nu[1]})", "smoother": args.smoother,
                        "rtol": rtol, "unknowns": U, "l2": "flushed between steps (512 MB write)",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
             "iters": rh["stats"].iters, "levels": rh["levels"], "setup_ms": rh["setup_ms"],
@@ -789,6 +826,10 @@ def main():
     ap.add_argument("--serve-max-side", type=int, default=2049, help="serve: largest grid side")
     ap.add_argument("--serve-loads", type=float, nargs="*", default=[0.5, 0.8, 0.95],
                     help="serve: open-loop arrival rates as fractions of the saturated rate")
+    ap.add_argument("--smoother", default="gs4", choices=["gs4", "xline"],
+                    help="four-colour point Gauss-Seidel, or zebra x-line Gauss-Seidel")
+    ap.add_argument("--nu", type=lambda v: tuple(int(t) for t in v.split(",")), default=(2, 2),
+                    help="pre,post smoothing sweeps of the V-cycle")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the size-threshold smoother choice instead of timing the families")

@@ -118,7 +118,8 @@ int mgk_coarse_solve_f32(const mgk_op_f32 *A, const double *inv, const float *b,
  * inv the coarsest inverse from mgk_coarse_factor on ops[nlev-1].  Starts from the
  * iterate in x[0] (coarse iterates start from zero) and leaves the result in x[0];
  * smoother: 0 four-colour Gauss-Seidel (forward colours before the coarse-grid
- * correction, reverse after), 1 weighted Jacobi (omega 0.8).  Same kernels as mg_solve. */
+ * correction, reverse after), 1 weighted Jacobi (omega 0.8); the line smoother (2) needs
+ * mgk_vcycle_line_*.  Same kernels as mg_solve. */
 int mgk_vcycle_f64(int nlev, const mgk_op_f64 *ops, double *const *x, double *const *b,
                    double *const *t, const double *inv, int nu1, int nu2, int smoother,
                    void *stream);
@@ -159,6 +160,43 @@ int mgk_pipe_sweeps(int f32);
 int mgk_smooth_march_f32(const mgk_op_f32 *A, const float *xin, float *xout, const float *b,
                          int reverse, const float *eH, int pitch_c, void *stream);
 int mgk_march_sweeps(void);
+
+/* Zebra x-line Gauss-Seidel (an addition to the paper's point smoother for operators whose
+ * coupling along x dominates, such as the annulus of Eq. 29 in polar coordinates).  A
+ * half-sweep of parity p solves, for every row j with j mod 2 == p, the tridiagonal system
+ * of the row's unknowns (diagonal, W and E couplings) with the couplings to rows j-1 and
+ * j+1 (N, S, NE, NW, SE, SW) and to the row's two Dirichlet end nodes moved to the
+ * right-hand side; rows of one parity are independent.  The row systems are solved by
+ * cyclic reduction (row length nx - 2 padded to a power of two) with factors that depend
+ * on A only:
+ *   mgk_line_factor_elems(nx, ny, periodic): elements (of the operator's precision) that
+ *     the factors of an nx x ny level take; 0 for sizes below 3;
+ *   mgk_line_factor_*: fills `factors` for every row of A; call it again when A changes;
+ *   mgk_line_rows_*: one half-sweep of parity 0 or 1, phi updated in place;
+ *   mgk_line_smooth_*: `sweeps` sweeps, each parity 0 then 1 (reverse != 0: 1 then 0).
+ * Rows of up to 8192 unknowns in FP64 and 16384 in FP32 (shared-memory bound); longer
+ * rows, or a periodic grid with an odd row count, return 1. */
+size_t mgk_line_factor_elems(int nx, int ny, int periodic);
+int mgk_line_factor_f64(const mgk_op_f64 *A, double *factors, void *stream);
+int mgk_line_factor_f32(const mgk_op_f32 *A, float *factors, void *stream);
+int mgk_line_rows_f64(const mgk_op_f64 *A, const double *factors, double *phi, const double *b,
+                      int parity, void *stream);
+int mgk_line_rows_f32(const mgk_op_f32 *A, const float *factors, float *phi, const float *b,
+                      int parity, void *stream);
+int mgk_line_smooth_f64(const mgk_op_f64 *A, const double *factors, double *phi, const double *b,
+                        int sweeps, int reverse, void *stream);
+int mgk_line_smooth_f32(const mgk_op_f32 *A, const float *factors, float *phi, const float *b,
+                        int sweeps, int reverse, void *stream);
+
+/* mgk_vcycle_* with the zebra x-line smoother (pre-smoothing parity 0 first, post-smoothing
+ * parity 1 first) on levels 0 .. nlev-2; factors[l] holds the mgk_line_factor_* result of
+ * ops[l] for those levels. */
+int mgk_vcycle_line_f64(int nlev, const mgk_op_f64 *ops, double *const *x, double *const *b,
+                        double *const *t, const double *inv, double *const *factors, int nu1,
+                        int nu2, void *stream);
+int mgk_vcycle_line_f32(int nlev, const mgk_op_f32 *ops, float *const *x, float *const *b,
+                        float *const *t, const double *inv, float *const *factors, int nu1,
+                        int nu2, void *stream);
 
 /* Weighted-Jacobi sweeps exactly as mgk_jacobi_f64, for callers that cannot allocate
  * device memory when they call it (a latency-critical loop where cudaMalloc/cudaFree would

@@ -107,6 +107,8 @@ mg_status batch_solve_impl(mg_ctx* ctx, int count, mg_problem* const* probs,
       snprintf(msg, sizeof msg, "%s", mg_last_error());
       return set_error(st, "batch entry %d: %s", k, msg);
     }
+    if (o.smoother == MG_SMOOTH_XLINE && (st = line_prepare(probs[k], ctx->stream)))
+      return st;
   }
   const std::string key = batch_key(probs, count, o);
   BatchEntry* b = nullptr;

@@ -106,6 +106,7 @@ struct mg_problem {
   mg::SolveArgs* args = nullptr;
   int* flags = nullptr;
   double* stage = nullptr;  // device copies of host inputs/outputs (3 node arrays)
+  void* line = nullptr;     // line-smoother factors of levels 0 .. nlev-2 (cycle precision)
   mg::SolveArgs* h_args = nullptr;
   mg::SolveState* h_state = nullptr;
   int* h_flags = nullptr;  // folded, coarse status, kernel wait timeout
@@ -139,6 +140,8 @@ mg_status build_batch_graph(mg_ctx* ctx, mg_problem* const* probs, int count, co
 void batch_cache_clear(mg_ctx* ctx);
 uint64_t graph_key(const mg_solve_opts& o);
 mg_status check_opts(const mg_problem* P, const mg_solve_opts& o);
+// Allocate and compute the line-smoother factors on stream s if the problem has none yet.
+mg_status line_prepare(mg_problem* P, cudaStream_t s);
 mg_status batch_solve_impl(mg_ctx* ctx, int count, mg_problem* const* probs,
                            const double* const* rho, const double* const* bc, double* const* phi,
                            mg_mem_kind mem, const mg_solve_opts& o, mg_solve_stats* stats);

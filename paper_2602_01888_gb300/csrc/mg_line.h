@@ -1,0 +1,48 @@
+// Zebra x-line Gauss-Seidel smoother (k_line.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+
+#include "mg_launch.h"
+
+namespace mg {
+
+// Largest dynamic shared memory a line kernel may use (one CTA per SM).
+constexpr size_t kLineSmemMax = 227 * 1024;
+
+// Cyclic-reduction factors of the tridiagonal row systems of one level (row stride np).
+template <typename T>
+struct LineFactors {
+  int np = 0;  // padded row length: nx - 2 rounded up to a power of two (at least 2)
+  T *alpha = nullptr, *gamma = nullptr;                 // reduction multipliers, by level
+  T *afin = nullptr, *cfin = nullptr, *binv = nullptr;  // back-substitution coefficients
+};
+
+// Elements of type T that the factors of an nx x ny level take.
+template <typename T>
+size_t line_factor_elems(int nx, int ny, int periodic);
+
+// Whether a level of width nx fits the line kernels' shared memory.
+template <typename T>
+bool line_supported(int nx);
+
+// View of the factors of an nx x ny level stored from `base`.
+template <typename T>
+LineFactors<T> line_factors_at(T* base, int nx, int ny, int periodic);
+
+// Factor every row of A (call again whenever A changes).
+template <typename T>
+cudaError_t launch_line_factor(const Op<T>& A, const LineFactors<T>& F, cudaStream_t s);
+
+// One half-sweep: solve every row j with j mod 2 == par for its unknowns, in place in x.
+template <typename T>
+cudaError_t launch_line_rows(const Op<T>& A, const LineFactors<T>& F, T* x, const T* b, int par,
+                             const int* skip, cudaStream_t s);
+
+// `sweeps` zebra sweeps: parity 0 then 1 per sweep (rev: 1 then 0).
+template <typename T>
+cudaError_t launch_line_smooth(const Op<T>& A, const LineFactors<T>& F, T* x, const T* b, int sweeps,
+                               int rev, const int* skip, cudaStream_t s);
+
+}  // namespace mg

@@ -17,6 +17,7 @@
 #include "mg_launch.h"
 #include "mg_solve_kernels.h"
 #include "mg_internal_host.h"
+#include "mg_line.h"
 #include "mg_vcycle.h"
 
 namespace mg {
@@ -300,6 +301,40 @@ static mg_status problem_alloc(mg_problem* P, bool mixed) {
   return MG_OK;
 }
 
+// Line-smoother factors: levels 0 .. nlev-2 back to back, in the precision of the cycle
+// (FP32 for the mixed path).
+template <typename T>
+static T* line_base(const mg_problem* P, int l) {
+  T* p = (T*)P->line;
+  for (int q = 0; q < l; ++q) p += line_factor_elems<T>(P->nxs[q], P->nys[q], P->grid.periodic_y);
+  return p;
+}
+
+template <typename T>
+static LineFactors<T> line_level(const mg_problem* P, int l) {
+  return line_factors_at<T>(line_base<T>(P, l), P->nxs[l], P->nys[l], P->grid.periodic_y);
+}
+
+static mg_status line_enqueue_factor(mg_problem* P, cudaStream_t s) {
+  for (int l = 0; l < P->nlev - 1; ++l) {
+    if (P->mixed) CU(launch_line_factor<float>(P->lev[l].A32, line_level<float>(P, l), s));
+    else CU(launch_line_factor<double>(P->lev[l].A, line_level<double>(P, l), s));
+  }
+  return MG_OK;
+}
+
+mg_status line_prepare(mg_problem* P, cudaStream_t s) {
+  if (P->line || P->nlev < 2) return MG_OK;
+  const size_t esz = P->mixed ? sizeof(float) : sizeof(double);
+  size_t elems = 0;
+  for (int l = 0; l < P->nlev - 1; ++l) elems += line_factor_elems<double>(P->nxs[l], P->nys[l], P->grid.periodic_y);
+  void* p = P->ctx->pool.alloc(elems * esz);
+  if (!p) return set_error(MG_ERR_OOM, "device memory budget exhausted (line-smoother factors)");
+  P->allocs.push_back(p);
+  P->line = p;
+  return line_enqueue_factor(P, s);
+}
+
 // Coefficients of the finest level from the map, then the Galerkin hierarchy and the
 // coarsest inverse, enqueued on stream s.  Reads host or device inputs.  The map and SPD
 // flags land in P->h_flags; problem_check_build reads them once s has been synchronised.
@@ -358,6 +393,11 @@ mg_status problem_enqueue_build(mg_problem* P, const mg_map_desc* map, const dou
   }
   CU(launch_coarse_factor(P->lev[P->nlev - 1].A, P->inv, P->flags + 1, s));
   P->setup_kernels = 1 + 2 + (P->mixed ? 1 + (P->nlev - 1) + (P->nlev > 1 ? 1 : 0) : P->nlev - 1) + 1;
+  if (P->line) {  // the line smoother's row factors follow the new operators
+    mg_status ls = line_enqueue_factor(P, s);
+    if (ls) return ls;
+    P->setup_kernels += P->nlev - 1;
+  }
   // restore the scratch vectors used as staging
   CU(cudaMemsetAsync(P->z, 0, 3 * np * sizeof(double), s));
   CU(cudaEventRecord(P->evb1, s));
@@ -588,6 +628,8 @@ static void level_table(mg_problem* P, T* x0, T* b0, VLevels<T>* V) {
   V->b[0] = b0;
   V->err = P->flags + 2;
   V->pol = P->ctx->tuned ? &P->ctx->pol[sizeof(T) == 4 ? 1 : 0] : nullptr;
+  if (P->line && (sizeof(T) == 4) == (P->mixed != 0))
+    for (int l = 0; l < P->nlev - 1; ++l) V->lf[l] = line_level<T>(P, l);
 }
 
 template <typename T>
@@ -833,8 +875,12 @@ mg_status check_opts(const mg_problem* P, const mg_solve_opts& o) {
     return set_error(MG_ERR_ARG, "solve precision differs from the precision the problem was set up with");
   if (o.outer != MG_OUTER_VCYCLE && o.outer != MG_OUTER_FCG)
     return set_error(MG_ERR_ARG, "bad outer iteration %d", o.outer);
-  if (o.smoother != MG_SMOOTH_GS4 && o.smoother != MG_SMOOTH_JACOBI)
+  if (o.smoother != MG_SMOOTH_GS4 && o.smoother != MG_SMOOTH_JACOBI && o.smoother != MG_SMOOTH_XLINE)
     return set_error(MG_ERR_ARG, "bad smoother %d", o.smoother);
+  if (o.smoother == MG_SMOOTH_XLINE &&
+      !(P->mixed ? line_supported<float>(P->grid.nx) : line_supported<double>(P->grid.nx)))
+    return set_error(MG_ERR_SIZE, "line smoother: rows of %d nodes exceed the line kernels' shared memory",
+                     P->grid.nx);
   if (o.nu1 < 0 || o.nu2 < 0 || o.nu1 + o.nu2 == 0 || o.nu1 > 16 || o.nu2 > 16)
     return set_error(MG_ERR_ARG, "bad smoothing counts %d, %d", o.nu1, o.nu2);
   if (o.max_iters < 1 || !(o.rtol >= 0)) return set_error(MG_ERR_ARG, "bad rtol / max_iters");
@@ -881,6 +927,10 @@ static mg_status run_host_loop(mg_problem* P, const mg_solve_opts& o, cudaStream
 mg_status enqueue_solve(mg_problem* P, const mg_solve_opts& o, const double* rho, const double* bc,
                         const double* phi_in, double* phi_out, cudaStream_t s) {
   const bool host_loop = host_loop_mode();
+  if (o.smoother == MG_SMOOTH_XLINE) {
+    mg_status lst = line_prepare(P, s);
+    if (lst) return lst;
+  }
   const uint64_t key = graph_key(o);
   auto it = P->graphs.find(key);
   if (it == P->graphs.end()) {  // also built in host-loop mode, for its kernel counts

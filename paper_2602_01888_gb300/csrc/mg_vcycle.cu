@@ -5,7 +5,7 @@
 // ping-pong iterates); the residual is fused with full-weighting restriction; the levels
 // at and below the tail threshold run in one single-CTA tail kernel that ends with the
 // coarsest dense solve.  The weighted-Jacobi smoother uses the per-sweep kernels on every
-// level.
+// level, the zebra x-line smoother its two launches a sweep on every level but the coarsest.
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -16,6 +16,7 @@
 #include "mg_kernels.h"
 #include "mg_launch.h"
 #include "mg_pipe.h"
+#include "mg_line.h"
 #include "mg_march.h"
 #include "mg_vcycle.h"
 
@@ -97,6 +98,21 @@ cudaError_t emit_vcycle(const VLevels<T>& V, int smoother, int nu1, int nu2, dou
     for (int l = L - 2; l >= 0; --l) {
       if ((e = launch_prolong_add(V.A[l], cur[l], cur[l + 1], V.A[l + 1].pitch, skip, s))) return e;
       if ((e = launch_jacobi(V.A[l], cur[l], V.b[l], alt[l], nu2, omega, skip, s))) return e;
+    }
+    *result = cur[0];
+    return cudaSuccess;
+  }
+  if (smoother == MG_SMOOTH_XLINE) {  // zebra x-line Gauss-Seidel on every level but the coarsest
+    for (int l = 0; l < L - 1; ++l) {
+      if ((e = launch_line_smooth(V.A[l], V.lf[l], cur[l], V.b[l], nu1, 0, skip, s))) return e;
+      if ((e = launch_resid_restrict(V.A[l], cur[l], V.b[l], V.b[l + 1], cur[l + 1],
+                                     V.A[l + 1].pitch, skip, s)))
+        return e;
+    }
+    if ((e = launch_coarse_solve(V.A[L - 1], V.inv, V.b[L - 1], cur[L - 1], skip, s))) return e;
+    for (int l = L - 2; l >= 0; --l) {
+      if ((e = launch_prolong_add(V.A[l], cur[l], cur[l + 1], V.A[l + 1].pitch, skip, s))) return e;
+      if ((e = launch_line_smooth(V.A[l], V.lf[l], cur[l], V.b[l], nu2, 1, skip, s))) return e;
     }
     *result = cur[0];
     return cudaSuccess;
@@ -225,10 +241,12 @@ using namespace mg;
 
 template <typename T, typename OPK>
 static int vcycle_abi(int nlev, const OPK* ops, T* const* x, T* const* b, T* const* t,
-                      const double* inv, int nu1, int nu2, int smoother, void* stream) {
+                      const double* inv, T* const* lf, int nu1, int nu2, int smoother, void* stream) {
   if (nlev < 1 || nlev > kMaxLevels || !ops || !x || !b || !t || !inv || nu1 < 0 || nu2 < 0 ||
       nu1 + nu2 == 0)
     return 1;
+  if (smoother != MG_SMOOTH_GS4 && smoother != MG_SMOOTH_JACOBI && smoother != MG_SMOOTH_XLINE) return 1;
+  if ((smoother == MG_SMOOTH_XLINE) != (lf != nullptr)) return 1;
   VLevels<T> V;
   V.L = nlev;
   V.inv = inv;
@@ -241,6 +259,10 @@ static int vcycle_abi(int nlev, const OPK* ops, T* const* x, T* const* b, T* con
     V.x[l] = x[l];
     V.b[l] = b[l];
     V.t[l] = t[l];
+    if (lf && l < nlev - 1) {
+      if (!lf[l] || !line_supported<T>(o.nx)) return 1;
+      V.lf[l] = line_factors_at<T>(lf[l], o.nx, o.ny, o.periodic);
+    }
   }
   if (coarse_unknowns(ops[nlev - 1].nx, ops[nlev - 1].ny, ops[nlev - 1].periodic) > kCoarseMax) return 1;
   cudaStream_t s = (cudaStream_t)stream;
@@ -256,13 +278,27 @@ static int vcycle_abi(int nlev, const OPK* ops, T* const* x, T* const* b, T* con
 extern "C" int mgk_vcycle_f64(int nlev, const mgk_op_f64* ops, double* const* x, double* const* b,
                               double* const* t, const double* inv, int nu1, int nu2, int smoother,
                               void* stream) {
-  return vcycle_abi<double>(nlev, ops, x, b, t, inv, nu1, nu2, smoother, stream);
+  return vcycle_abi<double>(nlev, ops, x, b, t, inv, nullptr, nu1, nu2, smoother, stream);
 }
 
 extern "C" int mgk_vcycle_f32(int nlev, const mgk_op_f32* ops, float* const* x, float* const* b,
                               float* const* t, const double* inv, int nu1, int nu2, int smoother,
                               void* stream) {
-  return vcycle_abi<float>(nlev, ops, x, b, t, inv, nu1, nu2, smoother, stream);
+  return vcycle_abi<float>(nlev, ops, x, b, t, inv, nullptr, nu1, nu2, smoother, stream);
+}
+
+extern "C" int mgk_vcycle_line_f64(int nlev, const mgk_op_f64* ops, double* const* x, double* const* b,
+                                   double* const* t, const double* inv, double* const* factors, int nu1,
+                                   int nu2, void* stream) {
+  if (!factors) return 1;
+  return vcycle_abi<double>(nlev, ops, x, b, t, inv, factors, nu1, nu2, MG_SMOOTH_XLINE, stream);
+}
+
+extern "C" int mgk_vcycle_line_f32(int nlev, const mgk_op_f32* ops, float* const* x, float* const* b,
+                                   float* const* t, const double* inv, float* const* factors, int nu1,
+                                   int nu2, void* stream) {
+  if (!factors) return 1;
+  return vcycle_abi<float>(nlev, ops, x, b, t, inv, factors, nu1, nu2, MG_SMOOTH_XLINE, stream);
 }
 
 // Single fused smoothing launch on caller memory (testing and profiling).

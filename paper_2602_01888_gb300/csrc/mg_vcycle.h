@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include "mg_launch.h"
+#include "mg_line.h"
 
 namespace mg {
 
@@ -35,6 +36,7 @@ struct VLevels {
   const double* inv = nullptr;
   int* err = nullptr;  // device flag set when a bounded wait of a kernel gives up
   const SmoothPolicy* pol = nullptr;  // measured smoother choice (nullable)
+  LineFactors<T> lf[kMaxVLevels];     // line-smoother factors of levels 0 .. L-2 (line smoother)
 };
 
 // Enqueue one V(nu1, nu2) cycle starting from the iterate in V.x[0]; *result receives the

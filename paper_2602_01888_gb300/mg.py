@@ -27,7 +27,8 @@ MG_ERR_NOT_SPD = 11
 MG_MEM_HOST, MG_MEM_DEVICE = 0, 1
 MG_PREC_FP64, MG_PREC_MIXED = 0, 1
 MG_OUTER_VCYCLE, MG_OUTER_FCG = 0, 1
-MG_SMOOTH_GS4, MG_SMOOTH_JACOBI = 0, 1
+MG_SMOOTH_GS4, MG_SMOOTH_JACOBI, MG_SMOOTH_XLINE = 0, 1, 2
+_SMOOTHERS = {"gs4": MG_SMOOTH_GS4, "jacobi": MG_SMOOTH_JACOBI, "xline": MG_SMOOTH_XLINE}
 MAP_CODES = {"identity": 0, "sine_warp": 1, "polar": 2, "sinh": 3, "affine": 4, "grid": 5}
 MG_HIST_MAX = 256
 
@@ -171,6 +172,23 @@ _SIGS = {
     "mgk_smooth_march_f32": ([C.POINTER(mgk_op_f32), C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                               C.c_void_p, C.c_int, C.c_void_p], C.c_int),
     "mgk_march_sweeps": ([], C.c_int),
+    "mgk_line_factor_elems": ([C.c_int, C.c_int, C.c_int], C.c_size_t),
+    "mgk_line_factor_f64": ([C.POINTER(mgk_op_f64), C.c_void_p, C.c_void_p], C.c_int),
+    "mgk_line_factor_f32": ([C.POINTER(mgk_op_f32), C.c_void_p, C.c_void_p], C.c_int),
+    "mgk_line_rows_f64": ([C.POINTER(mgk_op_f64), C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                           C.c_void_p], C.c_int),
+    "mgk_line_rows_f32": ([C.POINTER(mgk_op_f32), C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                           C.c_void_p], C.c_int),
+    "mgk_line_smooth_f64": ([C.POINTER(mgk_op_f64), C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                             C.c_int, C.c_void_p], C.c_int),
+    "mgk_line_smooth_f32": ([C.POINTER(mgk_op_f32), C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                             C.c_int, C.c_void_p], C.c_int),
+    "mgk_vcycle_line_f64": ([C.c_int, C.POINTER(mgk_op_f64), C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                             C.POINTER(C.c_void_p), C.c_void_p, C.POINTER(C.c_void_p), C.c_int, C.c_int,
+                             C.c_void_p], C.c_int),
+    "mgk_vcycle_line_f32": ([C.c_int, C.POINTER(mgk_op_f32), C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                             C.POINTER(C.c_void_p), C.c_void_p, C.POINTER(C.c_void_p), C.c_int, C.c_int,
+                             C.c_void_p], C.c_int),
     "mgk_jacobi_f64_static": ([C.POINTER(mgk_op_f64), C.c_void_p, C.c_void_p, C.c_int, C.c_double,
                                C.c_void_p], C.c_int),
     "mgk_jacobi_f64_static_capacity": ([], C.c_size_t),
@@ -560,7 +578,9 @@ def make_opts(precision="fp64", outer="fcg", rtol=1e-10, max_iters=200, nu1=2, n
     o = mg_default_opts()
     o.precision = MG_PREC_MIXED if precision == "mixed" else MG_PREC_FP64
     o.outer = MG_OUTER_FCG if outer == "fcg" else MG_OUTER_VCYCLE
-    o.smoother = MG_SMOOTH_JACOBI if smoother == "jacobi" else MG_SMOOTH_GS4
+    if smoother not in _SMOOTHERS:
+        raise ValueError(f"unknown smoother {smoother!r} (one of {sorted(_SMOOTHERS)})")
+    o.smoother = _SMOOTHERS[smoother]
     o.rtol, o.max_iters, o.nu1, o.nu2 = rtol, max_iters, nu1, nu2
     o.coarse_max, o.omega_j, o.warm_start = coarse_max, omega_j, int(warm_start)
     return o

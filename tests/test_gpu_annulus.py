@@ -31,12 +31,13 @@ def ctx(libmg, cuda):
     c.close()
 
 
+@pytest.mark.parametrize("smoother", ["gs4", "xline"])
 @pytest.mark.parametrize("prec", ["mixed", "fp64"])
-def test_annulus_recipe_1025_matches_oracle(libmg, oracle, ctx, prec):
+def test_annulus_recipe_1025_matches_oracle(libmg, oracle, ctx, prec, smoother):
     inst = I.config3(1025)
     P = oracle.prepare(inst)
     ref, it, hist = oracle.pcg_solve(P.A, P.b, P.phi0, rtol=0.0, max_iters=400, stagnate=3)
-    prob = libmg.Problem(ctx, inst, libmg.make_opts(prec, "fcg", rtol=RTOL, max_iters=400))
+    prob = libmg.Problem(ctx, inst, libmg.make_opts(prec, "fcg", rtol=RTOL, max_iters=400, smoother=smoother))
     phi, st = prob.solve()
     err = oracle.rel_l2(phi, ref, inst.grid.interior_mask())
     assert err <= 1e-9, (prec, err, st.iters)
@@ -90,17 +91,19 @@ def test_annulus_full_size_sampled_residuals(libmg, oracle, ctx, cuda):
     assert np.abs(phi_h).max() > 1e-6
 
 
-def test_annulus_full_size_matches_oracle_golden(libmg, ctx, cuda):
-    """8193^2 annulus, mixed path at the benchmark's rtol, against the oracle's phi* at 4096
-    seeded sample nodes (tests/golden/annulus_8193_samples.npz, written by
-    tests/golden/make_golden.py from the oracle alone): relative L2 error over the samples
-    within the 1e-9 target."""
+@pytest.mark.parametrize("smoother,nu", [("gs4", 2), ("xline", 2), ("xline", 1)])
+def test_annulus_full_size_matches_oracle_golden(libmg, ctx, cuda, smoother, nu):
+    """8193^2 annulus, mixed path at the benchmark's rtol (point smoother V(2,2), line
+    smoother V(2,2) and V(1,1)), against the oracle's phi* at 4096 seeded sample nodes
+    (tests/golden/annulus_8193_samples.npz, written by tests/golden/make_golden.py from the
+    oracle alone): relative L2 error over the samples within the 1e-9 target."""
     import os
     torch = cuda
     gold = np.load(os.path.join(os.path.dirname(__file__), "golden", "annulus_8193_samples.npz"))
     inst = I.config3(8193)
     g = inst.grid
-    prob = libmg.Problem(ctx, inst, libmg.make_opts("mixed", "fcg", rtol=RTOL_FULL, max_iters=400))
+    prob = libmg.Problem(ctx, inst, libmg.make_opts("mixed", "fcg", rtol=RTOL_FULL, max_iters=400,
+                                                    smoother=smoother, nu1=nu, nu2=nu))
     rho = torch.from_numpy(np.ascontiguousarray(inst.rho_phys)).cuda()
     phi = torch.zeros(g.shape, dtype=torch.float64, device="cuda")
     _, st = prob.solve(rho=rho, phi=phi)

@@ -364,9 +364,14 @@ def run_kernel_only(args):
     pc = (nc + 31) // 32 * 32
     bH = torch.zeros((nc, pc), dtype=dt, device="cuda")
     sfx = "f64" if f64 else "f32"
+    if args.kernel.startswith("line"):
+        fac = torch.zeros(mg.lib().mgk_line_factor_elems(n, n, 0), dtype=dt, device="cuda")
+        mg.mgk(f"mgk_line_factor_{sfx}", C.byref(st), fac.data_ptr(), s)
 
     def once():
-        if args.kernel.startswith("march"):
+        if args.kernel.startswith("line"):  # one zebra sweep: two launches of k_line_zebra
+            mg.mgk(f"mgk_line_smooth_{sfx}", C.byref(st), fac.data_ptr(), x.data_ptr(), b.data_ptr(), 1, 0, s)
+        elif args.kernel.startswith("march"):
             # "march32p": with the coarse-grid correction fused (post-smoothing form)
             corr = args.kernel.startswith("march32p")
             mg.mgk("mgk_smooth_march_f32", C.byref(st), x.data_ptr(), x2.data_ptr(), b.data_ptr(), 0,
@@ -834,8 +839,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the size-threshold smoother choice instead of timing the families")
     ap.add_argument("--kernel-only", dest="kernel", default=None,
-                    help="smooth64|smooth32|fused64|fused32|pipe64|pipe32|march32|march32p|restrict64|restrict32|"
-                         "prolong64|prolong32")
+                    help="smooth64|smooth32|fused64|fused32|pipe64|pipe32|march32|march32p|line64|line32|"
+                         "restrict64|restrict32|prolong64|prolong32")
     ap.add_argument("--side", type=int, default=2049)
     ap.add_argument("--reps", type=int, default=5)
     args = ap.parse_args()

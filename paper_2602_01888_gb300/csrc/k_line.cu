@@ -14,8 +14,12 @@
 // Layout of the factors (per row, row stride Np elements, in five arrays):
 //   alpha, gamma: the multipliers of reduction level k (stride s = 2^k) for the combining
 //     equations i = 2s(m + 1) - 1, stored at offset Np - Np/2^k + m;
-//   afin, cfin, binv: for every equation i, its sub/super-diagonal entries and reciprocal
-//     pivot at the level where it is eliminated (back substitution).
+//   afin, cfin, binv: the sub/super-diagonal entries and reciprocal pivot of the equations
+//     eliminated at level k (i = 2s m + s - 1), at the same offset Np - Np/2^k + m; the
+//     last equation (the root of the reduction) at Np - 1.
+// Every phase of both kernels thus reads its factors as one contiguous run.  In shared
+// memory, element i sits at i + i / (128 / sizeof(T)): one pad word per 128 bytes, so the
+// strided accesses of the reduction levels (stride 2^(k+1)) hit distinct banks.
 #include <cuda_runtime.h>
 
 #include "mg_common.cuh"
@@ -25,7 +29,7 @@
 
 namespace mg {
 
-static constexpr int kLT = 256;
+static constexpr int kLT = 256;  // threads of a line CTA
 
 __host__ __device__ inline int line_np(int nx) {
   int np = 1;
@@ -39,129 +43,227 @@ __host__ __device__ inline int line_levels(int np) {
   return k;
 }
 
+// Padded shared-memory index and the padded length of a row of Np elements.
+template <typename T>
+__host__ __device__ __forceinline__ int sx(int i) {
+  return i + i / (128 / (int)sizeof(T));
+}
+template <typename T>
+__host__ __device__ inline size_t line_row_smem(int np) {
+  return (size_t)(sx<T>(np - 1) + 1) * sizeof(T);
+}
+
+// Asynchronous copy of one element from global to shared memory (4 or 8 bytes, naturally
+// aligned).
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  if constexpr (sizeof(T) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+
 template <typename T>
 __device__ __forceinline__ bool row_active(const Lvl<T>& L, int j) {
   return L.periodic || (j >= 1 && j <= L.ny - 2);
 }
 
-// Reduction multipliers of row blockIdx.x.  Shared memory: a, b, c of Np entries each.
+// Reduction multipliers of row blockIdx.x.  Shared memory: a, b, c of Np entries each
+// (padded rows).
 template <typename T>
 __global__ void __launch_bounds__(kLT) k_line_factor(Lvl<T> L, LineFactors<T> F) {
   const int j = blockIdx.x;
   if (j >= L.nyr || !row_active(L, j)) return;
   const int N = L.nx - 2, Np = F.np, K = line_levels(Np);
   extern __shared__ __align__(16) unsigned char line_smem[];
+  const int rs = (int)(line_row_smem<T>(Np) / sizeof(T));
   T* a = reinterpret_cast<T*>(line_smem);
-  T* bb = a + Np;
-  T* c = bb + Np;
+  T* bb = a + rs;
+  T* c = bb + rs;
   const size_t r0 = (size_t)j * L.pitch, f0 = (size_t)j * Np;
   for (int t = threadIdx.x; t < Np; t += blockDim.x) {
+    const int q = sx<T>(t);
     if (t < N) {
       const int i = t + 1;
-      a[t] = t >= 1 ? L.cE[r0 + i - 1] : T(0);
-      bb[t] = L.diag[r0 + i];
-      c[t] = t <= N - 2 ? L.cE[r0 + i] : T(0);
+      a[q] = t >= 1 ? L.cE[r0 + i - 1] : T(0);
+      bb[q] = L.diag[r0 + i];
+      c[q] = t <= N - 2 ? L.cE[r0 + i] : T(0);
     } else {  // padding: identity equations
-      a[t] = T(0);
-      bb[t] = T(1);
-      c[t] = T(0);
+      a[q] = T(0);
+      bb[q] = T(1);
+      c[q] = T(0);
     }
   }
   __syncthreads();
   for (int k = 0; k < K; ++k) {
-    const int s = 1 << k;
+    const int s = 1 << k, off = Np - Np / s;
     // equations eliminated at this level (i = 2s m + s - 1) are final now
     for (int m = threadIdx.x; m < Np / (2 * s); m += blockDim.x) {
-      const int i = 2 * s * m + s - 1;
-      F.afin[f0 + i] = a[i];
-      F.cfin[f0 + i] = c[i];
-      F.binv[f0 + i] = T(1) / bb[i];
+      const int q = sx<T>(2 * s * m + s - 1);
+      F.afin[f0 + off + m] = a[q];
+      F.cfin[f0 + off + m] = c[q];
+      F.binv[f0 + off + m] = T(1) / bb[q];
     }
     // combining equations i = 2s(m + 1) - 1 absorb their neighbours at distance s; the
     // neighbours are not combining at this level, so reading and writing do not overlap
-    const int off = Np - Np / s;
     for (int m = threadIdx.x; m < Np / (2 * s); m += blockDim.x) {
       const int i = 2 * s * (m + 1) - 1;
       const bool up = i + s < Np;
-      const T al = -a[i] / bb[i - s];
-      const T ga = up ? -c[i] / bb[i + s] : T(0);
+      const int q = sx<T>(i), qd = sx<T>(i - s), qu = up ? sx<T>(i + s) : q;
+      const T al = -a[q] / bb[qd];
+      const T ga = up ? -c[q] / bb[qu] : T(0);
       F.alpha[f0 + off + m] = al;
       F.gamma[f0 + off + m] = ga;
-      const T na = al * a[i - s];
-      const T nc = up ? ga * c[i + s] : T(0);
-      const T nb = bb[i] + al * c[i - s] + (up ? ga * a[i + s] : T(0));
-      a[i] = na;
-      c[i] = nc;
-      bb[i] = nb;
+      const T na = al * a[qd];
+      const T nc = up ? ga * c[qu] : T(0);
+      const T nb = bb[q] + al * c[qd] + (up ? ga * a[qu] : T(0));
+      a[q] = na;
+      c[q] = nc;
+      bb[q] = nb;
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0) {  // the last combining equation has no neighbour left
+  if (threadIdx.x == 0) {  // the root: no neighbour left
     F.afin[f0 + Np - 1] = T(0);
     F.cfin[f0 + Np - 1] = T(0);
-    F.binv[f0 + Np - 1] = T(1) / bb[Np - 1];
+    F.binv[f0 + Np - 1] = T(1) / bb[sx<T>(Np - 1)];
   }
 }
 
-// One half-sweep: rows j = par, par + 2, ... (grid: one CTA per such row).  Shared memory:
-// the row's right-hand side, overwritten by its solution, Np entries.
+// Factors of the deepest reduction levels (those with at most kLineDeep / 2 equations),
+// the last kLineDeep entries of each factor row, are staged in shared memory when a CTA
+// starts: their levels then cost no global round trip (the reduction is a chain of
+// dependent levels, and each global round trip is one DRAM latency).
+constexpr int kLineDeep = 128;
+
 template <typename T>
-__global__ void __launch_bounds__(kLT) k_line_zebra(Lvl<T> L, LineFactors<T> F, T* __restrict__ x,
-                                                    const T* __restrict__ b, int par,
-                                                    const int* __restrict__ skip) {
+__host__ __device__ inline size_t zebra_smem(int np) {
+  return line_row_smem<T>(np) + (size_t)5 * (np < kLineDeep ? np : kLineDeep) * sizeof(T);
+}
+
+// One half-sweep: rows j = par, par + 2, ... (grid: one CTA per such row).  Shared memory:
+// the row's right-hand side, overwritten by its solution (padded row), then the deep-level
+// factors.  A half-sweep reads rows of the other parity only (and the Dirichlet row ends),
+// which no CTA of the launch writes, so x is read through the read-only path.  LU: loop
+// iterations whose global loads a thread issues together (the kernel is bound by load
+// latency); resident CTAs per SM at the longest rows: 6 (FP32) / 3 (FP64), which is also
+// what shared memory allows there.
+template <typename T, int LU>
+__global__ void __launch_bounds__(kLT, sizeof(T) == 8 ? 3 : 6)
+    k_line_zebra(Lvl<T> L, LineFactors<T> F, T* __restrict__ x, const T* __restrict__ b, int par,
+                 const int* __restrict__ skip) {
   if (skip && *skip) return;
   const int j = par + 2 * blockIdx.x;
   if (j >= L.nyr || !row_active(L, j)) return;
   const int N = L.nx - 2, Np = F.np, K = line_levels(Np);
+  const int deep = Np < kLineDeep ? Np : kLineDeep, d0 = Np - deep;
+  const size_t f0 = (size_t)j * Np;
   extern __shared__ __align__(16) unsigned char line_smem[];
   T* d = reinterpret_cast<T*>(line_smem);
+  T* dfac = reinterpret_cast<T*>(line_smem + line_row_smem<T>(Np));  // 5 x deep: alpha gamma afin cfin binv
+  // deep-level factors: asynchronous copies now, waited for before the first reduction level
+  for (int e = threadIdx.x; e < 5 * deep; e += kLT) {
+    const int a = e / deep, m = e - a * deep;
+    const T* src = a == 0 ? F.alpha : a == 1 ? F.gamma : a == 2 ? F.afin : a == 3 ? F.cfin : F.binv;
+    cp_async_elem(dfac + e, src + f0 + d0 + m);
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
   const int p = L.pitch;
   const int jd = row_dn(j, L.nyr), ju = row_up(j, L.nyr);
-  const size_t r0 = (size_t)j * p, rd = (size_t)jd * p, ru = (size_t)ju * p, f0 = (size_t)j * Np;
-  for (int t = threadIdx.x; t < Np; t += blockDim.x) {
-    T v = T(0);
-    if (t < N) {
-      const int i = t + 1;
-      // couplings leaving the row, in the order of the point smoother's sum minus E/W
-      T off = L.cN[r0 + i] * x[ru + i];
-      off = fma(L.cN[rd + i], x[rd + i], off);
-      off = fma(L.cNE[r0 + i], x[ru + i + 1], off);
-      off = fma(L.cNE[rd + i - 1], x[rd + i - 1], off);
-      off = fma(L.cNW[r0 + i], x[ru + i - 1], off);
-      off = fma(L.cNW[rd + i + 1], x[rd + i + 1], off);
-      if (i == 1) off = fma(L.cE[r0], x[r0], off);
-      if (i == N) off = fma(L.cE[r0 + i], x[r0 + i + 1], off);
-      v = b[r0 + i] - off;
+  const size_t r0 = (size_t)j * p, rd = (size_t)jd * p, ru = (size_t)ju * p;
+  for (int t0 = threadIdx.x; t0 < Np; t0 += LU * kLT) {
+    T v[LU];
+#pragma unroll
+    for (int u = 0; u < LU; ++u) {
+      const int t = t0 + u * kLT;
+      v[u] = T(0);
+      if (t < N) {
+        const int i = t + 1;
+        // couplings leaving the row, in the order of the point smoother's sum minus E/W
+        T off = __ldg(L.cN + r0 + i) * __ldg(x + ru + i);
+        off = fma(__ldg(L.cN + rd + i), __ldg(x + rd + i), off);
+        off = fma(__ldg(L.cNE + r0 + i), __ldg(x + ru + i + 1), off);
+        off = fma(__ldg(L.cNE + rd + i - 1), __ldg(x + rd + i - 1), off);
+        off = fma(__ldg(L.cNW + r0 + i), __ldg(x + ru + i - 1), off);
+        off = fma(__ldg(L.cNW + rd + i + 1), __ldg(x + rd + i + 1), off);
+        if (i == 1) off = fma(L.cE[r0], __ldg(x + r0), off);
+        if (i == N) off = fma(L.cE[r0 + i], __ldg(x + r0 + i + 1), off);
+        v[u] = __ldg(b + r0 + i) - off;
+      }
     }
-    d[t] = v;
+#pragma unroll
+    for (int u = 0; u < LU; ++u)
+      if (t0 + u * kLT < Np) d[sx<T>(t0 + u * kLT)] = v[u];
   }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
   __syncthreads();
   // forward reduction of the right-hand side
   for (int k = 0; k < K; ++k) {
-    const int s = 1 << k, off = Np - Np / s;
-    for (int m = threadIdx.x; m < Np / (2 * s); m += blockDim.x) {
-      const int i = 2 * s * (m + 1) - 1;
-      T v = fma(F.alpha[f0 + off + m], d[i - s], d[i]);
-      if (i + s < Np) v = fma(F.gamma[f0 + off + m], d[i + s], v);
-      d[i] = v;
+    const int s = 1 << k, off = Np - Np / s, cnt = Np / (2 * s);
+    const bool staged = off >= d0;
+    for (int m0 = threadIdx.x; m0 < cnt; m0 += LU * kLT) {
+      T al[LU], ga[LU];
+#pragma unroll
+      for (int u = 0; u < LU; ++u) {
+        const int m = m0 + u * kLT;
+        if (staged) {
+          al[u] = m < cnt ? dfac[off - d0 + m] : T(0);
+          ga[u] = m < cnt ? dfac[deep + off - d0 + m] : T(0);
+        } else {
+          al[u] = m < cnt ? __ldg(F.alpha + f0 + off + m) : T(0);
+          ga[u] = m < cnt ? __ldg(F.gamma + f0 + off + m) : T(0);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < LU; ++u) {
+        const int m = m0 + u * kLT;
+        if (m < cnt) {
+          const int i = 2 * s * (m + 1) - 1, q = sx<T>(i);
+          T v = fma(al[u], d[sx<T>(i - s)], d[q]);
+          if (i + s < Np) v = fma(ga[u], d[sx<T>(i + s)], v);
+          d[q] = v;
+        }
+      }
     }
     __syncthreads();
   }
-  // back substitution, from the last equation down; solutions overwrite d
-  if (threadIdx.x == 0) d[Np - 1] *= F.binv[f0 + Np - 1];
+  // back substitution, from the root down; solutions overwrite d
+  if (threadIdx.x == 0) d[sx<T>(Np - 1)] *= dfac[4 * deep + deep - 1];
   __syncthreads();
   for (int k = K - 1; k >= 0; --k) {
-    const int s = 1 << k;
-    for (int m = threadIdx.x; m < Np / (2 * s); m += blockDim.x) {
-      const int i = 2 * s * m + s - 1;
-      T v = d[i];
-      if (i - s >= 0) v -= F.afin[f0 + i] * d[i - s];
-      v -= F.cfin[f0 + i] * d[i + s];
-      d[i] = v * F.binv[f0 + i];
+    const int s = 1 << k, off = Np - Np / s, cnt = Np / (2 * s);
+    const bool staged = off >= d0;
+    for (int m0 = threadIdx.x; m0 < cnt; m0 += LU * kLT) {
+      T af[LU], cf[LU], bi[LU];
+#pragma unroll
+      for (int u = 0; u < LU; ++u) {
+        const int m = m0 + u * kLT;
+        if (staged) {
+          af[u] = m < cnt ? dfac[2 * deep + off - d0 + m] : T(0);
+          cf[u] = m < cnt ? dfac[3 * deep + off - d0 + m] : T(0);
+          bi[u] = m < cnt ? dfac[4 * deep + off - d0 + m] : T(0);
+        } else {
+          af[u] = m < cnt ? __ldg(F.afin + f0 + off + m) : T(0);
+          cf[u] = m < cnt ? __ldg(F.cfin + f0 + off + m) : T(0);
+          bi[u] = m < cnt ? __ldg(F.binv + f0 + off + m) : T(0);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < LU; ++u) {
+        const int m = m0 + u * kLT;
+        if (m < cnt) {
+          const int i = 2 * s * m + s - 1, q = sx<T>(i);
+          T v = d[q];
+          if (i - s >= 0) v -= af[u] * d[sx<T>(i - s)];
+          v -= cf[u] * d[sx<T>(i + s)];
+          d[q] = v * bi[u];
+        }
+      }
     }
     __syncthreads();
   }
-  for (int t = threadIdx.x; t < N; t += blockDim.x) x[r0 + t + 1] = d[t];
+  for (int t = threadIdx.x; t < N; t += kLT) x[r0 + t + 1] = d[sx<T>(t)];
 }
 
 // ------------------------------------------------------------------ launchers
@@ -172,7 +274,8 @@ size_t line_factor_elems(int nx, int ny, int periodic) {
 
 template <typename T>
 bool line_supported(int nx) {
-  return nx >= 3 && (size_t)3 * line_np(nx) * sizeof(T) <= kLineSmemMax;
+  return nx >= 3 && 3 * line_row_smem<T>(line_np(nx)) <= kLineSmemMax &&
+         3 * zebra_smem<T>(line_np(nx)) <= kLineSmemMax;
 }
 
 template <typename T>
@@ -192,7 +295,7 @@ template <typename T>
 cudaError_t launch_line_factor(const Op<T>& A, const LineFactors<T>& F, cudaStream_t s) {
   if (!line_supported<T>(A.nx) || F.np != line_np(A.nx)) return cudaErrorInvalidValue;
   const Lvl<T> L = lvl_of(A);
-  const size_t sm = (size_t)3 * F.np * sizeof(T);
+  const size_t sm = 3 * line_row_smem<T>(F.np);
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k_line_factor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -208,18 +311,19 @@ template <typename T>
 cudaError_t launch_line_rows(const Op<T>& A, const LineFactors<T>& F, T* x, const T* b, int par,
                              const int* skip, cudaStream_t s) {
   if (!line_supported<T>(A.nx) || F.np != line_np(A.nx)) return cudaErrorInvalidValue;
+  constexpr int LU = sizeof(T) == 8 ? 2 : 1;  // measured best per precision
   const Lvl<T> L = lvl_of(A);
-  const size_t sm = (size_t)F.np * sizeof(T);
+  const size_t sm = zebra_smem<T>(F.np);
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_line_zebra<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_line_zebra<T, LU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)(kLineSmemMax / 3));
     if (e != cudaSuccess) return e;
     attr = true;
   }
   const int rows = (L.nyr - par + 1) / 2;
   if (rows <= 0) return cudaSuccess;
-  k_line_zebra<T><<<rows, kLT, sm, s>>>(L, F, x, b, par, skip);
+  k_line_zebra<T, LU><<<rows, kLT, sm, s>>>(L, F, x, b, par, skip);
   return cudaGetLastError();
 }
 

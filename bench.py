@@ -40,7 +40,11 @@ MARCH_NODES = 2000000  # FP32 levels of at least this many nodes are smoothed by
 PROFILED_TRAFFIC = {("k_gs_colour<double>", 1025): (46.06e6 + 46.35e6 + 46.26e6 + 11.5e3) / 3,
                     # captured at 4097^2 (profiles/march_f32_4097.md), scaled by the node count
                     ("k_smooth_march<float,2>", 8193): (486.628e6 + 55.349e6) * (8193 / 4097) ** 2,
-                    ("k_smooth_march<float,2>", 4097): 486.628e6 + 55.349e6}
+                    ("k_smooth_march<float,2>", 4097): 486.628e6 + 55.349e6,
+                    # profiles/line_zebra_f32_4097.md (mean of two launches), and scaled to 8193^2
+                    ("k_line_zebra<float>", 4097): (437.738e6 + 29.910e6 + 437.952e6 + 30.042e6) / 2,
+                    ("k_line_zebra<float>", 8193): (437.738e6 + 29.910e6 + 437.952e6 + 30.042e6) / 2
+                    * (8193 / 4097) ** 2}
 
 # Single-instance workloads: (builder, precisions with the headline first, outer iteration,
 # residual tolerance, builder of the bounded CPU sample).  Each tolerance is calibrated so
@@ -56,6 +60,18 @@ WORKLOADS = {
     "annulus_8193": (lambda: I.config3(8193), ("mixed", "fp64"), "fcg", 1e-8,
                      lambda: I.config3(1025)),
 }
+
+
+# Smoother and (nu1, nu2) per workload unless given on the command line: zebra x-line
+# Gauss-Seidel where the map makes the operator anisotropic (the annulus of Eq. 29: x coupling
+# up to 62 times the y coupling; 7 FCG iterations instead of 31), four-colour point
+# Gauss-Seidel elsewhere.
+SMOOTHER_DEFAULT = {"annulus_8193": ("xline", (1, 1))}
+
+
+def smoother_of(args):
+    sm, nu = SMOOTHER_DEFAULT.get(args.workload, ("gs4", (2, 2)))
+    return (args.smoother or sm), (args.nu or nu)
 
 
 def workload(name: str):
@@ -137,11 +153,13 @@ def allmax(dist, v):
 
 
 # ------------------------------------------------------------------ reference arm (oracle)
-def oracle_solve_seconds(inst, rtol=RTOL):
+def oracle_solve_seconds(inst, rtol=RTOL, smoother="gs4", nu=(2, 2)):
     import oracle as O
+    sm = {"gs4": O.SMOOTHER_GS4, "xline": O.SMOOTHER_XLINE}[smoother]
     t0 = time.perf_counter()
     P = O.prepare(inst)
-    phi, it, hist = O.pcg_solve(P.A, P.b, P.phi0, rtol=rtol, max_iters=400)
+    phi, it, hist = O.pcg_solve(P.A, P.b, P.phi0, rtol=rtol, max_iters=400, smoother=sm, nu1=nu[0],
+                                nu2=nu[1])
     return time.perf_counter() - t0, it
 
 
@@ -161,17 +179,19 @@ def run_reference(args):
                   workload(args.workload).grid.unknowns else
                   f"{args.workload} recipe at {inst.grid.nx}^2 per step, same rtol")
     U = inst.grid.unknowns
+    smoother, nu = smoother_of(args)
     for _ in range(args.warmup):
-        oracle_solve_seconds(inst, rtol)
+        oracle_solve_seconds(inst, rtol, smoother, nu)
     tot = 0.0
     for _ in range(args.steps):
-        dt, it = oracle_solve_seconds(inst, rtol)
+        dt, it = oracle_solve_seconds(inst, rtol, smoother, nu)
         tot += dt
     v = U * args.steps / tot
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "unknowns/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": args.workload, "rtol": rtol},
+            "data": "synthetic", "config": {"workload": args.workload, "rtol": rtol, "smoother": smoother,
+                                            "outer": f"fcg+vcycle({nu[0]},{nu[1]})"},
             "cpu_baseline": {"value": v, "unit": "unknowns/s", "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": v, "unit": "unknowns/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -425,6 +445,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     mg.lib()
     _, precisions, outer, rtol, sample_builder = WORKLOADS[args.workload]
+    smoother, nu = smoother_of(args)
     inst = workload(args.workload)
     g = inst.grid
     U = g.unknowns
@@ -443,8 +464,7 @@ def run_ours(args):
     n_in = 1 + (2 if grid_map else 0) + (1 if inst.eps_phys is not None else 0) + \
         (1 if inst.bc is not None else 0)
     for prec in precisions:
-        opts = mg.make_opts(prec, outer, rtol=rtol, max_iters=400, smoother=args.smoother,
-                            nu1=args.nu[0], nu2=args.nu[1])
+        opts = mg.make_opts(prec, outer, rtol=rtol, max_iters=400, smoother=smoother, nu1=nu[0], nu2=nu[1])
         prob = mg.Problem(ctx, inst, opts, device_inputs=True)
 
         def step():
@@ -491,7 +511,7 @@ def run_ours(args):
                      "setup_ms": st.setup_ms, "solve_ms": st.solve_ms}
         prob.close()
     del flush
-    roof = measure_smoother(mg, torch, inst, precisions[0], smoother=args.smoother) if rank == 0 else None
+    roof = measure_smoother(mg, torch, inst, precisions[0], smoother=smoother) if rank == 0 else None
     gridgen = None
     if rank == 0 and grid_map and "r" in inst.meta:
         gridgen = measure_grid_generation(mg, torch, ctx, g.nx, inst.meta["r"], cpu=not args.no_cpu_baseline)
@@ -500,10 +520,11 @@ def run_ours(args):
         import oracle as O
         O.build()
         sample = sample_builder()
-        dt, it = oracle_solve_seconds(sample, rtol)
+        dt, it = oracle_solve_seconds(sample, rtol, smoother, nu)
         cpu = {"value": sample.grid.unknowns / dt, "unit": "unknowns/s", "cores": 1, "kind": "oracle",
                "sample": (f"one {sample.grid.nx}^2 solve of the {args.workload} recipe (coefficients + "
-                          f"MG-preconditioned CG to rtol {rtol}), 1 thread")}
+                          f"MG-preconditioned CG with the same cycle ({smoother}, V({nu[0]},{nu[1]})) to "
+                          f"rtol {rtol}), 1 thread")}
     if rank == 0:
         h, others = precisions[0], precisions[1:]
         rh = res[h]
@@ -514,7 +535,7 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if h == "fp64" else "f32 cycle in f64 refinement", "data": "synthetic",
             "config": {"workload": args.workload, "precision": h,
-                       "outer": f"{outer}+vcycle({args.nu[0]},{args.nu[1]})", "smoother": args.smoother,
+                       "outer": f"{outer}+vcycle({nu[0]},{nu[1]})", "smoother": smoother,
                        "rtol": rtol, "unknowns": U, "l2": "flushed between steps (512 MB write)",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
             "iters": rh["stats"].iters, "levels": rh["levels"], "setup_ms": rh["setup_ms"],
@@ -563,6 +584,7 @@ def run_batch(args):
     dist = dist_init(ws)
     torch.cuda.set_device(local)
     mg.lib()
+    smoother, nu = smoother_of(args)
     insts = [I.inclusion_instance(n, r, e, sd) for n, r, e, sd in specs]
     U = sum(x.grid.unknowns for x in insts)
     nodes = sum(x.grid.nx * x.grid.nyr for x in insts)
@@ -575,7 +597,7 @@ def run_batch(args):
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     res = {}
     for prec in ("mixed", "fp64"):
-        opts = mg.make_opts(prec, "fcg", rtol=BATCH_RTOL, max_iters=400)
+        opts = mg.make_opts(prec, "fcg", rtol=BATCH_RTOL, max_iters=400, smoother=smoother, nu1=nu[0], nu2=nu[1])
         probs = [mg.Problem(ctx, x, opts, device_inputs=True) for x in insts]
         hs = [p.h for p in probs]
         rhos = [d["rho"] for d in dev]
@@ -671,7 +693,8 @@ def run_batch(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 cycle in f64 refinement", "data": "synthetic",
             "config": {"workload": "batch512", "instances": BATCH_COUNT, "sides": [65, 129, 257, 513],
-                       "precision": "mixed", "outer": "fcg+vcycle(2,2)", "rtol": BATCH_RTOL, "unknowns": U,
+                       "precision": "mixed", "outer": f"fcg+vcycle({nu[0]},{nu[1]})", "smoother": smoother,
+                       "rtol": BATCH_RTOL, "unknowns": U,
                        "l2": "flushed between steps (512 MB write)",
                        "parallelism": f"{BATCH_COUNT} instances per GPU x{ws}" if ws > 1 else "1 GPU"},
             "solve_ms": 1e3 * rm["solve"] / args.steps,
@@ -831,10 +854,10 @@ def main():
     ap.add_argument("--serve-max-side", type=int, default=2049, help="serve: largest grid side")
     ap.add_argument("--serve-loads", type=float, nargs="*", default=[0.5, 0.8, 0.95],
                     help="serve: open-loop arrival rates as fractions of the saturated rate")
-    ap.add_argument("--smoother", default="gs4", choices=["gs4", "xline"],
-                    help="four-colour point Gauss-Seidel, or zebra x-line Gauss-Seidel")
-    ap.add_argument("--nu", type=lambda v: tuple(int(t) for t in v.split(",")), default=(2, 2),
-                    help="pre,post smoothing sweeps of the V-cycle")
+    ap.add_argument("--smoother", default=None, choices=["gs4", "xline"],
+                    help="four-colour point Gauss-Seidel, or zebra x-line Gauss-Seidel (default per workload)")
+    ap.add_argument("--nu", type=lambda v: tuple(int(t) for t in v.split(",")), default=None,
+                    help="pre,post smoothing sweeps of the V-cycle (default per workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the size-threshold smoother choice instead of timing the families")

@@ -23,51 +23,80 @@ __device__ __forceinline__ void store_eps(double a, double b, double c, double d
   eyy[k] = sd * (c * c + a * a);        // Eq. 15
 }
 
-__global__ void k_eps_analytic(int kind, double p0, double p1, double p2, double p3, int nx,
-                               int nyr, double x0, double y0, double hx, double hy,
-                               const double* __restrict__ eps, int pitch, double* D, double* exx,
-                               double* exy, double* eyy, int* folded) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i >= nx || j >= nyr) return;
-  const double x = x0 + i * hx, y = y0 + j * hy;
-  double a = 1.0, b = 0.0, c = 0.0, d = 1.0;  // Jxx Jxy Jyx Jyy
-  switch (kind) {
-    case 1: {  // sine warp
-      double sx, cx, sy, cy, s2x, c2x;
-      sincos(kPi * x, &sx, &cx);
-      sincos(kPi * y, &sy, &cy);
-      sincos(2.0 * kPi * x, &s2x, &c2x);
-      a = 1.0 + p0 * kPi * cx * sy;
-      b = p0 * kPi * sx * cy;
-      c = p0 * 2.0 * kPi * c2x * sy;
-      d = 1.0 + p0 * kPi * s2x * cy;
-      break;
+// One CTA per 32 x 32 tile of nodes (32 x 8 threads, four rows each).  Every analytic map's
+// Jacobian is built from transcendental factors of x alone and of y alone, so they are
+// evaluated once per column and once per row of the tile, in shared memory, rather than once
+// per node: FP64 transcendentals, not memory traffic, bound this kernel otherwise.  The
+// factors are the same calls on the same arguments as a per-node evaluation, so the results
+// do not change.
+constexpr int kEpsTile = 32;
+
+__global__ void __launch_bounds__(256) k_eps_analytic(int kind, double p0, double p1, double p2,
+                                                      double p3, int nx, int nyr, double x0, double y0,
+                                                      double hx, double hy,
+                                                      const double* __restrict__ eps, int pitch,
+                                                      double* D, double* exx, double* exy, double* eyy,
+                                                      int* folded) {
+  __shared__ double colv[4][kEpsTile], rowv[2][kEpsTile];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int i0 = blockIdx.x * kEpsTile, j0 = blockIdx.y * kEpsTile;
+  if (ty == 0) {  // factors of x
+    const double x = x0 + (i0 + tx) * hx;
+    if (kind == 1) {
+      sincos(kPi * x, &colv[0][tx], &colv[1][tx]);
+      sincos(2.0 * kPi * x, &colv[2][tx], &colv[3][tx]);
+    } else if (kind == 3) {
+      colv[0][tx] = cosh(p1 * x);
     }
-    case 2: {  // polar, Eq. 29
-      double sy, cy;
-      sincos(y, &sy, &cy);
-      a = cy;
-      b = -x * sy;
-      c = sy;
-      d = x * cy;
-      break;
-    }
-    case 3:  // sinh stretching, Eq. 52
-      a = p0 * p1 * cosh(p1 * x);
-      d = p0 * p1 * cosh(p1 * y);
-      break;
-    case 4:  // affine
-      a = p0;
-      b = p1;
-      c = p2;
-      d = p3;
-      break;
-    default:
-      break;
+  } else if (ty == 1) {  // factors of y
+    const double y = y0 + (j0 + tx) * hy;
+    if (kind == 1) sincos(kPi * y, &rowv[0][tx], &rowv[1][tx]);
+    else if (kind == 2) sincos(y, &rowv[0][tx], &rowv[1][tx]);
+    else if (kind == 3) rowv[0][tx] = cosh(p1 * y);
   }
-  const size_t k = (size_t)j * pitch + i;
-  store_eps(a, b, c, d, eps ? eps[k] : 1.0, k, D, exx, exy, eyy, folded);
+  __syncthreads();
+  const int i = i0 + tx;
+  if (i >= nx) return;
+  const double x = x0 + i * hx;
+#pragma unroll
+  for (int r = 0; r < kEpsTile / 8; ++r) {
+    const int ly = ty + 8 * r, j = j0 + ly;
+    if (j >= nyr) break;
+    double a = 1.0, b = 0.0, c = 0.0, d = 1.0;  // Jxx Jxy Jyx Jyy
+    switch (kind) {
+      case 1: {  // sine warp
+        const double sx = colv[0][tx], cx = colv[1][tx], s2x = colv[2][tx], c2x = colv[3][tx];
+        const double sy = rowv[0][ly], cy = rowv[1][ly];
+        a = 1.0 + p0 * kPi * cx * sy;
+        b = p0 * kPi * sx * cy;
+        c = p0 * 2.0 * kPi * c2x * sy;
+        d = 1.0 + p0 * kPi * s2x * cy;
+        break;
+      }
+      case 2: {  // polar, Eq. 29
+        const double sy = rowv[0][ly], cy = rowv[1][ly];
+        a = cy;
+        b = -x * sy;
+        c = sy;
+        d = x * cy;
+        break;
+      }
+      case 3:  // sinh stretching, Eq. 52
+        a = p0 * p1 * colv[0][tx];
+        d = p0 * p1 * rowv[0][ly];
+        break;
+      case 4:  // affine
+        a = p0;
+        b = p1;
+        c = p2;
+        d = p3;
+        break;
+      default:
+        break;
+    }
+    const size_t k = (size_t)j * pitch + i;
+    store_eps(a, b, c, d, eps ? eps[k] : 1.0, k, D, exx, exy, eyy, folded);
+  }
 }
 
 // d/dx: central difference (Eqs. 39, 41), one-sided second order at the line ends;
@@ -325,9 +354,9 @@ cudaError_t launch_eps_analytic(int kind, const double* prm, int nx, int ny, int
                                 int pitch, double* D, double* exx, double* exy, double* eyy,
                                 int* folded, cudaStream_t s) {
   const int nyr = rows_stored(ny, periodic);
-  dim3 b(32, 8);
-  k_eps_analytic<<<grid2(nx, nyr, b), b, 0, s>>>(kind, prm[0], prm[1], prm[2], prm[3], nx, nyr, x0,
-                                                 y0, hx, hy, eps, pitch, D, exx, exy, eyy, folded);
+  dim3 b(32, 8), g((nx + kEpsTile - 1) / kEpsTile, (nyr + kEpsTile - 1) / kEpsTile);
+  k_eps_analytic<<<g, b, 0, s>>>(kind, prm[0], prm[1], prm[2], prm[3], nx, nyr, x0, y0, hx, hy, eps, pitch,
+                                 D, exx, exy, eyy, folded);
   return cudaGetLastError();
 }
 

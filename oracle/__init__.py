@@ -40,6 +40,7 @@ _handle = None
 SMOOTHER_GS4 = 0
 SMOOTHER_JACOBI = 1
 SMOOTHER_XLINE = 2  # zebra x-line Gauss-Seidel
+SMOOTHER_SOR4 = 3   # four-colour SOR (single-level iteration; factor in omega_j)
 DEFAULT_COARSE_MAX = 64
 
 
@@ -81,6 +82,7 @@ def lib():
             "orc_paper_sor": [i, i, d, d, D, D, D, D, D, d, d, i],
             "orc_pcg_solve": [i, i, i, D, D, D, D, D, D, D, i, i, i, d, i, d, i, i, D],
             "orc_line_rows": [i, i, i, D, D, D, D, D, D, D, i],
+            "orc_sor_solve": [i, i, i, D, D, D, D, D, D, D, d, d, i, i, D],
             "orc_mask_dirichlet": [i, i, i, D, D, D, D, D, ctypes.POINTER(ctypes.c_ubyte), D, D],
             "orc_hier_free": [ctypes.c_void_p],
             "orc_hier_vcycle": [ctypes.c_void_p, D, D],
@@ -212,6 +214,15 @@ def smooth(A: Operator, phi, b, sweeps=1, reverse=False, smoother=SMOOTHER_GS4, 
     out = _f64(phi).copy()
     lib().orc_smooth(*A._args(), _p(out), _p(_f64(b)), smoother, sweeps, int(reverse), omega_j)
     return out
+
+
+def sor_solve(A: Operator, b, phi0, omega=1.875, rtol=1e-10, max_sweeps=200000, check=16):
+    """Four-colour SOR (single-level) to a relative residual rtol, checked every `check`
+    sweeps.  Returns (phi, sweeps, history of relative residuals at the checks)."""
+    phi = _f64(phi0).copy()
+    hist = np.zeros(max_sweeps // max(check, 1) + 2)
+    sw = lib().orc_sor_solve(*A._args(), _p(_f64(b)), _p(phi), omega, rtol, max_sweeps, check, _p(hist))
+    return phi, sw, hist[:sw // max(check, 1) + 1].copy()
 
 
 def line_rows(A: Operator, phi, b, parity):

@@ -392,3 +392,62 @@ def test_line_smoothing_makes_the_annulus_cycle_robust(oracle):
     _, it_ln, _ = oracle.pcg_solve(P.A, P.b, P.phi0, rtol=1e-8, max_iters=200, nu1=1, nu2=1,
                                    smoother=oracle.SMOOTHER_XLINE)
     assert it_ln <= 8 and it_pt >= 3 * it_ln, (it_ln, it_pt)
+
+
+# ---------------------------------------------------------------- SOR (Sec. 4 comparison method)
+def _rows_decoupled_laplacian(N, rows=1):
+    """1-D Poisson rows (diag 2, E/W -1) with every coupling between rows removed."""
+    import oracle as O
+    nx, ny = N + 2, rows + 2
+    cE = np.zeros((ny, nx))
+    cE[:, :-1] = -1.0
+    z = np.zeros((ny, nx))
+    diag = np.full((ny, nx), 2.0)
+    return O.Operator(nx, ny, False, cE, z.copy(), z.copy(), z.copy(), diag)
+
+
+@pytest.mark.parametrize("omega", [1.5, 1.9])
+def test_sor_contraction_factor_matches_youngs_theorem(oracle, omega):
+    """On one row of the 1-D Poisson matrix the four-colour order is red-black, a consistent
+    ordering, so Young's theorem gives SOR's asymptotic contraction factor from the Jacobi
+    spectral radius mu = cos(pi h): (omega mu + sqrt(omega^2 mu^2 - 4 (omega - 1)))^2 / 4 below
+    the optimal omega, omega - 1 above it.  The measured per-sweep residual contraction
+    (geometric mean over the last sweeps) must match."""
+    N = 31
+    A = _rows_decoupled_laplacian(N)
+    mu = np.cos(np.pi / (N + 1))
+    w_opt = 2.0 / (1.0 + np.sqrt(1.0 - mu * mu))
+    if omega < w_opt:
+        rho = ((omega * mu + np.sqrt(omega * omega * mu * mu - 4.0 * (omega - 1.0))) / 2.0) ** 2
+    else:
+        rho = omega - 1.0
+    rng = np.random.default_rng(4)
+    phi0 = np.zeros(A.cE.shape)
+    phi0[1, 1:-1] = rng.standard_normal(N)
+    _, sw, hist = oracle.sor_solve(A, np.zeros(A.cE.shape), phi0, omega=omega, rtol=0.0, max_sweeps=400,
+                                   check=1)
+    assert sw == 400
+    rate = (hist[400] / hist[200]) ** (1.0 / 200)
+    assert abs(rate - rho) < 2e-3 * rho, (rate, rho)
+
+
+def test_sor_with_unit_factor_is_gauss_seidel(oracle):
+    inst = I.config1(33)
+    P = oracle.prepare(inst)
+    rng = np.random.default_rng(6)
+    phi = rng.standard_normal(P.A.cE.shape)
+    gs = oracle.smooth(P.A, phi, P.b, sweeps=2, smoother=oracle.SMOOTHER_GS4)
+    sor = oracle.smooth(P.A, phi, P.b, sweeps=2, smoother=oracle.SMOOTHER_SOR4, omega_j=1.0)
+    assert np.abs(gs - sor).max() < 1e-13 * np.abs(gs).max()
+
+
+def test_sor_solve_reaches_the_dense_solution(oracle):
+    """SOR at the paper's omega = 1.875 on a warped 17^2 grid, to rtol 1e-12, against numpy's
+    dense solve of the same system."""
+    inst = I.config1(17)
+    P = oracle.prepare(inst)
+    phi, sw, hist = oracle.sor_solve(P.A, P.b, P.phi0, omega=1.875, rtol=1e-12, max_sweeps=20000, check=4)
+    ref = oracle.dense_solve(P.A, P.b) + P.phi0 * ~inst.grid.interior_mask()
+    assert hist[-1] <= 1e-12 and sw < 20000
+    m = inst.grid.interior_mask()
+    assert np.abs(phi[m] - ref[m]).max() < 1e-10 * np.abs(ref[m]).max()

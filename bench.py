@@ -841,6 +841,66 @@ def run_serve(args):
     return 0
 
 
+# ------------------------------------------------------------------ SOR baseline
+SOR_CASES = (("sine_warp_129", lambda: I.config1(129)), ("circle_poisson_257", lambda: I.circle_poisson(257)),
+             ("inclusion_257", lambda: I.inclusion_instance(257, 0.25, 10.0, 2)))
+SOR_OMEGA, SOR_RTOL = 1.875, 1e-10
+
+
+def run_sor(args):
+    """The paper's comparison (Sec. 4): the single-level SOR iteration (omega 1.875) against
+    multigrid on the same problems and to the same residual tolerance, here both on the GPU
+    (four-colour SOR, MG_OUTER_SOR, 16 sweeps per residual test; FP64 FCG + V(2,2)) and both
+    in the CPU oracle (one thread).  Reports solve times (hierarchy resident, inputs on the
+    device) and their ratio per problem."""
+    import torch
+    from paper_2602_01888_gb300 import mg
+    import oracle as O
+    torch.cuda.set_device(0)
+    ctx = mg.Context(0)
+    ctx.use_torch_stream()
+    rows = []
+    for name, build in SOR_CASES:
+        inst = build()
+        rho = torch.from_numpy(np.ascontiguousarray(inst.rho_phys)).cuda()
+        bc = None if inst.bc is None else torch.from_numpy(np.ascontiguousarray(inst.bc)).cuda()
+        phi = torch.zeros(inst.grid.shape, dtype=torch.float64, device="cuda")
+        so = mg.make_opts("fp64", "sor", rtol=SOR_RTOL, max_iters=200000, nu1=16, omega_j=SOR_OMEGA)
+        go = mg.make_opts("fp64", "fcg", rtol=SOR_RTOL, max_iters=400)
+        pr = mg.Problem(ctx, inst, go, device_inputs=True)
+        res = {}
+        for tag, o in (("gmg", go), ("sor", so)):
+            for _ in range(args.warmup if tag == "gmg" else 1):
+                mg.mg_solve(pr.h, rho, bc, phi, o)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = args.steps if tag == "gmg" else 1
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(reps):
+                st = mg.mg_solve(pr.h, rho, bc, phi, o)
+            e1.record()
+            torch.cuda.synchronize()
+            res[tag] = (e0.elapsed_time(e1) / reps, st.iters, st.rel_residual)
+        pr.close()
+        P = O.prepare(inst)
+        t0 = time.perf_counter()
+        _, sw_cpu, _ = O.sor_solve(P.A, P.b, P.phi0, omega=SOR_OMEGA, rtol=SOR_RTOL, max_sweeps=400000, check=16)
+        t_sor_cpu = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        _, it_cpu, _ = O.pcg_solve(P.A, P.b, P.phi0, rtol=SOR_RTOL, max_iters=400)
+        t_gmg_cpu = time.perf_counter() - t0
+        rows.append({"problem": name, "unknowns": inst.grid.unknowns,
+                     "gpu": {"sor_ms": res["sor"][0], "sor_sweeps": 16 * res["sor"][1], "gmg_ms": res["gmg"][0],
+                             "gmg_iters": res["gmg"][1], "sor_over_gmg": res["sor"][0] / res["gmg"][0]},
+                     "cpu_oracle_1_thread": {"sor_ms": 1e3 * t_sor_cpu, "sor_sweeps": sw_cpu,
+                                             "gmg_ms": 1e3 * t_gmg_cpu, "gmg_iters": it_cpu,
+                                             "sor_over_gmg": t_sor_cpu / t_gmg_cpu}})
+    ctx.close()
+    print(json.dumps({"metric": "solve time of SOR (omega 1.875) over multigrid, same residual tolerance",
+                      "rtol": SOR_RTOL, "dtype": "f64", "data": "synthetic", "cases": rows}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -848,7 +908,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="inclusion_1025",
-                    choices=sorted(WORKLOADS) + ["batch512", "serve"])
+                    choices=sorted(WORKLOADS) + ["batch512", "serve", "sor_vs_gmg"])
     ap.add_argument("--requests", type=int, default=2000, help="serve: requests per pass")
     ap.add_argument("--inflight", type=int, default=16, help="serve: concurrent request slots")
     ap.add_argument("--serve-max-side", type=int, default=2049, help="serve: largest grid side")
@@ -877,6 +937,8 @@ def main():
         return run_batch(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "sor_vs_gmg":
+        return run_sor(args)
     return run_ours(args)
 
 

@@ -69,7 +69,11 @@ typedef enum {
 } mg_map_kind;
 
 typedef enum { MG_PREC_FP64 = 0, MG_PREC_MIXED = 1 } mg_precision;
-typedef enum { MG_OUTER_VCYCLE = 0, MG_OUTER_FCG = 1 } mg_outer;
+/* Outer iteration: plain V-cycles, flexible CG preconditioned by one V-cycle, or - as the
+ * single-level baseline the paper compares multigrid against (Sec. 4) - four-colour SOR on the
+ * finest operator: each iteration is nu1 sweeps (1..16) with factor omega_j (0 < omega_j < 2;
+ * the paper uses 1.875), the residual tested before each iteration; FP64 only, no cycle. */
+typedef enum { MG_OUTER_VCYCLE = 0, MG_OUTER_FCG = 1, MG_OUTER_SOR = 2 } mg_outer;
 /* Smoother: four-colour point Gauss-Seidel (the paper's smoother in parallel order),
  * weighted Jacobi, or zebra x-line Gauss-Seidel (rows of one parity solved as tridiagonal
  * systems; for operators dominated by the x coupling, e.g. the annulus of Eq. 29).  The line
@@ -100,9 +104,9 @@ typedef struct {
   int outer;          /* mg_outer: plain V-cycles, or flexible CG preconditioned by one V-cycle */
   int smoother;       /* mg_smoother */
   int nu1, nu2;       /* pre / post smoothing sweeps */
-  double omega_j;     /* weighted-Jacobi factor */
+  double omega_j;     /* weighted-Jacobi factor; the SOR factor for MG_OUTER_SOR */
   double rtol;        /* stop when ||r||_2 / ||r_0||_2 <= rtol (r_0: residual of zero unknowns) */
-  int max_iters;      /* cycles (VCYCLE) or CG iterations (FCG) */
+  int max_iters;      /* cycles (VCYCLE), CG iterations (FCG) or SOR iterations of nu1 sweeps (SOR) */
   int coarse_max;     /* coarsest level: first level with at most this many unknowns (<= 256) */
   int warm_start;     /* 1: phi holds the initial guess of the unknowns */
 } mg_solve_opts;

@@ -75,6 +75,14 @@ int mgk_smooth_f64(const mgk_op_f64 *A, double *phi, const double *b, int sweeps
 int mgk_smooth_f32(const mgk_op_f32 *A, float *phi, const float *b, int sweeps, int reverse,
                    void *stream);
 
+/* Four-colour successive over-relaxation, the single-level iteration the paper compares
+ * against (Sec. 4, omega = 1.875 there): `sweeps` sweeps in the forward colour order; at each
+ * unknown of a colour phi += omega (gs - phi), gs its Gauss-Seidel value.  0 < omega < 2. */
+int mgk_sor_f64(const mgk_op_f64 *A, double *phi, const double *b, int sweeps, double omega,
+                void *stream);
+int mgk_sor_f32(const mgk_op_f32 *A, float *phi, const float *b, int sweeps, double omega,
+                void *stream);
+
 /* Weighted Jacobi: phi += omega (b - A phi) / diag at unknowns, `sweeps` times; tmp is a
  * pitched scratch array of the same shape. */
 int mgk_jacobi_f64(const mgk_op_f64 *A, double *phi, const double *b, double *tmp, int sweeps,

@@ -23,6 +23,20 @@ __global__ void __launch_bounds__(256) k_gs_colour(Lvl<T> L, T* __restrict__ x,
   x[k] = (b[k] - offdiag(L, x, i, j)) * L.dinv[k];
 }
 
+// One colour phase of successive over-relaxation: x += omega (gs - x) at the unknowns of
+// the colour, gs the Gauss-Seidel value (the comparison iteration of Sec. 4).
+template <typename T>
+__global__ void __launch_bounds__(256) k_sor_colour(Lvl<T> L, T* __restrict__ x, const T* __restrict__ b,
+                                                    int ci, int cj, T omega, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  const int i = ci + 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const int j = cj + 2 * (blockIdx.y * blockDim.y + threadIdx.y);
+  if (!is_unknown(L, i, j)) return;
+  const size_t k = (size_t)j * L.pitch + i;
+  const T gs = (b[k] - offdiag(L, x, i, j)) * L.dinv[k];
+  x[k] = fma(omega, gs - x[k], x[k]);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_residual(Lvl<T> L, const T* __restrict__ x,
                                                   const T* __restrict__ b, T* __restrict__ r,
@@ -160,6 +174,20 @@ cudaError_t launch_smooth(const Op<T>& A, T* phi, const T* b, int sweeps, int re
 }
 
 template <typename T>
+cudaError_t launch_sor(const Op<T>& A, T* phi, const T* b, int sweeps, double omega, const int* skip,
+                       cudaStream_t s) {
+  const Lvl<T> L = lvl_of(A);
+  dim3 bl(32, 8);
+  for (int sw = 0; sw < sweeps; ++sw)
+    for (int c = 0; c < 4; ++c) {
+      const int ci = colour_ci(c), cj = colour_cj(c);
+      const int ncx = (L.nx - ci + 1) / 2, ncy = (L.nyr - cj + 1) / 2;
+      k_sor_colour<T><<<g2(ncx, ncy, bl), bl, 0, s>>>(L, phi, b, ci, cj, (T)omega, skip);
+    }
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_residual(const Op<T>& A, const T* phi, const T* b, T* r, const int* skip,
                             cudaStream_t s) {
   const Lvl<T> L = lvl_of(A);
@@ -215,6 +243,8 @@ cudaError_t launch_coarse_solve(const Op<T>& A, const double* inv, const T* b, T
                                            cudaStream_t);                                        \
   template cudaError_t launch_smooth<T>(const Op<T>&, T*, const T*, int, int, const int*,      \
                                         cudaStream_t);                                           \
+  template cudaError_t launch_sor<T>(const Op<T>&, T*, const T*, int, double, const int*,       \
+                                     cudaStream_t);                                              \
   template cudaError_t launch_residual<T>(const Op<T>&, const T*, const T*, T*, const int*,    \
                                           cudaStream_t);                                         \
   template cudaError_t launch_jacobi<T>(const Op<T>&, T*, const T*, T*, int, double,           \
@@ -251,6 +281,16 @@ extern "C" int mgk_smooth_f32(const mgk_op_f32* A, float* phi, const float* b, i
                               int reverse, void* stream) {
   if (!opk(A) || !phi || !b || sweeps < 0) return 1;
   return rc(launch_smooth(op_from(*A), phi, b, sweeps, reverse, nullptr, (cudaStream_t)stream));
+}
+extern "C" int mgk_sor_f64(const mgk_op_f64* A, double* phi, const double* b, int sweeps, double omega,
+                           void* stream) {
+  if (!opk(A) || !phi || !b || sweeps < 0 || !(omega > 0.0 && omega < 2.0)) return 1;
+  return rc(launch_sor(op_from(*A), phi, b, sweeps, omega, nullptr, (cudaStream_t)stream));
+}
+extern "C" int mgk_sor_f32(const mgk_op_f32* A, float* phi, const float* b, int sweeps, double omega,
+                           void* stream) {
+  if (!opk(A) || !phi || !b || sweeps < 0 || !(omega > 0.0 && omega < 2.0)) return 1;
+  return rc(launch_sor(op_from(*A), phi, b, sweeps, omega, nullptr, (cudaStream_t)stream));
 }
 extern "C" int mgk_jacobi_f64(const mgk_op_f64* A, double* phi, const double* b, double* tmp,
                               int sweeps, double omega, void* stream) {

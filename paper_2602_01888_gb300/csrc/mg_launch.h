@@ -76,6 +76,10 @@ cudaError_t launch_gs_colour(const Op<T>& A, T* phi, const T* b, int colour, con
 template <typename T>
 cudaError_t launch_smooth(const Op<T>& A, T* phi, const T* b, int sweeps, int reverse,
                           const int* skip, cudaStream_t s);
+// `sweeps` sweeps of four-colour SOR with factor omega (forward colour order).
+template <typename T>
+cudaError_t launch_sor(const Op<T>& A, T* phi, const T* b, int sweeps, double omega, const int* skip,
+                       cudaStream_t s);
 template <typename T>
 cudaError_t launch_residual(const Op<T>& A, const T* phi, const T* b, T* r, const int* skip,
                             cudaStream_t s);

@@ -649,6 +649,12 @@ static mg_status emit_body(mg_problem* P, const mg_solve_opts& o, cudaGraphCondi
   const size_t n0 = (size_t)F.A.pitch * rows_stored(F.A.ny, F.A.periodic);
   const bool mixed = (o.precision == MG_PREC_MIXED);
   mg_status st;
+  if (o.outer == MG_OUTER_SOR) {  // single-level baseline: nu1 SOR sweeps per tested iteration
+    CU(launch_resid_check(F.A, F.x, F.b, nullptr, P->st, P->part, h, has_h, s));
+    CU(launch_sor<double>(F.A, F.x, F.b, o.nu1, o.omega_j, skip, s));
+    CU(launch_iter_inc(P->st, s));
+    return MG_OK;
+  }
   if (o.outer == MG_OUTER_VCYCLE) {
     if (!mixed) {
       CU(launch_resid_check(F.A, F.x, F.b, nullptr, P->st, P->part, h, has_h, s));
@@ -873,8 +879,15 @@ mg_status check_opts(const mg_problem* P, const mg_solve_opts& o) {
     return set_error(MG_ERR_ARG, "bad precision %d", o.precision);
   if ((o.precision == MG_PREC_MIXED) != (P->mixed != 0))
     return set_error(MG_ERR_ARG, "solve precision differs from the precision the problem was set up with");
-  if (o.outer != MG_OUTER_VCYCLE && o.outer != MG_OUTER_FCG)
+  if (o.outer != MG_OUTER_VCYCLE && o.outer != MG_OUTER_FCG && o.outer != MG_OUTER_SOR)
     return set_error(MG_ERR_ARG, "bad outer iteration %d", o.outer);
+  if (o.outer == MG_OUTER_SOR) {
+    if (o.precision != MG_PREC_FP64) return set_error(MG_ERR_ARG, "the SOR iteration runs in FP64 only");
+    if (o.nu1 < 1 || o.nu1 > 16) return set_error(MG_ERR_ARG, "SOR: nu1 (sweeps per iteration) must be 1..16");
+    if (!(o.omega_j > 0.0 && o.omega_j < 2.0)) return set_error(MG_ERR_ARG, "SOR: omega_j must lie in (0, 2)");
+    if (o.max_iters < 1 || !(o.rtol >= 0)) return set_error(MG_ERR_ARG, "bad rtol / max_iters");
+    return MG_OK;
+  }
   if (o.smoother != MG_SMOOTH_GS4 && o.smoother != MG_SMOOTH_JACOBI && o.smoother != MG_SMOOTH_XLINE)
     return set_error(MG_ERR_ARG, "bad smoother %d", o.smoother);
   if (o.smoother == MG_SMOOTH_XLINE &&

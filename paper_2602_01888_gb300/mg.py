@@ -26,7 +26,8 @@ MG_ERR_NOT_CONVERGED, MG_ERR_DIVERGED, MG_ERR_TIMEOUT, MG_ERR_BUSY, MG_ERR_NOT_F
 MG_ERR_NOT_SPD = 11
 MG_MEM_HOST, MG_MEM_DEVICE = 0, 1
 MG_PREC_FP64, MG_PREC_MIXED = 0, 1
-MG_OUTER_VCYCLE, MG_OUTER_FCG = 0, 1
+MG_OUTER_VCYCLE, MG_OUTER_FCG, MG_OUTER_SOR = 0, 1, 2
+_OUTERS = {"vcycle": MG_OUTER_VCYCLE, "fcg": MG_OUTER_FCG, "sor": MG_OUTER_SOR}
 MG_SMOOTH_GS4, MG_SMOOTH_JACOBI, MG_SMOOTH_XLINE = 0, 1, 2
 _SMOOTHERS = {"gs4": MG_SMOOTH_GS4, "jacobi": MG_SMOOTH_JACOBI, "xline": MG_SMOOTH_XLINE}
 MAP_CODES = {"identity": 0, "sine_warp": 1, "polar": 2, "sinh": 3, "affine": 4, "grid": 5}
@@ -142,6 +143,10 @@ _SIGS = {
                         C.c_void_p], C.c_int),
     "mgk_smooth_f32": ([C.POINTER(mgk_op_f32), C.c_void_p, C.c_void_p, C.c_int, C.c_int,
                         C.c_void_p], C.c_int),
+    "mgk_sor_f64": ([C.POINTER(mgk_op_f64), C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_void_p],
+                    C.c_int),
+    "mgk_sor_f32": ([C.POINTER(mgk_op_f32), C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_void_p],
+                    C.c_int),
     "mgk_jacobi_f64": ([C.POINTER(mgk_op_f64), C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                         C.c_double, C.c_void_p], C.c_int),
     "mgk_residual_f64": ([C.POINTER(mgk_op_f64), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
@@ -577,7 +582,9 @@ def make_opts(precision="fp64", outer="fcg", rtol=1e-10, max_iters=200, nu1=2, n
               smoother="gs4", coarse_max=64, omega_j=0.8, warm_start=False) -> mg_solve_opts:
     o = mg_default_opts()
     o.precision = MG_PREC_MIXED if precision == "mixed" else MG_PREC_FP64
-    o.outer = MG_OUTER_FCG if outer == "fcg" else MG_OUTER_VCYCLE
+    if outer not in _OUTERS:
+        raise ValueError(f"unknown outer iteration {outer!r} (one of {sorted(_OUTERS)})")
+    o.outer = _OUTERS[outer]
     if smoother not in _SMOOTHERS:
         raise ValueError(f"unknown smoother {smoother!r} (one of {sorted(_SMOOTHERS)})")
     o.smoother = _SMOOTHERS[smoother]

@@ -26,7 +26,7 @@ import ctypes
 import os
 import subprocess
 import threading
-from dataclasses import dataclass
+from dataclasses import dataclass, replace
 from typing import Optional
 
 import numpy as np
@@ -326,6 +326,11 @@ class Prepared:
     b: np.ndarray
     phi0: np.ndarray
     status: int
+    take: Optional[np.ndarray] = None  # Neumann grids: row of the doubled system per grid row
+
+    def extract(self, phi):
+        """The solution on the instance's own grid from a solution of the system A."""
+        return np.asarray(phi) if self.take is None else np.asarray(phi)[self.take]
 
 
 def boundary_ring(grid, bc):
@@ -337,9 +342,45 @@ def boundary_ring(grid, bc):
     return phi0
 
 
+def doubled_grid(g):
+    """The periodic grid of twice the height on which a grid with Neumann y sides is solved:
+    y in [y0 - ly, y0 + ly), 2 (ny - 1) stored rows."""
+    return replace(g, ny=2 * (g.ny - 1) + 1, y0=g.y0 - g.ly, ly=2.0 * g.ly, periodic_y=True, neumann_y=False)
+
+
+def neumann_rows(ny):
+    """Even reflection of an ny-row grid into the doubled periodic grid: for each row of the
+    doubled grid the row of the original it copies and the factor applied to eps_xy there
+    (+1 in the original half, -1 in the mirrored half, 0 on the two Neumann rows, where an odd
+    function vanishes); and for each original row its row in the doubled grid."""
+    n = ny - 1
+    jd = np.arange(2 * n)
+    src = np.where(jd >= n, jd - n, n - jd)
+    sign = np.where(jd >= n, 1.0, -1.0)
+    sign[0] = sign[n] = 0.0
+    take = np.where(np.arange(ny) < n, np.arange(ny) + n, 0)
+    return src, sign, take
+
+
 def prepare(inst) -> Prepared:
-    """Coefficient build (Eqs. 10-15, 39-42), operator and right-hand side (Eq. 11)."""
+    """Coefficient build (Eqs. 10-15, 39-42), operator and right-hand side (Eq. 11).
+
+    A grid with Neumann y sides (Eq. 28) is solved as the periodic problem on the doubled
+    grid whose coefficients, charge, Dirichlet data and D are the even reflection of the
+    original ones (eps_xy odd): its solution is even about both sides, so its normal
+    derivative there vanishes, and the boundary rows carry the standard mirror-node
+    discretization of the Neumann condition."""
     g = inst.grid
+    if getattr(g, "neumann_y", False):
+        g0 = replace(g, neumann_y=False)
+        J = jacobian(g0, inst.map)  # one-sided differences on the Neumann rows (grid maps)
+        D, exx, exy, eyy, st = eps_tensor(J, inst.eps_phys)
+        src, sign, take = neumann_rows(g.ny)
+        gd = doubled_grid(g)
+        A = assemble(gd, exx[src], exy[src] * sign[:, None], eyy[src])
+        b = rhs(gd, np.asarray(inst.rho_phys)[src], D[src])
+        phi0 = boundary_ring(gd, None if inst.bc is None else np.asarray(inst.bc)[src])
+        return Prepared(J, D, exx, exy, eyy, A, b, phi0, st, take=take)
     J = jacobian(g, inst.map)
     D, exx, exy, eyy, st = eps_tensor(J, inst.eps_phys)
     A = assemble(g, exx, exy, eyy)

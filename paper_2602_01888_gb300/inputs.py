@@ -49,7 +49,9 @@ class Grid:
     """Uniform computational grid of nx x ny vertices on [x0, x0+lx] x [y0, y0+ly].
 
     Arrays are row-major (nyr, nx) with i (x) contiguous.  A grid periodic in y has
-    ny - 1 stored rows (row ny-1 coincides with row 0).
+    ny - 1 stored rows (row ny-1 coincides with row 0).  With neumann_y the two y sides
+    carry a homogeneous Neumann condition (their nodes are unknowns); the x sides stay
+    Dirichlet.
     """
 
     nx: int
@@ -59,6 +61,7 @@ class Grid:
     lx: float = 1.0
     ly: float = 1.0
     periodic_y: bool = False
+    neumann_y: bool = False
 
     @property
     def hx(self) -> float:
@@ -78,7 +81,7 @@ class Grid:
 
     @property
     def unknowns(self) -> int:
-        return (self.nx - 2) * (self.nyr if self.periodic_y else self.ny - 2)
+        return (self.nx - 2) * (self.nyr if (self.periodic_y or self.neumann_y) else self.ny - 2)
 
     def coords(self):
         x = self.x0 + self.hx * np.arange(self.nx)
@@ -87,7 +90,7 @@ class Grid:
 
     def interior_mask(self):
         m = np.zeros(self.shape, dtype=bool)
-        if self.periodic_y:
+        if self.periodic_y or self.neumann_y:
             m[:, 1:-1] = True
         else:
             m[1:-1, 1:-1] = True
@@ -577,6 +580,27 @@ def annulus_log(n: int) -> Instance:
     x, _ = grid.coords()
     exact = np.log(1.0 / x) / np.log(1.0 / 0.2)
     return Instance(f"annulus_log_{n}", grid, mp, np.zeros(grid.shape), bc=exact.copy(),
+                    exact=exact)
+
+
+def semi_annulus(n: int, a: float = 2.0, R: float = 5.0, phi0: float = 1.0) -> Instance:
+    """The semi-annulus of Sec. 4.1 (Eq. 28): r in [a, R], theta in [0, pi] by the polar map
+    (Eq. 29), phi = phi0 at r = a, 0 at r = R, zero normal derivative at theta = 0 and pi,
+    charge-free; exact solution phi0 ln(R/r) / ln(R/a) (Eq. 28-a)."""
+    grid = Grid(n, n, x0=a, y0=0.0, lx=R - a, ly=math.pi, neumann_y=True)
+    x, _ = grid.coords()
+    exact = phi0 * np.log(R / x) / np.log(R / a)
+    return Instance(f"semi_annulus_{n}", grid, MapSpec("polar"), np.zeros(grid.shape), bc=exact.copy(),
+                    exact=exact)
+
+
+def neumann_manufactured(n: int) -> Instance:
+    """Unit square, identity map, phi = sin(pi x) cos(pi y): zero at x = 0, 1 and zero normal
+    derivative at y = 0, 1; rho = 2 pi^2 phi."""
+    grid = Grid(n, n, neumann_y=True)
+    x, y = grid.coords()
+    exact = np.sin(np.pi * x) * np.cos(np.pi * y)
+    return Instance(f"neumann_mms_{n}", grid, MapSpec("identity"), 2 * np.pi ** 2 * exact, bc=np.zeros(grid.shape),
                     exact=exact)
 
 

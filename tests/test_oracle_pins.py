@@ -451,3 +451,84 @@ def test_sor_solve_reaches_the_dense_solution(oracle):
     assert hist[-1] <= 1e-12 and sw < 20000
     m = inst.grid.interior_mask()
     assert np.abs(phi[m] - ref[m]).max() < 1e-10 * np.abs(ref[m]).max()
+
+
+# ---------------------------------------------------------------- Neumann sides (Sec. 4.1, Eq. 28)
+def _neumann_solution(oracle, inst, rtol=1e-14):
+    P = oracle.prepare(inst)
+    phi, _, _ = oracle.pcg_solve(P.A, P.b, P.phi0, rtol=rtol, max_iters=400, stagnate=5)
+    return P.extract(phi)
+
+
+@pytest.mark.parametrize("n", [17, 33, 65])
+def test_semi_annulus_is_the_one_dimensional_radial_solution(oracle, n):
+    """The polar map gives eps = diag(r, 1/r) and rows that are all alike, so with zero normal
+    derivative on the two straight sides the discrete solution cannot depend on theta: every
+    row equals the solution of the 1-D radial problem -d/dr(r dphi/dr) = 0 discretized with
+    the same face means (r_i + r_{i+1}) / 2, solved here by numpy."""
+    inst = I.semi_annulus(n)
+    phi = _neumann_solution(oracle, inst)
+    g = inst.grid
+    r = g.x0 + g.hx * np.arange(g.nx)
+    e = 0.5 * (r[:-1] + r[1:])
+    N = g.nx - 2
+    M = np.zeros((N, N))
+    rhs = np.zeros(N)
+    for k in range(N):
+        M[k, k] = e[k] + e[k + 1]
+        if k > 0:
+            M[k, k - 1] = -e[k]
+        if k < N - 1:
+            M[k, k + 1] = -e[k + 1]
+    rhs[0] += e[0] * 1.0  # phi0 = 1 at r = a; 0 at r = R
+    ref = np.concatenate([[1.0], np.linalg.solve(M, rhs), [0.0]])
+    assert np.abs(phi - ref[None, :]).max() < 1e-12
+
+
+def test_semi_annulus_converges_at_second_order_to_eq_28a(oracle):
+    errs = []
+    for n in (33, 65, 129):
+        inst = I.semi_annulus(n)
+        phi = _neumann_solution(oracle, inst)
+        errs.append(np.abs(phi - inst.exact).max())
+    assert errs[0] / errs[1] > 3.6 and errs[1] / errs[2] > 3.6, errs
+
+
+def test_neumann_manufactured_solution_converges_at_second_order(oracle):
+    """phi = sin(pi x) cos(pi y) varies along the Neumann sides: the boundary rows are
+    exercised, not only the interior."""
+    errs = []
+    for n in (17, 33, 65):
+        inst = I.neumann_manufactured(n)
+        phi = _neumann_solution(oracle, inst)
+        errs.append(np.abs(phi - inst.exact).max())
+    assert errs[0] / errs[1] > 3.6 and errs[1] / errs[2] > 3.6, errs
+
+
+def _skew_map(x, y):
+    return x + 0.08 * np.sin(np.pi * x) * np.cos(np.pi * y), y + 0.08 * np.sin(np.pi * x) * np.sin(np.pi * y)
+
+
+@pytest.mark.parametrize("n", [33, 65])
+def test_neumann_reflection_equals_the_doubled_problem_of_a_skewed_grid(oracle, n):
+    """A skewed mapped grid (eps_xy != 0 inside) that is itself mirror-symmetric about both y
+    sides: the Neumann problem on [0,1]^2 must equal the periodic problem on y in [-1, 1)
+    built directly from the map (central differences everywhere, y' jumping by 2 across the
+    seam).  The two differ only by the one-sided Jacobian on the Neumann rows, O(h^2); an
+    eps_xy of the wrong sign in the mirrored half would leave an O(1) difference."""
+    g = I.Grid(n, n, neumann_y=True)
+    x, y = g.coords()
+    xp, yp = _skew_map(x, y)
+    rho = 1.0 + xp * np.cos(np.pi * yp)
+    inst = I.Instance("skew", g, I.MapSpec("grid", xp=xp, yp=yp), rho, bc=np.zeros(g.shape))
+    phi = _neumann_solution(oracle, inst)
+    gd = oracle.doubled_grid(g)
+    xd, yd = gd.coords()
+    xpd, ypd = _skew_map(xd, yd)
+    direct = I.Instance("skew2", gd, I.MapSpec("grid", xp=xpd, yp=ypd, jump=(0.0, 2.0)),
+                        1.0 + xpd * np.cos(np.pi * ypd), bc=np.zeros(gd.shape))
+    Pd = oracle.prepare(direct)
+    phid, _, _ = oracle.pcg_solve(Pd.A, Pd.b, Pd.phi0, rtol=1e-14, max_iters=400, stagnate=5)
+    _, _, take = oracle.neumann_rows(n)
+    diff = np.abs(phi - phid[take]).max() / np.abs(phi).max()
+    assert diff < 2.0 * g.hx ** 2, diff

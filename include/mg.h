@@ -87,6 +87,13 @@ typedef struct {
   int nx, ny;
   double x0, y0, lx, ly;
   int periodic_y;
+  /* 1: homogeneous Neumann condition on the two y sides (zero normal derivative, Eq. 28); their
+   * nodes are unknowns, the x sides stay Dirichlet, periodic_y must be 0.  Caller arrays keep
+   * the nx x ny layout.  Solved as the periodic problem of twice the height whose coefficients,
+   * charge and data are the even reflection of these (eps_xy odd, so set to 0 on the two
+   * Neumann rows): exact for grids that meet the Neumann sides orthogonally, twice the
+   * unknowns and memory of the grid.  Not for mg_harmonic_grid. */
+  int neumann_y;
 } mg_grid_desc;
 
 /* Coordinate map (Eq. 1).  For MG_MAP_GRID, xp and yp hold the mapped coordinates of

@@ -99,6 +99,26 @@ __global__ void __launch_bounds__(256) k_eps_analytic(int kind, double p0, doubl
   }
 }
 
+// Even reflection of a grid with Neumann y sides into the periodic grid of twice the height
+// (2n rows, n = ny - 1): row j' of the doubled grid copies row j' - n (j' >= n) or n - j'
+// (j' < n) of the source, with eps_xy negated in the mirrored half and zero on the two
+// Neumann rows (j' = 0, n), where an odd function vanishes.
+__global__ void k_mirror_eps(int nx, int n, int ps, const double* __restrict__ D0,
+                             const double* __restrict__ exx0, const double* __restrict__ exy0,
+                             const double* __restrict__ eyy0, int pd, double* D, double* exx,
+                             double* exy, double* eyy) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int jd = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= nx || jd >= 2 * n) return;
+  const int js = jd >= n ? jd - n : n - jd;
+  const double sg = (jd == 0 || jd == n) ? 0.0 : (jd > n ? 1.0 : -1.0);
+  const size_t s = (size_t)js * ps + i, d = (size_t)jd * pd + i;
+  D[d] = D0[s];
+  exx[d] = exx0[s];
+  exy[d] = sg * exy0[s];
+  eyy[d] = eyy0[s];
+}
+
 // d/dx: central difference (Eqs. 39, 41), one-sided second order at the line ends;
 // i2h = 1 / (2 hx).
 __device__ __forceinline__ double ddx(const double* __restrict__ f, size_t r, int i, int nx,
@@ -357,6 +377,14 @@ cudaError_t launch_eps_analytic(int kind, const double* prm, int nx, int ny, int
   dim3 b(32, 8), g((nx + kEpsTile - 1) / kEpsTile, (nyr + kEpsTile - 1) / kEpsTile);
   k_eps_analytic<<<g, b, 0, s>>>(kind, prm[0], prm[1], prm[2], prm[3], nx, nyr, x0, y0, hx, hy, eps, pitch,
                                  D, exx, exy, eyy, folded);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mirror_eps(int nx, int n, int ps, const double* D0, const double* exx0,
+                              const double* exy0, const double* eyy0, int pd, double* D, double* exx,
+                              double* exy, double* eyy, cudaStream_t s) {
+  dim3 b(32, 8);
+  k_mirror_eps<<<grid2(nx, 2 * n, b), b, 0, s>>>(nx, n, ps, D0, exx0, exy0, eyy0, pd, D, exx, exy, eyy);
   return cudaGetLastError();
 }
 

@@ -78,9 +78,11 @@ __global__ void __launch_bounds__(kNT) k_solve_init(Lvl<double> L, const SolveAr
                                                     const double* __restrict__ D,
                                                     double* __restrict__ x, double* __restrict__ b,
                                                     SolveState* st) {
-  const int up = a->user_pitch;
+  const int up = a->user_pitch, n = a->mirror;
   NODE_LOOP(L) {
-    const size_t k = (size_t)j * L.pitch + i, u = (size_t)j * up + i;
+    // caller row of this node: itself, or through the even reflection of a Neumann grid
+    const int jr = n == 0 ? j : (j >= n ? j - n : n - j);
+    const size_t k = (size_t)j * L.pitch + i, u = (size_t)jr * up + i;
     if (is_unknown(L, i, j)) {
       x[k] = a->warm ? a->phi_in[u] : 0.0;
       b[k] = a->rho[u] * D[k];
@@ -453,9 +455,17 @@ __global__ void k_gather_states(SolveState* const* __restrict__ src, int* const*
 // phi_out (caller layout) = x at every node.
 __global__ void __launch_bounds__(kNT) k_copy_out(Lvl<double> L, const double* __restrict__ x,
                                                   const SolveArgs* __restrict__ a) {
-  const int up = a->user_pitch;
+  const int up = a->user_pitch, n = a->mirror;
   double* out = a->phi_out;
-  NODE_LOOP(L) { out[(size_t)j * up + i] = x[(size_t)j * L.pitch + i]; }
+  NODE_LOOP(L) {
+    int jr = j;  // Neumann grid: rows n.. of the doubled system are the caller's rows 0.., row 0 its row n
+    if (n) {
+      if (j >= n) jr = j - n;
+      else if (j == 0) jr = n;
+      else continue;
+    }
+    out[(size_t)jr * up + i] = x[(size_t)j * L.pitch + i];
+  }
 }
 
 // ------------------------------------------------------------------ launchers

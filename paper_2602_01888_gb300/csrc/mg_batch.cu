@@ -123,7 +123,7 @@ mg_status batch_solve_impl(mg_ctx* ctx, int count, mg_problem* const* probs,
   cudaStream_t s = ctx->stream;
   for (int k = 0; k < count; ++k) {
     mg_problem* P = probs[k];
-    const size_t n = (size_t)P->grid.nx * rows_stored(P->grid.ny, P->grid.periodic_y);
+    const size_t n = (size_t)P->user.nx * rows_stored(P->user.ny, P->user.periodic_y);
     const double *r = rho[k], *bcv = bc ? bc[k] : nullptr, *pin = phi[k];
     double* pout = phi[k];
     if (mem == MG_MEM_HOST) {
@@ -149,6 +149,7 @@ mg_status batch_solve_impl(mg_ctx* ctx, int count, mg_problem* const* probs,
     a.phi_in = pin;
     a.phi_out = pout;
     a.user_pitch = P->grid.nx;
+    a.mirror = P->mirror;
     a.warm = o.warm_start ? 1 : 0;
     a.max_iters = o.max_iters;
     a.rtol = o.rtol;
@@ -170,7 +171,7 @@ mg_status batch_solve_impl(mg_ctx* ctx, int count, mg_problem* const* probs,
   if (!st && mem == MG_MEM_HOST) {
     for (int k = 0; k < count; ++k) {
       mg_problem* P = probs[k];
-      const size_t n = (size_t)P->grid.nx * rows_stored(P->grid.ny, P->grid.periodic_y);
+      const size_t n = (size_t)P->user.nx * rows_stored(P->user.ny, P->user.periodic_y);
       if (cudaMemcpyAsync(phi[k], P->stage + 2 * n, n * sizeof(double), cudaMemcpyDeviceToHost, s) !=
           cudaSuccess) {
         st = set_error(MG_ERR_CUDA, "batch entry %d: result copy failed", k);

@@ -102,6 +102,7 @@ extern "C" mg_status mg_harmonic_grid(mg_ctx* ctx, const mg_grid_desc* grid, con
     return set_error(MG_ERR_ARG, "mg_harmonic_grid: NULL argument");
   if (mem != MG_MEM_HOST && mem != MG_MEM_DEVICE) return set_error(MG_ERR_ARG, "mg_harmonic_grid: bad memory kind");
   if (!(rtol > 0.0)) return set_error(MG_ERR_ARG, "mg_harmonic_grid: rtol must be positive");
+  if (grid->neumann_y) return set_error(MG_ERR_ARG, "mg_harmonic_grid: Neumann sides are not supported");
   mg_solve_opts o;
   mg_default_opts(&o);
   o.precision = MG_PREC_FP64;

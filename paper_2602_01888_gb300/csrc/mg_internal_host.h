@@ -94,7 +94,9 @@ struct mg_ctx {
 
 struct mg_problem {
   mg_ctx* ctx = nullptr;
-  mg_grid_desc grid{};
+  mg_grid_desc grid{};  // the grid the hierarchy is built on (the doubled periodic grid for Neumann sides)
+  mg_grid_desc user{};  // the caller's grid (its arrays' layout)
+  int mirror = 0;       // Neumann sides: ny - 1 of the caller's grid, else 0
   int nlev = 0, coarse_max = 64, mixed = 0;
   int nxs[mg::kMaxLevels] = {}, nys[mg::kMaxLevels] = {};
   mg::LevelMem lev[mg::kMaxLevels];

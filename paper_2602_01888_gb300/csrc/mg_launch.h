@@ -58,6 +58,11 @@ cudaError_t launch_eps_grid(int nx, int ny, int periodic, double hx, double hy, 
                             const double* yp, double jx, double jy, const double* eps, int pitch,
                             double* D, double* exx, double* exy, double* eyy, int* folded,
                             cudaStream_t s);
+// Reflect coefficients built on a grid with Neumann y sides (ny = n + 1 rows, pitch ps) into
+// the periodic grid of twice the height (2n rows, pitch pd).
+cudaError_t launch_mirror_eps(int nx, int n, int ps, const double* D0, const double* exx0,
+                              const double* exy0, const double* eyy0, int pd, double* D, double* exx,
+                              double* exy, double* eyy, cudaStream_t s);
 cudaError_t launch_assemble(const OpF64& A, double hx, double hy, const double* exx,
                             const double* exy, const double* eyy, cudaStream_t s);
 cudaError_t launch_rhs(const OpF64& A, const double* rho, int rho_pitch, const double* D, double* b,

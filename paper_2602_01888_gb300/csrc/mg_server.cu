@@ -79,8 +79,8 @@ static size_t nodes_of(const mg_grid_desc& g) {
 // hierarchy does not fit the memory budget.
 static std::string shape_key(const mg_grid_desc& g, const mg_solve_opts& o) {
   char k[256];
-  snprintf(k, sizeof k, "%d:%d:%d:%.17g:%.17g:%.17g:%.17g:%d:%d:%d", g.nx, g.ny, g.periodic_y, g.x0,
-           g.y0, g.lx, g.ly, (int)o.precision, o.coarse_max, (int)o.outer);
+  snprintf(k, sizeof k, "%d:%d:%d:%d:%.17g:%.17g:%.17g:%.17g:%d:%d:%d", g.nx, g.ny, g.periodic_y, g.neumann_y,
+           g.x0, g.y0, g.lx, g.ly, (int)o.precision, o.coarse_max, (int)o.outer);
   return k;
 }
 
@@ -212,7 +212,7 @@ static void server_loop(Server* S) {
       S->lat_ms.push_back(std::chrono::duration<double, std::milli>(R->t_done - R->t_submit).count());
       if (st) S->failed++; else S->completed++;
       S->unknowns_done += (double)(R->grid.nx - 2) *
-                          (double)(R->grid.periodic_y ? R->grid.ny - 1 : R->grid.ny - 2);
+                          (double)(R->grid.periodic_y ? R->grid.ny - 1 : R->grid.neumann_y ? R->grid.ny : R->grid.ny - 2);
       S->slot_free.push_back(R->slot);
       S->inflight.erase(S->inflight.begin() + k);
       progressed = true;

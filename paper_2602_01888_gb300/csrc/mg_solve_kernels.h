@@ -19,7 +19,8 @@ struct SolveArgs {
   int user_pitch;
   int warm;
   int max_iters;
-  int pad;
+  int mirror;  // Neumann y sides: n = ny - 1 of the caller's grid (its row r is row r + n of the
+               // doubled system, r < n; row n is row 0; row j' < n mirrors row n - j'); else 0
   double rtol;
   long long n_unknowns;
 };

@@ -340,17 +340,26 @@ mg_status line_prepare(mg_problem* P, cudaStream_t s) {
 // flags land in P->h_flags; problem_check_build reads them once s has been synchronised.
 mg_status problem_enqueue_build(mg_problem* P, const mg_map_desc* map, const double* eps_phys,
                                 mg_mem_kind mem, cudaStream_t s, const FineHook* hook) {
-  const mg_grid_desc& g = P->grid;
+  // coefficients are computed on the caller's grid (for Neumann sides, then reflected into
+  // the doubled periodic grid the hierarchy lives on)
+  const mg_grid_desc& g = P->user;
   const int nx = g.nx, ny = g.ny, nyr = rows_stored(ny, g.periodic_y);
   const double hx = g.lx / (nx - 1), hy = g.ly / (ny - 1);
   const size_t nn = (size_t)nx * nyr;
   LevelMem& F = P->lev[0];
   const int pt = F.A.pitch;
-  const size_t np = (size_t)pt * nyr;
+  const size_t np = (size_t)pt * rows_stored(P->grid.ny, P->grid.periodic_y);
   CU(cudaEventRecord(P->evb0, s));
   // temporaries: eps components in the fine level's scratch arrays (x, b, t), inputs
-  // staged in pitched layout in q / z / p
-  double *exx = F.x, *exy = F.b, *eyy = F.t;
+  // staged in pitched layout in q / z / p; a Neumann grid's own D and eps go to x, b, t, r
+  // and their reflection to D, q, z, p (the staged inputs are consumed by then)
+  double *Dk = P->D, *exx = F.x, *exy = F.b, *eyy = F.t;
+  if (P->mirror) {
+    Dk = F.x;
+    exx = F.b;
+    exy = F.t;
+    eyy = P->r;
+  }
   const double* eps_d = nullptr;
   const double *xp_d = nullptr, *yp_d = nullptr;
   auto stage = [&](const double* src, double* dst) -> cudaError_t {
@@ -372,10 +381,16 @@ mg_status problem_enqueue_build(mg_problem* P, const mg_map_desc* map, const dou
   CU(cudaMemsetAsync(P->flags, 0, 4 * sizeof(int), s));
   if (map->kind == MG_MAP_GRID) {
     CU(launch_eps_grid(nx, ny, g.periodic_y, hx, hy, xp_d, yp_d, map->jump_x, map->jump_y, eps_d, pt,
-                       P->D, exx, exy, eyy, P->flags, s));
+                       Dk, exx, exy, eyy, P->flags, s));
   } else {
     CU(launch_eps_analytic(map->kind, map->params, nx, ny, g.periodic_y, g.x0, g.y0, hx, hy, eps_d,
-                           pt, P->D, exx, exy, eyy, P->flags, s));
+                           pt, Dk, exx, exy, eyy, P->flags, s));
+  }
+  if (P->mirror) {
+    CU(launch_mirror_eps(nx, P->mirror, pt, Dk, exx, exy, eyy, pt, P->D, P->q, P->z, P->p, s));
+    exx = P->q;
+    exy = P->z;
+    eyy = P->p;
   }
   CU(launch_assemble(F.A, hx, hy, exx, exy, eyy, s));
   if (hook && *hook) {  // a caller's change of the finest operator before coarsening
@@ -392,7 +407,8 @@ mg_status problem_enqueue_build(mg_problem* P, const mg_map_desc* map, const dou
     if (P->nlev > 1) CU(launch_op_to_f64(P->lev[P->nlev - 1].A32, P->lev[P->nlev - 1].A, s));
   }
   CU(launch_coarse_factor(P->lev[P->nlev - 1].A, P->inv, P->flags + 1, s));
-  P->setup_kernels = 1 + 2 + (P->mixed ? 1 + (P->nlev - 1) + (P->nlev > 1 ? 1 : 0) : P->nlev - 1) + 1;
+  P->setup_kernels = 1 + 2 + (P->mixed ? 1 + (P->nlev - 1) + (P->nlev > 1 ? 1 : 0) : P->nlev - 1) + 1 +
+                     (P->mirror ? 1 : 0);
   if (P->line) {  // the line smoother's row factors follow the new operators
     mg_status ls = line_enqueue_factor(P, s);
     if (ls) return ls;
@@ -465,9 +481,22 @@ mg_status problem_create(mg_ctx* ctx, const mg_grid_desc* grid, const mg_solve_o
   mg_problem* P = new mg_problem();
   P->ctx = ctx;
   P->grid = *grid;
+  P->user = *grid;
+  if (grid->neumann_y) {  // solved on the periodic grid of twice the height (even reflection)
+    if (grid->periodic_y || grid->neumann_y != 1 || grid->ny < 3) {
+      delete P;
+      return set_error(MG_ERR_ARG, "neumann_y must be 0 or 1 and excludes periodic_y");
+    }
+    P->mirror = grid->ny - 1;
+    P->grid.ny = 2 * (grid->ny - 1) + 1;
+    P->grid.y0 = grid->y0 - grid->ly;
+    P->grid.ly = 2.0 * grid->ly;
+    P->grid.periodic_y = 1;
+    P->grid.neumann_y = 0;
+  }
   P->coarse_max = o.coarse_max;
   P->mixed = (o.precision == MG_PREC_MIXED);
-  mg_status st = check_grid(grid, o.coarse_max, &P->nlev, P->nxs, P->nys);
+  mg_status st = check_grid(&P->grid, o.coarse_max, &P->nlev, P->nxs, P->nys);
   if (!st) st = problem_alloc(P, P->mixed);
   if (!st && cudaStreamSynchronize(ctx->stream) != cudaSuccess)
     st = set_error(MG_ERR_CUDA, "problem_create: %s", cudaGetErrorString(cudaGetLastError()));
@@ -517,7 +546,7 @@ extern "C" mg_status mg_setup_transform(mg_ctx* ctx, const mg_grid_desc* grid,
 extern "C" mg_status mg_update_transform(mg_problem* P, const mg_map_desc* map,
                                          const double* eps_phys, mg_mem_kind mem) {
   if (!P) return set_error(MG_ERR_ARG, "mg_update_transform: problem is NULL");
-  mg_status st = check_map(&P->grid, map);
+  mg_status st = check_map(&P->user, map);
   if (st) return st;
   cudaSetDevice(P->ctx->device);
   return problem_build(P, map, eps_phys, mem);
@@ -531,7 +560,7 @@ extern "C" mg_status mg_batch_update_transform(mg_ctx* ctx, int count, mg_proble
   for (int k = 0; k < count; ++k) {
     if (!probs[k] || probs[k]->ctx != ctx)
       return set_error(MG_ERR_ARG, "mg_batch_update_transform: problem %d is NULL or from another context", k);
-    mg_status st = check_map(&probs[k]->grid, &maps[k]);
+    mg_status st = check_map(&probs[k]->user, &maps[k]);
     if (st) return st;
   }
   if (count == 0) return MG_OK;
@@ -958,6 +987,7 @@ mg_status enqueue_solve(mg_problem* P, const mg_solve_opts& o, const double* rho
   a->phi_in = phi_in;
   a->phi_out = phi_out;
   a->user_pitch = P->grid.nx;
+  a->mirror = P->mirror;
   a->warm = o.warm_start ? 1 : 0;
   a->max_iters = o.max_iters;
   a->rtol = o.rtol;
@@ -1026,7 +1056,7 @@ extern "C" mg_status mg_solve(mg_problem* P, const double* rho_phys, const doubl
   if (st) return st;
   cudaSetDevice(P->ctx->device);
   cudaStream_t s = P->ctx->stream;
-  const size_t n = (size_t)P->grid.nx * rows_stored(P->grid.ny, P->grid.periodic_y);
+  const size_t n = (size_t)P->user.nx * rows_stored(P->user.ny, P->user.periodic_y);
   const double *rho = rho_phys, *bcd = bc, *pin = phi;
   double* pout = phi;
   if (mem == MG_MEM_HOST) {

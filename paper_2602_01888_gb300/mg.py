@@ -39,7 +39,7 @@ _FP = C.POINTER(C.c_float)
 
 class mg_grid_desc(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("x0", C.c_double), ("y0", C.c_double),
-                ("lx", C.c_double), ("ly", C.c_double), ("periodic_y", C.c_int)]
+                ("lx", C.c_double), ("ly", C.c_double), ("periodic_y", C.c_int), ("neumann_y", C.c_int)]
 
 
 class mg_map_desc(C.Structure):
@@ -308,7 +308,8 @@ def _check_array(a, shape, name):
 
 
 def grid_desc(grid) -> mg_grid_desc:
-    return mg_grid_desc(grid.nx, grid.ny, grid.x0, grid.y0, grid.lx, grid.ly, int(grid.periodic_y))
+    return mg_grid_desc(grid.nx, grid.ny, grid.x0, grid.y0, grid.lx, grid.ly, int(grid.periodic_y),
+                        int(getattr(grid, "neumann_y", False)))
 
 
 def map_desc(mapspec, xp=None, yp=None) -> mg_map_desc:

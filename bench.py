@@ -288,6 +288,27 @@ def measure_smoother(mg, torch, inst, prec, reps=20, smoother="gs4"):
             "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2.07 GHz (probe: 1.20 TFLOP/s at 1.99 GHz)"}
 
 
+def cycle_model(prec, smoother, nu):
+    """Algorithmic bytes and flops per fine node of one V(nu1, nu2) cycle, coarser levels
+    included (x 4/3).  Point smoother, two sweeps per pass: each pass reads the five
+    operator arrays (C = 5 elements) and moves the iterate in and out and b; the residual +
+    restriction pass reads the operator, iterate and b and writes a quarter node; the first
+    post-smoothing pass also reads the quarter-size correction (68 + 3C bytes at FP64 for
+    V(2,2)).  Line smoother: 14 elements per sweep (six off-row couplings, iterate in and
+    out, b, five factor arrays), plus the residual + restriction pass and a prolongation
+    pass.  Flops: 18 per unknown update and per residual."""
+    e = 8.0 if prec == "fp64" else 4.0
+    n1, n2 = nu
+    if smoother == "xline":
+        fine = (n1 + n2) * 14 * e + (7 + 0.25) * e + (2 + 0.25) * e
+        flops = (n1 + n2) * 24.0 + 18.0 + 8.0
+    else:
+        p1, p2 = -(-n1 // 2), -(-n2 // 2)
+        fine = (p1 + 1 + p2) * 5 * e + p1 * 3 * e + (2 + 0.25) * e + p2 * 3 * e + 0.25 * e
+        flops = (n1 + n2) * 18.0 + 18.0 + 8.0
+    return fine * 4.0 / 3.0, flops * 4.0 / 3.0
+
+
 def _measure_line(mg, torch, g, st, x, b, f32, s, reps):
     """Zebra x-line sweep (two launches of k_line_zebra, one per row parity) on the finest
     level.  Bytes-bound; algorithmic bytes per node and sweep: 14 elements (the N, NE, NW
@@ -506,7 +527,8 @@ def run_ours(args):
             mg.mg_update_transform(prob.h, g, inst.map, eps_h, xp_h, yp_h)
             mg.mg_solve(prob.h, rho_h, bc_h, phi_h, opts)
         e2e_t = allmax(dist, time.perf_counter() - t0)
-        res[prec] = {"tot": tot, "times": times, "stats": st, "clocks": clocks,
+        cycle_ms = mg.mg_cycle_time(prob.h, opts, reps=20)
+        res[prec] = {"tot": tot, "times": times, "stats": st, "clocks": clocks, "cycle_ms": cycle_ms,
                      "e2e": ws * U * e2e_steps / e2e_t, "levels": len(prob.levels()),
                      "setup_ms": st.setup_ms, "solve_ms": st.solve_ms}
         prob.close()
@@ -545,6 +567,19 @@ def run_ours(args):
             "gpu_launches": args.steps * (rh["stats"].kernel_launches + rh["stats"].setup_kernel_launches),
             "roofline": roof, "cpu_baseline": cpu, "clocks": rh["clocks"],
         }
+        vc = {}
+        for prec in precisions:
+            bpn, fpn = cycle_model(prec, smoother, nu)
+            nodes = g.nx * g.nyr
+            t = res[prec]["cycle_ms"] * 1e-3
+            ent = {"ms": 1e3 * t, "bytes_per_cycle": bpn * nodes, "achieved_gbs": bpn * nodes / t / 1e9,
+                   "frac_hbm": bpn * nodes / t / 1e9 / HBM_PEAK_GBS, "bytes_per_fine_node": bpn}
+            if prec == "fp64":  # the FP64 cycle is bound by the FP64 pipe, not HBM
+                ent["achieved_tflops"] = fpn * nodes / t / 1e12
+                ent["frac_fp64"] = ent["achieved_tflops"] / FP64_PEAK_TFLOPS
+            vc[prec] = ent
+        line["vcycle"] = dict(vc, model="algorithmic bytes per fine node and cycle (coarse levels x 4/3), "
+                                        "see cycle_model; measured by mg_cycle_time (graph replay, warm)")
         if gridgen:
             line["grid_generation"] = gridgen
         line["autotune"] = tuned

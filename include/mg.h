@@ -195,6 +195,13 @@ mg_status mg_problem_info(const mg_problem *prob, int *levels, int *nx_out, int 
  * Errors: MG_ERR_NOT_CONVERGED (phi and stats still written), MG_ERR_DIVERGED, MG_ERR_ARG,
  * MG_ERR_CUDA.
  */
+/* Device time of one multigrid cycle of a resident problem as its solves with `opts` run it
+ * (the same levels, kernels and smoother choice; FP32 cycle for a mixed problem), captured once
+ * and replayed `reps` times after two warm-up replays on the context's stream; *ms_per_cycle
+ * receives the mean.  Benchmarking aid (project addition): the cycle reads the level-0
+ * right-hand side left by the last solve and writes only the cycle's scratch arrays. */
+mg_status mg_cycle_time(mg_problem *prob, const mg_solve_opts *opts, int reps, double *ms_per_cycle);
+
 mg_status mg_solve(mg_problem *prob, const double *rho_phys, const double *bc, double *phi,
                    mg_mem_kind mem, const mg_solve_opts *opts, mg_solve_stats *stats);
 

@@ -64,6 +64,14 @@ __device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
 }
 
+// Bilinear prolongation (Eq. 24) at a node of an even fine row jn (a coarse row): the coarse
+// value at even columns, the mean of its two coarse neighbours at odd ones.
+template <typename T>
+__device__ __forceinline__ T prolong_even_row(const T* __restrict__ eH, int pitch_c, int jn, int c) {
+  const size_t a = (size_t)(jn >> 1) * pitch_c + (c >> 1);
+  return (c & 1) ? T(0.5) * (__ldg(eH + a) + __ldg(eH + a + 1)) : __ldg(eH + a);
+}
+
 template <typename T>
 __device__ __forceinline__ bool row_active(const Lvl<T>& L, int j) {
   return L.periodic || (j >= 1 && j <= L.ny - 2);
@@ -152,7 +160,7 @@ __host__ __device__ inline size_t zebra_smem(int np) {
 template <typename T, int LU>
 __global__ void __launch_bounds__(kLT, sizeof(T) == 8 ? 3 : 6)
     k_line_zebra(Lvl<T> L, LineFactors<T> F, T* __restrict__ x, const T* __restrict__ b, int par,
-                 const int* __restrict__ skip) {
+                 const int* __restrict__ skip, const T* __restrict__ eH, int pitch_c, int zero_start) {
   if (skip && *skip) return;
   const int j = par + 2 * blockIdx.x;
   if (j >= L.nyr || !row_active(L, j)) return;
@@ -180,16 +188,26 @@ __global__ void __launch_bounds__(kLT, sizeof(T) == 8 ? 3 : 6)
       v[u] = T(0);
       if (t < N) {
         const int i = t + 1;
-        // couplings leaving the row, in the order of the point smoother's sum minus E/W
-        T off = __ldg(L.cN + r0 + i) * __ldg(x + ru + i);
-        off = fma(__ldg(L.cN + rd + i), __ldg(x + rd + i), off);
-        off = fma(__ldg(L.cNE + r0 + i), __ldg(x + ru + i + 1), off);
-        off = fma(__ldg(L.cNE + rd + i - 1), __ldg(x + rd + i - 1), off);
-        off = fma(__ldg(L.cNW + r0 + i), __ldg(x + ru + i - 1), off);
-        off = fma(__ldg(L.cNW + rd + i + 1), __ldg(x + rd + i + 1), off);
-        if (i == 1) off = fma(L.cE[r0], __ldg(x + r0), off);
-        if (i == N) off = fma(L.cE[r0 + i], __ldg(x + r0 + i + 1), off);
-        v[u] = __ldg(b + r0 + i) - off;
+        if (zero_start) {  // the iterate is zero: every coupling term vanishes
+          v[u] = __ldg(b + r0 + i);
+        } else {
+          // neighbour rows' values, with the coarse correction added where it is fused
+          auto nb = [&](size_t row0, int jn, int c) -> T {
+            T val = __ldg(x + row0 + c);
+            if (eH != nullptr && c >= 1 && c <= L.nx - 2 && row_active(L, jn)) val += prolong_even_row(eH, pitch_c, jn, c);
+            return val;
+          };
+          // couplings leaving the row, in the order of the point smoother's sum minus E/W
+          T off = __ldg(L.cN + r0 + i) * nb(ru, ju, i);
+          off = fma(__ldg(L.cN + rd + i), nb(rd, jd, i), off);
+          off = fma(__ldg(L.cNE + r0 + i), nb(ru, ju, i + 1), off);
+          off = fma(__ldg(L.cNE + rd + i - 1), nb(rd, jd, i - 1), off);
+          off = fma(__ldg(L.cNW + r0 + i), nb(ru, ju, i - 1), off);
+          off = fma(__ldg(L.cNW + rd + i + 1), nb(rd, jd, i + 1), off);
+          if (i == 1) off = fma(L.cE[r0], __ldg(x + r0), off);
+          if (i == N) off = fma(L.cE[r0 + i], __ldg(x + r0 + i + 1), off);
+          v[u] = __ldg(b + r0 + i) - off;
+        }
       }
     }
 #pragma unroll
@@ -309,8 +327,9 @@ cudaError_t launch_line_factor(const Op<T>& A, const LineFactors<T>& F, cudaStre
 
 template <typename T>
 cudaError_t launch_line_rows(const Op<T>& A, const LineFactors<T>& F, T* x, const T* b, int par,
-                             const int* skip, cudaStream_t s) {
+                             const int* skip, cudaStream_t s, const T* eH, int pitch_c, int zero_start) {
   if (!line_supported<T>(A.nx) || F.np != line_np(A.nx)) return cudaErrorInvalidValue;
+  if (eH && (par != 1 || (A.nx - 1) % 2 || (A.ny - 1) % 2)) return cudaErrorInvalidValue;
   constexpr int LU = sizeof(T) == 8 ? 2 : 1;  // measured best per precision
   const Lvl<T> L = lvl_of(A);
   const size_t sm = zebra_smem<T>(F.np);
@@ -323,16 +342,20 @@ cudaError_t launch_line_rows(const Op<T>& A, const LineFactors<T>& F, T* x, cons
   }
   const int rows = (L.nyr - par + 1) / 2;
   if (rows <= 0) return cudaSuccess;
-  k_line_zebra<T, LU><<<rows, kLT, sm, s>>>(L, F, x, b, par, skip);
+  k_line_zebra<T, LU><<<rows, kLT, sm, s>>>(L, F, x, b, par, skip, eH, pitch_c, zero_start);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_line_smooth(const Op<T>& A, const LineFactors<T>& F, T* x, const T* b, int sweeps,
-                               int rev, const int* skip, cudaStream_t s) {
+                               int rev, const int* skip, cudaStream_t s, const T* eH, int pitch_c,
+                               int zero_start) {
+  if (eH && (!rev || sweeps < 1)) return cudaErrorInvalidValue;
   for (int sw = 0; sw < sweeps; ++sw)
     for (int h = 0; h < 2; ++h) {
-      const cudaError_t e = launch_line_rows<T>(A, F, x, b, rev ? 1 - h : h, skip, s);
+      const bool first = sw == 0 && h == 0;
+      const cudaError_t e = launch_line_rows<T>(A, F, x, b, rev ? 1 - h : h, skip, s, first ? eH : nullptr,
+                                                pitch_c, first ? zero_start : 0);
       if (e != cudaSuccess) return e;
     }
   return cudaSuccess;
@@ -344,9 +367,9 @@ cudaError_t launch_line_smooth(const Op<T>& A, const LineFactors<T>& F, T* x, co
   template LineFactors<T> line_factors_at<T>(T*, int, int, int);                                \
   template cudaError_t launch_line_factor<T>(const Op<T>&, const LineFactors<T>&, cudaStream_t); \
   template cudaError_t launch_line_rows<T>(const Op<T>&, const LineFactors<T>&, T*, const T*, int, \
-                                           const int*, cudaStream_t);                           \
+                                           const int*, cudaStream_t, const T*, int, int);       \
   template cudaError_t launch_line_smooth<T>(const Op<T>&, const LineFactors<T>&, T*, const T*, int, \
-                                             int, const int*, cudaStream_t);
+                                             int, const int*, cudaStream_t, const T*, int, int);
 MG_LINE_INST(float)
 MG_LINE_INST(double)
 

@@ -663,10 +663,10 @@ static void level_table(mg_problem* P, T* x0, T* b0, VLevels<T>* V) {
 
 template <typename T>
 static mg_status emit_vcycle_on(mg_problem* P, T* x0, T* b0, const mg_solve_opts& o,
-                                const int* skip, cudaStream_t s, T** result) {
+                                const int* skip, cudaStream_t s, T** result, bool x0_zero = false) {
   VLevels<T> V;
   level_table<T>(P, x0, b0, &V);
-  CU(emit_vcycle<T>(V, o.smoother, o.nu1, o.nu2, o.omega_j, skip, s, result));
+  CU(emit_vcycle<T>(V, o.smoother, o.nu1, o.nu2, o.omega_j, skip, s, result, x0_zero));
   return MG_OK;
 }
 
@@ -693,9 +693,9 @@ static mg_status emit_body(mg_problem* P, const mg_solve_opts& o, cudaGraphCondi
     } else {
       CU(launch_resid_check(F.A, F.x, F.b, P->r, P->st, P->part, h, has_h, s));
       CU(launch_r_to_f32(F.A, P->r, F.b32, F.A32.pitch, P->st, s));
-      CU(cudaMemsetAsync(F.x32, 0, n0 * sizeof(float), s));
+      if (vcycle_reads_x0(o.smoother, o.nu1)) CU(cudaMemsetAsync(F.x32, 0, n0 * sizeof(float), s));
       float* res = nullptr;
-      if ((st = emit_vcycle_on<float>(P, F.x32, F.b32, o, skip, s, &res))) return st;
+      if ((st = emit_vcycle_on<float>(P, F.x32, F.b32, o, skip, s, &res, true))) return st;
       CU(launch_add_f32(F.A, F.x, res, F.A32.pitch, P->st, s));
     }
     CU(launch_iter_inc(P->st, s));
@@ -706,15 +706,15 @@ static mg_status emit_body(mg_problem* P, const mg_solve_opts& o, cudaGraphCondi
   CU(launch_fcg_verify(F.A, F.x, F.b, P->r, mixed ? F.b32 : nullptr, F.A32.pitch, P->st, P->part, h,
                        has_h, s));
   if (!mixed) {
-    CU(cudaMemsetAsync(P->z, 0, n0 * sizeof(double), s));
+    if (vcycle_reads_x0(o.smoother, o.nu1)) CU(cudaMemsetAsync(P->z, 0, n0 * sizeof(double), s));
     double* res = nullptr;
-    if ((st = emit_vcycle_on<double>(P, P->z, P->r, o, skip, s, &res))) return st;
+    if ((st = emit_vcycle_on<double>(P, P->z, P->r, o, skip, s, &res, true))) return st;
     CU(launch_fcg_zq<double>(F.A, res, F.A.pitch, P->q, P->st, P->part, s));
     CU(launch_fcg_pq<double>(F.A, res, F.A.pitch, P->p, P->q, P->r, P->st, P->part, s));
   } else {
-    CU(cudaMemsetAsync(F.x32, 0, n0 * sizeof(float), s));
+    if (vcycle_reads_x0(o.smoother, o.nu1)) CU(cudaMemsetAsync(F.x32, 0, n0 * sizeof(float), s));
     float* res = nullptr;
-    if ((st = emit_vcycle_on<float>(P, F.x32, F.b32, o, skip, s, &res))) return st;
+    if ((st = emit_vcycle_on<float>(P, F.x32, F.b32, o, skip, s, &res, true))) return st;
     CU(launch_fcg_zq<float>(F.A, res, F.A32.pitch, P->q, P->st, P->part, s));
     CU(launch_fcg_pq<float>(F.A, res, F.A32.pitch, P->p, P->q, P->r, P->st, P->part, s));
   }
@@ -1046,6 +1046,57 @@ mg_status finish_from(mg_problem* P, const SolveState& S, const int* flags, mg_s
 }
 
 }  // namespace mg
+
+extern "C" mg_status mg_cycle_time(mg_problem* P, const mg_solve_opts* opts, int reps, double* ms_per_cycle) {
+  if (!P || !ms_per_cycle || reps < 1) return set_error(MG_ERR_ARG, "mg_cycle_time: bad argument");
+  mg_solve_opts o;
+  if (opts) o = *opts; else mg_default_opts(&o);
+  mg_status st = check_opts(P, o);
+  if (st) return st;
+  if (o.outer == MG_OUTER_SOR) return set_error(MG_ERR_ARG, "mg_cycle_time: the SOR iteration has no cycle");
+  cudaSetDevice(P->ctx->device);
+  cudaStream_t s = P->ctx->stream, cs = P->ctx->cap_stream;
+  if (o.smoother == MG_SMOOTH_XLINE && (st = line_prepare(P, s))) return st;
+  CU(cudaStreamSynchronize(s));
+  // one cycle as the solves run it (same levels, kernels and smoother policy), captured once;
+  // it reads the level-0 right-hand side and writes only cycle scratch arrays
+  LevelMem& F = P->lev[0];
+  CU(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  if (P->mixed) {
+    float* res = nullptr;
+    st = emit_vcycle_on<float>(P, F.x32, F.b32, o, nullptr, cs, &res, true);
+  } else {
+    double* res = nullptr;
+    st = emit_vcycle_on<double>(P, P->z, P->r, o, nullptr, cs, &res, true);
+  }
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(cs, &g);
+  if (st || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return st ? st : set_error(MG_ERR_CUDA, "mg_cycle_time: capture failed: %s", cudaGetErrorString(e));
+  }
+  cudaGraphExec_t ex = nullptr;
+  e = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return set_error(MG_ERR_CUDA, "mg_cycle_time: %s", cudaGetErrorString(e));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  for (int w = 0; w < 2 && e == cudaSuccess; ++w) e = cudaGraphLaunch(ex, s);
+  if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+  for (int r = 0; r < reps && e == cudaSuccess; ++r) e = cudaGraphLaunch(ex, s);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaGraphExecDestroy(ex);
+  if (e != cudaSuccess) return set_error(MG_ERR_CUDA, "mg_cycle_time: %s", cudaGetErrorString(e));
+  *ms_per_cycle = ms / reps;
+  return MG_OK;
+}
 
 extern "C" mg_status mg_solve(mg_problem* P, const double* rho_phys, const double* bc, double* phi,
                               mg_mem_kind mem, const mg_solve_opts* opts, mg_solve_stats* stats) {

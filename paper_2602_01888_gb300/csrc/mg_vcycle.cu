@@ -78,7 +78,7 @@ int SmoothPolicy::lookup(long long nodes) const {
 
 template <typename T>
 cudaError_t emit_vcycle(const VLevels<T>& V, int smoother, int nu1, int nu2, double omega,
-                        const int* skip, cudaStream_t s, T** result) {
+                        const int* skip, cudaStream_t s, T** result, bool x0_zero) {
   const int L = V.L;
   T* cur[kMaxLevels];
   T* alt[kMaxLevels];
@@ -102,17 +102,30 @@ cudaError_t emit_vcycle(const VLevels<T>& V, int smoother, int nu1, int nu2, dou
     *result = cur[0];
     return cudaSuccess;
   }
-  if (smoother == MG_SMOOTH_XLINE) {  // zebra x-line Gauss-Seidel on every level but the coarsest
+  if (smoother == MG_SMOOTH_XLINE) {
+    // zebra x-line Gauss-Seidel on every level but the coarsest.  A coarse level's iterate
+    // starts at zero, so with pre-smoothing its first half-sweep reads no iterate and the
+    // restriction need not clear it; the coarse correction is interpolated inside the first
+    // post-smoothing half-sweep instead of being added by a separate pass (see
+    // launch_line_rows): identical values, two fewer passes over each level's iterate.
+    const bool zs = nu1 > 0;
     for (int l = 0; l < L - 1; ++l) {
-      if ((e = launch_line_smooth(V.A[l], V.lf[l], cur[l], V.b[l], nu1, 0, skip, s))) return e;
-      if ((e = launch_resid_restrict(V.A[l], cur[l], V.b[l], V.b[l + 1], cur[l + 1],
+      const int zero = l == 0 ? (x0_zero && zs) : zs;
+      if ((e = launch_line_smooth(V.A[l], V.lf[l], cur[l], V.b[l], nu1, 0, skip, s, (const T*)nullptr, 0, zero)))
+        return e;
+      if ((e = launch_resid_restrict(V.A[l], cur[l], V.b[l], V.b[l + 1], zs ? nullptr : cur[l + 1],
                                      V.A[l + 1].pitch, skip, s)))
         return e;
     }
     if ((e = launch_coarse_solve(V.A[L - 1], V.inv, V.b[L - 1], cur[L - 1], skip, s))) return e;
     for (int l = L - 2; l >= 0; --l) {
-      if ((e = launch_prolong_add(V.A[l], cur[l], cur[l + 1], V.A[l + 1].pitch, skip, s))) return e;
-      if ((e = launch_line_smooth(V.A[l], V.lf[l], cur[l], V.b[l], nu2, 1, skip, s))) return e;
+      if (nu2 > 0) {
+        if ((e = launch_line_smooth(V.A[l], V.lf[l], cur[l], V.b[l], nu2, 1, skip, s, (const T*)cur[l + 1],
+                                    V.A[l + 1].pitch, 0)))
+          return e;
+      } else if ((e = launch_prolong_add(V.A[l], cur[l], cur[l + 1], V.A[l + 1].pitch, skip, s))) {
+        return e;
+      }
     }
     *result = cur[0];
     return cudaSuccess;
@@ -231,9 +244,9 @@ cudaError_t emit_vcycle(const VLevels<T>& V, int smoother, int nu1, int nu2, dou
 template int tail_nodes<double>();
 template int tail_nodes<float>();
 template cudaError_t emit_vcycle<double>(const VLevels<double>&, int, int, int, double, const int*,
-                                         cudaStream_t, double**);
+                                         cudaStream_t, double**, bool);
 template cudaError_t emit_vcycle<float>(const VLevels<float>&, int, int, int, double, const int*,
-                                        cudaStream_t, float**);
+                                        cudaStream_t, float**, bool);
 
 }  // namespace mg
 

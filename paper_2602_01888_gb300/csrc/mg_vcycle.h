@@ -40,10 +40,17 @@ struct VLevels {
 };
 
 // Enqueue one V(nu1, nu2) cycle starting from the iterate in V.x[0]; *result receives the
-// array (V.x[0] or V.t[0]) that holds the level-0 result.
+// array (V.x[0] or V.t[0]) that holds the level-0 result.  x0_zero: the caller's iterate is
+// zero at every unknown (the preconditioner's start) and its Dirichlet nodes are zero, so a
+// smoother that can use it need not read it (the caller may skip clearing it when
+// vcycle_reads_x0() says so).
 template <typename T>
 cudaError_t emit_vcycle(const VLevels<T>& V, int smoother, int nu1, int nu2, double omega,
-                        const int* skip, cudaStream_t s, T** result);
+                        const int* skip, cudaStream_t s, T** result, bool x0_zero = false);
+
+// Whether emit_vcycle with x0_zero reads the unknowns of V.x[0]: false for the line
+// smoother with pre-smoothing, whose first half-sweep starts from zero without reading.
+inline bool vcycle_reads_x0(int smoother, int nu1) { return !(smoother == 2 && nu1 > 0); }
 
 template <typename T>
 int tail_nodes();

@@ -117,6 +117,7 @@ _SIGS = {
                         C.c_int),
     "mg_solve": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                   C.POINTER(mg_solve_opts), C.POINTER(mg_solve_stats)], C.c_int),
+    "mg_cycle_time": ([C.c_void_p, C.POINTER(mg_solve_opts), C.c_int, C.POINTER(C.c_double)], C.c_int),
     "mg_batch_solve": ([C.c_void_p, C.c_int, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
                         C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int,
                         C.POINTER(mg_solve_opts), C.POINTER(mg_solve_stats)], C.c_int),
@@ -395,6 +396,14 @@ def mg_solve(prob: int, rho_phys, bc, phi, opts: Optional[mg_solve_opts] = None,
         return stats
     _check(st, "mg_solve")
     return stats
+
+
+def mg_cycle_time(prob: int, opts: Optional[mg_solve_opts] = None, reps: int = 10) -> float:
+    """Milliseconds per multigrid cycle of a resident problem (see mg.h)."""
+    ms = C.c_double()
+    _check(lib().mg_cycle_time(prob, C.byref(opts) if opts is not None else None, reps, C.byref(ms)),
+           "mg_cycle_time")
+    return ms.value
 
 
 def mg_batch_solve(ctx: int, probs: Sequence[int], rhos, bcs, phis,

@@ -238,3 +238,24 @@ def test_server_host_staging_budget_gives_busy_then_recovers(libmg, ctx):
         assert libmg.mg_serve_poll(srv, t, 60000, None)[0] == 0
     rep = libmg.mg_server_stop(srv)
     assert rep.completed == 3 and rep.failed == 0
+
+
+def test_cycle_time_of_a_resident_problem(libmg, cuda):
+    """mg_cycle_time runs the problem's own cycle: positive, below the whole solve's time per
+    iteration (which adds the outer FP64 vector work), refused for the SOR iteration, and it
+    leaves the next solve's result unchanged (bitwise)."""
+    ctx = libmg.Context(0)
+    inst = I.config2(257)
+    for prec in ("fp64", "mixed"):
+        opts = libmg.make_opts(prec, "fcg", rtol=1e-10)
+        pr = libmg.Problem(ctx, inst, opts)
+        phi0, st = pr.solve()
+        ms = libmg.mg_cycle_time(pr.h, opts, reps=10)
+        assert 0.0 < ms < st.solve_ms / max(st.iters, 1) * 1.5, (prec, ms, st.solve_ms, st.iters)
+        phi1, _ = pr.solve()
+        assert np.array_equal(phi0, phi1)
+        if prec == "fp64":
+            with pytest.raises(libmg.MGError):
+                libmg.mg_cycle_time(pr.h, libmg.make_opts("fp64", "sor", nu1=4, omega_j=1.5))
+        pr.close()
+    ctx.close()

@@ -41,10 +41,9 @@ PROFILED_TRAFFIC = {("k_gs_colour<double>", 1025): (46.06e6 + 46.35e6 + 46.26e6 
                     # captured at 4097^2 (profiles/march_f32_4097.md), scaled by the node count
                     ("k_smooth_march<float,2>", 8193): (486.628e6 + 55.349e6) * (8193 / 4097) ** 2,
                     ("k_smooth_march<float,2>", 4097): 486.628e6 + 55.349e6,
-                    # profiles/line_zebra_f32_4097.md (mean of two launches), and scaled to 8193^2
-                    ("k_line_zebra<float>", 4097): (437.738e6 + 29.910e6 + 437.952e6 + 30.042e6) / 2,
-                    ("k_line_zebra<float>", 8193): (437.738e6 + 29.910e6 + 437.952e6 + 30.042e6) / 2
-                    * (8193 / 4097) ** 2}
+                    # profiles/line_zebra_f32.md: 8193 x 1025 capture (mean of two launches), scaled
+                    # to 8193^2 by the node count
+                    ("k_line_zebra<float>", 8193): (218.201e6 + 5.958e6 + 218.633e6 + 3.337e6) / 2 * (8193 / 1025)}
 
 # Single-instance workloads: (builder, precisions with the headline first, outer iteration,
 # residual tolerance, builder of the bounded CPU sample).  Each tolerance is calibrated so
@@ -380,7 +379,7 @@ def run_kernel_only(args):
     from paper_2602_01888_gb300 import mg
     torch.cuda.set_device(0)
     n = args.side
-    g = I.Grid(n, n)
+    g = I.Grid(n, args.ny or n)
     pitch = (n + 31) // 32 * 32
     f64 = args.kernel.endswith("64")
     dt = torch.float64 if f64 else torch.float32
@@ -389,24 +388,24 @@ def run_kernel_only(args):
     folded = torch.zeros(1, dtype=torch.int32, device="cuda")
     s = torch.cuda.current_stream().cuda_stream
     prm = (C.c_double * 4)(0.1, 0.0, 0.0, 0.0)
-    mg.mgk("mgk_eps_analytic", 1, prm, n, n, 0, 0.0, 0.0, g.hx, g.hy, None, pitch, D.data_ptr(),
+    mg.mgk("mgk_eps_analytic", 1, prm, n, g.ny, 0, 0.0, 0.0, g.hx, g.hy, None, pitch, D.data_ptr(),
            exx.data_ptr(), exy.data_ptr(), eyy.data_ptr(), folded.data_ptr(), s)
     ops = [z() for _ in range(6)]
-    st = mg.op_struct(ops, n, n, False)
+    st = mg.op_struct(ops, n, g.ny, False)
     mg.mgk("mgk_assemble", C.byref(st), g.hx, g.hy, exx.data_ptr(), exy.data_ptr(), eyy.data_ptr(), s)
     if not f64:
         ops32 = [z(torch.float32) for _ in range(6)]
-        st32 = mg.op_struct(ops32, n, n, False, f32=True)
+        st32 = mg.op_struct(ops32, n, g.ny, False, f32=True)
         mg.mgk("mgk_op_to_f32", C.byref(st), C.byref(st32), s)
         st = st32
     x, b = z(dt), torch.randn((g.nyr, pitch), dtype=torch.float64, device="cuda").to(dt)
     x2 = z(dt)
     nc = (n - 1) // 2 + 1
     pc = (nc + 31) // 32 * 32
-    bH = torch.zeros((nc, pc), dtype=dt, device="cuda")
+    bH = torch.zeros(((g.ny - 1) // 2 + 1, pc), dtype=dt, device="cuda")
     sfx = "f64" if f64 else "f32"
     if args.kernel.startswith("line"):
-        fac = torch.zeros(mg.lib().mgk_line_factor_elems(n, n, 0), dtype=dt, device="cuda")
+        fac = torch.zeros(mg.lib().mgk_line_factor_elems(n, g.ny, 0), dtype=dt, device="cuda")
         mg.mgk(f"mgk_line_factor_{sfx}", C.byref(st), fac.data_ptr(), s)
 
     def once():
@@ -441,7 +440,7 @@ def run_kernel_only(args):
         once()
     e1.record()
     torch.cuda.synchronize()
-    print(json.dumps({"kernel": args.kernel, "side": n, "reps": args.reps,
+    print(json.dumps({"kernel": args.kernel, "side": n, "ny": g.ny, "reps": args.reps,
                       "ms_per_call": e0.elapsed_time(e1) / args.reps}))
     return 0
 
@@ -960,6 +959,7 @@ def main():
                     help="smooth64|smooth32|fused64|fused32|pipe64|pipe32|march32|march32p|line64|line32|"
                          "restrict64|restrict32|prolong64|prolong32")
     ap.add_argument("--side", type=int, default=2049)
+    ap.add_argument("--ny", type=int, default=0, help="kernel-only: rows (default: --side)")
     ap.add_argument("--reps", type=int, default=5)
     args = ap.parse_args()
     if args.kernel:

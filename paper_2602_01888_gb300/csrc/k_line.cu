@@ -22,6 +22,8 @@
 // strided accesses of the reduction levels (stride 2^(k+1)) hit distinct banks.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "mg_common.cuh"
 #include "mg_kernels.h"
 #include "mg_launch.h"
@@ -157,10 +159,15 @@ __host__ __device__ inline size_t zebra_smem(int np) {
 // iterations whose global loads a thread issues together (the kernel is bound by load
 // latency); resident CTAs per SM at the longest rows: 6 (FP32) / 3 (FP64), which is also
 // what shared memory allows there.
-template <typename T, int LU>
-__global__ void __launch_bounds__(kLT, sizeof(T) == 8 ? 3 : 6)
+// Right-hand-side variants of a half-sweep (compile-time, so the common one carries no extra
+// code): the iterate as stored; a zero iterate (nothing read); the stored iterate plus the
+// coarse correction interpolated on the fly at the (even) neighbour rows.
+enum LineMode : int { LM_PLAIN = 0, LM_ZERO = 1, LM_FUSED = 2 };
+
+template <typename T, int LU, int MODE>
+__global__ void __launch_bounds__(kLT, sizeof(T) == 8 ? 3 : (LU <= 2 ? 6 : 5))
     k_line_zebra(Lvl<T> L, LineFactors<T> F, T* __restrict__ x, const T* __restrict__ b, int par,
-                 const int* __restrict__ skip, const T* __restrict__ eH, int pitch_c, int zero_start) {
+                 const int* __restrict__ skip, const T* __restrict__ eH, int pitch_c) {
   if (skip && *skip) return;
   const int j = par + 2 * blockIdx.x;
   if (j >= L.nyr || !row_active(L, j)) return;
@@ -188,13 +195,14 @@ __global__ void __launch_bounds__(kLT, sizeof(T) == 8 ? 3 : 6)
       v[u] = T(0);
       if (t < N) {
         const int i = t + 1;
-        if (zero_start) {  // the iterate is zero: every coupling term vanishes
+        if constexpr (MODE == LM_ZERO) {  // the iterate is zero: every coupling term vanishes
           v[u] = __ldg(b + r0 + i);
         } else {
           // neighbour rows' values, with the coarse correction added where it is fused
           auto nb = [&](size_t row0, int jn, int c) -> T {
             T val = __ldg(x + row0 + c);
-            if (eH != nullptr && c >= 1 && c <= L.nx - 2 && row_active(L, jn)) val += prolong_even_row(eH, pitch_c, jn, c);
+            if constexpr (MODE == LM_FUSED)
+              if (c >= 1 && c <= L.nx - 2 && row_active(L, jn)) val += prolong_even_row(eH, pitch_c, jn, c);
             return val;
           };
           // couplings leaving the row, in the order of the point smoother's sum minus E/W
@@ -325,25 +333,55 @@ cudaError_t launch_line_factor(const Op<T>& A, const LineFactors<T>& F, cudaStre
   return cudaGetLastError();
 }
 
+// Raise the dynamic shared-memory limit of every half-sweep variant of precision T, once
+// (thread-safe static initialisation).  All variants share one function type, so the limit
+// is set for each explicitly.
+template <typename T>
+static cudaError_t zebra_attributes() {
+  static const cudaError_t st = [] {
+    const void* ks[] = {
+        (const void*)k_line_zebra<T, 1, LM_PLAIN>, (const void*)k_line_zebra<T, 1, LM_ZERO>,
+        (const void*)k_line_zebra<T, 1, LM_FUSED>, (const void*)k_line_zebra<T, 2, LM_PLAIN>,
+        (const void*)k_line_zebra<T, 2, LM_ZERO>,  (const void*)k_line_zebra<T, 2, LM_FUSED>,
+        (const void*)k_line_zebra<T, 4, LM_PLAIN>, (const void*)k_line_zebra<T, 4, LM_ZERO>,
+        (const void*)k_line_zebra<T, 4, LM_FUSED>};
+    for (const void* k : ks) {
+      const cudaError_t e =
+          cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kLineSmemMax / 3));
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }();
+  return st;
+}
+
 template <typename T>
 cudaError_t launch_line_rows(const Op<T>& A, const LineFactors<T>& F, T* x, const T* b, int par,
                              const int* skip, cudaStream_t s, const T* eH, int pitch_c, int zero_start) {
   if (!line_supported<T>(A.nx) || F.np != line_np(A.nx)) return cudaErrorInvalidValue;
   if (eH && (par != 1 || (A.nx - 1) % 2 || (A.ny - 1) % 2)) return cudaErrorInvalidValue;
-  constexpr int LU = sizeof(T) == 8 ? 2 : 1;  // measured best per precision
   const Lvl<T> L = lvl_of(A);
   const size_t sm = zebra_smem<T>(F.np);
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_line_zebra<T, LU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(kLineSmemMax / 3));
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
   const int rows = (L.nyr - par + 1) / 2;
   if (rows <= 0) return cudaSuccess;
-  k_line_zebra<T, LU><<<rows, kLT, sm, s>>>(L, F, x, b, par, skip, eH, pitch_c, zero_start);
-  return cudaGetLastError();
+  // loads batched per thread: measured best on GB300 per precision and row length (FP32 8193^2:
+  // 0.90 ms per sweep at 4, 0.97 at 2, 1.02 at 1; 4097^2: 2 best; FP64: 2)
+  const int lu = sizeof(T) == 8 ? 2 : (F.np >= 8192 ? 4 : 2);
+  const cudaError_t ea = zebra_attributes<T>();
+  if (ea != cudaSuccess) return ea;
+  auto go = [&](auto kern) -> cudaError_t {
+    kern<<<rows, kLT, sm, s>>>(L, F, x, b, par, skip, eH, pitch_c);
+    return cudaGetLastError();
+  };
+  auto mode = [&](auto lu_c) -> cudaError_t {
+    constexpr int U = decltype(lu_c)::value;
+    if (zero_start) return go(k_line_zebra<T, U, LM_ZERO>);
+    if (eH) return go(k_line_zebra<T, U, LM_FUSED>);
+    return go(k_line_zebra<T, U, LM_PLAIN>);
+  };
+  if (lu == 4) return mode(std::integral_constant<int, 4>());
+  if (lu == 2) return mode(std::integral_constant<int, 2>());
+  return mode(std::integral_constant<int, 1>());
 }
 
 template <typename T>

@@ -99,6 +99,7 @@ __global__ void __launch_bounds__(kNT) k_solve_init(Lvl<double> L, const SolveAr
     st->verify = 0;
     st->guard = 0;
     st->verify_fail = 0;
+    st->x_zero = (!a->warm && a->bc == nullptr) ? 1 : 0;
     st->rtol = a->rtol;
     st->max_iters = a->max_iters;
     st->beta = 0.0;
@@ -118,9 +119,21 @@ __global__ void __launch_bounds__(kNT) k_resid_init(Lvl<double> L, const double*
   __shared__ double sh[kNT / 32];
   __shared__ int flag;
   double s_rr = 0.0, s_r0 = 0.0;
+  // a zero iterate (no Dirichlet data, cold start) has r = r_0 = b: every product of the
+  // stencil is a zero, so skipping it gives the same values
+  const bool xz = st->x_zero != 0;
   NODE_LOOP(L) {
     const size_t k = (size_t)j * L.pitch + i;
     double rv = 0.0;
+    if (xz) {
+      if (is_unknown(L, i, j)) {
+        rv = b[k];
+        s_r0 += rv * rv;
+        s_rr += rv * rv;
+      }
+      if (r) r[k] = rv;
+      continue;
+    }
     if (is_unknown(L, i, j)) {
       rv = b[k] - fma(L.diag[k], x[k], offdiag(L, x, i, j));
       // residual of the same ring with zero unknowns: only Dirichlet neighbours count

@@ -77,6 +77,8 @@ struct SolveState {
   int verify;         // recursive residual met rtol: recompute the true one next
   int guard;          // body passes; bounds the device-driven loop whatever happens
   int verify_fail;    // true-residual checks that did not meet rtol
+  int x_zero;         // the initial iterate is zero everywhere (cold start, no Dirichlet data)
+  int pad_;
   long long n_unknowns;  // for the rms used by the FP32 scaling
   unsigned int ticket[8];  // arrival counters of the last-block reductions
   double hist[256];

@@ -1,0 +1,66 @@
+"""Host-side arithmetic of the benchmark's figures (CPU): the algorithmic bytes per fine node
+of one multigrid cycle behind the V-cycle bandwidth, the per-workload smoother defaults,
+and the profiled-traffic table the roofline lines read."""
+import argparse
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def test_point_cycle_bytes_match_the_three_pass_count():
+    """V(2,2) with two sweeps per pass: pre-smoothing pass, residual + restriction pass,
+    post-smoothing pass with the coarse correction; each pass reads the five operator arrays
+    (C = 5 elements per node); vectors 3 + 2.25 + 3.25 elements: 68 + 3C bytes at FP64 =
+    188 B, 94 B at FP32, times 4/3 for the coarser levels."""
+    b64, f64 = bench.cycle_model("fp64", "gs4", (2, 2))
+    b32, f32 = bench.cycle_model("mixed", "gs4", (2, 2))
+    assert b64 == pytest.approx(188.0 * 4 / 3)
+    assert b32 == pytest.approx(94.0 * 4 / 3)
+    assert f64 == f32 == pytest.approx((4 * 18 + 18 + 8) * 4 / 3)
+    # three sweeps a side take two passes a side
+    b33, _ = bench.cycle_model("fp64", "gs4", (3, 3))
+    assert b33 == pytest.approx((5 * 5 * 8 + 2 * 3 * 8 + 2.25 * 8 + 2 * 3 * 8 + 0.25 * 8) * 4 / 3)
+
+
+def test_line_cycle_bytes():
+    """x-line V(1,1): two sweeps of 14 elements, the residual + restriction pass (7.25) and
+    the prolongation pass (2.25): 150 B per fine node at FP32."""
+    b, _ = bench.cycle_model("mixed", "xline", (1, 1))
+    assert b == pytest.approx(150.0 * 4 / 3)
+    b64, _ = bench.cycle_model("fp64", "xline", (1, 1))
+    assert b64 == pytest.approx(2 * b)
+
+
+def _args(workload, smoother=None, nu=None):
+    return argparse.Namespace(workload=workload, smoother=smoother, nu=nu)
+
+
+def test_smoother_defaults_per_workload():
+    assert bench.smoother_of(_args("annulus_8193")) == ("xline", (1, 1))
+    assert bench.smoother_of(_args("inclusion_1025")) == ("gs4", (2, 2))
+    assert bench.smoother_of(_args("batch512")) == ("gs4", (2, 2))
+    assert bench.smoother_of(_args("annulus_8193", "gs4", (2, 2))) == ("gs4", (2, 2))
+    assert bench.smoother_of(_args("inclusion_1025", None, (2, 1))) == ("gs4", (2, 1))
+
+
+def test_profiled_traffic_against_the_algorithmic_bytes():
+    """Every recorded per-launch DRAM figure belongs to a kernel the roofline line can name and
+    lies in the band its capture documented: the per-colour kernels re-read most rows of the
+    operator in each of a sweep's four launches (2-3.5x their share of a sweep's bytes); the
+    marching and line kernels move their algorithmic bytes (0.9-1.2x)."""
+    band = {"k_gs_colour<double>": (2.0, 3.5), "k_gs_colour<float>": (2.0, 3.5),
+            "k_smooth_march<float,2>": (0.9, 1.2), "k_line_zebra<float>": (0.9, 1.2)}
+    for (kern, n), traffic in bench.PROFILED_TRAFFIC.items():
+        assert kern in band, kern
+        nodes = float(n) * n
+        algo = {"k_gs_colour<double>": 64.0 * nodes / 4,       # a sweep's 8 FP64 arrays over 4 launches
+                "k_gs_colour<float>": 32.0 * nodes / 4,
+                "k_smooth_march<float,2>": 32.0 * nodes,       # two sweeps, each array once
+                "k_line_zebra<float>": 14 * 4.0 * nodes / 2}[kern]
+        lo, hi = band[kern]
+        assert lo <= traffic / algo <= hi, (kern, n, traffic / algo)

@@ -162,9 +162,53 @@ def oracle_solve_seconds(inst, rtol=RTOL, smoother="gs4", nu=(2, 2)):
     return time.perf_counter() - t0, it
 
 
+def run_reference_instances(args):
+    """Reference arm of the many-instance workloads: the oracle (FCG preconditioned by its
+    V(2,2), one thread) on a fixed bounded subset of the workload's own instances per step:
+    the first 8 of the 512 batch instances, or the first 6 requests of the served stream with
+    sides up to 513 (the mapped grids of larger ones take minutes to generate on the CPU)."""
+    import oracle as O
+    O.build()
+    if args.workload == "batch512":
+        insts = [I.inclusion_instance(*sp) for sp in I.config4_specs(BATCH_COUNT)[:8]]
+        rtol, sample = BATCH_RTOL, "the first 8 of the 512 batch instances per step, same rtol"
+    else:
+        stream = [q for q in I.config5_stream(2000, seed=5, rate=1.0, side_range=(129, 2049)) if q[1] <= 513][:6]
+        insts = [I.inclusion_instance(n, r, ratio, sd) for _, n, r, ratio, sd in stream]
+        rtol, sample = SERVE_RTOL, "the first 6 served requests with sides up to 513 per step, same rtol"
+    U = sum(x.grid.unknowns for x in insts)
+
+    def step():
+        t = 0.0
+        for x in insts:
+            dt, _ = oracle_solve_seconds(x, rtol)
+            t += dt
+        return t
+
+    for _ in range(args.warmup):
+        step()
+    tot = sum(step() for _ in range(args.steps))
+    v = U * args.steps / tot
+    print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": "unknowns/s", "n_gpus": args.gpus,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+                      "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                      "data": "synthetic", "config": {"workload": args.workload, "rtol": rtol, "smoother": "gs4",
+                                                      "outer": "fcg+vcycle(2,2)"},
+                      "cpu_baseline": {"value": v, "unit": "unknowns/s", "cores": 1, "kind": "oracle",
+                                       "sample": sample},
+                      "e2e": {"value": v, "unit": "unknowns/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+    return 0
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
+        return 0
+    if args.workload in ("batch512", "serve"):
+        return run_reference_instances(args)
+    if args.workload == "sor_vs_gmg":
+        print(json.dumps({"impl": "reference", "unavailable": "sor_vs_gmg already times the oracle itself "
+                                                              "(its cpu_oracle_1_thread entries)"}))
         return 0
     import oracle as O
     O.build()

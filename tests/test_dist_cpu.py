@@ -52,3 +52,16 @@ def test_reference_arm_under_torchrun_prints_once():
     rec = json.loads(lines[0])
     assert rec["impl"] == "reference" and rec["n_gpus"] == 2 and rec["value"] > 0
     assert rec["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_reference_arm_of_the_batch_workload():
+    """The oracle on the batch workload's own instances (a fixed bounded subset per step),
+    one JSON line with the arm's metric and unit."""
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload", "batch512",
+                        "--steps", "1", "--warmup", "3"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1, r.stdout
+    rec = json.loads(lines[0])
+    assert rec["impl"] == "reference" and rec["unit"] == "unknowns/s" and rec["value"] > 0
+    assert rec["config"]["workload"] == "batch512" and "8 of the 512" in rec["cpu_baseline"]["sample"]

@@ -243,7 +243,7 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ our arm
-def measure_smoother(mg, torch, inst, prec, reps=20, smoother="gs4"):
+def measure_smoother(mg, torch, inst, prec, reps=20, smoother="gs4", family=None):
     """Dominant kernel of the level-0 smoothing timed alone with CUDA events on this
     workload's finest level, operator built by the library's own kernels: one four-colour
     Gauss-Seidel sweep (4 launches of k_gs_colour), or on FP32 levels of at least
@@ -288,6 +288,8 @@ def measure_smoother(mg, torch, inst, prec, reps=20, smoother="gs4"):
     if smoother == "xline":
         return _measure_line(mg, torch, g, st, x, b, f32, s, reps)
     march = f32 and g.nx * g.nyr >= MARCH_NODES
+    if family in ("pipelined", "fused") and not march:
+        return _measure_tile_family(mg, torch, g, st, x, z(dt), b, f32, s, reps, family)
     x2 = z(dt) if march else None
 
     def once():
@@ -328,6 +330,47 @@ def measure_smoother(mg, torch, inst, prec, reps=20, smoother="gs4"):
     return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP64_PEAK_TFLOPS, "traffic": PROFILED_TRAFFIC.get((kern, g.nx)), "kernel": kern,
             "launch_us": per_launch_s * 1e6,
+            "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2.07 GHz (probe: 1.20 TFLOP/s at 1.99 GHz)"}
+
+
+def _measure_tile_family(mg, torch, g, st, x, x2, b, f32, s, reps, family):
+    """The tile families the autotuner may pick for the finest level (pipelined: tiles staged
+    by bulk asynchronous copies; fused: tiles in shared memory), `ns` sweeps per launch,
+    ping-pong iterates.  FP64: flop-bound (18 flop per unknown and sweep); FP32: bytes-bound
+    (32 B per node and launch: each array read once, the iterate written once)."""
+    import ctypes as C
+    tag = "f32" if f32 else "f64"
+    pipe = family == "pipelined"
+    ns = mg.lib().mgk_pipe_sweeps(int(f32)) if pipe else mg.lib().mgk_fused_sweeps(int(f32))
+
+    def once():
+        if pipe:
+            mg.mgk(f"mgk_smooth_pipe_{tag}", C.byref(st), x.data_ptr(), x2.data_ptr(), b.data_ptr(), 0, None, 0,
+                   None, s)
+        else:
+            mg.mgk(f"mgk_smooth_fused_{tag}", C.byref(st), x.data_ptr(), x2.data_ptr(), b.data_ptr(), 0, None, 0, s)
+
+    for _ in range(3):
+        once()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        once()
+    e1.record()
+    torch.cuda.synchronize()
+    per_launch_s = e0.elapsed_time(e1) * 1e-3 / reps
+    kern = f"k_smooth_{'pipe' if pipe else 'fused'}<{'float' if f32 else 'double'}>"
+    note = f"the autotuner's family for this level size ({family}), {ns} sweep(s) per launch"
+    if f32:
+        ach = 32.0 * g.nx * g.nyr / per_launch_s / 1e9
+        return {"bound": "hbm", "achieved": ach, "peak": HBM_PEAK_GBS, "unit": "GB/s", "frac": ach / HBM_PEAK_GBS,
+                "traffic": PROFILED_TRAFFIC.get((kern, g.nx)), "kernel": kern, "launch_us": per_launch_s * 1e6,
+                "sweeps_per_launch": ns, "note": note, "peak_source": "measured copy (MEASURED_PEAKS.json)"}
+    achieved = g.unknowns * 18.0 * ns / per_launch_s / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": PROFILED_TRAFFIC.get((kern, g.nx)), "kernel": kern,
+            "launch_us": per_launch_s * 1e6, "sweeps_per_launch": ns, "note": note,
             "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2.07 GHz (probe: 1.20 TFLOP/s at 1.99 GHz)"}
 
 
@@ -576,7 +619,8 @@ def run_ours(args):
                      "setup_ms": st.setup_ms, "solve_ms": st.solve_ms}
         prob.close()
     del flush
-    roof = measure_smoother(mg, torch, inst, precisions[0], smoother=smoother) if rank == 0 else None
+    family = (tuned or {}).get(precisions[0], {}).get(str(g.nx))  # the tuner's choice for the finest level
+    roof = measure_smoother(mg, torch, inst, precisions[0], smoother=smoother, family=family) if rank == 0 else None
     gridgen = None
     if rank == 0 and grid_map and "r" in inst.meta:
         gridgen = measure_grid_generation(mg, torch, ctx, g.nx, inst.meta["r"], cpu=not args.no_cpu_baseline)

@@ -1,14 +1,15 @@
 """Benchmark: unknowns solved per second to 1e-9 relative error on one GB300.
 
-Workload (default): the 1025^2 unit square with a circular inclusion of radius 0.25
-(local boundary-fitted map, Jacobian by central differences of the mapped grid, eps'
-ratio 10, 16 seeded Gaussian blobs, phi = 0 on the boundary).  One step is one pass of
-the whole hot path on resident inputs: coefficient build + Galerkin hierarchy + coarsest
-inverse (mg_update_transform) and the solve (mg_solve) to the residual tolerance whose
-error against the FP64 oracle is at most 1e-10, a tenth of the 1e-9 target (checked by the
-GPU test suite at these settings).
+Workload (default): the 8193^2 annulus (polar map of Eq. 29, r in [0.2, 1], periodic in
+theta, Dirichlet at both radii; 64-mode seeded Fourier source), 67.1 M unknowns.  The
+mixed path (FP32 x-line V(1,1) cycles inside FP64 flexible CG) is the headline value; the
+FP64 path runs beside it.  One step is one pass of the whole hot path on resident inputs:
+coefficient build + Galerkin hierarchy + coarsest inverse (mg_update_transform) and the
+solve (mg_solve) to the residual tolerance whose error against the FP64 oracle is at most
+a tenth of the 1e-9 target (checked by the GPU test suite at these settings).
 
-Prints one JSON line.  --impl reference times the FP64 CPU oracle on the same workload.
+Prints one JSON line.  --impl reference times the FP64 CPU oracle on a bounded sample of
+the same workload.
 """
 from __future__ import annotations
 
@@ -31,19 +32,83 @@ from paper_2602_01888_gb300 import inputs as I  # noqa: E402
 
 METRIC = "unknowns solved/sec to 1e-9 rel. error (FP64 vs mixed, 1 GB300)"
 RTOL = 1e-9
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # 2 FP64 FMA/clk/SM x 152 SMs x 2.07 GHz
-HBM_PEAK_GBS = 6681.2
-# DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture, keyed
-# by (kernel, side); cold-cache figures (profiles/gs_colour_f64_1025.md).  Null for any
-# kernel or size not captured since its last change.
+# Nominal FP64 rate (2 FP64 FMA per clock per SM x 152 SMs x 2.07 GHz), context only: the
+# FP64 fractions use the rate the FMA-chain probe measures in the same run (fp64_peak()).
+FP64_NOMINAL_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def _hbm_peak():
+    """HBM denominator: the copy bandwidth measured on this GPU pool (MEASURED_PEAKS.json
+    beside this file), else the fallback figure of an earlier GB300 measurement."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "of measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, ValueError, KeyError, TypeError):
+        return 6800.0, "of fallback (6.8 TB/s, MEASURED_PEAKS.json absent)"
+
+
+HBM_PEAK_GBS, HBM_PEAK_SOURCE = _hbm_peak()
 MARCH_NODES = 2000000  # FP32 levels of at least this many nodes are smoothed by the marching kernel
-PROFILED_TRAFFIC = {("k_gs_colour<double>", 1025): (46.06e6 + 46.35e6 + 46.26e6 + 11.5e3) / 3,
-                    # captured at 4097^2 (profiles/march_f32_4097.md), scaled by the node count
-                    ("k_smooth_march<float,2>", 8193): (486.628e6 + 55.349e6) * (8193 / 4097) ** 2,
-                    ("k_smooth_march<float,2>", 4097): 486.628e6 + 55.349e6,
-                    # profiles/line_zebra_f32.md: 8193 x 1025 capture (mean of two launches), scaled
-                    # to 8193^2 by the node count
-                    ("k_line_zebra<float>", 8193): (218.201e6 + 5.958e6 + 218.633e6 + 3.337e6) / 2 * (8193 / 1025)}
+
+
+def _traffic_table():
+    try:
+        with open(os.path.join(ROOT, "profiles", "dram_traffic.json")) as f:
+            return json.load(f)["entries"]
+    except (OSError, ValueError, KeyError):
+        return []
+
+
+def profiled_traffic(kernel, nx, rows):
+    """DRAM bytes per launch of `kernel` on an nx x rows level from the committed ncu
+    figures (profiles/dram_traffic.json), scaled by the node count from the captured size;
+    None if that kernel was not captured since its last change."""
+    for e in _traffic_table():
+        if e["kernel"] == kernel:
+            cx, cy = e["captured"]
+            return e["bytes"] * (nx * rows) / (cx * cy)
+    return None
+
+
+_FP64_PEAK = None
+
+
+def fp64_peak(mg, torch, seconds=0.6):
+    """FP64 FMA rate of this GPU, measured now by the library's FMA-chain probe
+    (mgk_fma_rate: 8 independent register chains per thread, 2432 CTAs of 256 threads),
+    timed with CUDA events, best of several launches; the SM clock is sampled meanwhile."""
+    global _FP64_PEAK
+    if _FP64_PEAK is None:
+        _FP64_PEAK = fma_probe(mg, torch, True, seconds)
+    return _FP64_PEAK
+
+
+def fma_probe(mg, torch, f64, seconds=0.6):
+    blocks = 152 * 16
+    iters = 4000 if f64 else 100000
+    out = torch.empty(blocks * 256, dtype=torch.float64 if f64 else torch.float32, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    flops = mg.lib().mgk_fma_rate_flops(blocks, iters)
+    mg.mgk("mgk_fma_rate", int(f64), blocks, iters, out.data_ptr(), s)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    best, t_end = 0.0, time.perf_counter() + seconds
+    while time.perf_counter() < t_end:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        mg.mgk("mgk_fma_rate", int(f64), blocks, iters, out.data_ptr(), s)
+        e1.record()
+        e1.synchronize()
+        best = max(best, flops / (e0.elapsed_time(e1) * 1e-3) / 1e12)
+    clocks = sampler.stop()
+    r = {"tflops": best, "sm_mhz": clocks.get("sm_mhz"), "sm_max_mhz": clocks.get("sm_max_mhz"),
+         "reasons": clocks.get("reasons"),
+         "source": "FMA-chain probe mgk_fma_rate (FP64)" if f64 else "FMA-chain probe mgk_fma_rate (FP32)"}
+    if r["sm_mhz"] and r["sm_max_mhz"]:
+        r["tflops_at_max_clock"] = best * r["sm_max_mhz"] / r["sm_mhz"]
+    return r
+
 
 # Single-instance workloads: (builder, precisions with the headline first, outer iteration,
 # residual tolerance, builder of the bounded CPU sample).  Each tolerance is calibrated so
@@ -200,6 +265,99 @@ def run_reference_instances(args):
     return 0
 
 
+# Bounded CPU samples of each single-instance workload (the oracle's inputs), by name.
+SAMPLES = {
+    "annulus_8193": lambda: I.config3(1025),
+    "inclusion_1025": lambda: I.config2(1025),
+    "inclusion_513": lambda: I.inclusion_instance(513, 0.25, 10.0, 2),
+    "sine_warp_129": lambda: I.config1(129),
+}
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def _core_worker(conn, key, rtol, smoother, nu):
+    """One host core: builds its copy of the sample once, then runs one oracle step (the
+    coefficient build and the MG-preconditioned CG solve) per request from the parent."""
+    import oracle as O  # noqa: F401  (built by the parent)
+    inst = SAMPLES[key]()
+    conn.send("ready")
+    while conn.recv() is not None:
+        t0 = time.monotonic()
+        oracle_solve_seconds(inst, rtol, smoother, nu)
+        conn.send((t0, time.monotonic(), inst.grid.unknowns))
+
+
+class OracleCores:
+    """The oracle as it stands, one independent copy per host core (spawned processes, so it
+    is safe after CUDA was initialised): a step runs one sample solve on every core at once
+    and takes from the first start to the last finish."""
+
+    def __init__(self, n, key, rtol, smoother, nu):
+        import multiprocessing as mp
+        ctx = mp.get_context("spawn")
+        self.conns, self.procs = [], []
+        for _ in range(n):
+            a, b = ctx.Pipe()
+            pr = ctx.Process(target=_core_worker, args=(b, key, rtol, smoother, nu), daemon=True)
+            pr.start()
+            self.conns.append(a)
+            self.procs.append(pr)
+        for c in self.conns:
+            if c.recv() != "ready":
+                raise RuntimeError("oracle worker failed to start")
+
+    def step(self):
+        for c in self.conns:
+            c.send(1)
+        outs = [c.recv() for c in self.conns]
+        return max(o[1] for o in outs) - min(o[0] for o in outs), sum(o[2] for o in outs)
+
+    def close(self):
+        for c in self.conns:
+            c.send(None)
+        for pr in self.procs:
+            pr.join(timeout=60)
+
+
+def cpu_baseline(key, rtol, smoother, nu, what):
+    """The oracle timed on this host: one thread on one sample, and every core running its
+    own copy of the same sample at once (aggregate unknowns/s)."""
+    import oracle as O
+    O.build()
+    inst = SAMPLES[key]()
+    dt, it = oracle_solve_seconds(inst, rtol, smoother, nu)
+    one = inst.grid.unknowns / dt
+    n = os.cpu_count() or 1
+    pool = OracleCores(n, key, rtol, smoother, nu)
+    try:
+        wall, U = pool.step()
+    finally:
+        pool.close()
+    desc = (f"one {inst.grid.nx}^2 solve of the {what} recipe (coefficients + MG-preconditioned CG "
+            f"with the same cycle ({smoother}, V({nu[0]},{nu[1]})) to rtol {rtol})")
+    return {"value": U / wall, "unit": "unknowns/s", "cores": n, "kind": "oracle",
+            "sample": f"{desc} on each of the {n} host cores at once, aggregate",
+            "single_thread": {"value": one, "cores": 1, "sample": desc + ", 1 thread"},
+            "nproc": n, "cpu_model": cpu_model()}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -212,31 +370,34 @@ def run_reference(args):
         return 0
     import oracle as O
     O.build()
-    _, _, outer, rtol, sample_builder = WORKLOADS[args.workload]
+    _, _, outer, rtol, _ = WORKLOADS[args.workload]
+    key = args.workload
     if args.workload == "inclusion_1025" and (args.steps + args.warmup) > 16:
-        inst, sample = (I.inclusion_instance(513, 0.25, 10.0, 2),
-                        "inclusion recipe at 513^2 per step (1/4 of the unknowns), same rtol")
-    else:
-        inst = sample_builder()
-        sample = (f"full {args.workload} workload per step" if inst.grid.unknowns ==
-                  workload(args.workload).grid.unknowns else
-                  f"{args.workload} recipe at {inst.grid.nx}^2 per step, same rtol")
-    U = inst.grid.unknowns
+        key = "inclusion_513"
     smoother, nu = smoother_of(args)
-    for _ in range(args.warmup):
-        oracle_solve_seconds(inst, rtol, smoother, nu)
-    tot = 0.0
-    for _ in range(args.steps):
-        dt, it = oracle_solve_seconds(inst, rtol, smoother, nu)
-        tot += dt
-    v = U * args.steps / tot
+    n = args.ref_cores or os.cpu_count() or 1
+    inst = SAMPLES[key]()
+    sample = (f"{args.workload} recipe at {inst.grid.nx}^2 (the full workload is too large for the CPU "
+              f"in the run's time), same rtol and cycle; one copy per host core, {n} at once")
+    pool = OracleCores(n, key, rtol, smoother, nu)
+    try:
+        for _ in range(args.warmup):
+            pool.step()
+        tot, U = 0.0, 0
+        for _ in range(args.steps):
+            dt, u = pool.step()
+            tot += dt
+            U += u
+    finally:
+        pool.close()
+    v = U / tot
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "unknowns/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": args.workload, "rtol": rtol, "smoother": smoother,
                                             "outer": f"fcg+vcycle({nu[0]},{nu[1]})"},
-            "cpu_baseline": {"value": v, "unit": "unknowns/s", "cores": 1, "kind": "oracle",
-                             "sample": sample},
+            "cpu_baseline": {"value": v, "unit": "unknowns/s", "cores": n, "kind": "oracle",
+                             "sample": sample, "cpu_model": cpu_model()},
             "e2e": {"value": v, "unit": "unknowns/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -313,24 +474,16 @@ def measure_smoother(mg, torch, inst, prec, reps=20, smoother="gs4", family=None
         kern = "k_smooth_march<float,2>"
         bytes_per_launch = 32.0 * g.nx * g.nyr  # x, b, 4 couplings, 1/diag read once, x written
         ach = bytes_per_launch / per_launch_s / 1e9
-        return {"bound": "hbm", "achieved": ach, "peak": HBM_PEAK_GBS, "unit": "GB/s",
-                "frac": ach / HBM_PEAK_GBS, "traffic": PROFILED_TRAFFIC.get((kern, g.nx)), "kernel": kern,
-                "launch_us": per_launch_s * 1e6, "sweeps_per_launch": 2,
-                "peak_source": "measured copy (MEASURED_PEAKS.json)"}
+        return _hbm_roof(kern, ach, per_launch_s, g, sweeps_per_launch=2)
     per_launch_s = e0.elapsed_time(e1) * 1e-3 / (reps * 4)
     kern = "k_gs_colour<float>" if f32 else "k_gs_colour<double>"
     if f32:
         bytes_per_launch = 32.0 * g.nx * g.nyr / 4  # a sweep's algorithmic bytes over its 4 launches
         ach = bytes_per_launch / per_launch_s / 1e9
-        return {"bound": "hbm", "achieved": ach, "peak": HBM_PEAK_GBS, "unit": "GB/s",
-                "frac": ach / HBM_PEAK_GBS, "traffic": PROFILED_TRAFFIC.get((kern, g.nx)), "kernel": kern,
-                "launch_us": per_launch_s * 1e6, "peak_source": "measured copy (MEASURED_PEAKS.json)"}
+        return _hbm_roof(kern, ach, per_launch_s, g)
     flops_per_launch = g.unknowns / 4 * 18.0  # 8 FMA + subtract + scale per updated unknown
     achieved = flops_per_launch / per_launch_s / 1e12
-    return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": PROFILED_TRAFFIC.get((kern, g.nx)), "kernel": kern,
-            "launch_us": per_launch_s * 1e6,
-            "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2.07 GHz (probe: 1.20 TFLOP/s at 1.99 GHz)"}
+    return _fp64_roof(mg, torch, kern, achieved, per_launch_s, g)
 
 
 def _measure_tile_family(mg, torch, g, st, x, x2, b, f32, s, reps, family):
@@ -364,14 +517,9 @@ def _measure_tile_family(mg, torch, g, st, x, x2, b, f32, s, reps, family):
     note = f"the autotuner's family for this level size ({family}), {ns} sweep(s) per launch"
     if f32:
         ach = 32.0 * g.nx * g.nyr / per_launch_s / 1e9
-        return {"bound": "hbm", "achieved": ach, "peak": HBM_PEAK_GBS, "unit": "GB/s", "frac": ach / HBM_PEAK_GBS,
-                "traffic": PROFILED_TRAFFIC.get((kern, g.nx)), "kernel": kern, "launch_us": per_launch_s * 1e6,
-                "sweeps_per_launch": ns, "note": note, "peak_source": "measured copy (MEASURED_PEAKS.json)"}
+        return _hbm_roof(kern, ach, per_launch_s, g, sweeps_per_launch=ns, note=note)
     achieved = g.unknowns * 18.0 * ns / per_launch_s / 1e12
-    return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": PROFILED_TRAFFIC.get((kern, g.nx)), "kernel": kern,
-            "launch_us": per_launch_s * 1e6, "sweeps_per_launch": ns, "note": note,
-            "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2.07 GHz (probe: 1.20 TFLOP/s at 1.99 GHz)"}
+    return _fp64_roof(mg, torch, kern, achieved, per_launch_s, g, sweeps_per_launch=ns, note=note)
 
 
 def cycle_model(prec, smoother, nu):
@@ -423,9 +571,7 @@ def _measure_line(mg, torch, g, st, x, b, f32, s, reps):
     kern = f"k_line_zebra<{'float' if f32 else 'double'}>"
     bytes_per_launch = 14.0 * esz * g.nx * g.nyr / 2
     ach = bytes_per_launch / per_launch_s / 1e9
-    return {"bound": "hbm", "achieved": ach, "peak": HBM_PEAK_GBS, "unit": "GB/s",
-            "frac": ach / HBM_PEAK_GBS, "traffic": PROFILED_TRAFFIC.get((kern, g.nx)), "kernel": kern,
-            "launch_us": per_launch_s * 1e6, "peak_source": "measured copy (MEASURED_PEAKS.json)"}
+    return _hbm_roof(kern, ach, per_launch_s, g)
 
 
 def measure_grid_generation(mg, torch, ctx, n, r, cpu=False):
@@ -460,11 +606,17 @@ def measure_grid_generation(mg, torch, ctx, n, r, cpu=False):
 def run_kernel_only(args):
     """Run one library kernel `--reps` times on a sine-warp operator of side `--side`
     (built by the library's own kernels) and print its mean CUDA-event time per launch;
-    used for profiling a single kernel at a chosen size."""
+    used for profiling a single kernel at a chosen size.  fp64peak / fp32peak instead run
+    the FMA-chain probe for about a second and print the best rate with the SM clock
+    sampled meanwhile (the FP64 figure is the denominator of the FP64 roofline fractions)."""
     import ctypes as C
     import torch
     from paper_2602_01888_gb300 import mg
     torch.cuda.set_device(0)
+    if args.kernel in ("fp64peak", "fp32peak"):
+        r = fma_probe(mg, torch, args.kernel == "fp64peak", seconds=1.0)
+        print(json.dumps(dict(r, kernel=args.kernel, nominal_fp64_tflops=FP64_NOMINAL_TFLOPS)))
+        return 0
     n = args.side
     g = I.Grid(n, args.ny or n)
     pitch = (n + 31) // 32 * 32
@@ -626,14 +778,7 @@ def run_ours(args):
         gridgen = measure_grid_generation(mg, torch, ctx, g.nx, inst.meta["r"], cpu=not args.no_cpu_baseline)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        import oracle as O
-        O.build()
-        sample = sample_builder()
-        dt, it = oracle_solve_seconds(sample, rtol, smoother, nu)
-        cpu = {"value": sample.grid.unknowns / dt, "unit": "unknowns/s", "cores": 1, "kind": "oracle",
-               "sample": (f"one {sample.grid.nx}^2 solve of the {args.workload} recipe (coefficients + "
-                          f"MG-preconditioned CG with the same cycle ({smoother}, V({nu[0]},{nu[1]})) to "
-                          f"rtol {rtol}), 1 thread")}
+        cpu = cpu_baseline(args.workload, rtol, smoother, nu, args.workload)
     if rank == 0:
         h, others = precisions[0], precisions[1:]
         rh = res[h]
@@ -663,13 +808,15 @@ def run_ours(args):
                    "frac_hbm": bpn * nodes / t / 1e9 / HBM_PEAK_GBS, "bytes_per_fine_node": bpn}
             if prec == "fp64":  # the FP64 cycle is bound by the FP64 pipe, not HBM
                 ent["achieved_tflops"] = fpn * nodes / t / 1e12
-                ent["frac_fp64"] = ent["achieved_tflops"] / FP64_PEAK_TFLOPS
+                ent["frac_fp64"] = ent["achieved_tflops"] / fp64_peak(mg, torch)["tflops"]
             vc[prec] = ent
         line["vcycle"] = dict(vc, model="algorithmic bytes per fine node and cycle (coarse levels x 4/3), "
                                         "see cycle_model; measured by mg_cycle_time (graph replay, warm)")
         if gridgen:
             line["grid_generation"] = gridgen
         line["autotune"] = tuned
+        if "fp64" in precisions:
+            line["fp64_peak"] = fp64_peak(mg, torch)
         for o in others:
             ro = res[o]
             line[o] = {"value": ws * U * args.steps / ro["tot"], "ms_per_step": 1e3 * ro["tot"] / args.steps,
@@ -1029,7 +1176,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="inclusion_1025",
+    ap.add_argument("--workload", default="annulus_8193",
                     choices=sorted(WORKLOADS) + ["batch512", "serve", "sor_vs_gmg"])
     ap.add_argument("--requests", type=int, default=2000, help="serve: requests per pass")
     ap.add_argument("--inflight", type=int, default=16, help="serve: concurrent request slots")
@@ -1041,11 +1188,13 @@ def main():
     ap.add_argument("--nu", type=lambda v: tuple(int(t) for t in v.split(",")), default=None,
                     help="pre,post smoothing sweeps of the V-cycle (default per workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-cores", type=int, default=0,
+                    help="reference arm: host cores running the oracle at once (default: all)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the size-threshold smoother choice instead of timing the families")
     ap.add_argument("--kernel-only", dest="kernel", default=None,
                     help="smooth64|smooth32|fused64|fused32|pipe64|pipe32|march32|march32p|line64|line32|"
-                         "restrict64|restrict32|prolong64|prolong32")
+                         "restrict64|restrict32|prolong64|prolong32|fp64peak|fp32peak")
     ap.add_argument("--side", type=int, default=2049)
     ap.add_argument("--ny", type=int, default=0, help="kernel-only: rows (default: --side)")
     ap.add_argument("--reps", type=int, default=5)

@@ -28,7 +28,9 @@
  *  - Every call returns an mg_status and never aborts; mg_last_error() gives a
  *    thread-local message for the last failing call on the calling thread.
  *  - A context is used by one host thread at a time (or under external locking);
- *    the server is internally synchronized.
+ *    the server is internally synchronized.  While a server runs on a context, use the
+ *    context only through the mg_serve_* calls: the scheduler thread creates, runs and
+ *    frees problems on it.
  *  - Sizes: nx, ny >= 3 and each of nx-1, ny-1 must be m * 2^k with m <= 32 so the
  *    multigrid hierarchy is exact; anything else is MG_ERR_SIZE.
  */

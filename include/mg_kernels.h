@@ -212,13 +212,31 @@ int mgk_vcycle_line_f32(int nlev, const mgk_op_f32 *ops, float *const *x, float 
  * allocator).  The paper has no counterpart: this is a deployment variant.  Instead of the
  * caller's tmp array it uses one fixed device array of mgk_jacobi_f64_static_capacity()
  * doubles (8 MiB) that every device loading the library keeps until the process exits.
- * Returns 2 (message in mg_last_error) when pitch * rows exceeds that capacity.  The first
- * call on a device looks up the array's device address, so make it before capturing any
- * stream.  All calls on a device share the array and it keeps the last call's contents;
- * calls that overlap on the GPU race on it. */
+ * Returns 2 (message in mg_last_error) when pitch * rows exceeds that capacity.  Every call
+ * looks up the array's device address in the current context; the first one on a device may
+ * load the library's device code, so make it before capturing any stream.  All calls on a
+ * device share the array and it keeps the last call's contents; calls that overlap on the
+ * GPU race on it. */
 int mgk_jacobi_f64_static(const mgk_op_f64 *A, double *phi, const double *b, int sweeps,
                           double omega, void *stream);
 size_t mgk_jacobi_f64_static_capacity(void);
+
+/* FMA-rate probe (no counterpart in the paper: it measures the arithmetic peak that the
+ * FP64 stencil kernels are reported against, since their bound is the FP64 pipe, not HBM).
+ * Launches `blocks` CTAs of 256 threads; every thread runs 8 independent chains of `iters`
+ * dependent fused multiply-adds in registers (FP64 if f64 != 0, else FP32) and writes one
+ * value to out[blocks * 256] (device memory, caller-owned).  Time the launch with CUDA
+ * events on `stream`; mgk_fma_rate_flops gives its flop count.  Returns 1 on bad arguments,
+ * 4 if the launch fails. */
+int mgk_fma_rate(int f64, int blocks, int iters, void *out, void *stream);
+double mgk_fma_rate_flops(int blocks, int iters);
+
+/* Test hook of the request server (mg_serve_*): the next `count` completion queries of
+ * in-flight requests report a failure (cudaErrorLaunchFailure) without asking the runtime,
+ * so tests can drive the server's failure path on the host, with no fault on the device.
+ * A request that meets one finishes with MG_ERR_CUDA, its slot is freed and
+ * mg_server_stop still returns.  0 turns it off. */
+void mgk_server_fail_event_queries(int count);
 
 #ifdef __cplusplus
 }

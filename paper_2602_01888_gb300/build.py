@@ -20,7 +20,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmg.so")
 
 SOURCES = ["k_setup.cu", "k_cycle.cu", "k_solve.cu", "k_fused.cu", "k_pipe.cu", "k_march.cu", "k_line.cu", "mg_vcycle.cu", "mg_solver.cu", "mg_batch.cu", "mg_grid.cu", "mg_tune.cu",
-           "mg_server.cu", "k_noalloc.cu"]
+           "mg_server.cu", "k_noalloc.cu", "k_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-I", INCLUDE, "-I", CSRC]
 

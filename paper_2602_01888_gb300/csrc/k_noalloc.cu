@@ -14,8 +14,6 @@
 // streams, or concurrent host threads) would use the array at the same time and race.
 #include <cuda_runtime.h>
 
-#include <mutex>
-
 #include "mg_internal_host.h"
 #include "mg_kernels.h"
 #include "mg_launch.h"
@@ -23,27 +21,17 @@
 namespace mg {
 
 constexpr size_t kStaticScratchElems = size_t(1) << 20;  // 8 MiB of doubles
-constexpr int kMaxDevicesStatic = 64;
-
 static __device__ __align__(256) double g_jacobi_scratch[kStaticScratchElems];
 
-// Device address of g_jacobi_scratch on the current device, looked up once per device.
-// The host-side symbol is only a stand-in; the address must come from the runtime.
+// Device address of g_jacobi_scratch in the current device's context.  The host-side
+// symbol is only a stand-in; the address comes from the runtime, looked up on every call
+// (cheap next to the launches) so that a context created again after cudaDeviceReset,
+// where the module may load at another address, never gets a stale pointer.
 static cudaError_t scratch_address(double** out) {
-  static std::mutex mu;
-  static double* addr[kMaxDevicesStatic] = {};
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_jacobi_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevicesStatic) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lk(mu);
-  if (!addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_jacobi_scratch);
-    if (e != cudaSuccess) return e;
-    addr[dev] = static_cast<double*>(p);
-  }
-  *out = addr[dev];
+  *out = static_cast<double*>(p);
   return cudaSuccess;
 }
 

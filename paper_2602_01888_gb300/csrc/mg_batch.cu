@@ -9,9 +9,11 @@
 // its branch runs the same kernels on the same data in the same order.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <set>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -20,18 +22,33 @@
 
 namespace mg {
 
+static void entry_free(mg_ctx* ctx, BatchEntry* b) {
+  if (b->ge.exec) cudaGraphExecDestroy(b->ge.exec);
+  if (b->ge.graph) cudaGraphDestroy(b->ge.graph);
+  for (void* a : b->allocs) ctx->pool.release(a);
+  if (b->h_args) cudaFreeHost(b->h_args);
+  if (b->h_states) cudaFreeHost(b->h_states);
+  if (b->h_flags) cudaFreeHost(b->h_flags);
+  delete b;
+}
+
 void batch_cache_clear(mg_ctx* ctx) {
-  for (auto& kv : ctx->batches) {
-    BatchEntry* b = kv.second;
-    if (b->ge.exec) cudaGraphExecDestroy(b->ge.exec);
-    if (b->ge.graph) cudaGraphDestroy(b->ge.graph);
-    for (void* a : b->allocs) ctx->pool.release(a);
-    if (b->h_args) cudaFreeHost(b->h_args);
-    if (b->h_states) cudaFreeHost(b->h_states);
-    if (b->h_flags) cudaFreeHost(b->h_flags);
-    delete b;
-  }
+  std::lock_guard<std::mutex> lk(ctx->batches_mu);
+  for (auto& kv : ctx->batches) entry_free(ctx, kv.second);
   ctx->batches.clear();
+}
+
+void batch_cache_drop(mg_ctx* ctx, const mg_problem* P) {
+  std::lock_guard<std::mutex> lk(ctx->batches_mu);
+  for (auto it = ctx->batches.begin(); it != ctx->batches.end();) {
+    const auto& pr = it->second->probs;
+    if (std::find(pr.begin(), pr.end(), P) != pr.end()) {
+      entry_free(ctx, it->second);
+      it = ctx->batches.erase(it);
+    } else {
+      ++it;
+    }
+  }
 }
 
 static std::string batch_key(mg_problem* const* probs, int count, const mg_solve_opts& o) {
@@ -111,6 +128,9 @@ mg_status batch_solve_impl(mg_ctx* ctx, int count, mg_problem* const* probs,
       return st;
   }
   const std::string key = batch_key(probs, count, o);
+  // held until the batch has run: a problem freed meanwhile on another thread (the server's
+  // eviction) cannot destroy an entry in use
+  std::lock_guard<std::mutex> batches_lock(ctx->batches_mu);
   BatchEntry* b = nullptr;
   auto it = ctx->batches.find(key);
   if (it != ctx->batches.end()) {

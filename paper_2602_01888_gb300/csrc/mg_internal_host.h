@@ -29,6 +29,14 @@ class Pool {
   void* alloc(size_t n);
   void release(void* p);
   size_t used() const { return used_; }
+  size_t budget() {
+    std::lock_guard<std::mutex> lk(mu_);
+    return budget_;
+  }
+  void set_budget(size_t b) {
+    std::lock_guard<std::mutex> lk(mu_);
+    budget_ = b;
+  }
   ~Pool();
   size_t budget_ = 0;
   bool pinned_ = false;  // slabs of page-locked host memory instead of device memory
@@ -86,6 +94,7 @@ struct mg_ctx {
   std::set<mg_problem*> problems;  // live problems, freed by mg_destroy if still there
   std::mutex problems_mu;          // the server's scheduler thread creates problems too
   std::map<std::string, mg::BatchEntry*> batches;
+  std::mutex batches_mu;  // batches: the server's scheduler thread frees problems too
   cudaStream_t stream = nullptr, own_stream = nullptr, cap_stream = nullptr, cap_stream2 = nullptr;
   cudaStream_t batch[mg::kBatchStreams] = {};
   mg::SmoothPolicy pol[2];  // measured smoother choice: [0] FP64, [1] FP32 (mg_autotune)
@@ -140,6 +149,8 @@ mg_status build_batch_graph(mg_ctx* ctx, mg_problem* const* probs, int count, co
                             SolveState* d_states, int* d_flags, GraphEntry* ge,
                             std::vector<int>* fixed, std::vector<int>* body);
 void batch_cache_clear(mg_ctx* ctx);
+// Drop the captured batches that contain problem P (its arrays are about to be freed).
+void batch_cache_drop(mg_ctx* ctx, const mg_problem* P);
 uint64_t graph_key(const mg_solve_opts& o);
 mg_status check_opts(const mg_problem* P, const mg_solve_opts& o);
 // Allocate and compute the line-smoother factors on stream s if the problem has none yet.

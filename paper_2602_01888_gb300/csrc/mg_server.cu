@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -28,6 +29,18 @@
 namespace mg {
 
 using Clock = std::chrono::steady_clock;
+
+// Completion query of a request.  Tests make it fail on the host (mgk_server_fail_event_queries):
+// the next `n` queries report cudaErrorLaunchFailure instead of asking the runtime, so the
+// failure path runs without any fault on the device.
+static std::atomic<int> g_fail_queries{0};
+
+static cudaError_t event_query(cudaEvent_t ev) {
+  int n = g_fail_queries.load();
+  while (n > 0)
+    if (g_fail_queries.compare_exchange_weak(n, n - 1)) return cudaErrorLaunchFailure;
+  return cudaEventQuery(ev);
+}
 
 struct Request {
   uint64_t ticket = 0;
@@ -63,6 +76,7 @@ struct Server {
   double unknowns_done = 0.0;
   long long batch_sum = 0;
   int ticks = 0;
+  size_t ctx_budget = 0;  // the context's device budget before the server lowered it
   bool stopping = false;
   std::thread th;
   Clock::time_point t_start;
@@ -165,9 +179,15 @@ static void server_loop(Server* S) {
                            P->stage + 2 * n, s);
       }
       if (!st) {
-        cudaMemcpyAsync(R->phi, P->stage + 2 * n, n * sizeof(double), cudaMemcpyDeviceToHost, s);
-        cudaEventCreateWithFlags(&R->done_ev, cudaEventDisableTiming);
-        cudaEventRecord(R->done_ev, s);
+        cudaError_t e = cudaMemcpyAsync(R->phi, P->stage + 2 * n, n * sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&R->done_ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(R->done_ev, s);
+        if (e != cudaSuccess) {
+          if (R->done_ev) cudaEventDestroy(R->done_ev);
+          R->done_ev = nullptr;
+          st = set_error(MG_ERR_CUDA, "server: enqueue of request %llu: %s", (unsigned long long)R->ticket,
+                         cudaGetErrorString(e));
+        }
       }
       lk.lock();
       if (st) {
@@ -190,20 +210,31 @@ static void server_loop(Server* S) {
       S->ticks++;
       S->batch_sum += (long long)S->inflight.size();
     }
-    // retire finished requests
+    // retire finished requests: cudaErrorNotReady keeps a request in flight; any other
+    // error fails it (its slot is freed and its problem released, so stop still returns)
     for (size_t k = 0; k < S->inflight.size();) {
       auto R = S->inflight[k];
-      if (cudaEventQuery(R->done_ev) != cudaSuccess) {
+      const cudaError_t q = event_query(R->done_ev);
+      if (q == cudaErrorNotReady) {
         ++k;
         continue;
       }
       mg_problem* P = R->prob;
       lk.unlock();
-      mg_status st = problem_check_build(P);
-      if (!st) st = finish_solve(P, &R->stats);
+      mg_status st = MG_OK;
+      if (q != cudaSuccess) {
+        st = set_error(MG_ERR_CUDA, "server: completion of request %llu: %s",
+                       (unsigned long long)R->ticket, cudaGetErrorString(q));
+        cudaStreamSynchronize(S->slots[R->slot]);  // nothing of it may still run on its arrays
+        mg_problem_free(P);                         // its state is unknown
+        P = nullptr;
+      } else {
+        st = problem_check_build(P);
+        if (!st) st = finish_solve(P, &R->stats);
+      }
       cudaEventDestroy(R->done_ev);
       lk.lock();
-      S->idle.emplace_back(shape_key(R->grid, R->opts), P);  // stays resident for reuse
+      if (P) S->idle.emplace_back(shape_key(R->grid, R->opts), P);  // stays resident for reuse
       R->prob = nullptr;
       R->status = st;
       R->finished = true;
@@ -251,7 +282,8 @@ extern "C" mg_status mg_server_start(mg_ctx* ctx, const mg_server_opts* opts, mg
   if (S->opts.max_inflight <= 0) S->opts.max_inflight = 16;
   S->opts.max_inflight = std::min(S->opts.max_inflight, 64);
   if (S->opts.queue_capacity <= 0) S->opts.queue_capacity = 1 << 16;
-  if (S->opts.mem_budget && S->opts.mem_budget < ctx->pool.budget_) ctx->pool.budget_ = S->opts.mem_budget;
+  S->ctx_budget = ctx->pool.budget();
+  if (S->opts.mem_budget && S->opts.mem_budget < S->ctx_budget) ctx->pool.set_budget(S->opts.mem_budget);
   S->host.pinned_ = true;
   S->host.budget_ = S->opts.host_budget ? S->opts.host_budget : ((size_t)8 << 30);
   cudaSetDevice(ctx->device);
@@ -373,6 +405,9 @@ extern "C" mg_status mg_server_stop(mg_server* h, mg_serve_report* rep) {
     rep->evicted = S->evicted;
   }
   for (auto s : S->slots) cudaStreamDestroy(s);
+  S->ctx->pool.set_budget(S->ctx_budget);  // the context gets its own budget back
   delete h;
   return MG_OK;
 }
+
+extern "C" void mgk_server_fail_event_queries(int count) { g_fail_queries.store(count > 0 ? count : 0); }

@@ -611,7 +611,7 @@ extern "C" void mg_problem_free(mg_problem* P) {
   if (!P) return;
   cudaSetDevice(P->ctx->device);
   cudaStreamSynchronize(P->ctx->stream);
-  batch_cache_clear(P->ctx);  // captured batches reference the problem's arrays
+  batch_cache_drop(P->ctx, P);  // captured batches that reference the problem's arrays
   {
     std::lock_guard<std::mutex> lk(P->ctx->problems_mu);
     P->ctx->problems.erase(P);
@@ -931,17 +931,13 @@ mg_status check_opts(const mg_problem* P, const mg_solve_opts& o) {
   return MG_OK;
 }
 
-// Host-driven loop (MG_SOLVE_LOOP=host): the same kernels in the same order launched
-// directly on the stream, with one stream synchronisation per outer iteration to read
-// the convergence flag.  Used by per-kernel profilers, which do not support kernels
-// inside graphs with conditional nodes.
+// Host-driven loop (MG_SOLVE_LOOP=host, read at every solve): the same kernels in the same
+// order launched directly on the stream, with one stream synchronisation per outer
+// iteration to read the convergence flag.  Used by per-kernel profilers, which do not
+// support kernels inside graphs with conditional nodes.
 static bool host_loop_mode() {
-  static int v = -1;
-  if (v < 0) {
-    const char* e = getenv("MG_SOLVE_LOOP");
-    v = (e && strcmp(e, "host") == 0) ? 1 : 0;
-  }
-  return v == 1;
+  const char* e = getenv("MG_SOLVE_LOOP");
+  return e && strcmp(e, "host") == 0;
 }
 
 static mg_status run_host_loop(mg_problem* P, const mg_solve_opts& o, cudaStream_t s, int* passes) {

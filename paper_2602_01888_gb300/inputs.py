@@ -606,3 +606,41 @@ def neumann_manufactured(n: int) -> Instance:
 
 def random_field(shape, seed: int, lo: float = -1.0, hi: float = 1.0) -> np.ndarray:
     return np.random.default_rng(seed).uniform(lo, hi, shape)
+
+
+def _gaussian_potential(r: np.ndarray, rho0: float, sigma: float) -> np.ndarray:
+    """Radially symmetric potential of the charge -rho0 exp(-r^2 / (2 sigma^2)) in the plane
+    under -lap(phi) = rho: r phi'(r) = rho0 sigma^2 (1 - exp(-u)), u = r^2 / (2 sigma^2), so
+    phi = (rho0 sigma^2 / 2) (ln(2 sigma^2) + ln u + E1(u)) up to a constant.  ln u + E1(u)
+    is -gamma + Ein(u) with Ein(u) = sum_k (-1)^(k+1) u^k / (k k!), summed directly for small u
+    (finite at the beam centre), by scipy's E1 elsewhere."""
+    from scipy.special import exp1
+    u = np.asarray(r, dtype=np.float64) ** 2 / (2.0 * sigma * sigma)
+    g = np.empty_like(u)
+    small = u < 1.0
+    us = u[small]
+    ein = np.zeros_like(us)
+    term = np.ones_like(us)
+    for k in range(1, 40):
+        term = term * (-us) / k  # (-u)^k / k!
+        ein -= term / k
+    g[small] = -np.euler_gamma + ein
+    ub = u[~small]
+    g[~small] = np.log(ub) + exp1(ub)
+    return 0.5 * rho0 * sigma * sigma * (math.log(2.0 * sigma * sigma) + g)
+
+
+def sinh_beam(n: int = 129, s: float = 5.0, alpha: float = 0.6, rho0: float = 100.0,
+              sigma: float = 0.5) -> Instance:
+    """The stretched-grid example of Sec. 5.1: computational square [-3, 3]^2 (Lx = Ly = 6),
+    map x' = s sinh(alpha x), y' = s sinh(alpha y) (Eq. 52, s = 5, alpha = 0.6), Gaussian beam
+    rho' = -rho0 exp(-(x'^2 + y'^2) / (2 sigma^2)) at the origin (Eq. 53, rho0 = 100,
+    sigma = 0.5).  The paper does not state its boundary condition; here the Dirichlet data
+    are the beam's free-space potential, which is then the exact solution."""
+    grid = Grid(n, n, x0=-3.0, y0=-3.0, lx=6.0, ly=6.0)
+    mp = MapSpec("sinh", (s, alpha))
+    xp, yp = mp.physical(grid)
+    r2 = xp * xp + yp * yp
+    rho = -rho0 * np.exp(-r2 / (2.0 * sigma * sigma))
+    exact = _gaussian_potential(np.sqrt(r2), rho0, sigma)
+    return Instance(f"sinh_beam_{n}", grid, mp, rho, bc=exact.copy(), exact=exact)

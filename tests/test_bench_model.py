@@ -49,18 +49,38 @@ def test_smoother_defaults_per_workload():
 
 
 def test_profiled_traffic_against_the_algorithmic_bytes():
-    """Every recorded per-launch DRAM figure belongs to a kernel the roofline line can name and
-    lies in the band its capture documented: the per-colour kernels re-read most rows of the
-    operator in each of a sweep's four launches (2-3.5x their share of a sweep's bytes); the
-    marching and line kernels move their algorithmic bytes (0.9-1.2x)."""
+    """Every recorded per-launch DRAM figure (profiles/dram_traffic.json) belongs to a kernel
+    the roofline line can name, names its capture command, and lies in the band its capture
+    documented: the per-colour kernels re-read most rows of the operator in each of a sweep's
+    four launches (2-3.5x their share of a sweep's bytes); the marching and line kernels move
+    their algorithmic bytes (0.9-1.2x).  Scaling to another level size goes by node count."""
     band = {"k_gs_colour<double>": (2.0, 3.5), "k_gs_colour<float>": (2.0, 3.5),
             "k_smooth_march<float,2>": (0.9, 1.2), "k_line_zebra<float>": (0.9, 1.2)}
-    for (kern, n), traffic in bench.PROFILED_TRAFFIC.items():
+    entries = bench._traffic_table()
+    assert entries
+    for e in entries:
+        kern = e["kernel"]
         assert kern in band, kern
-        nodes = float(n) * n
+        assert e["command"].startswith("ncu ") and "--clock-control none" in e["command"]
+        assert os.path.exists(os.path.join(ROOT, "profiles", e["summary"]))
+        nx, rows = e["captured"]
+        nodes = float(nx) * rows
+        traffic = bench.profiled_traffic(kern, nx, rows)
         algo = {"k_gs_colour<double>": 64.0 * nodes / 4,       # a sweep's 8 FP64 arrays over 4 launches
                 "k_gs_colour<float>": 32.0 * nodes / 4,
                 "k_smooth_march<float,2>": 32.0 * nodes,       # two sweeps, each array once
                 "k_line_zebra<float>": 14 * 4.0 * nodes / 2}[kern]
         lo, hi = band[kern]
-        assert lo <= traffic / algo <= hi, (kern, n, traffic / algo)
+        assert lo <= traffic / algo <= hi, (kern, traffic / algo)
+        assert bench.profiled_traffic(kern, 2 * nx, rows) == pytest.approx(2 * traffic)
+    assert bench.profiled_traffic("k_not_captured", 1025, 1025) is None
+
+
+def test_hbm_peak_comes_from_the_measured_file_or_the_fallback():
+    peak, src = bench._hbm_peak()
+    if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")):
+        import json
+        assert peak == json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+        assert "of measured" in src
+    else:
+        assert peak == 6800.0 and "of fallback" in src

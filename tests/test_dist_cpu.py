@@ -65,3 +65,17 @@ def test_reference_arm_of_the_batch_workload():
     rec = json.loads(lines[0])
     assert rec["impl"] == "reference" and rec["unit"] == "unknowns/s" and rec["value"] > 0
     assert rec["config"]["workload"] == "batch512" and "8 of the 512" in rec["cpu_baseline"]["sample"]
+
+
+def test_reference_arm_of_the_default_workload_runs_on_every_requested_core():
+    """Default workload (the annulus): the oracle on its 1025^2 sample, one copy per host core
+    at once (two here, to bound the test's time); the line states the sample and the cores."""
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "3",
+                        "--ref-cores", "2"], cwd=ROOT, capture_output=True, text=True, timeout=900)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1, r.stdout
+    rec = json.loads(lines[0])
+    assert rec["config"]["workload"] == "annulus_8193" and rec["config"]["smoother"] == "xline"
+    assert rec["cpu_baseline"]["cores"] == 2 and "1025^2" in rec["cpu_baseline"]["sample"]
+    assert rec["e2e"]["value"] == rec["value"] > 0

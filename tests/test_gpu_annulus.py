@@ -1,7 +1,8 @@
 """Annulus workload (polar map Eq. 29, periodic in theta, 64-mode Fourier source).
 
 * At 1025^2 the whole solution is compared with the oracle's phi* (mixed and FP64, at the
-  rtol the benchmark uses for this workload): relative L2 error <= 1e-9.
+  rtol the benchmark uses for this workload): relative L2 error <= 1e-9 (mixed) and
+  <= 1e-10 (FP64).
 * At the benchmark's full size (8193^2) the oracle cannot solve in test time.  Its phi* at
   seeded sample nodes is stored under tests/golden/ (written from the oracle alone) and the
   GPU solution is compared with it; independently, the test checks the GPU solution node by node: at seeded sample nodes it rebuilds the operator on a 5x5
@@ -9,6 +10,8 @@
   the GPU's phi.  Since ||r||_2 <= rtol ||r_0||_2 over all nodes, every sampled |r_i| must be
   below rtol ||r_0||_2, where ||r_0|| = ||b|| (zero Dirichlet data) is also computed by the
   oracle."""
+import functools
+
 import numpy as np
 import pytest
 
@@ -22,6 +25,12 @@ RTOL = 6e-10  # 1025^2 cases
 # above the error it corresponds to: at rtol 1e-8 the solution is within ~1e-10 of the
 # oracle's phi* (checked below against the stored samples).
 RTOL_FULL = 1e-8
+
+
+@functools.lru_cache(maxsize=1)
+def _full():
+    """The 8193^2 workload's inputs, generated once for every full-size test here."""
+    return I.config3(8193)
 
 
 @pytest.fixture(scope="module")
@@ -40,7 +49,7 @@ def test_annulus_recipe_1025_matches_oracle(libmg, oracle, ctx, prec, smoother):
     prob = libmg.Problem(ctx, inst, libmg.make_opts(prec, "fcg", rtol=RTOL, max_iters=400, smoother=smoother))
     phi, st = prob.solve()
     err = oracle.rel_l2(phi, ref, inst.grid.interior_mask())
-    assert err <= 1e-9, (prec, err, st.iters)
+    assert err <= (1e-10 if prec == "fp64" else 1e-9), (prec, err, st.iters)
     prob.close()
 
 
@@ -61,7 +70,7 @@ def _patch_residual(oracle, inst, phi_gpu, i, j):
 
 def test_annulus_full_size_sampled_residuals(libmg, oracle, ctx, cuda):
     torch = cuda
-    inst = I.config3(8193)
+    inst = _full()
     g = inst.grid
     prob = libmg.Problem(ctx, inst, libmg.make_opts("mixed", "fcg", rtol=RTOL_FULL, max_iters=400))
     rho = torch.from_numpy(np.ascontiguousarray(inst.rho_phys)).cuda()
@@ -91,18 +100,20 @@ def test_annulus_full_size_sampled_residuals(libmg, oracle, ctx, cuda):
     assert np.abs(phi_h).max() > 1e-6
 
 
-@pytest.mark.parametrize("smoother,nu", [("gs4", 2), ("xline", 2), ("xline", 1)])
-def test_annulus_full_size_matches_oracle_golden(libmg, ctx, cuda, smoother, nu):
-    """8193^2 annulus, mixed path at the benchmark's rtol (point smoother V(2,2), line
-    smoother V(2,2) and V(1,1)), against the oracle's phi* at 4096 seeded sample nodes
+@pytest.mark.parametrize("prec,smoother,nu", [("mixed", "gs4", 2), ("mixed", "xline", 2), ("mixed", "xline", 1),
+                                              ("fp64", "xline", 1), ("fp64", "gs4", 2)])
+def test_annulus_full_size_matches_oracle_golden(libmg, ctx, cuda, prec, smoother, nu):
+    """8193^2 annulus at the benchmark's rtol (point smoother V(2,2), line smoother V(2,2)
+    and V(1,1)), against the oracle's phi* at 4096 seeded sample nodes
     (tests/golden/annulus_8193_samples.npz, written by tests/golden/make_golden.py from the
-    oracle alone): relative L2 error over the samples within the 1e-9 target."""
+    oracle alone): relative L2 error over the samples within 1e-9 for the mixed path and
+    1e-10 for the FP64 path."""
     import os
     torch = cuda
     gold = np.load(os.path.join(os.path.dirname(__file__), "golden", "annulus_8193_samples.npz"))
-    inst = I.config3(8193)
+    inst = _full()
     g = inst.grid
-    prob = libmg.Problem(ctx, inst, libmg.make_opts("mixed", "fcg", rtol=RTOL_FULL, max_iters=400,
+    prob = libmg.Problem(ctx, inst, libmg.make_opts(prec, "fcg", rtol=RTOL_FULL, max_iters=400,
                                                     smoother=smoother, nu1=nu, nu2=nu))
     rho = torch.from_numpy(np.ascontiguousarray(inst.rho_phys)).cuda()
     phi = torch.zeros(g.shape, dtype=torch.float64, device="cuda")
@@ -113,4 +124,4 @@ def test_annulus_full_size_matches_oracle_golden(libmg, ctx, cuda, smoother, nu)
     prob.close()
     ref = gold["phi"]
     err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
-    assert err <= 1e-9, (err, st.iters, st.rel_residual)
+    assert err <= (1e-10 if prec == "fp64" else 1e-9), (prec, err, st.iters, st.rel_residual)

@@ -13,6 +13,9 @@ from paper_2602_01888_gb300 import inputs as I
 pytestmark = pytest.mark.gpu
 
 RTOL = 1e-9
+# FP64 rows aim at the FP64 path's 1e-10 error bound.  At rtol 1e-9 the oracle's own MG-PCG
+# leaves up to 8.2e-11 on these instances (129^2, ratio 49); at 5e-10 at most 1.5e-11.
+RTOL_FP64 = 5e-10
 
 
 @pytest.fixture(scope="module")
@@ -34,7 +37,8 @@ def _picks():
 @pytest.mark.parametrize("prec", ["mixed", "fp64"])
 def test_batched_instances_match_oracle(libmg, oracle, ctx, prec):
     insts = [I.inclusion_instance(*s) for s in _picks()]
-    opts = libmg.make_opts(prec, "fcg", rtol=RTOL, max_iters=400)
+    rtol = RTOL_FP64 if prec == "fp64" else RTOL
+    opts = libmg.make_opts(prec, "fcg", rtol=rtol, max_iters=400)
     probs = [libmg.Problem(ctx, x, opts) for x in insts]
     phis = [np.zeros(x.grid.shape) for x in insts]
     stats = libmg.mg_batch_solve(ctx.h, [p.h for p in probs],
@@ -43,8 +47,8 @@ def test_batched_instances_match_oracle(libmg, oracle, ctx, prec):
         P = oracle.prepare(x)
         ref, _, _ = oracle.pcg_solve(P.A, P.b, P.phi0, rtol=0.0, max_iters=400, stagnate=10)
         err = oracle.rel_l2(phi, ref, x.grid.interior_mask())
-        assert st.rel_residual <= RTOL
-        assert err <= 1e-9, (x.name, prec, err, st.iters)
+        assert st.rel_residual <= rtol
+        assert err <= (1e-10 if prec == "fp64" else 1e-9), (x.name, prec, err, st.iters)
     for p in probs:
         p.close()
 

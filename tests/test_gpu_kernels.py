@@ -20,6 +20,8 @@ CASES = {
                                      I.MapSpec("affine", (1.1, 0.2, -0.1, 0.9)), np.ones((17, 33))),
     "tiny_5": lambda: I.config1(5),
     "periodic_17": lambda: I.annulus_log(17),
+    # the stretched grid of Sec. 5.1 (Eq. 52, s = 5, alpha = 0.6) on [-3, 3]^2
+    "sinh_65": lambda: I.sinh_beam(65),
 }
 
 

@@ -259,3 +259,86 @@ def test_cycle_time_of_a_resident_problem(libmg, cuda):
                 libmg.mg_cycle_time(pr.h, libmg.make_opts("fp64", "sor", nu1=4, omega_j=1.5))
         pr.close()
     ctx.close()
+
+
+@pytest.mark.parametrize("case", ["config1_129", "inclusion_257", "annulus_129"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_jacobi_smoothed_solve_matches_oracle(libmg, oracle, ctx, case, precision):
+    """Weighted Jacobi (omega_J = 4/5, the smoother option of Sec. 3) inside flexible CG: the
+    solution reaches the oracle's phi* like the Gauss-Seidel solves do."""
+    make, rtol = CASES[case]
+    inst = make()
+    ref = _ref(oracle, inst)
+    opts = libmg.make_opts(precision, "fcg", rtol=rtol, max_iters=400, smoother="jacobi", omega_j=0.8)
+    prob = libmg.Problem(ctx, inst, opts)
+    phi, st = prob.solve()
+    err = _err(oracle, inst, phi, ref)
+    assert err <= (FP64_TOL if precision == "fp64" else MIXED_TOL), (case, precision, err, st.iters)
+    assert st.rel_residual <= rtol
+    # the smoother is in use: the residual history differs from the Gauss-Seidel solve's
+    gs = libmg.Problem(ctx, inst, libmg.make_opts(precision, "fcg", rtol=rtol, max_iters=400))
+    _, st_gs = gs.solve()
+    assert st.hist[1] != st_gs.hist[1] and st.iters >= st_gs.iters, (st.iters, st_gs.iters)
+    gs.close()
+    prob.close()
+
+
+def test_served_results_match_oracle(libmg, oracle, ctx):
+    """Requests of three grid sides and different geometries submitted while earlier ones are
+    still on the device (three slots, seven requests), polled in a different order than
+    submitted: every served result is within the mixed path's 1e-9 of the oracle's phi*."""
+    specs = [(257, 0.3, 40.0, 21), (65, 0.2, 5.0, 22), (129, 0.15, 12.0, 23), (257, 0.25, 2.0, 24),
+             (129, 0.3, 49.0, 25), (65, 0.1, 30.0, 26), (129, 0.2, 1.0, 27)]
+    insts = [I.inclusion_instance(*s) for s in specs]
+    opts = libmg.make_opts("mixed", "fcg", rtol=1e-9, max_iters=400)
+    srv = libmg.mg_server_start(ctx.h, max_inflight=3)
+    tickets = []
+    for inst in insts:
+        st, t = libmg.mg_serve_submit(srv, inst.grid, inst.map, np.ascontiguousarray(inst.rho_phys),
+                                      None, np.ascontiguousarray(inst.eps_phys), opts)
+        assert st == 0
+        tickets.append(t)
+    order = [3, 0, 6, 1, 5, 2, 4]
+    for k in order:
+        inst = insts[k]
+        out = np.zeros(inst.grid.shape)
+        st, stats = libmg.mg_serve_poll(srv, tickets[k], 120000, out)
+        assert st == 0, (k, st)
+        err = _err(oracle, inst, out, _ref(oracle, inst))
+        assert err <= MIXED_TOL, (inst.name, err, stats.iters)
+    rep = libmg.mg_server_stop(srv)
+    assert rep.completed == len(insts) and rep.failed == 0
+
+
+def test_server_request_whose_completion_query_fails_is_reported_and_stop_returns(libmg, ctx):
+    """A request whose completion query reports an error (made on the host by the server's
+    test hook, nothing faults on the device) finishes with MG_ERR_CUDA instead of staying in
+    flight; its slot is freed, later requests are served normally and mg_server_stop
+    returns with the failure counted."""
+    insts = [I.inclusion_instance(65, 0.2, 3.0 + k, 400 + k) for k in range(3)]
+    opts = libmg.make_opts("mixed", "fcg", rtol=1e-10)
+    srv = libmg.mg_server_start(ctx.h, max_inflight=1)
+    sub = lambda x: libmg.mg_serve_submit(srv, x.grid, x.map, np.ascontiguousarray(x.rho_phys), None,
+                                          np.ascontiguousarray(x.eps_phys), opts)
+    try:
+        libmg.lib().mgk_server_fail_event_queries(1)
+        st0, t0 = sub(insts[0])
+        assert st0 == 0
+        st, _ = libmg.mg_serve_poll(srv, t0, 60000, np.zeros(insts[0].grid.shape))
+        assert st == libmg.MG_ERR_CUDA, st
+    finally:
+        libmg.lib().mgk_server_fail_event_queries(0)
+    outs = []
+    for x in insts[1:]:
+        st, t = sub(x)
+        assert st == 0
+        out = np.zeros(x.grid.shape)
+        assert libmg.mg_serve_poll(srv, t, 60000, out)[0] == 0
+        outs.append(out)
+    rep = libmg.mg_server_stop(srv)
+    assert rep.failed == 1 and rep.completed == 2
+    for x, out in zip(insts[1:], outs):
+        p = libmg.Problem(ctx, x, opts)
+        want, _ = p.solve()
+        p.close()
+        assert np.array_equal(out, want)

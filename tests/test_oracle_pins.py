@@ -532,3 +532,91 @@ def test_neumann_reflection_equals_the_doubled_problem_of_a_skewed_grid(oracle, 
     _, _, take = oracle.neumann_rows(n)
     diff = np.abs(phi - phid[take]).max() / np.abs(phi).max()
     assert diff < 2.0 * g.hx ** 2, diff
+
+
+# ---------------------------------------------------------------- weighted Jacobi (smoother 1)
+@pytest.mark.parametrize("case", ["inclusion", "annulus"])
+def test_jacobi_sweep_equals_the_matrix_definition(oracle, case):
+    """One weighted-Jacobi sweep (Sec. 3's smoother choice, omega_J = 4/5) is
+    x + omega diag(A)^-1 (b - A x) at the unknowns, the boundary ring untouched.  A and its
+    diagonal come from the independent sparse construction, not from the oracle's couplings;
+    a wrong sign, a missing omega or a wrong diagonal fails here."""
+    inst = {"inclusion": lambda: I.inclusion_instance(33, 0.25, 10.0, 8),
+            "annulus": lambda: I.annulus_log(33)}[case]()
+    g = inst.grid
+    P = oracle.prepare(inst)
+    A = X.full_operator(g, P.exx, P.exy, P.eyy)
+    d = A.diagonal()
+    rng = np.random.default_rng(21)
+    x = rng.standard_normal(g.shape)
+    b = rng.standard_normal(g.shape) * np.abs(d).max()
+    u = X.unknown_ids(g)
+    want = x.ravel().copy()
+    r = b.ravel() - A @ x.ravel()
+    want[u] += 0.8 * r[u] / d[u]
+    got = oracle.smooth(P.A, x, b, sweeps=1, smoother=oracle.SMOOTHER_JACOBI, omega_j=0.8).ravel()
+    scale = np.abs(want).max()
+    assert np.abs(got - want).max() <= 1e-14 * scale * 10, np.abs(got - want).max() / scale
+    m = ~g.interior_mask().ravel()
+    assert np.array_equal(got[m], x.ravel()[m])
+    # two sweeps are the map applied twice
+    y = want.reshape(g.shape)
+    want2 = y.ravel().copy()
+    want2[u] += 0.8 * (b.ravel() - A @ y.ravel())[u] / d[u]
+    got2 = oracle.smooth(P.A, x, b, sweeps=2, smoother=oracle.SMOOTHER_JACOBI, omega_j=0.8).ravel()
+    assert np.abs(got2 - want2).max() <= 1e-13 * np.abs(want2).max()
+
+
+@pytest.mark.parametrize("omega", [0.8, 1.2])
+def test_jacobi_contraction_factor_matches_the_one_dimensional_spectrum(oracle, omega):
+    """On a row of the 1-D Poisson matrix (diag 2, neighbours -1; rows decoupled) the
+    weighted-Jacobi iteration matrix I - omega D^-1 A has the eigenvalues
+    1 - omega (1 - cos(k pi h)), k = 1..N, h = 1/(N+1).  With b = 0 the iterate is the error;
+    its measured asymptotic growth per sweep must equal the largest |eigenvalue|: the
+    smoothest mode for omega = 0.8 (0.9846 at N = 15), the most oscillatory one for
+    omega = 1.2 (1.377: the iteration diverges)."""
+    N = 15
+    A = _rows_decoupled_laplacian(N)
+    h = 1.0 / (N + 1)
+    lam = 1.0 - omega * (1.0 - np.cos(np.arange(1, N + 1) * np.pi * h))
+    rho = np.abs(lam).max()
+    rng = np.random.default_rng(9)
+    phi = np.zeros(A.cE.shape)
+    phi[1, 1:-1] = rng.standard_normal(N)
+    b = np.zeros(A.cE.shape)
+    norms = []
+    for _ in range(600):
+        phi = oracle.smooth(A, phi, b, sweeps=1, smoother=oracle.SMOOTHER_JACOBI, omega_j=omega)
+        norms.append(np.linalg.norm(phi))
+    rate = (norms[-1] / norms[299]) ** (1.0 / 300)
+    assert abs(rate - rho) < 1e-6 * rho, (rate, rho)
+
+
+# ---------------------------------------------------------------- stretched grid (Sec. 5.1)
+def test_sinh_beam_converges_at_second_order(oracle):
+    """The Gaussian beam (Eq. 53) on the sinh-stretched grid (Eq. 52) with the beam's
+    free-space potential as Dirichlet data (closed form through the exponential integral,
+    checked against its own ODE in the next test): the oracle's solution converges to it at
+    second order in L1, L2 and Linf (Eqs. 25-27) over 65, 129, 257, 513."""
+    o = _orders(oracle, I.sinh_beam, (65, 129, 257, 513))
+    assert all(1.9 < v < 2.1 for v in o[-1]), o
+    assert all(1.8 < v < 2.2 for v in o[-2]), o
+
+
+def test_gaussian_potential_solves_the_radial_equation():
+    """The closed form used as exact solution satisfies (1/r) (r phi')' = rho0 exp(-r^2/(2
+    sigma^2)), i.e. -lap(phi) = rho' of Eq. 53, checked by fourth-order finite differences in
+    r; and it is finite and smooth through the beam centre."""
+    rho0, sigma = 100.0, 0.5
+    f = lambda r: I._gaussian_potential(np.asarray(r, dtype=float), rho0, sigma)
+    d = 1e-3
+    for r in (0.2, 0.5, 0.7071, 0.9, 1.5, 3.0, 8.0):
+        rr = r + d * np.arange(-2, 3)
+        p = f(rr)
+        d1 = (p[0] - 8 * p[1] + 8 * p[3] - p[4]) / (12 * d)
+        d2 = (-p[0] + 16 * p[1] - 30 * p[2] + 16 * p[3] - p[4]) / (12 * d * d)
+        lap = d2 + d1 / r
+        want = rho0 * np.exp(-r * r / (2 * sigma * sigma))
+        assert abs(lap - want) < 1e-6 * max(1.0, want), (r, lap, want)
+    c = f([0.0, 1e-4])
+    assert abs(c[1] - c[0]) < 1e-5

@@ -60,3 +60,40 @@ def test_static_scratch_rejects_grids_beyond_its_capacity(libmg, cuda):
     rc = libmg.lib().mgk_jacobi_f64_static(C.byref(s), dummy.data_ptr(), dummy.data_ptr(), 1, 0.8, None)
     assert rc == 2
     assert "static array" in libmg.mg_last_error()
+
+
+def _random_pitched_operator(torch, libmg, nx, ny, pitch, seed):
+    """A diagonally dominant random 9-point operator in pitched device arrays (the two entry
+    points are compared with each other, so any operator with a nonzero diagonal serves)."""
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    off = [(-torch.rand((ny, pitch), generator=g, dtype=torch.float64)).cuda() for _ in range(4)]
+    diag = (8.0 + torch.rand((ny, pitch), generator=g, dtype=torch.float64)).cuda()
+    ops = off + [diag, 1.0 / diag]
+    return ops, libmg.op_struct(ops, nx, ny, False)
+
+
+def test_static_scratch_accepts_a_grid_of_exactly_its_capacity(libmg, cuda):
+    """pitch x rows equal to the capacity (1024 x 1024 = 2^20, nx = 1000) is accepted and
+    gives bitwise the caller-scratch result on two calls in a row; zero sweeps leave phi
+    unchanged."""
+    torch = cuda
+    nx, ny, pitch = 1000, 1024, 1024
+    assert pitch * ny == libmg.lib().mgk_jacobi_f64_static_capacity()
+    ops, st = _random_pitched_operator(torch, libmg, nx, ny, pitch, 61)
+    stream = torch.cuda.current_stream().cuda_stream
+    g = torch.Generator(device="cpu").manual_seed(62)
+    for call in range(2):
+        phi0 = torch.randn((ny, pitch), generator=g, dtype=torch.float64).cuda()
+        b = torch.randn((ny, pitch), generator=g, dtype=torch.float64).cuda()
+        x_ref, x_new = phi0.clone(), phi0.clone()
+        tmp = torch.zeros((ny, pitch), dtype=torch.float64, device="cuda")
+        libmg.mgk("mgk_jacobi_f64", C.byref(st), x_ref.data_ptr(), b.data_ptr(), tmp.data_ptr(), 2, 0.8,
+                  stream)
+        libmg.mgk("mgk_jacobi_f64_static", C.byref(st), x_new.data_ptr(), b.data_ptr(), 2, 0.8, stream)
+        torch.cuda.synchronize()
+        assert torch.equal(x_new, x_ref), call
+        assert not torch.equal(x_new, phi0)
+        x0 = phi0.clone()
+        libmg.mgk("mgk_jacobi_f64_static", C.byref(st), x0.data_ptr(), b.data_ptr(), 0, 0.8, stream)
+        torch.cuda.synchronize()
+        assert torch.equal(x0, phi0)

@@ -158,16 +158,19 @@ int mgk_smooth_pipe_f32(const mgk_op_f32 *A, const float *xin, float *xout, cons
                         int reverse, const float *eH, int pitch_c, int *err, void *stream);
 int mgk_pipe_sweeps(int f32);
 
-/* Row-marching variant for large FP32 levels: xout = mgk_march_sweeps() four-colour
- * Gauss-Seidel sweeps (Sec. 2.1, omega = 1; reverse = 1 reverses the colour order) of
- * xin [+ P eH] (Eq. 24) in one pass over the level.  Each CTA streams a strip of columns
- * upward through a ring of rows in shared memory, so every array is read about once.
- * Same result as mgk_smooth_fused_f32 up to FP32 rounding order (identical operations in
- * the same order per node).  Needs xin != xout, 16-byte aligned arrays and a pitch that
- * keeps rows 16-byte aligned (else returns 1); 4 on a CUDA error. */
+/* Row-marching variant for large levels: xout = mgk_march_sweeps() (FP32) or
+ * mgk_march_sweeps_f64() (FP64) four-colour Gauss-Seidel sweeps (Sec. 2.1, omega = 1;
+ * reverse = 1 reverses the colour order) of xin [+ P eH] (Eq. 24) in one pass over the
+ * level.  Each CTA streams a strip of columns upward through a ring of rows in shared
+ * memory, so every array is read about once.  Same result as the per-colour kernels
+ * (identical operations in the same order per node).  Needs xin != xout, 16-byte aligned
+ * arrays and a pitch that keeps rows 16-byte aligned (else returns 1); 4 on a CUDA error. */
 int mgk_smooth_march_f32(const mgk_op_f32 *A, const float *xin, float *xout, const float *b,
                          int reverse, const float *eH, int pitch_c, void *stream);
+int mgk_smooth_march_f64(const mgk_op_f64 *A, const double *xin, double *xout, const double *b,
+                         int reverse, const double *eH, int pitch_c, void *stream);
 int mgk_march_sweeps(void);
+int mgk_march_sweeps_f64(void);
 
 /* Zebra x-line Gauss-Seidel (an addition to the paper's point smoother for operators whose
  * coupling along x dominates, such as the annulus of Eq. 29 in polar coordinates).  A
@@ -223,13 +226,13 @@ size_t mgk_jacobi_f64_static_capacity(void);
 
 /* FMA-rate probe (no counterpart in the paper: it measures the arithmetic peak that the
  * FP64 stencil kernels are reported against, since their bound is the FP64 pipe, not HBM).
- * Launches `blocks` CTAs of 256 threads; every thread runs 8 independent chains of `iters`
- * dependent fused multiply-adds in registers (FP64 if f64 != 0, else FP32) and writes one
- * value to out[blocks * 256] (device memory, caller-owned).  Time the launch with CUDA
- * events on `stream`; mgk_fma_rate_flops gives its flop count.  Returns 1 on bad arguments,
- * 4 if the launch fails. */
-int mgk_fma_rate(int f64, int blocks, int iters, void *out, void *stream);
-double mgk_fma_rate_flops(int blocks, int iters);
+ * Launches `blocks` CTAs of 256 threads; every thread runs `chains` (4, 8 or 16)
+ * independent chains of `iters` dependent fused multiply-adds in registers (FP64 if
+ * f64 != 0, else FP32) and writes one value to out[blocks * 256] (device memory,
+ * caller-owned).  Time the launch with CUDA events on `stream`; mgk_fma_rate_flops gives
+ * its flop count.  Returns 1 on bad arguments, 4 if the launch fails. */
+int mgk_fma_rate(int f64, int chains, int blocks, int iters, void *out, void *stream);
+double mgk_fma_rate_flops(int chains, int blocks, int iters);
 
 /* Test hook of the request server (mg_serve_*): the next `count` completion queries of
  * in-flight requests report a failure (cudaErrorLaunchFailure) without asking the runtime,

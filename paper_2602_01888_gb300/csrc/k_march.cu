@@ -19,6 +19,9 @@
 // columns at distance > ph from the loaded edge; after 4 NS phases the owned rows and
 // columns hold exactly the result of NS sequential sweeps.
 //
+// Geometry per precision: FP32 two sweeps a pass on 256-column strips, FP64 one sweep a
+// pass on 128-column strips (MarchGeom below).
+//
 // The threads of a CTA have one role each, in whole warps: compute threads run the
 // phases; loader threads request rows D steps ahead with asynchronous 16-byte copies into
 // a small staging ring (a barrier does not wait for these, unlike for plain loads, so the
@@ -46,6 +49,17 @@ struct MarchGeom<float, 2> {
   static constexpr int THREADS = 1024, CTAS_PER_SM = 1;
 };
 
+// FP64: 128 loaded columns (64 per parity), one sweep a pass.  FP64 smoothing is bound by
+// the FP64 pipe, not by HBM, once each array is read once per sweep, so a second sweep per
+// pass would only add redundant halo work.  640 threads: 128 compute (2 active phases x 64
+// nodes), 448 loaders (one 16-byte chunk of each of the 7 arrays' rows) and 64 writers (60
+// of them copy the owned 120 columns of a finished row).
+template <>
+struct MarchGeom<double, 1> {
+  static constexpr int C = 128, HX = 4, W = C - 2 * HX, HY = 4, R = 12, D = 4, NPT = 1;
+  static constexpr int THREADS = 640, CTAS_PER_SM = 1;
+};
+
 template <typename T, int NS>
 struct MarchLayout {
   using G = MarchGeom<T, NS>;
@@ -71,8 +85,46 @@ struct MarchLayout {
   static_assert((G::HX * sizeof(T)) % 16 == 0, "strip start must stay 16-byte aligned");
   // rows touched at step s: s - 2 (4 NS - 1) - 2 (written out) .. s + 2 (de-interleaved)
   static_assert(G::R >= 2 * (4 * NS - 1) + 5, "ring must hold the live rows");
-  static_assert(sizeof(T) == 4, "de-interleave of 16-byte chunks assumes FP32");
+  static_assert(VEC % 2 == 0, "a 16-byte chunk holds whole even/odd column pairs");
 };
+
+// 16-byte vector of T: a chunk of VEC consecutive columns.
+template <typename T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using type = float4;
+  __device__ static void split(const float4& v, float* e) { e[0] = v.x; e[1] = v.y; e[2] = v.z; e[3] = v.w; }
+  __device__ static float4 join(const float* e) { return make_float4(e[0], e[1], e[2], e[3]); }
+};
+template <>
+struct Vec16<double> {
+  using type = double2;
+  __device__ static void split(const double2& v, double* e) { e[0] = v.x; e[1] = v.y; }
+  __device__ static double2 join(const double* e) { return make_double2(e[0], e[1]); }
+};
+
+// VEC/2 consecutive elements of one parity half of a ring row (8-byte aligned for FP32
+// pairs, one element for FP64).
+template <typename T, int K>
+__device__ __forceinline__ void put_half(T* dst, const T* e) {
+  if constexpr (K == 2) {
+    *reinterpret_cast<float2*>(dst) = make_float2(e[0], e[1]);
+  } else {
+    static_assert(K == 1, "half chunks of 1 (FP64) or 2 (FP32) elements");
+    dst[0] = e[0];
+  }
+}
+template <typename T, int K>
+__device__ __forceinline__ void get_half(const T* src, T* e) {
+  if constexpr (K == 2) {
+    const float2 v = *reinterpret_cast<const float2*>(src);
+    e[0] = v.x;
+    e[1] = v.y;
+  } else {
+    e[0] = src[0];
+  }
+}
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -120,7 +172,7 @@ __global__ void __launch_bounds__(MarchGeom<T, NS>::THREADS, MarchGeom<T, NS>::C
   constexpr int C = G::C, HX = G::HX, W = G::W, HY = G::HY, D = G::D, M = Y::M, VEC = Y::VEC;
   constexpr int R = G::R, ROW = Y::ROW, RAWS = Y::RAWS;
   constexpr int LAG = 2 * (4 * NS - 1);  // rows between phase 0 and the last phase
-  T* const sm = march_smem;  // ring at 0, staging rows at RAW0, coarse staging at EST0
+  T* const sm = reinterpret_cast<T*>(march_smem);  // ring at 0, staging rows at RAW0, coarse staging at EST0
   constexpr int RAW0 = R * ROW, EST0 = RAW0 + RAWS * ROW;
   T* const raw = sm + RAW0;
   T* const estage = sm + EST0;
@@ -187,31 +239,40 @@ __global__ void __launch_bounds__(MarchGeom<T, NS>::THREADS, MarchGeom<T, NS>::C
   // the same group, so the whole x-loader warp pair waits for them (named barrier 1).
   auto settle = [&](int q, int rs, int sr) {
     if (!loader || q >= Q) return;
-    float4 v = *reinterpret_cast<const float4*>(raw + rs * ROW + raw_off);
+    constexpr int K = VEC / 2;  // even (and odd) columns of a chunk
+    T v[VEC];
+    Vec16<T>::split(*reinterpret_cast<const typename Vec16<T>::type*>(raw + rs * ROW + raw_off), v);
     if (corr) {
       asm volatile("bar.sync 1, %0;" ::"n"(Y::CHUNKS) : "memory");
       const int j = grow(q);
       if (j >= 0) {
-        // local coarse columns 2 lc .. 2 lc + 2 of rows J (a) and J + 1 (c)
-        const T* ed = estage + rs * Y::ESTAGE + 2 * lc;
-        const T a0 = ed[0], a1 = ed[1], a2 = ed[2];
+        // local coarse columns K lc .. K lc + K of rows J (a) and J + 1 (c)
+        const T* ed = estage + rs * Y::ESTAGE + K * lc;
         if (!(j & 1)) {
-          v.x += a0;
-          v.y += T(0.5) * (a0 + a1);
-          v.z += a1;
-          v.w += T(0.5) * (a1 + a2);
+#pragma unroll
+          for (int e = 0; e < K; ++e) {
+            v[2 * e] += ed[e];
+            v[2 * e + 1] += T(0.5) * (ed[e] + ed[e + 1]);
+          }
         } else {
-          const T c0 = ed[Y::CW], c1 = ed[Y::CW + 1], c2 = ed[Y::CW + 2];
-          v.x += T(0.5) * (a0 + c0);
-          v.y += T(0.25) * ((a0 + a1) + (c0 + c1));
-          v.z += T(0.5) * (a1 + c1);
-          v.w += T(0.25) * ((a1 + a2) + (c1 + c2));
+          const T* ec = ed + Y::CW;
+#pragma unroll
+          for (int e = 0; e < K; ++e) {
+            v[2 * e] += T(0.5) * (ed[e] + ec[e]);
+            v[2 * e + 1] += T(0.25) * ((ed[e] + ed[e + 1]) + (ec[e] + ec[e + 1]));
+          }
         }
       }
     }
+    T ev[K], od[K];
+#pragma unroll
+    for (int e = 0; e < K; ++e) {
+      ev[e] = v[2 * e];
+      od[e] = v[2 * e + 1];
+    }
     T* row = sm + sr * ROW + put_off;
-    *reinterpret_cast<float2*>(row) = make_float2(v.x, v.z);      // even columns
-    *reinterpret_cast<float2*>(row + M) = make_float2(v.y, v.w);  // odd columns
+    put_half<T, K>(row, ev);      // even columns
+    put_half<T, K>(row + M, od);  // odd columns
   };
 
   // ---- compute role: group grp runs phase 2 grp + parity on node m of a parity half
@@ -307,16 +368,22 @@ __global__ void __launch_bounds__(MarchGeom<T, NS>::THREADS, MarchGeom<T, NS>::C
       if (writer) {
         const int qo = s - LAG - 2;
         if (qo >= HY && qo < HY + Seff) {
+          constexpr int K = VEC / 2;
           const T* xr = sm + wrapR(sbase + u - LAG - 2) * ROW;
-          const float2 ev = *reinterpret_cast<const float2*>(xr + wl / 2);
-          const float2 od = *reinterpret_cast<const float2*>(xr + M + wl / 2);
+          T ev[K], od[K], e[VEC];
+          get_half<T, K>(xr + wl / 2, ev);
+          get_half<T, K>(xr + M + wl / 2, od);
+#pragma unroll
+          for (int k = 0; k < K; ++k) {
+            e[2 * k] = ev[k];
+            e[2 * k + 1] = od[k];
+          }
           T* dst = wdst + (size_t)(jb + qo) * p;
           if (wcol + VEC <= L.nx) {
-            *reinterpret_cast<float4*>(dst) = make_float4(ev.x, od.x, ev.y, od.y);
+            *reinterpret_cast<typename Vec16<T>::type*>(dst) = Vec16<T>::join(e);
           } else {
-            const T e[4] = {ev.x, od.x, ev.y, od.y};
 #pragma unroll
-            for (int v = 0; v < 4; ++v)
+            for (int v = 0; v < VEC; ++v)
               if (wcol + v < L.nx) dst[v] = e[v];
           }
         }
@@ -342,6 +409,10 @@ struct MarchCfg;
 template <>
 struct MarchCfg<float> {
   static constexpr int NS = 2;
+};
+template <>
+struct MarchCfg<double> {
+  static constexpr int NS = 1;
 };
 
 template <typename T>
@@ -408,9 +479,14 @@ cudaError_t launch_smooth_march(const Op<T>& A, const T* xin, T* xout, const T* 
 }
 
 template int march_sweeps<float>();
+template int march_sweeps<double>();
 template int march_strip_width<float>();
+template int march_strip_width<double>();
 template cudaError_t launch_smooth_march<float>(const Op<float>&, const float*, float*,
                                                 const float*, int, const float*, int, const int*,
                                                 cudaStream_t);
+template cudaError_t launch_smooth_march<double>(const Op<double>&, const double*, double*,
+                                                 const double*, int, const double*, int, const int*,
+                                                 cudaStream_t);
 
 }  // namespace mg

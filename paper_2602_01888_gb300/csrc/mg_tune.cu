@@ -2,7 +2,7 @@
 //
 // For square levels of a range of sides it builds a sine-warp operator with the library's
 // own set-up kernels and times nu = 2 Gauss-Seidel sweeps with every family that can run
-// there (per-colour kernels, fused tiles, pipelined tiles, row marching for FP32), with
+// there (per-colour kernels, fused tiles, pipelined tiles, row marching), with
 // CUDA events on the context's stream after a warm-up.  The fastest family per size becomes
 // the context's policy (SmoothPolicy), used by every V-cycle captured afterwards.  All the
 // families perform the same operations per node in the same order, so the policy changes
@@ -47,16 +47,20 @@ static float time_family(mg_ctx* ctx, int kind, const Op<T>& A, T* x, T* x2, con
           e = launch_smooth_pipe<T>(A, k & 1 ? x2 : x, k & 1 ? x : x2, b, 0, nullptr, 0, nullptr, err, s);
         return e;
       }
-      case SK_MARCH:
-        if constexpr (sizeof(T) == 4) return launch_smooth_march<float>(A, x, x2, b, 0, nullptr, 0, nullptr, s);
-        return cudaErrorInvalidValue;
+      case SK_MARCH: {
+        const int ns = march_sweeps<T>();
+        cudaError_t e = cudaSuccess;
+        for (int k = 0; k < 2 / ns && !e; ++k)
+          e = launch_smooth_march<T>(A, k & 1 ? x2 : x, k & 1 ? x : x2, b, 0, nullptr, 0, nullptr, s);
+        return e;
+      }
     }
     return cudaErrorInvalidValue;
   };
   // the same applicability rules as the cycle
   if (kind == SK_FUSED && 2 % fused_sweeps<T>()) return -1.f;
   if (kind == SK_PIPE && (2 % pipe_sweeps<T>() || nyr < 64 || A.nx < 160)) return -1.f;
-  if (kind == SK_MARCH && (sizeof(T) != 4 || nyr < 128)) return -1.f;
+  if (kind == SK_MARCH && (2 % march_sweeps<T>() || nyr < 128)) return -1.f;
   for (int w = 0; w < 2; ++w)
     if (once() != cudaSuccess) return -1.f;
   cudaEvent_t e0, e1;

@@ -1,7 +1,7 @@
 // One multigrid V(nu1, nu2) cycle (Sec. 3, Eqs. 19-24) enqueued on a stream.  Smoothing
-// per level, by size: the largest FP32 levels use the row-marching kernel (two sweeps a
-// pass), other large FP32 levels the pipelined tile kernel, large FP64 levels the
-// per-colour kernels, mid-size levels the fused tile kernel (NS sweeps per launch,
+// per level, by size: the largest levels use the row-marching kernel (FP32 two sweeps a
+// pass, FP64 one), other large FP32 levels the pipelined tile kernel, other large FP64
+// levels the per-colour kernels, mid-size levels the fused tile kernel (NS sweeps per launch,
 // ping-pong iterates); the residual is fused with full-weighting restriction; the levels
 // at and below the tail threshold run in one single-CTA tail kernel that ends with the
 // coarsest dense solve.  The weighted-Jacobi smoother uses the per-sweep kernels on every
@@ -54,8 +54,8 @@ int colour_nodes() {
   return v;
 }
 
-// FP32 levels with at least this many nodes use the row-marching smoother (two sweeps a
-// pass); below it the grid has too few strips and segments to fill the GPU.
+// Levels with at least this many nodes use the row-marching smoother; below it the grid has
+// too few strips and segments to fill the GPU.
 inline long long march_nodes() {
   static long long v = -1;
   if (v < 0) {
@@ -156,16 +156,15 @@ cudaError_t emit_vcycle(const VLevels<T>& V, int smoother, int nu1, int nu2, dou
     const int nyr = rows_stored(V.A[l].ny, V.A[l].periodic);
     const int pc = eH ? V.A[l + 1].pitch : 0;
     // which families can run this level with this many sweeps
-    const bool can_march = sizeof(T) == 4 && sweeps % march_sweeps<float>() == 0 && sweeps > 0 &&
-                           V.A[l].pitch % 4 == 0 && nyr >= 128;
+    const bool can_march = sweeps % march_sweeps<T>() == 0 && sweeps > 0 &&
+                           V.A[l].pitch % (16 / (int)sizeof(T)) == 0 && nyr >= 128;
     const bool can_pipe = sweeps % pipe_sweeps<T>() == 0 && sweeps > 0 && nyr >= 64 && V.A[l].nx >= 160 &&
                           V.A[l].pitch % (16 / (int)sizeof(T)) == 0 &&
                           (!V.A[l].periodic || nyr % (32 / (int)sizeof(T)) == 0);
     const bool can_fused = sweeps % NS == 0 && sweeps > 0;
     // size-threshold rule
     int kind;
-    if (sizeof(T) == 4 && nodes >= march_nodes() && sweeps % march_sweeps<float>() == 0 && sweeps > 0 &&
-        V.A[l].pitch % 4 == 0)
+    if (nodes >= march_nodes() && can_march)
       kind = SK_MARCH;
     else if (sizeof(T) == 4 && nodes > cthr && can_pipe)
       kind = SK_PIPE;
@@ -186,15 +185,12 @@ cudaError_t emit_vcycle(const VLevels<T>& V, int smoother, int nu1, int nu2, dou
       alt[l] = tmp;
     };
     if (kind == SK_MARCH) {
-      if constexpr (sizeof(T) == 4) {
-        for (int k = 0; k < sweeps / march_sweeps<float>(); ++k) {
-          err = launch_smooth_march<float>(V.A[l], cur[l], alt[l], V.b[l], rev, k == 0 ? eH : nullptr,
-                                           pc, skip, s);
-          if (err) return err;
-          swap_cur();
-        }
-        return cudaSuccess;
+      for (int k = 0; k < sweeps / march_sweeps<T>(); ++k) {
+        err = launch_smooth_march<T>(V.A[l], cur[l], alt[l], V.b[l], rev, k == 0 ? eH : nullptr, pc, skip, s);
+        if (err) return err;
+        swap_cur();
       }
+      return cudaSuccess;
     }
     if (kind == SK_PIPE) {
       for (int k = 0; k < sweeps / pipe_sweeps<T>(); ++k) {
@@ -205,7 +201,7 @@ cudaError_t emit_vcycle(const VLevels<T>& V, int smoother, int nu1, int nu2, dou
       }
       return cudaSuccess;
     }
-    if (kind == SK_COLOUR || (kind == SK_MARCH && sizeof(T) == 8)) {  // per-colour kernels, in place
+    if (kind == SK_COLOUR) {  // per-colour kernels, in place
       if (eH && (err = launch_prolong_add(V.A[l], cur[l], eH, pc, skip, s))) return err;
       return launch_smooth(V.A[l], cur[l], V.b[l], sweeps, rev, skip, s);
     }
@@ -368,16 +364,28 @@ extern "C" int mgk_smooth_pipe_f32(const mgk_op_f32* A, const float* xin, float*
 
 extern "C" int mgk_pipe_sweeps(int f32) { return f32 ? pipe_sweeps<float>() : pipe_sweeps<double>(); }
 
-extern "C" int mgk_smooth_march_f32(const mgk_op_f32* A, const float* xin, float* xout, const float* b,
-                                    int reverse, const float* eH, int pitch_c, void* stream) {
+template <typename T, typename OPK>
+static int march_abi(const OPK* A, const T* xin, T* xout, const T* b, int reverse, const T* eH, int pitch_c,
+                     void* stream) {
   if (!A || A->nx < 3 || A->ny < 3 || A->pitch < A->nx || !xin || !xout || !b || xin == xout)
     return 1;
   if (A->periodic && (A->ny - 1) % 2) return 1;
   if (eH && ((A->nx - 1) % 2 || (A->ny - 1) % 2 || pitch_c < (A->nx - 1) / 2 + 1)) return 1;
-  const cudaError_t e = launch_smooth_march<float>(op_from(*A), xin, xout, b, reverse, eH, pitch_c,
-                                                   nullptr, (cudaStream_t)stream);
+  const cudaError_t e = launch_smooth_march<T>(op_from(*A), xin, xout, b, reverse, eH, pitch_c, nullptr,
+                                               (cudaStream_t)stream);
   if (e == cudaErrorInvalidValue) return 1;
   return e == cudaSuccess ? 0 : 4;
 }
 
+extern "C" int mgk_smooth_march_f32(const mgk_op_f32* A, const float* xin, float* xout, const float* b,
+                                    int reverse, const float* eH, int pitch_c, void* stream) {
+  return march_abi<float>(A, xin, xout, b, reverse, eH, pitch_c, stream);
+}
+
+extern "C" int mgk_smooth_march_f64(const mgk_op_f64* A, const double* xin, double* xout, const double* b,
+                                    int reverse, const double* eH, int pitch_c, void* stream) {
+  return march_abi<double>(A, xin, xout, b, reverse, eH, pitch_c, stream);
+}
+
 extern "C" int mgk_march_sweeps(void) { return march_sweeps<float>(); }
+extern "C" int mgk_march_sweeps_f64(void) { return march_sweeps<double>(); }

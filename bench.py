@@ -247,6 +247,7 @@ def run_reference_instances(args):
         rtol, sample = BATCH_RTOL, "the first 8 of the 512 batch instances per step, same rtol"
     else:
         stream = [q for q in I.config5_stream(2000, seed=5, rate=1.0, side_range=(129, 2049)) if q[1] <= 513][:6]
+        # the CPU generates these requests' mapped grids itself (numpy multigrid of the inputs)
         insts = [I.inclusion_instance(n, r, ratio, sd) for _, n, r, ratio, sd in stream]
         rtol, sample = SERVE_RTOL, "the first 6 served requests with sides up to 513 per step, same rtol"
     U = sum(x.grid.unknowns for x in insts)
@@ -476,17 +477,14 @@ def measure_smoother(mg, torch, inst, prec, reps=20, smoother="gs4", family=None
     b = torch.randn((g.nyr, pitch), dtype=torch.float64, device="cuda").to(dt)
     if smoother == "xline":
         return _measure_line(mg, torch, g, st, x, b, f32, s, reps)
-    march = f32 and g.nx * g.nyr >= MARCH_NODES
-    if family in ("pipelined", "fused") and not march:
-        return _measure_tile_family(mg, torch, g, st, x, z(dt), b, f32, s, reps, family)
-    x2 = z(dt) if march else None
+    fam, shape = parse_choice(family)
+    if fam is None:  # untuned: the size rule of the cycle
+        fam = "marching" if g.nx * g.nyr >= MARCH_NODES else "colour"
+    if fam in ("pipelined", "fused", "marching"):
+        return _measure_variant(mg, torch, g, st, x, z(dt), b, f32, s, reps, fam, shape)
 
     def once():
-        if march:  # the kernel the V-cycle uses at this size: two sweeps in one pass
-            mg.mgk("mgk_smooth_march_f32", C.byref(st), x.data_ptr(), x2.data_ptr(), b.data_ptr(), 0,
-                   None, 0, s)
-        else:
-            mg.mgk(name, C.byref(st), x.data_ptr(), b.data_ptr(), 1, 0, s)
+        mg.mgk(name, C.byref(st), x.data_ptr(), b.data_ptr(), 1, 0, s)
 
     for _ in range(3):
         once()
@@ -497,12 +495,6 @@ def measure_smoother(mg, torch, inst, prec, reps=20, smoother="gs4", family=None
         once()
     e1.record()
     torch.cuda.synchronize()
-    if march:
-        per_launch_s = e0.elapsed_time(e1) * 1e-3 / reps
-        kern = "k_smooth_march<float,2>"
-        bytes_per_launch = 32.0 * g.nx * g.nyr  # x, b, 4 couplings, 1/diag read once, x written
-        ach = bytes_per_launch / per_launch_s / 1e9
-        return _hbm_roof(kern, ach, per_launch_s, g, sweeps_per_launch=2)
     per_launch_s = e0.elapsed_time(e1) * 1e-3 / (reps * 4)
     kern = "k_gs_colour<float>" if f32 else "k_gs_colour<double>"
     if f32:
@@ -514,22 +506,42 @@ def measure_smoother(mg, torch, inst, prec, reps=20, smoother="gs4", family=None
     return _fp64_roof(mg, torch, kern, achieved, per_launch_s, g)
 
 
-def _measure_tile_family(mg, torch, g, st, x, x2, b, f32, s, reps, family):
-    """The tile families the autotuner may pick for the finest level (pipelined: tiles staged
-    by bulk asynchronous copies; fused: tiles in shared memory), `ns` sweeps per launch,
-    ping-pong iterates.  FP64: flop-bound (18 flop per unknown and sweep); FP32: bytes-bound
-    (32 B per node and launch: each array read once, the iterate written once)."""
+FAMILY_CODES = {"fused": 2, "pipelined": 3, "marching": 4}
+
+
+def parse_choice(desc):
+    """("fused", (64, 16, 2)) from the bench's autotune entry "fused 64x16/2"; ("marching",
+    (240, 0, 2)) from "marching w240/2"; (family, None) without a shape; (None, None) if
+    untuned."""
+    if not desc:
+        return None, None
+    parts = desc.split()
+    if len(parts) == 1:
+        return parts[0], None
+    dims, ns = parts[1].split("/")
+    if dims.startswith("w"):
+        return parts[0], (int(dims[1:]), 0, int(ns))
+    tx, ty = dims.split("x")
+    return parts[0], (int(tx), int(ty), int(ns))
+
+
+def _measure_variant(mg, torch, g, st, x, x2, b, f32, s, reps, family, shape):
+    """One launch shape of the tile or row-marching smoothers (the autotuner's choice for
+    the finest level, else the family's default), ping-pong iterates.  FP64: flop-bound (18
+    flop per unknown and sweep); FP32: bytes-bound (32 B per node and launch: each array read
+    once, the iterate written once)."""
     import ctypes as C
     tag = "f32" if f32 else "f64"
-    pipe = family == "pipelined"
-    ns = mg.lib().mgk_pipe_sweeps(int(f32)) if pipe else mg.lib().mgk_fused_sweeps(int(f32))
+    code = FAMILY_CODES[family]
+    vs = mg.smooth_variants(f32, code)
+    v, tile, ns = vs[0]
+    for cand in vs:
+        if shape is not None and (cand[1][0], cand[1][1], cand[2]) == shape:
+            v, tile, ns = cand
 
     def once():
-        if pipe:
-            mg.mgk(f"mgk_smooth_pipe_{tag}", C.byref(st), x.data_ptr(), x2.data_ptr(), b.data_ptr(), 0, None, 0,
-                   None, s)
-        else:
-            mg.mgk(f"mgk_smooth_fused_{tag}", C.byref(st), x.data_ptr(), x2.data_ptr(), b.data_ptr(), 0, None, 0, s)
+        mg.mgk(f"mgk_smooth_variant_{tag}", C.byref(st), code, v, x.data_ptr(), x2.data_ptr(), b.data_ptr(), 0,
+               None, 0, None, s)
 
     for _ in range(3):
         once()
@@ -541,8 +553,12 @@ def _measure_tile_family(mg, torch, g, st, x, x2, b, f32, s, reps, family):
     e1.record()
     torch.cuda.synchronize()
     per_launch_s = e0.elapsed_time(e1) * 1e-3 / reps
-    kern = f"k_smooth_{'pipe' if pipe else 'fused'}<{'float' if f32 else 'double'}>"
-    note = f"the autotuner's family for this level size ({family}), {ns} sweep(s) per launch"
+    T = "float" if f32 else "double"
+    if family == "marching":
+        kern = f"k_smooth_march<{T},{ns}>"
+    else:
+        kern = f"k_smooth_{'pipe' if family == 'pipelined' else 'fused'}<{T},{tile[0]},{tile[1]},{ns}>"
+    note = f"the autotuner's choice for this level size ({family}), {ns} sweep(s) per launch"
     if f32:
         ach = 32.0 * g.nx * g.nyr / per_launch_s / 1e9
         return _hbm_roof(kern, ach, per_launch_s, g, sweeps_per_launch=ns, note=note)
@@ -648,7 +664,7 @@ def run_kernel_only(args):
     n = args.side
     g = I.Grid(n, args.ny or n)
     pitch = (n + 31) // 32 * 32
-    f64 = args.kernel.endswith("64")
+    f64 = args.kernel.rstrip("p").endswith("64")
     dt = torch.float64 if f64 else torch.float32
     z = lambda d=torch.float64: torch.zeros((g.nyr, pitch), dtype=d, device="cuda")
     D, exx, exy, eyy = z(), z(), z(), z()
@@ -675,20 +691,20 @@ def run_kernel_only(args):
         fac = torch.zeros(mg.lib().mgk_line_factor_elems(n, g.ny, 0), dtype=dt, device="cuda")
         mg.mgk(f"mgk_line_factor_{sfx}", C.byref(st), fac.data_ptr(), s)
 
+    # the family's default variant unless --variant picks another (fused: FP64 32x32/1, FP32 64x24/2)
+    var = args.variant if args.variant >= 0 else (5 if args.kernel.startswith("fused") and not f64 else 0)
+
     def once():
         if args.kernel.startswith("line"):  # one zebra sweep: two launches of k_line_zebra
             mg.mgk(f"mgk_line_smooth_{sfx}", C.byref(st), fac.data_ptr(), x.data_ptr(), b.data_ptr(), 1, 0, s)
-        elif args.kernel.startswith("march"):
-            # "march32p": with the coarse-grid correction fused (post-smoothing form)
-            corr = args.kernel.startswith("march32p")
-            mg.mgk("mgk_smooth_march_f32", C.byref(st), x.data_ptr(), x2.data_ptr(), b.data_ptr(), 0,
-                   bH.data_ptr() if corr else None, pc if corr else 0, s)
-        elif args.kernel.startswith("pipe"):
-            mg.mgk(f"mgk_smooth_pipe_{sfx}", C.byref(st), x.data_ptr(), x2.data_ptr(), b.data_ptr(), 0,
-                   None, 0, None, s)
-        elif args.kernel.startswith("fused"):
-            mg.mgk(f"mgk_smooth_fused_{sfx}", C.byref(st), x.data_ptr(), x2.data_ptr(), b.data_ptr(), 0,
-                   None, 0, s)
+        elif args.kernel.startswith(("march", "pipe", "fused")):
+            # "march32p" / "march64p": with the coarse-grid correction fused (post-smoothing form);
+            # --variant k: the autotuner's variant k of the family (tile shape, sweeps per launch)
+            corr = args.kernel.endswith("p") and args.kernel.startswith("march")
+            fam = FAMILY_CODES["marching" if args.kernel.startswith("march") else
+                               "pipelined" if args.kernel.startswith("pipe") else "fused"]
+            mg.mgk(f"mgk_smooth_variant_{sfx}", C.byref(st), fam, var, x.data_ptr(), x2.data_ptr(),
+                   b.data_ptr(), 0, bH.data_ptr() if corr else None, pc if corr else 0, None, s)
         elif args.kernel.startswith("smooth"):
             mg.mgk(f"mgk_smooth_{sfx}", C.byref(st), x.data_ptr(), b.data_ptr(), 1, 0, s)
         elif args.kernel.startswith("restrict"):
@@ -707,19 +723,33 @@ def run_kernel_only(args):
         once()
     e1.record()
     torch.cuda.synchronize()
-    print(json.dumps({"kernel": args.kernel, "side": n, "ny": g.ny, "reps": args.reps,
-                      "ms_per_call": e0.elapsed_time(e1) / args.reps}))
+    rec = {"kernel": args.kernel, "side": n, "ny": g.ny, "reps": args.reps,
+           "ms_per_call": e0.elapsed_time(e1) / args.reps}
+    if args.kernel.startswith(("march", "pipe", "fused")):
+        fam = FAMILY_CODES["marching" if args.kernel.startswith("march") else
+                           "pipelined" if args.kernel.startswith("pipe") else "fused"]
+        v, tile, ns = mg.smooth_variants(not f64, fam)[var]
+        rec.update(variant=v, tile=tile, sweeps=ns, ms_per_sweep=rec["ms_per_call"] / ns)
+    print(json.dumps(rec))
     return 0
 
 
 def autotune(mg, ctx, max_side, enabled):
-    """Time the smoother families per level size on this GPU (mg_autotune) before the
-    problems are set up; returns {precision: {side: chosen family}} for the bench line."""
+    """Time the smoother families in every variant per level size on this GPU (mg_autotune)
+    before the problems are set up; returns {precision: {side: "family tile/sweeps"}} for the
+    bench line (tile tx x ty for tile kernels, owned strip columns for row marching)."""
     if not enabled:
         return None
     out = {}
-    for prec, side, _, choice in mg.mg_autotune(ctx.h, max(33, max_side)):
-        out.setdefault(prec, {})[str(side)] = choice
+    for prec, side, _, choice, var in mg.mg_autotune(ctx.h, max(33, max_side), variants=True):
+        tx, ty = var["tile"]
+        if choice in ("fused", "pipelined"):
+            desc = f"{choice} {tx}x{ty}/{var['sweeps']}"
+        elif choice == "marching":
+            desc = f"{choice} w{tx}/{var['sweeps']}"
+        else:
+            desc = choice
+        out.setdefault(prec, {})[str(side)] = desc
     return out
 
 
@@ -1017,14 +1047,45 @@ def run_batch(args):
 SERVE_RTOL = 1e-9
 
 
-def _serve_requests(stream):
-    """(arrival, grid, map, rho, eps, unknowns) per request; sources come from the
-    pre-drawn cache, eps' from the request's own ratio."""
+def _blobs_device(torch, xp, yp, seed, count=16, sigma=0.02):
+    """The 16-blob source of the inclusion recipe (centres U[0,1]^2, amplitudes U[-1,1],
+    sigma 0.02; parameters drawn by numpy from the seed) evaluated on the device."""
+    rng = np.random.default_rng(seed)
+    cx, cy, amp = rng.uniform(0.0, 1.0, count), rng.uniform(0.0, 1.0, count), rng.uniform(-1.0, 1.0, count)
+    rho = torch.zeros_like(xp)
+    for k in range(count):
+        rho += float(amp[k]) * torch.exp(-((xp - float(cx[k])) ** 2 + (yp - float(cy[k])) ** 2) /
+                                         (2 * sigma * sigma))
+    return rho
+
+
+def serve_inputs(mg, torch, ctx, stream, sources=2):
+    """Host inputs of every distinct (side, inclusion ring) of a request stream: the mapped
+    grid generated on the GPU by the library's harmonic grid generator (Sec. 4.2, Eq. 44
+    data on the ring, mg_harmonic_grid to rtol 1e-13) and `sources` seeded 16-blob sources
+    per grid.  Returns ({(n, i0): (xp, yp, [rho, ...])}, seconds spent)."""
+    t0 = time.perf_counter()
+    out = {}
+    for n, i0 in sorted({(n, I.snap_ring(n, r)) for _, n, r, _, _ in stream}, key=lambda k: -k[0]):
+        ring, xp0, yp0 = I.inclusion_ring_data(n, i0)
+        d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+        fx, xi, yi = d(ring.astype(np.uint8)), d(xp0), d(yp0)
+        xo, yo = torch.empty_like(xi), torch.empty_like(yi)
+        mg.mg_harmonic_grid(ctx.h, I.Grid(n, n), fx, xi, yi, xo, yo, rtol=1e-13)
+        srcs = [_blobs_device(torch, xo, yo, 1009 * n + 7919 * v + i0).cpu().numpy() for v in range(sources)]
+        out[(n, i0)] = (xo.cpu().numpy(), yo.cpu().numpy(), srcs)
+    torch.cuda.synchronize()
+    return out, time.perf_counter() - t0
+
+
+def _serve_requests(stream, inputs):
+    """(arrival, grid, map, rho, eps key, unknowns) per request."""
     out = []
-    for t, n, r, ratio, seed in stream:
-        xp, yp, i0, rs = I.inclusion_grid(n, r)
-        out.append((t, I.Grid(n, n), I.MapSpec("grid", (), xp, yp), I.cached_source(n, i0, seed),
-                    (n, i0, ratio), (n - 2) ** 2))
+    for q, (t, n, r, ratio, seed) in enumerate(stream):
+        i0 = I.snap_ring(n, r)
+        xp, yp, srcs = inputs[(n, i0)]
+        out.append((t, I.Grid(n, n), I.MapSpec("grid", (), xp, yp), srcs[seed % len(srcs)], (n, i0, ratio),
+                    (n - 2) ** 2))
     return out
 
 
@@ -1064,6 +1125,8 @@ def _serve_pass(mg, ctx, reqs, arrivals, inflight, mem_budget):
         if st:
             raise RuntimeError(f"mg_serve_submit: status {st}: {mg.mg_last_error()}")
         tickets.append(tk)
+        while len(tickets) > 4 * inflight:  # keep the host staging bounded
+            collect(tickets.popleft())
     while tickets:
         collect(tickets.popleft())
     wall = time.perf_counter() - t0
@@ -1072,17 +1135,42 @@ def _serve_pass(mg, ctx, reqs, arrivals, inflight, mem_budget):
     return rep, wall
 
 
+def _plain_fp64(mg, ctx, reqs):
+    """The plain FP64 GPU solver on the same requests, one after another through the public
+    API with host arrays: a resident problem per grid shape, mg_update_transform + mg_solve
+    (FP64 flexible CG, the serving rtol) per request.  Returns unknowns/s."""
+    opts = mg.make_opts("fp64", "fcg", rtol=SERVE_RTOL, max_iters=400)
+    probs = {}
+    U = 0
+    t0 = time.perf_counter()
+    for _, grid, mp, rho, epsk, u in reqs:
+        h = probs.get(grid.nx)
+        eps = I.inclusion_eps(epsk[0], epsk[1], epsk[2])
+        if h is None:
+            h = probs[grid.nx] = mg.mg_setup_transform(ctx.h, grid, mp, eps, opts)
+        else:
+            mg.mg_update_transform(h, grid, mp, eps)
+        phi = np.zeros(grid.shape)
+        mg.mg_solve(h, np.ascontiguousarray(rho), None, phi, opts, True)
+        U += u
+    wall = time.perf_counter() - t0
+    for h in probs.values():
+        mg.mg_problem_free(h)
+    return U / wall
+
+
 def run_serve(args):
     """Poisson-arrival request stream (sides log-uniform in [129, 2049] snapped to m 2^k + 1,
-    inclusion geometry from a catalogue of radii, eps' ratio U[1,50]), solved by the
-    library's request server.  First a saturation pass (every request submitted at once)
-    measures throughput; then open-loop passes at fractions of that rate measure p50/p99
-    submit-to-result latency."""
+    inclusion radius drawn U[0.1, 0.35] per request and snapped so the ring lies on grid
+    lines, eps' ratio U[1,50]), solved by the library's request server.  The mapped grids are
+    generated by the library on the GPU before the timed passes.  First a saturation pass
+    (requests submitted as fast as the server takes them) measures throughput; then
+    open-loop passes at fractions of that rate measure p50/p99 submit-to-result latency; the
+    plain FP64 solver runs a sample of the same requests one by one for comparison."""
     ws, rank, local = dist_env()
     count = args.requests
     stream = I.config5_stream(count, seed=5 + 1000 * rank, rate=1.0, side_range=(129, args.serve_max_side))
     warm_stream = I.config5_stream(min(64, count), seed=99, rate=1.0, side_range=(129, 513))
-    I.prefetch_inclusion_grids([(n, r) for _, n, r, _, _ in stream + warm_stream], sources=2, seed=5)
     import torch
     from paper_2602_01888_gb300 import mg
 
@@ -1091,9 +1179,10 @@ def run_serve(args):
     mg.lib()
     ctx = mg.Context(local)
     tuned = autotune(mg, ctx, args.serve_max_side, not args.no_autotune)
-    reqs = _serve_requests(stream)
+    inputs, gen_s = serve_inputs(mg, torch, ctx, stream + warm_stream)
+    reqs = _serve_requests(stream, inputs)
     U = sum(q[5] for q in reqs)
-    warm = _serve_requests(warm_stream)
+    warm = _serve_requests(warm_stream, inputs)
     _serve_pass(mg, ctx, warm, None, args.inflight, 0)
     barrier(dist)
     sampler = ClockSampler(local) if rank == 0 else None
@@ -1114,6 +1203,8 @@ def run_serve(args):
                     "failed": r2.failed, "not_converged": r2.not_converged,
                     "mean_inflight": r2.mean_batch, "reused": r2.reused,
                     "evicted": r2.evicted})
+    sample = reqs[: min(len(reqs), args.plain_sample)]
+    plain = _plain_fp64(mg, ctx, sample)
     if rank == 0:
         bytes_in = sum(8 * q[1].nx * q[1].nyr * 4 for q in reqs)
         bytes_out = sum(8 * q[1].nx * q[1].nyr for q in reqs)
@@ -1123,13 +1214,17 @@ def run_serve(args):
             "vs_baseline": None, "dtype": "f32 cycle in f64 refinement", "data": "synthetic",
             "config": {"workload": "serve", "requests": count,
                        "sides": f"log-uniform [129,{args.serve_max_side}] snapped to m*2^k+1",
-                       "radii": list(I.SERVE_RADII), "rtol": SERVE_RTOL, "inflight_slots": args.inflight,
+                       "radius": "U[0.1,0.35] per request, snapped so the ring lies on grid lines",
+                       "distinct_grids": len(inputs), "rtol": SERVE_RTOL, "inflight_slots": args.inflight,
                        "unknowns": U, "l2": "inputs of consecutive requests exceed L2 in aggregate"},
             "saturated": {"requests_per_s": sat_rps, "p50_ms": rep.p50_ms, "p99_ms": rep.p99_ms,
                           "completed": rep.completed, "failed": rep.failed,
                           "not_converged": rep.not_converged, "mean_inflight": rep.mean_batch,
                           "reused": rep.reused, "evicted": rep.evicted},
             "latency": lat,
+            "fp64_plain": {"value": plain, "requests": len(sample),
+                           "how": "mg_update_transform + mg_solve per request, FP64, hierarchy per grid shape"},
+            "grid_generation_s": gen_s,
             "e2e": {"value": ws * U / wall, "unit": "unknowns/s", "h2d_bytes_per_step": bytes_in,
                     "d2h_bytes_per_step": bytes_out},
             "gpu_launches": None, "roofline": None, "cpu_baseline": None, "clocks": clocks,
@@ -1208,7 +1303,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="annulus_8193",
                     choices=sorted(WORKLOADS) + ["batch512", "serve", "sor_vs_gmg"])
-    ap.add_argument("--requests", type=int, default=2000, help="serve: requests per pass")
+    ap.add_argument("--requests", type=int, default=20000, help="serve: requests per pass")
+    ap.add_argument("--plain-sample", type=int, default=500,
+                    help="serve: requests solved one by one by the plain FP64 solver for comparison")
     ap.add_argument("--inflight", type=int, default=16, help="serve: concurrent request slots")
     ap.add_argument("--serve-max-side", type=int, default=2049, help="serve: largest grid side")
     ap.add_argument("--serve-loads", type=float, nargs="*", default=[0.5, 0.8, 0.95],
@@ -1223,11 +1320,14 @@ def main():
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the size-threshold smoother choice instead of timing the families")
     ap.add_argument("--kernel-only", dest="kernel", default=None,
-                    help="smooth64|smooth32|fused64|fused32|pipe64|pipe32|march32|march32p|line64|line32|"
+                    help="smooth64|smooth32|fused64|fused32|pipe64|pipe32|march32|march32p|march64|march64p|"
+                         "line64|line32|"
                          "restrict64|restrict32|prolong64|prolong32|fp64peak|fp32peak")
     ap.add_argument("--side", type=int, default=2049)
     ap.add_argument("--ny", type=int, default=0, help="kernel-only: rows (default: --side)")
     ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--variant", type=int, default=-1,
+                    help="kernel-only march/pipe/fused: the autotuner's variant index (default: the family's default)")
     args = ap.parse_args()
     if args.kernel:
         return run_kernel_only(args)

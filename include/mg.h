@@ -239,13 +239,17 @@ mg_status mg_harmonic_grid(mg_ctx *ctx, const mg_grid_desc *grid, const unsigned
  * sequential smoother).  For square levels of sides 33, 65, ..., up to max_side, in FP64 and
  * FP32, it times two Gauss-Seidel sweeps (Sec. 2.1) with each kernel family that can run at
  * that size -- per-colour kernels, fused shared-memory tiles, pipelined tiles, row marching
- * (FP32) -- on a sine-warp operator built by the library, and records the fastest.  Every
- * solve graph captured on the context afterwards takes, at each level, the choice of the
- * tuned size nearest in node count (the families compute the same values, so results do not
- * change); graphs captured before are dropped.  Call it when no solve or server is running
- * on the context.  report (nullable) receives per (precision, side) the times in ms of the
- * families in the order colour, fused, pipelined, marching (-1: cannot run) and the choice
- * (1-4 in that order).
+ * -- in each of the family's variants (tile shapes 32x32, 64x16, 64x24 and one or two
+ * sweeps per launch for the tile kernels, where shared memory allows; one or two sweeps per
+ * pass for row marching), on a sine-warp operator built by the library, and records the
+ * fastest.  Every solve graph captured on the context afterwards takes, at each level, the
+ * choice of the tuned size nearest in node count (all variants compute the same values, so
+ * results do not change); graphs captured before are dropped.  Call it when no solve or
+ * server is running on the context.  report (nullable) receives per (precision, side) the
+ * best time in ms of each family in the order colour, fused, pipelined, marching (-1: cannot
+ * run), the choice (1-4 in that order) and the chosen variant's tile (tile_x x tile_y owned
+ * nodes; marching: tile_x owned columns of a strip, tile_y 0; per-colour: 0 x 0) and sweeps
+ * per launch.
  */
 #define MG_TUNE_MAX 32
 typedef struct {
@@ -253,6 +257,7 @@ typedef struct {
   int side;
   float ms[4];
   int choice;
+  int tile_x, tile_y, sweeps_per_launch;
 } mg_tune_entry;
 typedef struct {
   int count;

@@ -172,6 +172,21 @@ int mgk_smooth_march_f64(const mgk_op_f64 *A, const double *xin, double *xout, c
 int mgk_march_sweeps(void);
 int mgk_march_sweeps_f64(void);
 
+/* Shapes the autotuner chooses among (mg_autotune).  family: 2 fused tiles, 3 pipelined
+ * tiles, 4 row marching (the mg_tune_entry.choice codes).  mgk_smooth_variant_info gives
+ * variant `variant` of a family in FP32 (f32 = 1) or FP64: owned tile tile_x x tile_y
+ * (marching: tile_x owned strip columns, tile_y 0) and sweeps per launch; returns 1 past the
+ * last variant.  mgk_smooth_variant_* runs one launch of that variant exactly as the
+ * mgk_smooth_fused_* / mgk_smooth_pipe_* / mgk_smooth_march_* entry points run their default
+ * one (same arguments and requirements; err is used by the pipelined tiles only). */
+int mgk_smooth_variant_info(int f32, int family, int variant, int *tile_x, int *tile_y, int *sweeps);
+int mgk_smooth_variant_f64(const mgk_op_f64 *A, int family, int variant, const double *xin, double *xout,
+                           const double *b, int reverse, const double *eH, int pitch_c, int *err,
+                           void *stream);
+int mgk_smooth_variant_f32(const mgk_op_f32 *A, int family, int variant, const float *xin, float *xout,
+                           const float *b, int reverse, const float *eH, int pitch_c, int *err,
+                           void *stream);
+
 /* Zebra x-line Gauss-Seidel (an addition to the paper's point smoother for operators whose
  * coupling along x dominates, such as the annulus of Eq. 29 in polar coordinates).  A
  * half-sweep of parity p solves, for every row j with j mod 2 == p, the tridiagonal system

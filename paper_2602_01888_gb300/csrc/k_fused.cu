@@ -10,9 +10,12 @@
 //  k_tail          one CTA runs the whole V-cycle below a small level (smoothing,
 //                  residual + full weighting, coarsest dense inverse, prolongation), with
 //                  __syncthreads between the phases instead of kernel launches.
+#include <mutex>
+
 #include "mg_common.cuh"
 #include "mg_fused.h"
 #include "mg_launch.h"
+#include "mg_tile.h"
 
 namespace mg {
 
@@ -262,41 +265,65 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(TailArgs<T> a, const int*
 }
 
 // ------------------------------------------------------------------ launchers
-template <typename T>
-struct FusedCfg;
-template <>
-struct FusedCfg<double> {
-  static constexpr int TX = 32, TY = 32, NS = 1;
-};
-template <>
-struct FusedCfg<float> {
-  static constexpr int TX = 64, TY = 24, NS = 2;
-};
+// Variants (owned tile, sweeps per launch); the staged region of a variant is
+// (tx + 8 ns) x (ty + 8 ns) nodes of seven arrays, at most 179 KB (FP64 64 x 24, two sweeps).
+constexpr SmoothVariant kFusedTable[] = {{32, 32, 1}, {64, 16, 1}, {64, 24, 1},
+                                         {32, 32, 2}, {64, 16, 2}, {64, 24, 2}};
+constexpr int kFusedCount = (int)(sizeof(kFusedTable) / sizeof(kFusedTable[0]));
 
 template <typename T>
-int fused_sweeps() {
-  return FusedCfg<T>::NS;
+static int fused_default() {
+  return sizeof(T) == 8 ? 0 : 5;  // FP64 32 x 32, one sweep; FP32 64 x 24, two sweeps
+}
+
+template <typename T>
+int fused_variants() {
+  return kFusedCount;
+}
+
+template <typename T>
+SmoothVariant fused_variant(int v) {
+  return kFusedTable[(v < 0 || v >= kFusedCount) ? fused_default<T>() : v];
+}
+
+template <typename T>
+int fused_sweeps(int v) {
+  return fused_variant<T>(v).ns;
+}
+
+template <typename T, int TX, int TY, int NS>
+static cudaError_t fused_impl(const Op<T>& A, const T* xin, T* xout, const T* b, int rev, const T* eH,
+                              int pitch_c, const int* skip, cudaStream_t s) {
+  constexpr int H = 4 * NS;
+  constexpr size_t sm = (size_t)7 * (TX + 2 * H) * (TY + 2 * H) * sizeof(T);
+  static_assert(sm <= 227 * 1024, "staged region must fit in shared memory");
+  auto kern = k_smooth_fused<T, TX, TY, NS>;
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [&] {
+    attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  });
+  if (attr != cudaSuccess) return attr;
+  const Lvl<T> L = lvl_of(A);
+  const int nyc = (A.ny - 1) / 2 + 1;
+  dim3 grid((L.nx + TX - 1) / TX, (L.nyr + TY - 1) / TY);
+  kern<<<grid, kFusedThreads, sm, s>>>(L, xin, xout, b, rev, eH, pitch_c,
+                                      eH ? rows_stored(nyc, A.periodic) : 0, skip);
+  return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_smooth_fused(const Op<T>& A, const T* xin, T* xout, const T* b, int rev,
-                                const T* eH, int pitch_c, const int* skip, cudaStream_t s) {
-  using C = FusedCfg<T>;
-  constexpr int H = 4 * C::NS;
-  const size_t sm = (size_t)7 * (C::TX + 2 * H) * (C::TY + 2 * H) * sizeof(T);
-  auto kern = k_smooth_fused<T, C::TX, C::TY, C::NS>;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    attr = true;
+                                const T* eH, int pitch_c, const int* skip, cudaStream_t s, int v) {
+  if (v < 0 || v >= kFusedCount) v = fused_default<T>();
+  switch (v) {
+    case 0: return fused_impl<T, 32, 32, 1>(A, xin, xout, b, rev, eH, pitch_c, skip, s);
+    case 1: return fused_impl<T, 64, 16, 1>(A, xin, xout, b, rev, eH, pitch_c, skip, s);
+    case 2: return fused_impl<T, 64, 24, 1>(A, xin, xout, b, rev, eH, pitch_c, skip, s);
+    case 3: return fused_impl<T, 32, 32, 2>(A, xin, xout, b, rev, eH, pitch_c, skip, s);
+    case 4: return fused_impl<T, 64, 16, 2>(A, xin, xout, b, rev, eH, pitch_c, skip, s);
+    default: return fused_impl<T, 64, 24, 2>(A, xin, xout, b, rev, eH, pitch_c, skip, s);
   }
-  const Lvl<T> L = lvl_of(A);
-  const int nyc = (A.ny - 1) / 2 + 1;
-  dim3 grid((L.nx + C::TX - 1) / C::TX, (L.nyr + C::TY - 1) / C::TY);
-  kern<<<grid, kFusedThreads, sm, s>>>(L, xin, xout, b, rev, eH, pitch_c,
-                                      eH ? rows_stored(nyc, A.periodic) : 0, skip);
-  return cudaGetLastError();
 }
 
 template <typename T>
@@ -321,13 +348,17 @@ size_t tail_bytes(const TailArgs<T>& a) {
 template size_t tail_bytes<double>(const TailArgs<double>&);
 template size_t tail_bytes<float>(const TailArgs<float>&);
 
-template int fused_sweeps<double>();
-template int fused_sweeps<float>();
+template int fused_sweeps<double>(int);
+template int fused_sweeps<float>(int);
+template int fused_variants<double>();
+template int fused_variants<float>();
+template SmoothVariant fused_variant<double>(int);
+template SmoothVariant fused_variant<float>(int);
 template cudaError_t launch_smooth_fused<double>(const Op<double>&, const double*, double*,
                                                  const double*, int, const double*, int, const int*,
-                                                 cudaStream_t);
+                                                 cudaStream_t, int);
 template cudaError_t launch_smooth_fused<float>(const Op<float>&, const float*, float*, const float*,
-                                                int, const float*, int, const int*, cudaStream_t);
+                                                int, const float*, int, const int*, cudaStream_t, int);
 template cudaError_t launch_tail<double>(const TailArgs<double>&, const int*, cudaStream_t);
 template cudaError_t launch_tail<float>(const TailArgs<float>&, const int*, cudaStream_t);
 

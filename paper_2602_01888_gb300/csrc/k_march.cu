@@ -20,7 +20,8 @@
 // columns hold exactly the result of NS sequential sweeps.
 //
 // Geometry per precision: FP32 two sweeps a pass on 256-column strips, FP64 one sweep a
-// pass on 128-column strips (MarchGeom below).
+// pass on 128-column strips by default; the other depth of each is a variant the autotuner
+// may pick (MarchGeom below).
 //
 // The threads of a CTA have one role each, in whole warps: compute threads run the
 // phases; loader threads request rows D steps ahead with asynchronous 16-byte copies into
@@ -29,11 +30,13 @@
 // writer threads copy finished owned rows out.  The iterate is read from xin and written
 // to xout (halos of neighbouring CTAs overlap).
 #include <cstdint>
+#include <mutex>
 #include <type_traits>
 
 #include "mg_common.cuh"
 #include "mg_launch.h"
 #include "mg_march.h"
+#include "mg_tile.h"
 
 namespace mg {
 
@@ -58,6 +61,24 @@ template <>
 struct MarchGeom<double, 1> {
   static constexpr int C = 128, HX = 4, W = C - 2 * HX, HY = 4, R = 12, D = 4, NPT = 1;
   static constexpr int THREADS = 640, CTAS_PER_SM = 1;
+};
+
+// The other depth of each precision, for the autotuner.  FP32 one sweep a pass: the x halo
+// stays 8 columns (the coarse-correction copies need strips that start on a multiple of 8
+// fine columns); 768 threads (256 compute, 448 loaders, 60 writers).  FP64 two sweeps a
+// pass: 8-column halo, 112 owned columns, a 20-row ring (184 KB); 768 threads (256
+// compute, 448 loaders, 56 writers).  Three or more sweeps a pass would need a ring of at
+// least 27 rows, which does not fit next to the staging rows in FP32 (256 columns) and
+// leaves FP64 strips with more halo than owned columns.
+template <>
+struct MarchGeom<float, 1> {
+  static constexpr int C = 256, HX = 8, W = C - 2 * HX, HY = 4, R = 12, D = 6, NPT = 1;
+  static constexpr int THREADS = 768, CTAS_PER_SM = 1;
+};
+template <>
+struct MarchGeom<double, 2> {
+  static constexpr int C = 128, HX = 8, W = C - 2 * HX, HY = 8, R = 20, D = 4, NPT = 1;
+  static constexpr int THREADS = 768, CTAS_PER_SM = 1;
 };
 
 template <typename T, int NS>
@@ -404,33 +425,42 @@ __global__ void __launch_bounds__(MarchGeom<T, NS>::THREADS, MarchGeom<T, NS>::C
   }
 }
 
+// Variants: sweeps per pass; variant 0 is each precision's default (FP32 two, FP64 one).
 template <typename T>
-struct MarchCfg;
-template <>
-struct MarchCfg<float> {
-  static constexpr int NS = 2;
-};
-template <>
-struct MarchCfg<double> {
-  static constexpr int NS = 1;
-};
-
-template <typename T>
-int march_sweeps() {
-  return MarchCfg<T>::NS;
+int march_variants() {
+  return 2;
 }
 
 template <typename T>
-int march_strip_width() {
-  return MarchGeom<T, MarchCfg<T>::NS>::W;
+static int march_ns(int v) {
+  const int d = sizeof(T) == 8 ? 1 : 2;
+  return v == 1 ? 3 - d : d;
 }
 
 template <typename T>
-cudaError_t launch_smooth_march(const Op<T>& A, const T* xin, T* xout, const T* b, int rev,
-                                const T* eH, int pitch_c, const int* skip, cudaStream_t s) {
-  constexpr int NS = MarchCfg<T>::NS;
+SmoothVariant march_variant(int v) {
+  const int ns = march_ns<T>(v);
+  return {ns == 1 ? (sizeof(T) == 8 ? MarchGeom<double, 1>::W : MarchGeom<float, 1>::W)
+                  : (sizeof(T) == 8 ? MarchGeom<double, 2>::W : MarchGeom<float, 2>::W),
+          0, ns};
+}
+
+template <typename T>
+int march_sweeps(int v) {
+  return march_ns<T>(v);
+}
+
+template <typename T>
+int march_strip_width(int v) {
+  return march_variant<T>(v).tx;
+}
+
+template <typename T, int NS>
+static cudaError_t march_impl(const Op<T>& A, const T* xin, T* xout, const T* b, int rev, const T* eH,
+                              int pitch_c, const int* skip, cudaStream_t s) {
   using G = MarchGeom<T, NS>;
   using Y = MarchLayout<T, NS>;
+  static_assert(Y::smem_bytes <= 227 * 1024, "ring and staging rows must fit in shared memory");
   if (A.pitch % Y::VEC != 0) return cudaErrorInvalidValue;
   if (((uintptr_t)xin | (uintptr_t)xout | (uintptr_t)b | (uintptr_t)A.cE | (uintptr_t)A.cN |
        (uintptr_t)A.cNE | (uintptr_t)A.cNW | (uintptr_t)A.dinv | (uintptr_t)eH) % 16 != 0)
@@ -438,13 +468,12 @@ cudaError_t launch_smooth_march(const Op<T>& A, const T* xin, T* xout, const T* 
   if (eH && pitch_c % Y::VEC != 0) return cudaErrorInvalidValue;
   if (xin == xout) return cudaErrorInvalidValue;
   auto kern = k_smooth_march<T, NS>;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)Y::smem_bytes);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [&] {
+    attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Y::smem_bytes);
+  });
+  if (attr != cudaSuccess) return attr;
   static int nsm = 0;
   if (nsm == 0) {
     int dev = 0;
@@ -478,15 +507,26 @@ cudaError_t launch_smooth_march(const Op<T>& A, const T* xin, T* xout, const T* 
   return cudaGetLastError();
 }
 
-template int march_sweeps<float>();
-template int march_sweeps<double>();
-template int march_strip_width<float>();
-template int march_strip_width<double>();
+template <typename T>
+cudaError_t launch_smooth_march(const Op<T>& A, const T* xin, T* xout, const T* b, int rev,
+                                const T* eH, int pitch_c, const int* skip, cudaStream_t s, int v) {
+  if (march_ns<T>(v) == 1) return march_impl<T, 1>(A, xin, xout, b, rev, eH, pitch_c, skip, s);
+  return march_impl<T, 2>(A, xin, xout, b, rev, eH, pitch_c, skip, s);
+}
+
+template int march_sweeps<float>(int);
+template int march_sweeps<double>(int);
+template int march_strip_width<float>(int);
+template int march_strip_width<double>(int);
+template int march_variants<float>();
+template int march_variants<double>();
+template SmoothVariant march_variant<float>(int);
+template SmoothVariant march_variant<double>(int);
 template cudaError_t launch_smooth_march<float>(const Op<float>&, const float*, float*,
                                                 const float*, int, const float*, int, const int*,
-                                                cudaStream_t);
+                                                cudaStream_t, int);
 template cudaError_t launch_smooth_march<double>(const Op<double>&, const double*, double*,
                                                  const double*, int, const double*, int, const int*,
-                                                 cudaStream_t);
+                                                 cudaStream_t, int);
 
 }  // namespace mg

@@ -15,11 +15,13 @@
 #include <cudaTypedefs.h>
 
 #include <cstdint>
+#include <mutex>
 
 #include "mg_common.cuh"
 #include "mg_fused.h"
 #include "mg_launch.h"
 #include "mg_pipe.h"
+#include "mg_tile.h"
 
 namespace mg {
 
@@ -211,20 +213,26 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
 }
 
 // ------------------------------------------------------------------ launcher
-template <typename T>
-struct PipeCfg;
-template <>
-struct PipeCfg<float> {
-  static constexpr int TX = 64, TY = 24, NS = 2;
-};
-template <>
-struct PipeCfg<double> {
-  static constexpr int TX = 32, TY = 32, NS = 1;
-};
+// Variants (owned tile, sweeps per launch).  Two stages of (tx + 8 ns) x (ty + 8 ns) nodes of
+// seven arrays must fit in shared memory; on a periodic level the boxes are copied in chunks
+// of 32 bytes' worth of rows, which the halo must be a multiple of (FP32: two sweeps).
+constexpr SmoothVariant kPipeTableF64[] = {{32, 32, 1}, {64, 16, 1}};
+constexpr SmoothVariant kPipeTableF32[] = {{64, 24, 2}, {32, 32, 2}, {64, 16, 2}};
 
 template <typename T>
-int pipe_sweeps() {
-  return PipeCfg<T>::NS;
+int pipe_variants() {
+  return sizeof(T) == 8 ? 2 : 3;
+}
+
+template <typename T>
+SmoothVariant pipe_variant(int v) {
+  if (v < 0 || v >= pipe_variants<T>()) v = 0;
+  return sizeof(T) == 8 ? kPipeTableF64[v] : kPipeTableF32[v];
+}
+
+template <typename T>
+int pipe_sweeps(int v) {
+  return pipe_variant<T>(v).ns;
 }
 
 static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -255,19 +263,18 @@ static bool make_map(CUtensorMap* m, const T* base, int nx, int nyr, int pitch, 
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <typename T>
-cudaError_t launch_smooth_pipe(const Op<T>& A, const T* xin, T* xout, const T* b, int rev,
-                               const T* eH, int pitch_c, const int* skip, int* err,
-                               cudaStream_t s) {
-  using C = PipeCfg<T>;
-  using G = PipeGeom<T, C::TX, C::TY, C::NS>;
+template <typename T, int TX, int TY, int NS>
+static cudaError_t pipe_impl(const Op<T>& A, const T* xin, T* xout, const T* b, int rev, const T* eH,
+                             int pitch_c, const int* skip, int* err, cudaStream_t s) {
+  using G = PipeGeom<T, TX, TY, NS>;
   constexpr int CH = 32 / (int)sizeof(T);  // chunk rows on periodic levels (8 FP32, 4 FP64)
+  static_assert(2 * G::stage_bytes <= 227 * 1024, "two stages must fit in shared memory");
   const int nyr = rows_stored(A.ny, A.periodic);
   if (A.pitch % (16 / (int)sizeof(T)) != 0) return cudaErrorInvalidValue;  // 16-byte row strides
   if (((uintptr_t)xin | (uintptr_t)b | (uintptr_t)A.cE | (uintptr_t)A.cN | (uintptr_t)A.cNE |
        (uintptr_t)A.cNW | (uintptr_t)A.dinv) % 16 != 0)
     return cudaErrorInvalidValue;
-  static_assert(C::TY % CH == 0 && G::H % CH == 0 && G::RY % CH == 0, "chunks must tile the box");
+  static_assert(TY % CH == 0 && G::H % CH == 0 && G::RY % CH == 0, "chunks must tile the box");
   const int chunk = A.periodic ? CH : 0;
   if (A.periodic && nyr % CH != 0) return cudaErrorInvalidValue;
   PipeMaps maps;
@@ -275,14 +282,14 @@ cudaError_t launch_smooth_pipe(const Op<T>& A, const T* xin, T* xout, const T* b
   for (int a = 0; a < 7; ++a)
     if (!make_map<T>(&maps.m[a], arr[a], A.nx, nyr, A.pitch, G::RX, chunk ? CH : G::RY))
       return cudaErrorInvalidValue;
-  auto kern = k_smooth_pipe<T, C::TX, C::TY, C::NS>;
+  auto kern = k_smooth_pipe<T, TX, TY, NS>;
   const size_t sm = 2 * G::stage_bytes;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [&] {
+    attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  });
+  if (attr != cudaSuccess) return attr;
   static int nsm = 0;
   if (nsm == 0) {
     int dev = 0;
@@ -290,7 +297,7 @@ cudaError_t launch_smooth_pipe(const Op<T>& A, const T* xin, T* xout, const T* b
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   }
   const Lvl<T> L = lvl_of(A);
-  const int tx = (L.nx + C::TX - 1) / C::TX, ty = (L.nyr + C::TY - 1) / C::TY;
+  const int tx = (L.nx + TX - 1) / TX, ty = (L.nyr + TY - 1) / TY;
   const int ntiles = tx * ty;
   const int grid = ntiles < nsm ? ntiles : nsm;
   const int nyc = (A.ny - 1) / 2 + 1;
@@ -300,13 +307,32 @@ cudaError_t launch_smooth_pipe(const Op<T>& A, const T* xin, T* xout, const T* b
   return cudaGetLastError();
 }
 
-template int pipe_sweeps<float>();
-template int pipe_sweeps<double>();
+template <typename T>
+cudaError_t launch_smooth_pipe(const Op<T>& A, const T* xin, T* xout, const T* b, int rev,
+                               const T* eH, int pitch_c, const int* skip, int* err,
+                               cudaStream_t s, int v) {
+  if (v < 0 || v >= pipe_variants<T>()) v = 0;
+  if constexpr (sizeof(T) == 8) {
+    if (v == 1) return pipe_impl<T, 64, 16, 1>(A, xin, xout, b, rev, eH, pitch_c, skip, err, s);
+    return pipe_impl<T, 32, 32, 1>(A, xin, xout, b, rev, eH, pitch_c, skip, err, s);
+  } else {
+    if (v == 1) return pipe_impl<T, 32, 32, 2>(A, xin, xout, b, rev, eH, pitch_c, skip, err, s);
+    if (v == 2) return pipe_impl<T, 64, 16, 2>(A, xin, xout, b, rev, eH, pitch_c, skip, err, s);
+    return pipe_impl<T, 64, 24, 2>(A, xin, xout, b, rev, eH, pitch_c, skip, err, s);
+  }
+}
+
+template int pipe_sweeps<float>(int);
+template int pipe_sweeps<double>(int);
+template int pipe_variants<float>();
+template int pipe_variants<double>();
+template SmoothVariant pipe_variant<float>(int);
+template SmoothVariant pipe_variant<double>(int);
 template cudaError_t launch_smooth_pipe<float>(const Op<float>&, const float*, float*, const float*,
                                                int, const float*, int, const int*, int*,
-                                               cudaStream_t);
+                                               cudaStream_t, int);
 template cudaError_t launch_smooth_pipe<double>(const Op<double>&, const double*, double*,
                                                 const double*, int, const double*, int, const int*,
-                                                int*, cudaStream_t);
+                                                int*, cudaStream_t, int);
 
 }  // namespace mg

@@ -30,15 +30,16 @@ struct TailArgs {
   TailLevel<T> lv[kMaxTail];
 };
 
-// Sweeps fused per launch of k_smooth_fused for this precision.
+// Sweeps fused per launch of k_smooth_fused for this precision and variant (mg_tile.h;
+// v < 0: the default variant).
 template <typename T>
-int fused_sweeps();
+int fused_sweeps(int v = -1);
 
 // xout = NS Gauss-Seidel sweeps applied to (xin + P eH when eH != nullptr); rev = colour
-// order reversed.  xin and xout must be different arrays.
+// order reversed.  xin and xout must be different arrays.  v: tile variant (mg_tile.h).
 template <typename T>
 cudaError_t launch_smooth_fused(const Op<T>& A, const T* xin, T* xout, const T* b, int rev,
-                                const T* eH, int pitch_c, const int* skip, cudaStream_t s);
+                                const T* eH, int pitch_c, const int* skip, cudaStream_t s, int v = -1);
 
 template <typename T>
 cudaError_t launch_tail(const TailArgs<T>& a, const int* skip, cudaStream_t s);

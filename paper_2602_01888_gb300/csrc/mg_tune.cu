@@ -2,11 +2,12 @@
 //
 // For square levels of a range of sides it builds a sine-warp operator with the library's
 // own set-up kernels and times nu = 2 Gauss-Seidel sweeps with every family that can run
-// there (per-colour kernels, fused tiles, pipelined tiles, row marching), with
-// CUDA events on the context's stream after a warm-up.  The fastest family per size becomes
-// the context's policy (SmoothPolicy), used by every V-cycle captured afterwards.  All the
-// families perform the same operations per node in the same order, so the policy changes
-// timings, not results.
+// there (per-colour kernels, fused tiles, pipelined tiles, row marching) in every variant
+// of it (tile shape and sweeps per launch for the tile kernels, sweeps per pass for row
+// marching; mg_tile.h), with CUDA events on the context's stream after a warm-up.  The
+// fastest (family, variant) per size becomes the context's policy (SmoothPolicy), used by
+// every V-cycle captured afterwards.  All of them perform the same operations per node in
+// the same order, so the policy changes timings, not results.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -19,48 +20,64 @@
 #include "mg_launch.h"
 #include "mg_march.h"
 #include "mg_pipe.h"
+#include "mg_tile.h"
 #include "mg_vcycle.h"
 
 namespace mg {
 
 static int pitch32(int n) { return (n + 31) & ~31; }
 
-// Time one family (ms per 2 sweeps); < 0 when it cannot run at this size.
+// Variants of a family for precision T (the per-colour kernels have one).
 template <typename T>
-static float time_family(mg_ctx* ctx, int kind, const Op<T>& A, T* x, T* x2, const T* b, int* err) {
+static int variants_of(int kind) {
+  switch (kind) {
+    case SK_FUSED: return fused_variants<T>();
+    case SK_PIPE: return pipe_variants<T>();
+    case SK_MARCH: return march_variants<T>();
+    default: return 1;
+  }
+}
+
+template <typename T>
+static SmoothVariant variant_of(int kind, int v) {
+  switch (kind) {
+    case SK_FUSED: return fused_variant<T>(v);
+    case SK_PIPE: return pipe_variant<T>(v);
+    case SK_MARCH: return march_variant<T>(v);
+    default: return {0, 0, 1};
+  }
+}
+
+// Time one family in one variant (ms per 2 sweeps); < 0 when it cannot run at this size.
+template <typename T>
+static float time_family(mg_ctx* ctx, int kind, int v, const Op<T>& A, T* x, T* x2, const T* b, int* err) {
   cudaStream_t s = ctx->stream;
   const int nyr = A.ny;
+  const int ns = variant_of<T>(kind, v).ns;
   auto once = [&]() -> cudaError_t {
+    cudaError_t e = cudaSuccess;
     switch (kind) {
       case SK_COLOUR:
         return launch_smooth<T>(A, x, b, 2, 0, nullptr, s);
-      case SK_FUSED: {
-        const int ns = fused_sweeps<T>();
-        cudaError_t e = cudaSuccess;
-        for (int k = 0; k < 2 / ns && !e; ++k) e = launch_smooth_fused<T>(A, k & 1 ? x2 : x, k & 1 ? x : x2, b, 0, nullptr, 0, nullptr, s);
-        return e;
-      }
-      case SK_PIPE: {
-        const int ns = pipe_sweeps<T>();
-        cudaError_t e = cudaSuccess;
+      case SK_FUSED:
         for (int k = 0; k < 2 / ns && !e; ++k)
-          e = launch_smooth_pipe<T>(A, k & 1 ? x2 : x, k & 1 ? x : x2, b, 0, nullptr, 0, nullptr, err, s);
+          e = launch_smooth_fused<T>(A, k & 1 ? x2 : x, k & 1 ? x : x2, b, 0, nullptr, 0, nullptr, s, v);
         return e;
-      }
-      case SK_MARCH: {
-        const int ns = march_sweeps<T>();
-        cudaError_t e = cudaSuccess;
+      case SK_PIPE:
         for (int k = 0; k < 2 / ns && !e; ++k)
-          e = launch_smooth_march<T>(A, k & 1 ? x2 : x, k & 1 ? x : x2, b, 0, nullptr, 0, nullptr, s);
+          e = launch_smooth_pipe<T>(A, k & 1 ? x2 : x, k & 1 ? x : x2, b, 0, nullptr, 0, nullptr, err, s, v);
         return e;
-      }
+      case SK_MARCH:
+        for (int k = 0; k < 2 / ns && !e; ++k)
+          e = launch_smooth_march<T>(A, k & 1 ? x2 : x, k & 1 ? x : x2, b, 0, nullptr, 0, nullptr, s, v);
+        return e;
     }
     return cudaErrorInvalidValue;
   };
   // the same applicability rules as the cycle
-  if (kind == SK_FUSED && 2 % fused_sweeps<T>()) return -1.f;
-  if (kind == SK_PIPE && (2 % pipe_sweeps<T>() || nyr < 64 || A.nx < 160)) return -1.f;
-  if (kind == SK_MARCH && (2 % march_sweeps<T>() || nyr < 128)) return -1.f;
+  if (kind != SK_COLOUR && 2 % ns) return -1.f;
+  if (kind == SK_PIPE && (nyr < 64 || A.nx < 160)) return -1.f;
+  if (kind == SK_MARCH && nyr < 128) return -1.f;
   for (int w = 0; w < 2; ++w)
     if (once() != cudaSuccess) return -1.f;
   cudaEvent_t e0, e1;
@@ -81,7 +98,7 @@ static float time_family(mg_ctx* ctx, int kind, const Op<T>& A, T* x, T* x2, con
 }
 
 template <typename T>
-static mg_status tune_size(mg_ctx* ctx, int n, float ms[4], int* best) {
+static mg_status tune_size(mg_ctx* ctx, int n, float ms[4], int* best, int* best_var) {
   cudaStream_t s = ctx->stream;
   const int pt = pitch32(n);
   const size_t np = (size_t)pt * n;
@@ -120,12 +137,18 @@ static mg_status tune_size(mg_ctx* ctx, int n, float ms[4], int* best) {
   }
   const int kinds[4] = {SK_COLOUR, SK_FUSED, SK_PIPE, SK_MARCH};
   *best = SK_DEFAULT;
+  *best_var = -1;
   float bt = 1e30f;
   for (int k = 0; k < 4; ++k) {
-    ms[k] = time_family<T>(ctx, kinds[k], A, x, x2, b, flags + 2);
-    if (ms[k] > 0.f && ms[k] < bt) {
-      bt = ms[k];
-      *best = kinds[k];
+    ms[k] = -1.f;  // the family's fastest variant
+    for (int v = 0; v < variants_of<T>(kinds[k]); ++v) {
+      const float t = time_family<T>(ctx, kinds[k], v, A, x, x2, b, flags + 2);
+      if (t > 0.f && (ms[k] < 0.f || t < ms[k])) ms[k] = t;
+      if (t > 0.f && t < bt) {
+        bt = t;
+        *best = kinds[k];
+        *best_var = v;
+      }
     }
   }
   cudaGetLastError();
@@ -145,11 +168,13 @@ extern "C" mg_status mg_autotune(mg_ctx* ctx, int max_side, mg_tune_report* repo
   for (int prec = 0; prec < 2; ++prec) {
     for (int n = 33; n <= max_side && pol[prec].n < 16; n = 2 * n - 1) {
       float ms[4] = {-1.f, -1.f, -1.f, -1.f};
-      int best = SK_DEFAULT;
-      const mg_status st = prec ? tune_size<float>(ctx, n, ms, &best) : tune_size<double>(ctx, n, ms, &best);
+      int best = SK_DEFAULT, var = -1;
+      const mg_status st =
+          prec ? tune_size<float>(ctx, n, ms, &best, &var) : tune_size<double>(ctx, n, ms, &best, &var);
       if (st) return st;
       pol[prec].side[pol[prec].n] = n;
       pol[prec].kind[pol[prec].n] = best;
+      pol[prec].var[pol[prec].n] = var;
       pol[prec].n++;
       if (report && report->count < MG_TUNE_MAX) {
         mg_tune_entry& e = report->entry[report->count++];
@@ -157,6 +182,10 @@ extern "C" mg_status mg_autotune(mg_ctx* ctx, int max_side, mg_tune_report* repo
         e.side = n;
         for (int k = 0; k < 4; ++k) e.ms[k] = ms[k];
         e.choice = best;
+        const SmoothVariant sv = prec ? variant_of<float>(best, var) : variant_of<double>(best, var);
+        e.tile_x = sv.tx;
+        e.tile_y = sv.ty;
+        e.sweeps_per_launch = sv.ns;
       }
     }
   }

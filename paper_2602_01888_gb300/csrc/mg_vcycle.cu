@@ -18,6 +18,7 @@
 #include "mg_pipe.h"
 #include "mg_line.h"
 #include "mg_march.h"
+#include "mg_tile.h"
 #include "mg_vcycle.h"
 
 namespace mg {
@@ -65,7 +66,8 @@ inline long long march_nodes() {
   return v;
 }
 
-int SmoothPolicy::lookup(long long nodes) const {
+int SmoothPolicy::lookup(long long nodes, int* var_out) const {
+  if (var_out) *var_out = -1;
   if (n <= 0 || nodes <= 0) return SK_DEFAULT;
   int best = 0;
   double bd = 1e300;
@@ -76,6 +78,7 @@ int SmoothPolicy::lookup(long long nodes) const {
       best = k;
     }
   }
+  if (var_out) *var_out = var[best];
   return kind[best];
 }
 
@@ -148,36 +151,46 @@ cudaError_t emit_vcycle(const VLevels<T>& V, int smoother, int nu1, int nu2, dou
       break;
     }
   }
-  const int NS = fused_sweeps<T>();
   const long long cthr = colour_nodes<T>();
   auto smooth = [&](int l, int sweeps, int rev, const T* eH) -> cudaError_t {
     cudaError_t err;
     const long long nodes = (long long)V.A[l].nx * rows_stored(V.A[l].ny, V.A[l].periodic);
     const int nyr = rows_stored(V.A[l].ny, V.A[l].periodic);
     const int pc = eH ? V.A[l + 1].pitch : 0;
-    // which families can run this level with this many sweeps
-    const bool can_march = sweeps % march_sweeps<T>() == 0 && sweeps > 0 &&
-                           V.A[l].pitch % (16 / (int)sizeof(T)) == 0 && nyr >= 128;
-    const bool can_pipe = sweeps % pipe_sweeps<T>() == 0 && sweeps > 0 && nyr >= 64 && V.A[l].nx >= 160 &&
-                          V.A[l].pitch % (16 / (int)sizeof(T)) == 0 &&
-                          (!V.A[l].periodic || nyr % (32 / (int)sizeof(T)) == 0);
-    const bool can_fused = sweeps % NS == 0 && sweeps > 0;
-    // size-threshold rule
-    int kind;
-    if (nodes >= march_nodes() && can_march)
+    // which families (in a given variant) can run this level with this many sweeps
+    auto can = [&](int kind, int v) {
+      if (sweeps <= 0) return kind == SK_COLOUR;
+      switch (kind) {
+        case SK_MARCH:
+          return sweeps % march_sweeps<T>(v) == 0 && V.A[l].pitch % (16 / (int)sizeof(T)) == 0 && nyr >= 128;
+        case SK_PIPE:
+          return sweeps % pipe_sweeps<T>(v) == 0 && nyr >= 64 && V.A[l].nx >= 160 &&
+                 V.A[l].pitch % (16 / (int)sizeof(T)) == 0 &&
+                 (!V.A[l].periodic || nyr % (32 / (int)sizeof(T)) == 0);
+        case SK_FUSED:
+          return sweeps % fused_sweeps<T>(v) == 0;
+        default:
+          return kind == SK_COLOUR;
+      }
+    };
+    // size-threshold rule, default variants
+    int kind, var = -1;
+    if (nodes >= march_nodes() && can(SK_MARCH, -1))
       kind = SK_MARCH;
-    else if (sizeof(T) == 4 && nodes > cthr && can_pipe)
+    else if (sizeof(T) == 4 && nodes > cthr && can(SK_PIPE, -1))
       kind = SK_PIPE;
-    else if (sweeps % NS != 0 || nodes > cthr)
+    else if (!can(SK_FUSED, -1) || nodes > cthr)
       kind = SK_COLOUR;
     else
       kind = SK_FUSED;
     // measured choice, where it can run
     if (V.pol) {
-      const int k = V.pol->lookup(nodes);
-      if ((k == SK_MARCH && can_march) || (k == SK_PIPE && can_pipe) || (k == SK_FUSED && can_fused) ||
-          k == SK_COLOUR)
+      int v = -1;
+      const int k = V.pol->lookup(nodes, &v);
+      if (k != SK_DEFAULT && can(k, v)) {
         kind = k;
+        var = v;
+      }
     }
     auto swap_cur = [&]() {
       T* tmp = cur[l];
@@ -185,17 +198,18 @@ cudaError_t emit_vcycle(const VLevels<T>& V, int smoother, int nu1, int nu2, dou
       alt[l] = tmp;
     };
     if (kind == SK_MARCH) {
-      for (int k = 0; k < sweeps / march_sweeps<T>(); ++k) {
-        err = launch_smooth_march<T>(V.A[l], cur[l], alt[l], V.b[l], rev, k == 0 ? eH : nullptr, pc, skip, s);
+      for (int k = 0; k < sweeps / march_sweeps<T>(var); ++k) {
+        err = launch_smooth_march<T>(V.A[l], cur[l], alt[l], V.b[l], rev, k == 0 ? eH : nullptr, pc, skip, s,
+                                     var);
         if (err) return err;
         swap_cur();
       }
       return cudaSuccess;
     }
     if (kind == SK_PIPE) {
-      for (int k = 0; k < sweeps / pipe_sweeps<T>(); ++k) {
+      for (int k = 0; k < sweeps / pipe_sweeps<T>(var); ++k) {
         err = launch_smooth_pipe<T>(V.A[l], cur[l], alt[l], V.b[l], rev, k == 0 ? eH : nullptr, pc, skip,
-                                    V.err, s);
+                                    V.err, s, var);
         if (err) return err;
         swap_cur();
       }
@@ -205,8 +219,8 @@ cudaError_t emit_vcycle(const VLevels<T>& V, int smoother, int nu1, int nu2, dou
       if (eH && (err = launch_prolong_add(V.A[l], cur[l], eH, pc, skip, s))) return err;
       return launch_smooth(V.A[l], cur[l], V.b[l], sweeps, rev, skip, s);
     }
-    for (int k = 0; k < sweeps / NS; ++k) {
-      err = launch_smooth_fused(V.A[l], cur[l], alt[l], V.b[l], rev, k == 0 ? eH : nullptr, pc, skip, s);
+    for (int k = 0; k < sweeps / fused_sweeps<T>(var); ++k) {
+      err = launch_smooth_fused(V.A[l], cur[l], alt[l], V.b[l], rev, k == 0 ? eH : nullptr, pc, skip, s, var);
       if (err) return err;
       swap_cur();
     }
@@ -389,3 +403,56 @@ extern "C" int mgk_smooth_march_f64(const mgk_op_f64* A, const double* xin, doub
 
 extern "C" int mgk_march_sweeps(void) { return march_sweeps<float>(); }
 extern "C" int mgk_march_sweeps_f64(void) { return march_sweeps<double>(); }
+
+template <typename T>
+static int variant_count(int family) {
+  switch (family) {
+    case SK_FUSED: return fused_variants<T>();
+    case SK_PIPE: return pipe_variants<T>();
+    case SK_MARCH: return march_variants<T>();
+    default: return 0;
+  }
+}
+
+extern "C" int mgk_smooth_variant_info(int f32, int family, int variant, int* tile_x, int* tile_y,
+                                       int* sweeps) {
+  const int n = f32 ? variant_count<float>(family) : variant_count<double>(family);
+  if (variant < 0 || variant >= n) return 1;
+  SmoothVariant v{};
+  if (family == SK_FUSED) v = f32 ? fused_variant<float>(variant) : fused_variant<double>(variant);
+  if (family == SK_PIPE) v = f32 ? pipe_variant<float>(variant) : pipe_variant<double>(variant);
+  if (family == SK_MARCH) v = f32 ? march_variant<float>(variant) : march_variant<double>(variant);
+  if (tile_x) *tile_x = v.tx;
+  if (tile_y) *tile_y = v.ty;
+  if (sweeps) *sweeps = v.ns;
+  return 0;
+}
+
+template <typename T, typename OPK>
+static int variant_abi(const OPK* A, int family, int variant, const T* xin, T* xout, const T* b, int reverse,
+                       const T* eH, int pitch_c, int* err, void* stream) {
+  if (!A || A->nx < 3 || A->ny < 3 || A->pitch < A->nx || !xin || !xout || !b || xin == xout) return 1;
+  if (variant < 0 || variant >= variant_count<T>(family)) return 1;
+  if (A->periodic && (A->ny - 1) % 2) return 1;
+  if (eH && ((A->nx - 1) % 2 || (A->ny - 1) % 2 || pitch_c < (A->nx - 1) / 2 + 1)) return 1;
+  const Op<T> op = op_from(*A);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  if (family == SK_FUSED) e = launch_smooth_fused<T>(op, xin, xout, b, reverse, eH, pitch_c, nullptr, s, variant);
+  else if (family == SK_PIPE) e = launch_smooth_pipe<T>(op, xin, xout, b, reverse, eH, pitch_c, nullptr, err, s, variant);
+  else e = launch_smooth_march<T>(op, xin, xout, b, reverse, eH, pitch_c, nullptr, s, variant);
+  if (e == cudaErrorInvalidValue) return 1;
+  return e == cudaSuccess ? 0 : 4;
+}
+
+extern "C" int mgk_smooth_variant_f64(const mgk_op_f64* A, int family, int variant, const double* xin,
+                                      double* xout, const double* b, int reverse, const double* eH,
+                                      int pitch_c, int* err, void* stream) {
+  return variant_abi<double>(A, family, variant, xin, xout, b, reverse, eH, pitch_c, err, stream);
+}
+
+extern "C" int mgk_smooth_variant_f32(const mgk_op_f32* A, int family, int variant, const float* xin,
+                                      float* xout, const float* b, int reverse, const float* eH,
+                                      int pitch_c, int* err, void* stream) {
+  return variant_abi<float>(A, family, variant, xin, xout, b, reverse, eH, pitch_c, err, stream);
+}

@@ -10,18 +10,20 @@ namespace mg {
 constexpr int kMaxVLevels = 24;
 
 // Smoother family for a level: the per-colour kernels (four launches a sweep), the fused
-// tile kernel, the pipelined tile kernel, the row-marching kernel (FP32).
+// tile kernel, the pipelined tile kernel, the row-marching kernel.
 enum SmoothKind : int { SK_DEFAULT = 0, SK_COLOUR = 1, SK_FUSED = 2, SK_PIPE = 3, SK_MARCH = 4 };
 
-// Measured choice of smoother family by level size (filled by mg_autotune): entry k says
-// that square levels of side[k] smooth fastest with kind[k].  A level takes the choice of the
-// entry nearest to it in node count (log scale); kinds that cannot run on a level fall back
-// to the size-threshold rule.
+// Measured choice of smoother family and variant by level size (filled by mg_autotune):
+// entry k says that square levels of side[k] smooth fastest with kind[k], variant var[k] (tile
+// shape or sweeps per pass, mg_tile.h).  A level takes the choice of the entry nearest to it
+// in node count (log scale); kinds that cannot run on a level fall back to the size-threshold
+// rule.
 struct SmoothPolicy {
   int n = 0;
   int side[16] = {};
   int kind[16] = {};
-  int lookup(long long nodes) const;
+  int var[16] = {};
+  int lookup(long long nodes, int* var_out = nullptr) const;
 };
 
 // A hierarchy as seen by one cycle: level l operator, iterate x, right-hand side b and a

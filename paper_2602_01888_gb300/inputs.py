@@ -487,12 +487,10 @@ def snap_side(side: float) -> int:
     return best
 
 
-SERVE_RADII = (0.125, 0.1875, 0.25, 0.3125)
-
-
 def config5_stream(count: int = 20000, seed: int = 5, rate: float = 100.0,
-                   side_range=(129, 2049), radii: Sequence[float] | None = SERVE_RADII) -> list:
-    """Request stream: list of (arrival_time_s, side, radius, ratio, source_seed)."""
+                   side_range=(129, 2049), radii: Sequence[float] | None = None) -> list:
+    """Request stream: list of (arrival_time_s, side, radius, ratio, source_seed); the
+    inclusion radius is drawn U[0.1, 0.35] per request unless a catalogue `radii` is given."""
     rng = np.random.default_rng(seed)
     t = np.cumsum(rng.exponential(1.0 / rate, count))
     lo, hi = math.log(side_range[0]), math.log(side_range[1])

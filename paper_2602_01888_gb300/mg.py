@@ -83,7 +83,8 @@ class mg_request(C.Structure):
 
 
 class mg_tune_entry(C.Structure):
-    _fields_ = [("precision", C.c_int), ("side", C.c_int), ("ms", C.c_float * 4), ("choice", C.c_int)]
+    _fields_ = [("precision", C.c_int), ("side", C.c_int), ("ms", C.c_float * 4), ("choice", C.c_int),
+                ("tile_x", C.c_int), ("tile_y", C.c_int), ("sweeps_per_launch", C.c_int)]
 
 
 class mg_tune_report(C.Structure):
@@ -181,6 +182,12 @@ _SIGS = {
                               C.c_void_p, C.c_int, C.c_void_p], C.c_int),
     "mgk_march_sweeps": ([], C.c_int),
     "mgk_march_sweeps_f64": ([], C.c_int),
+    "mgk_smooth_variant_info": ([C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                 C.POINTER(C.c_int)], C.c_int),
+    "mgk_smooth_variant_f64": ([C.POINTER(mgk_op_f64), C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p], C.c_int),
+    "mgk_smooth_variant_f32": ([C.POINTER(mgk_op_f32), C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p], C.c_int),
     "mgk_line_factor_elems": ([C.c_int, C.c_int, C.c_int], C.c_size_t),
     "mgk_line_factor_f64": ([C.POINTER(mgk_op_f64), C.c_void_p, C.c_void_p], C.c_int),
     "mgk_line_factor_f32": ([C.POINTER(mgk_op_f32), C.c_void_p, C.c_void_p], C.c_int),
@@ -441,17 +448,21 @@ def mg_harmonic_grid(ctx: int, grid, fixed, xp, yp, xp_out, yp_out, rtol: float 
     return list(stats)
 
 
-def mg_autotune(ctx: int, max_side: int = 2049):
-    """Time the smoother families per level size and make the fastest the context's choice.
-    Returns [(precision, side, {family: ms}, chosen family)]."""
+def mg_autotune(ctx: int, max_side: int = 2049, variants: bool = False):
+    """Time the smoother families (every variant of each) per level size and make the fastest
+    the context's choice.  Returns [(precision, side, {family: best ms}, chosen family)], with
+    a fifth element {"tile": (tx, ty), "sweeps": ns} for the chosen variant if variants=True."""
     r = mg_tune_report()
     _check(lib().mg_autotune(ctx, max_side, C.byref(r)), "mg_autotune")
     out = []
     for k in range(r.count):
         e = r.entry[k]
         ms = {SMOOTHER_FAMILIES[f + 1]: float(e.ms[f]) for f in range(4) if e.ms[f] > 0}
-        out.append(("mixed" if e.precision == MG_PREC_MIXED else "fp64", e.side, ms,
-                    SMOOTHER_FAMILIES.get(e.choice, "default")))
+        row = ("mixed" if e.precision == MG_PREC_MIXED else "fp64", e.side, ms,
+               SMOOTHER_FAMILIES.get(e.choice, "default"))
+        if variants:
+            row = row + ({"tile": (e.tile_x, e.tile_y), "sweeps": e.sweeps_per_launch},)
+        out.append(row)
     return out
 
 
@@ -507,6 +518,17 @@ def _stream(stream=None) -> int:
         return stream
     import torch
     return torch.cuda.current_stream().cuda_stream
+
+
+def smooth_variants(f32: bool, family: int):
+    """[(variant, (tile_x, tile_y), sweeps)] of a smoother family (2 fused, 3 pipelined,
+    4 marching) in FP32 or FP64."""
+    out, v = [], 0
+    tx, ty, ns = C.c_int(), C.c_int(), C.c_int()
+    while lib().mgk_smooth_variant_info(int(f32), family, v, C.byref(tx), C.byref(ty), C.byref(ns)) == 0:
+        out.append((v, (tx.value, ty.value), ns.value))
+        v += 1
+    return out
 
 
 def mgk(name: str, *args):

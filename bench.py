@@ -555,7 +555,7 @@ def _measure_variant(mg, torch, g, st, x, x2, b, f32, s, reps, family, shape):
     per_launch_s = e0.elapsed_time(e1) * 1e-3 / reps
     T = "float" if f32 else "double"
     if family == "marching":
-        kern = f"k_smooth_march<{T},{ns}>"
+        kern = f"k_smooth_march<{T}> w{tile[0]}/{ns}"  # owned strip columns / sweeps per pass
     else:
         kern = f"k_smooth_{'pipe' if family == 'pipelined' else 'fused'}<{T},{tile[0]},{tile[1]},{ns}>"
     note = f"the autotuner's choice for this level size ({family}), {ns} sweep(s) per launch"

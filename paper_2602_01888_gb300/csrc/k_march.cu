@@ -40,56 +40,82 @@
 
 namespace mg {
 
-template <typename T, int NS>
+template <typename T, int CFG>
 struct MarchGeom;
 
-// FP32: 256 loaded columns (128 per parity).  1024 threads in three roles: 512 compute
-// threads (4 active phases x 128 nodes), 448 loaders (one 16-byte chunk of each of the 7
-// arrays' rows) and 64 writers (60 of them copy the owned 240 columns of a finished row).
+// Geometries, by precision and configuration number (FP32: configuration 0 is the default;
+// FP64: configuration 3, see f64_cfg).  C loaded columns (C/2 per parity), HX halo columns and HY = 4 NS halo rows each
+// side, R ring rows, D rows in flight, LCH 16-byte chunks per loader thread and row.
+//
+// FP32 0: two sweeps a pass.  1024 threads: 512 compute (4 active phases x 128 nodes), 448
+// loaders (one chunk of each of the 7 arrays' rows each) and 64 writers (60 copy the owned 240
+// columns of a finished row).
 template <>
-struct MarchGeom<float, 2> {
-  static constexpr int C = 256, HX = 8, W = C - 2 * HX, HY = 8, R = 20, D = 6, NPT = 1;
+struct MarchGeom<float, 0> {
+  static constexpr int NS = 2, C = 256, HX = 8, W = C - 2 * HX, HY = 8, R = 20, D = 6, NPT = 1, LCH = 1;
   static constexpr int THREADS = 1024, CTAS_PER_SM = 1;
 };
-
-// FP64: 128 loaded columns (64 per parity), one sweep a pass.  FP64 smoothing is bound by
-// the FP64 pipe, not by HBM, once each array is read once per sweep, so a second sweep per
-// pass would only add redundant halo work.  640 threads: 128 compute (2 active phases x 64
-// nodes), 448 loaders (one 16-byte chunk of each of the 7 arrays' rows) and 64 writers (60
-// of them copy the owned 120 columns of a finished row).
-template <>
-struct MarchGeom<double, 1> {
-  static constexpr int C = 128, HX = 4, W = C - 2 * HX, HY = 4, R = 12, D = 4, NPT = 1;
-  static constexpr int THREADS = 640, CTAS_PER_SM = 1;
-};
-
-// The other depth of each precision, for the autotuner.  FP32 one sweep a pass: the x halo
-// stays 8 columns (the coarse-correction copies need strips that start on a multiple of 8
-// fine columns); 768 threads (256 compute, 448 loaders, 60 writers).  FP64 two sweeps a
-// pass: 8-column halo, 112 owned columns, a 20-row ring (184 KB); 768 threads (256
-// compute, 448 loaders, 56 writers).  Three or more sweeps a pass would need a ring of at
-// least 27 rows, which does not fit next to the staging rows in FP32 (256 columns) and
-// leaves FP64 strips with more halo than owned columns.
+// FP32 1: one sweep a pass; the x halo stays 8 columns (the coarse-correction copies need
+// strips that start on a multiple of 8 fine columns).  768 threads (256 compute, 448 loaders,
+// 60 writers).
 template <>
 struct MarchGeom<float, 1> {
-  static constexpr int C = 256, HX = 8, W = C - 2 * HX, HY = 4, R = 12, D = 6, NPT = 1;
+  static constexpr int NS = 1, C = 256, HX = 8, W = C - 2 * HX, HY = 4, R = 12, D = 6, NPT = 1, LCH = 1;
   static constexpr int THREADS = 768, CTAS_PER_SM = 1;
 };
+// FP32 2: two sweeps a pass on 128-column strips (112 owned), two CTAs resident per SM (98 KB
+// each) so that one CTA's per-row barrier overlaps the other's work.  512 threads: 256
+// compute, 224 loaders, 32 writers (28 copy the owned columns).
+template <>
+struct MarchGeom<float, 2> {
+  static constexpr int NS = 2, C = 128, HX = 8, W = C - 2 * HX, HY = 8, R = 20, D = 6, NPT = 1, LCH = 1;
+  static constexpr int THREADS = 512, CTAS_PER_SM = 2;
+};
+// FP64 0: one sweep a pass on 128-column strips.  FP64 smoothing is bound by the FP64 pipe,
+// not by HBM, once each array is read once per sweep, so extra sweeps per pass mostly add
+// redundant halo work.  640 threads: 128 compute (2 active phases x 64 nodes), 448 loaders
+// and 64 writers (60 copy the owned 120 columns).
+template <>
+struct MarchGeom<double, 0> {
+  static constexpr int NS = 1, C = 128, HX = 4, W = C - 2 * HX, HY = 4, R = 12, D = 4, NPT = 1, LCH = 1;
+  static constexpr int THREADS = 640, CTAS_PER_SM = 1;
+};
+// FP64 1: two sweeps a pass: 8-column halo, 112 owned columns, a 20-row ring (184 KB); 768
+// threads (256 compute, 448 loaders, 56 writers).
+template <>
+struct MarchGeom<double, 1> {
+  static constexpr int NS = 2, C = 128, HX = 8, W = C - 2 * HX, HY = 8, R = 20, D = 4, NPT = 1, LCH = 1;
+  static constexpr int THREADS = 768, CTAS_PER_SM = 1;
+};
+// FP64 2: one sweep a pass on 256-column strips: twice the compute warps of configuration 0
+// (two per scheduler, so one warp's dependent FMA chain hides behind the other's) and half
+// its redundant halo; an 11-row ring and 3 rows in flight fit 223 KB.  832 threads: 256
+// compute, 448 loaders (two chunks each), 128 writers (124 copy the owned 248 columns).
 template <>
 struct MarchGeom<double, 2> {
-  static constexpr int C = 128, HX = 8, W = C - 2 * HX, HY = 8, R = 20, D = 4, NPT = 1;
-  static constexpr int THREADS = 768, CTAS_PER_SM = 1;
+  static constexpr int NS = 1, C = 256, HX = 4, W = C - 2 * HX, HY = 4, R = 11, D = 3, NPT = 1, LCH = 2;
+  static constexpr int THREADS = 832, CTAS_PER_SM = 1;
+};
+// FP64 3: configuration 0's strips with two CTAs resident per SM (112 KB each): 416 threads
+// (128 compute, 224 loaders of two chunks, 64 writers), so one CTA's barrier overlaps the
+// other's compute.
+template <>
+struct MarchGeom<double, 3> {
+  static constexpr int NS = 1, C = 128, HX = 4, W = C - 2 * HX, HY = 4, R = 11, D = 3, NPT = 1, LCH = 2;
+  static constexpr int THREADS = 416, CTAS_PER_SM = 2;
 };
 
-template <typename T, int NS>
+template <typename T, int CFG>
 struct MarchLayout {
-  using G = MarchGeom<T, NS>;
+  using G = MarchGeom<T, CFG>;
+  static constexpr int NS = G::NS;
   static constexpr int M = G::C / 2;              // nodes per parity half
   static constexpr int VEC = 16 / sizeof(T);      // elements per 16-byte chunk
   static constexpr int CHUNKS = G::C / VEC;       // chunks per array row
+  static constexpr int LPA = CHUNKS / G::LCH;     // loader threads per array
   static constexpr int NPT = G::NPT;              // nodes per compute thread (m + k M/NPT)
   static constexpr int COMPUTE = 2 * NS * M / NPT;  // compute threads of the active phases
-  static constexpr int LOADERS = 7 * CHUNKS;      // threads moving one row of all arrays
+  static constexpr int LOADERS = 7 * LPA;         // threads moving one row of all arrays
   static constexpr int WRITERS = G::W / VEC;      // threads writing one owned row
   static constexpr int ROW = 7 * G::C;            // elements of one ring row
   static constexpr int RAWS = G::D + 1;           // staging slots: rows in flight + the landed one
@@ -101,12 +127,14 @@ struct MarchLayout {
       (size_t)G::R * ROW + (size_t)RAWS * ROW + (size_t)RAWS * ESTAGE;
   static constexpr size_t smem_bytes = smem_elems * sizeof(T);
   static_assert(COMPUTE + LOADERS + WRITERS <= G::THREADS, "one role per thread");
-  static_assert(COMPUTE % 32 == 0 && LOADERS % 32 == 0, "roles are whole warps");
+  static_assert(COMPUTE % 32 == 0 && LOADERS % 32 == 0 && LPA % 32 == 0, "roles are whole warps");
+  static_assert(CHUNKS % G::LCH == 0, "loader threads share a row's chunks evenly");
   static_assert(G::HY == 4 * NS && G::HX >= 4 * NS, "halo must cover the dependency cone");
   static_assert((G::HX * sizeof(T)) % 16 == 0, "strip start must stay 16-byte aligned");
   // rows touched at step s: s - 2 (4 NS - 1) - 2 (written out) .. s + 2 (de-interleaved)
   static_assert(G::R >= 2 * (4 * NS - 1) + 5, "ring must hold the live rows");
   static_assert(VEC % 2 == 0, "a 16-byte chunk holds whole even/odd column pairs");
+  static_assert(smem_bytes * G::CTAS_PER_SM <= 226 * 1024, "resident CTAs must fit in shared memory");
 };
 
 // 16-byte vector of T: a chunk of VEC consecutive columns.
@@ -182,14 +210,15 @@ struct MarchLane {
   bool col_ok;           // column inside the shrinking halo and an interior grid column
 };
 
-template <typename T, int NS>
-__global__ void __launch_bounds__(MarchGeom<T, NS>::THREADS, MarchGeom<T, NS>::CTAS_PER_SM)
+template <typename T, int CFG>
+__global__ void __launch_bounds__(MarchGeom<T, CFG>::THREADS, MarchGeom<T, CFG>::CTAS_PER_SM)
     k_smooth_march(Lvl<T> L, const T* __restrict__ xin, T* __restrict__ xout,
                    const T* __restrict__ b, int rev, const T* __restrict__ eH, int pitchc,
                    int nyrc, int S, const int* __restrict__ skip) {
   if (skip && *skip) return;
-  using G = MarchGeom<T, NS>;
-  using Y = MarchLayout<T, NS>;
+  using G = MarchGeom<T, CFG>;
+  using Y = MarchLayout<T, CFG>;
+  constexpr int NS = G::NS;
   constexpr int C = G::C, HX = G::HX, W = G::W, HY = G::HY, D = G::D, M = Y::M, VEC = Y::VEC;
   constexpr int R = G::R, ROW = Y::ROW, RAWS = Y::RAWS;
   constexpr int LAG = 2 * (4 * NS - 1);  // rows between phase 0 and the last phase
@@ -213,16 +242,26 @@ __global__ void __launch_bounds__(MarchGeom<T, NS>::THREADS, MarchGeom<T, NS>::C
   const int wt = t - Y::COMPUTE - Y::LOADERS;
   const bool writer = wt >= 0 && wt < Y::WRITERS;
 
-  // ---- loader role: array la, chunk lc (VEC consecutive columns) of every row
-  const int la = loader ? lt / Y::CHUNKS : 0, lc = loader ? lt % Y::CHUNKS : 0;
+  // ---- loader role: array la, chunks lcb + k LPA (k < LCH; VEC consecutive columns each) of
+  // every row
+  constexpr int LCH = G::LCH, LPA = Y::LPA;
+  const int la = loader ? lt / LPA : 0, lcb = loader ? lt % LPA : 0;
   const T* const lsrc = la == 0 ? xin : la == 1 ? b : la == 2 ? L.cE : la == 3 ? L.cN
                        : la == 4 ? L.cNE : la == 5 ? L.cNW : L.dinv;
-  const int lcol = xl0 + lc * VEC;  // first global column of the chunk
-  const bool lcol_ok = lcol >= 0 && lcol + VEC <= p;
-  const int raw_off = la * C + lc * VEC;        // chunk in a staging row
-  const int put_off = la * C + lc * (VEC / 2);  // first even column in a ring row
   const bool corr = loader && la == 0 && eH != nullptr;
-  const int I0b = xl0 >> 1;  // global coarse column of coarse staging column 0 (multiple of 4)
+  const int I0b = xl0 >> 1;  // global coarse column of coarse staging column 0 (multiple of VEC)
+  // per chunk of the thread: first global column, whether it lies in the array, offsets in a
+  // staging row and (first even column) in a ring row
+  int lcol[LCH], raw_off[LCH], put_off[LCH];
+  bool lcol_ok[LCH];
+#pragma unroll
+  for (int k = 0; k < LCH; ++k) {
+    const int lc = lcb + k * LPA;
+    lcol[k] = xl0 + lc * VEC;
+    lcol_ok[k] = lcol[k] >= 0 && lcol[k] + VEC <= p;
+    raw_off[k] = la * C + lc * VEC;
+    put_off[k] = la * C + lc * (VEC / 2);
+  }
 
   // global row of local row q (wrapped on a periodic level), -1 outside a non-periodic grid
   auto grow = [&](int q) -> int {
@@ -234,8 +273,11 @@ __global__ void __launch_bounds__(MarchGeom<T, NS>::THREADS, MarchGeom<T, NS>::C
   auto issue = [&](int q, int rs) {
     if (loader && q < Q) {
       const int j = grow(q);
-      const bool ok = lcol_ok && j >= 0;
-      cp_async16(raw + rs * ROW + raw_off, ok ? lsrc + (size_t)j * p + lcol : lsrc, ok ? 16 : 0);
+#pragma unroll
+      for (int k = 0; k < LCH; ++k) {
+        const bool ok = lcol_ok[k] && j >= 0;
+        cp_async16(raw + rs * ROW + raw_off[k], ok ? lsrc + (size_t)j * p + lcol[k] : lsrc, ok ? 16 : 0);
+      }
       if (corr) {
         // coarse rows J = j >> 1 and the next one (wrapped when periodic) over the strip's
         // coarse columns, in 16-byte chunks shared out among the x-loader threads
@@ -243,7 +285,7 @@ __global__ void __launch_bounds__(MarchGeom<T, NS>::THREADS, MarchGeom<T, NS>::C
         int Jp = J + 1;
         if (Jp == nyrc) Jp = L.periodic ? 0 : -1;
         T* ed = estage + rs * Y::ESTAGE;
-        for (int c = lc; c < Y::CCHUNKS; c += Y::CHUNKS) {
+        for (int c = lcb; c < Y::CCHUNKS; c += LPA) {
           const int k = c / (Y::CW / VEC), cc = c % (Y::CW / VEC);
           const int JJ = k ? Jp : J, I = I0b + cc * VEC;
           const bool ev = j >= 0 && JJ >= 0 && I >= 0 && I + VEC <= pitchc;
@@ -254,18 +296,23 @@ __global__ void __launch_bounds__(MarchGeom<T, NS>::THREADS, MarchGeom<T, NS>::C
     cp_async_commit();
   };
   // the landed local row q (staging slot rs) into ring slot sr, de-interleaved; the
-  // x-loader adds P eH (bilinear, Eq. 24) to its chunk on the way.  The coarse correction
+  // x-loaders add P eH (bilinear, Eq. 24) to their chunks on the way.  The coarse correction
   // is zero on the coarse boundary ring, so P eH vanishes at every fine node that is not an
   // unknown and needs no mask.  The coarse rows were brought by the x-loaders' copies of
-  // the same group, so the whole x-loader warp pair waits for them (named barrier 1).
+  // the same group, so the x-loader warps wait for all of them (named barrier 1).
   auto settle = [&](int q, int rs, int sr) {
     if (!loader || q >= Q) return;
     constexpr int K = VEC / 2;  // even (and odd) columns of a chunk
-    T v[VEC];
-    Vec16<T>::split(*reinterpret_cast<const typename Vec16<T>::type*>(raw + rs * ROW + raw_off), v);
+    int j = -1;
     if (corr) {
-      asm volatile("bar.sync 1, %0;" ::"n"(Y::CHUNKS) : "memory");
-      const int j = grow(q);
+      asm volatile("bar.sync 1, %0;" ::"n"(LPA) : "memory");
+      j = grow(q);
+    }
+#pragma unroll
+    for (int kk = 0; kk < LCH; ++kk) {
+      const int lc = lcb + kk * LPA;
+      T v[VEC];
+      Vec16<T>::split(*reinterpret_cast<const typename Vec16<T>::type*>(raw + rs * ROW + raw_off[kk]), v);
       if (j >= 0) {
         // local coarse columns K lc .. K lc + K of rows J (a) and J + 1 (c)
         const T* ed = estage + rs * Y::ESTAGE + K * lc;
@@ -284,16 +331,16 @@ __global__ void __launch_bounds__(MarchGeom<T, NS>::THREADS, MarchGeom<T, NS>::C
           }
         }
       }
-    }
-    T ev[K], od[K];
+      T ev[K], od[K];
 #pragma unroll
-    for (int e = 0; e < K; ++e) {
-      ev[e] = v[2 * e];
-      od[e] = v[2 * e + 1];
+      for (int e = 0; e < K; ++e) {
+        ev[e] = v[2 * e];
+        od[e] = v[2 * e + 1];
+      }
+      T* row = sm + sr * ROW + put_off[kk];
+      put_half<T, K>(row, ev);      // even columns
+      put_half<T, K>(row + M, od);  // odd columns
     }
-    T* row = sm + sr * ROW + put_off;
-    put_half<T, K>(row, ev);      // even columns
-    put_half<T, K>(row + M, od);  // odd columns
   };
 
   // ---- compute role: group grp runs phase 2 grp + parity on node m of a parity half
@@ -425,29 +472,44 @@ __global__ void __launch_bounds__(MarchGeom<T, NS>::THREADS, MarchGeom<T, NS>::C
   }
 }
 
-// Variants: sweeps per pass; variant 0 is each precision's default (FP32 two, FP64 one).
+// Variants: the configurations of MarchGeom; variant 0 is each precision's default.
 template <typename T>
 int march_variants() {
-  return 2;
+  return sizeof(T) == 8 ? 4 : 3;
 }
 
-template <typename T>
-static int march_ns(int v) {
-  const int d = sizeof(T) == 8 ? 1 : 2;
-  return v == 1 ? 3 - d : d;
+template <typename T, int CFG>
+static SmoothVariant march_cfg() {
+  return {MarchGeom<T, CFG>::W, 0, MarchGeom<T, CFG>::NS};
+}
+
+// FP64 variant -> configuration: variant 0 (the default) is configuration 3, measured the
+// fastest at 2049^2-8193^2 (1.46 ms a sweep at 8193^2 against 1.69 for configuration 2 and
+// 2.26 for configuration 0, whose four compute warps leave the FP64 pipe waiting on their
+// dependent FMA chains).
+static int f64_cfg(int v) {
+  constexpr int cfg[4] = {3, 1, 2, 0};
+  return cfg[(v < 0 || v >= 4) ? 0 : v];
 }
 
 template <typename T>
 SmoothVariant march_variant(int v) {
-  const int ns = march_ns<T>(v);
-  return {ns == 1 ? (sizeof(T) == 8 ? MarchGeom<double, 1>::W : MarchGeom<float, 1>::W)
-                  : (sizeof(T) == 8 ? MarchGeom<double, 2>::W : MarchGeom<float, 2>::W),
-          0, ns};
+  if (v < 0 || v >= march_variants<T>()) v = 0;
+  if constexpr (sizeof(T) == 8) {
+    switch (f64_cfg(v)) {
+      case 1: return march_cfg<double, 1>();
+      case 2: return march_cfg<double, 2>();
+      case 3: return march_cfg<double, 3>();
+      default: return march_cfg<double, 0>();
+    }
+  } else {
+    return v == 2 ? march_cfg<float, 2>() : v == 1 ? march_cfg<float, 1>() : march_cfg<float, 0>();
+  }
 }
 
 template <typename T>
 int march_sweeps(int v) {
-  return march_ns<T>(v);
+  return march_variant<T>(v).ns;
 }
 
 template <typename T>
@@ -455,11 +517,12 @@ int march_strip_width(int v) {
   return march_variant<T>(v).tx;
 }
 
-template <typename T, int NS>
+template <typename T, int CFG>
 static cudaError_t march_impl(const Op<T>& A, const T* xin, T* xout, const T* b, int rev, const T* eH,
                               int pitch_c, const int* skip, cudaStream_t s) {
-  using G = MarchGeom<T, NS>;
-  using Y = MarchLayout<T, NS>;
+  using G = MarchGeom<T, CFG>;
+  using Y = MarchLayout<T, CFG>;
+  constexpr int NS = G::NS;
   static_assert(Y::smem_bytes <= 227 * 1024, "ring and staging rows must fit in shared memory");
   if (A.pitch % Y::VEC != 0) return cudaErrorInvalidValue;
   if (((uintptr_t)xin | (uintptr_t)xout | (uintptr_t)b | (uintptr_t)A.cE | (uintptr_t)A.cN |
@@ -467,11 +530,15 @@ static cudaError_t march_impl(const Op<T>& A, const T* xin, T* xout, const T* b,
     return cudaErrorInvalidValue;
   if (eH && pitch_c % Y::VEC != 0) return cudaErrorInvalidValue;
   if (xin == xout) return cudaErrorInvalidValue;
-  auto kern = k_smooth_march<T, NS>;
+  auto kern = k_smooth_march<T, CFG>;
   static std::once_flag once;
   static cudaError_t attr = cudaSuccess;
   std::call_once(once, [&] {
     attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Y::smem_bytes);
+    // all of the SM's unified memory as shared memory, so CTAS_PER_SM rings fit side by side
+    if (attr == cudaSuccess)
+      attr = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                  (int)cudaSharedmemCarveoutMaxShared);
   });
   if (attr != cudaSuccess) return attr;
   static int nsm = 0;
@@ -510,8 +577,19 @@ static cudaError_t march_impl(const Op<T>& A, const T* xin, T* xout, const T* b,
 template <typename T>
 cudaError_t launch_smooth_march(const Op<T>& A, const T* xin, T* xout, const T* b, int rev,
                                 const T* eH, int pitch_c, const int* skip, cudaStream_t s, int v) {
-  if (march_ns<T>(v) == 1) return march_impl<T, 1>(A, xin, xout, b, rev, eH, pitch_c, skip, s);
-  return march_impl<T, 2>(A, xin, xout, b, rev, eH, pitch_c, skip, s);
+  if (v < 0 || v >= march_variants<T>()) v = 0;
+  if constexpr (sizeof(T) == 8) {
+    switch (f64_cfg(v)) {
+      case 1: return march_impl<double, 1>(A, xin, xout, b, rev, eH, pitch_c, skip, s);
+      case 2: return march_impl<double, 2>(A, xin, xout, b, rev, eH, pitch_c, skip, s);
+      case 3: return march_impl<double, 3>(A, xin, xout, b, rev, eH, pitch_c, skip, s);
+      default: return march_impl<double, 0>(A, xin, xout, b, rev, eH, pitch_c, skip, s);
+    }
+  } else {
+    if (v == 2) return march_impl<float, 2>(A, xin, xout, b, rev, eH, pitch_c, skip, s);
+    if (v == 1) return march_impl<float, 1>(A, xin, xout, b, rev, eH, pitch_c, skip, s);
+    return march_impl<float, 0>(A, xin, xout, b, rev, eH, pitch_c, skip, s);
+  }
 }
 
 template int march_sweeps<float>(int);

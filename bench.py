@@ -73,7 +73,7 @@ def profiled_traffic(kernel, nx, rows):
 _FP64_PEAK = None
 
 
-def fp64_peak(mg, torch, seconds=0.6):
+def fp64_peak(mg, torch, seconds=1.2):
     """FP64 FMA rate of this GPU, measured now by the library's FMA-chain probe
     (mgk_fma_rate: independent register FMA chains per thread, best over a few launch
     shapes), timed with CUDA events; the SM clock is sampled meanwhile."""
@@ -87,27 +87,27 @@ def fma_probe(mg, torch, f64, seconds=0.6):
     """Best FMA rate over a few launch shapes (independent chains per thread x CTAs per SM),
     each timed with CUDA events for a share of `seconds`; SM clock sampled meanwhile."""
     iters = 2000 if f64 else 50000
-    shapes = [(ch, 152 * k) for ch in (4, 8, 16) for k in (8, 16, 32)]
+    shapes = [(pat, ch, 152 * k) for pat in (0, 1) for ch in (4, 8, 16) for k in (8, 16, 32)]
     out = torch.empty(152 * 32 * 256, dtype=torch.float64 if f64 else torch.float32, device="cuda")
     s = torch.cuda.current_stream().cuda_stream
-    for ch, blocks in shapes:
-        mg.mgk("mgk_fma_rate", int(f64), ch, blocks, iters, out.data_ptr(), s)
+    for pat, ch, blocks in shapes:
+        mg.mgk("mgk_fma_rate", int(f64), pat, ch, blocks, iters, out.data_ptr(), s)
     torch.cuda.synchronize()
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
     best, best_shape = 0.0, None
-    for ch, blocks in shapes:
+    for pat, ch, blocks in shapes:
         flops = mg.lib().mgk_fma_rate_flops(ch, blocks, iters)
         t_end = time.perf_counter() + seconds / len(shapes)
         while time.perf_counter() < t_end:
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
-            mg.mgk("mgk_fma_rate", int(f64), ch, blocks, iters, out.data_ptr(), s)
+            mg.mgk("mgk_fma_rate", int(f64), pat, ch, blocks, iters, out.data_ptr(), s)
             e1.record()
             e1.synchronize()
             r = flops / (e0.elapsed_time(e1) * 1e-3) / 1e12
             if r > best:
-                best, best_shape = r, {"chains": ch, "ctas": blocks, "threads": 256}
+                best, best_shape = r, {"pattern": pat, "chains": ch, "ctas": blocks, "threads": 256}
     clocks = sampler.stop()
     r = {"tflops": best, "shape": best_shape, "sm_mhz": clocks.get("sm_mhz"),
          "sm_max_mhz": clocks.get("sm_max_mhz"), "reasons": clocks.get("reasons"),
@@ -1097,10 +1097,12 @@ def _serve_pass(mg, ctx, reqs, arrivals, inflight, mem_budget):
     tickets = collections.deque()
     unconverged = []
 
-    def collect(tk):
-        st, _ = mg.mg_serve_poll(srv, tk, 600_000, None)
+    def collect(item):
+        tk, k = item
+        st, stats = mg.mg_serve_poll(srv, tk, 600_000, None)
         if st == mg.MG_ERR_NOT_CONVERGED:
-            unconverged.append(tk)  # best iterate returned; counted in the report
+            # best iterate returned; counted in the report with the request and its residual
+            unconverged.append((k, stats.iters, stats.rel_residual))
         elif st:
             raise RuntimeError(f"mg_serve_poll: status {st}: {mg.mg_last_error()}")
 
@@ -1124,7 +1126,7 @@ def _serve_pass(mg, ctx, reqs, arrivals, inflight, mem_budget):
             collect(tickets.popleft())  # staging full: take the oldest result first
         if st:
             raise RuntimeError(f"mg_serve_submit: status {st}: {mg.mg_last_error()}")
-        tickets.append(tk)
+        tickets.append((tk, k))
         while len(tickets) > 4 * inflight:  # keep the host staging bounded
             collect(tickets.popleft())
     while tickets:
@@ -1132,6 +1134,7 @@ def _serve_pass(mg, ctx, reqs, arrivals, inflight, mem_budget):
     wall = time.perf_counter() - t0
     rep = mg.mg_server_stop(srv)
     rep.not_converged = len(unconverged)
+    rep.unconverged = unconverged
     return rep, wall
 
 
@@ -1220,7 +1223,11 @@ def run_serve(args):
             "saturated": {"requests_per_s": sat_rps, "p50_ms": rep.p50_ms, "p99_ms": rep.p99_ms,
                           "completed": rep.completed, "failed": rep.failed,
                           "not_converged": rep.not_converged, "mean_inflight": rep.mean_batch,
-                          "reused": rep.reused, "evicted": rep.evicted},
+                          "reused": rep.reused, "evicted": rep.evicted,
+                          "not_converged_requests": [
+                              {"index": k, "side": stream[k][1], "radius": stream[k][2], "ratio": stream[k][3],
+                               "seed": stream[k][4], "iters": it, "rel_residual": rr}
+                              for k, it, rr in rep.unconverged]},
             "latency": lat,
             "fp64_plain": {"value": plain, "requests": len(sample),
                            "how": "mg_update_transform + mg_solve per request, FP64, hierarchy per grid shape"},

@@ -242,11 +242,13 @@ size_t mgk_jacobi_f64_static_capacity(void);
 /* FMA-rate probe (no counterpart in the paper: it measures the arithmetic peak that the
  * FP64 stencil kernels are reported against, since their bound is the FP64 pipe, not HBM).
  * Launches `blocks` CTAs of 256 threads; every thread runs `chains` (4, 8 or 16)
- * independent chains of `iters` dependent fused multiply-adds in registers (FP64 if
- * f64 != 0, else FP32) and writes one value to out[blocks * 256] (device memory,
- * caller-owned).  Time the launch with CUDA events on `stream`; mgk_fma_rate_flops gives
- * its flop count.  Returns 1 on bad arguments, 4 if the launch fails. */
-int mgk_fma_rate(int f64, int chains, int blocks, int iters, void *out, void *stream);
+ * independent chains of `iters` fused multiply-adds in registers (FP64 if f64 != 0, else
+ * FP32), in operand pattern `pattern` (0: a = a b + c with two constants shared by all
+ * chains; 1: a = x y + a with per-chain x and y, the stencil-sum pattern), and writes one
+ * value to out[blocks * 256] (device memory, caller-owned).  Time the launch with CUDA
+ * events on `stream`; mgk_fma_rate_flops gives its flop count.  Returns 1 on bad arguments,
+ * 4 if the launch fails. */
+int mgk_fma_rate(int f64, int pattern, int chains, int blocks, int iters, void *out, void *stream);
 double mgk_fma_rate_flops(int chains, int blocks, int iters);
 
 /* Test hook of the request server (mg_serve_*): the next `count` completion queries of

@@ -71,6 +71,20 @@ struct MarchGeom<float, 2> {
   static constexpr int NS = 2, C = 128, HX = 8, W = C - 2 * HX, HY = 8, R = 20, D = 6, NPT = 1, LCH = 1;
   static constexpr int THREADS = 512, CTAS_PER_SM = 2;
 };
+// FP32 3 and 4: configuration 0 with fewer, busier threads, which spreads each thread's
+// per-step bookkeeping (row and ring-slot arithmetic, loop control, the barrier) over more
+// nodes: two chunks per loader thread (224 loaders), and in 3 also two nodes per compute
+// thread (256 compute threads).
+template <>
+struct MarchGeom<float, 3> {
+  static constexpr int NS = 2, C = 256, HX = 8, W = C - 2 * HX, HY = 8, R = 20, D = 6, NPT = 2, LCH = 2;
+  static constexpr int THREADS = 544, CTAS_PER_SM = 1;
+};
+template <>
+struct MarchGeom<float, 4> {
+  static constexpr int NS = 2, C = 256, HX = 8, W = C - 2 * HX, HY = 8, R = 20, D = 6, NPT = 1, LCH = 2;
+  static constexpr int THREADS = 800, CTAS_PER_SM = 1;
+};
 // FP64 0: one sweep a pass on 128-column strips.  FP64 smoothing is bound by the FP64 pipe,
 // not by HBM, once each array is read once per sweep, so extra sweeps per pass mostly add
 // redundant halo work.  640 threads: 128 compute (2 active phases x 64 nodes), 448 loaders
@@ -475,7 +489,7 @@ __global__ void __launch_bounds__(MarchGeom<T, CFG>::THREADS, MarchGeom<T, CFG>:
 // Variants: the configurations of MarchGeom; variant 0 is each precision's default.
 template <typename T>
 int march_variants() {
-  return sizeof(T) == 8 ? 4 : 3;
+  return sizeof(T) == 8 ? 4 : 5;
 }
 
 template <typename T, int CFG>
@@ -503,7 +517,13 @@ SmoothVariant march_variant(int v) {
       default: return march_cfg<double, 0>();
     }
   } else {
-    return v == 2 ? march_cfg<float, 2>() : v == 1 ? march_cfg<float, 1>() : march_cfg<float, 0>();
+    switch (v) {
+      case 1: return march_cfg<float, 1>();
+      case 2: return march_cfg<float, 2>();
+      case 3: return march_cfg<float, 3>();
+      case 4: return march_cfg<float, 4>();
+      default: return march_cfg<float, 0>();
+    }
   }
 }
 
@@ -586,9 +606,13 @@ cudaError_t launch_smooth_march(const Op<T>& A, const T* xin, T* xout, const T* 
       default: return march_impl<double, 0>(A, xin, xout, b, rev, eH, pitch_c, skip, s);
     }
   } else {
-    if (v == 2) return march_impl<float, 2>(A, xin, xout, b, rev, eH, pitch_c, skip, s);
-    if (v == 1) return march_impl<float, 1>(A, xin, xout, b, rev, eH, pitch_c, skip, s);
-    return march_impl<float, 0>(A, xin, xout, b, rev, eH, pitch_c, skip, s);
+    switch (v) {
+      case 1: return march_impl<float, 1>(A, xin, xout, b, rev, eH, pitch_c, skip, s);
+      case 2: return march_impl<float, 2>(A, xin, xout, b, rev, eH, pitch_c, skip, s);
+      case 3: return march_impl<float, 3>(A, xin, xout, b, rev, eH, pitch_c, skip, s);
+      case 4: return march_impl<float, 4>(A, xin, xout, b, rev, eH, pitch_c, skip, s);
+      default: return march_impl<float, 0>(A, xin, xout, b, rev, eH, pitch_c, skip, s);
+    }
   }
 }
 

@@ -209,7 +209,7 @@ _SIGS = {
                                C.c_void_p], C.c_int),
     "mgk_jacobi_f64_static_capacity": ([], C.c_size_t),
     "mgk_server_fail_event_queries": ([C.c_int], None),
-    "mgk_fma_rate": ([C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p], C.c_int),
+    "mgk_fma_rate": ([C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p], C.c_int),
     "mgk_fma_rate_flops": ([C.c_int, C.c_int, C.c_int], C.c_double),
     "mgk_vcycle_f64": ([C.c_int, C.POINTER(mgk_op_f64), C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
                         C.POINTER(C.c_void_p), C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p],

@@ -412,8 +412,9 @@ __global__ void __launch_bounds__(MarchGeom<T, CFG>::THREADS, MarchGeom<T, CFG>:
     for (int u = 0; u < 2; ++u) {
       const int s = s0 + u;
       // phase ph of the thread's group on local row s - 2 ph, for each of its nodes (they
-      // share the phase, hence the row and the ring slots)
-      {
+      // share the phase, hence the row and the ring slots).  Roles are whole warps, so the
+      // other roles' warps branch past this block instead of issuing it predicated off.
+      if (computer) {
         const MarchLane* zz = u ? l_odd : l_even;
         const MarchLane& za = zz[0];
         const int q = s - 2 * za.ph;
@@ -473,7 +474,7 @@ __global__ void __launch_bounds__(MarchGeom<T, CFG>::THREADS, MarchGeom<T, CFG>:
       // loaders: request row s + 2 + D into the staging slot that row s + 1 left, then
       // settle row s + 2 (requested D steps ago) into its ring slot, which last held row
       // s + 2 - R, no longer read
-      {
+      if (loader) {
         const int rs_new = rsn == 0 ? RAWS - 1 : rsn - 1;  // slot of row s + 1
         issue(s + 2 + D, rs_new);
         cp_async_wait<D>();

@@ -212,14 +212,74 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// Dynamic shared memory of the kernel, indexed by element offsets (32-bit addressing).
+// Dynamic shared memory of the kernel.  Every access below goes through a 32-bit shared
+// address (base + byte offset) so that no generic 64-bit pointer arithmetic is spent on it.
 extern __shared__ __align__(16) float march_smem[];
+
+// Shared-memory loads and stores at a 32-bit address plus a compile-time byte offset.  The
+// "memory" clobber keeps them ordered against the barriers and against each other.
+template <int OFF = 0>
+__device__ __forceinline__ float lds_f(uint32_t a) {
+  float v;
+  asm volatile("ld.shared.f32 %0, [%1+%2];" : "=f"(v) : "r"(a), "n"(OFF) : "memory");
+  return v;
+}
+template <int OFF = 0>
+__device__ __forceinline__ double lds_d(uint32_t a) {
+  double v;
+  asm volatile("ld.shared.f64 %0, [%1+%2];" : "=d"(v) : "r"(a), "n"(OFF) : "memory");
+  return v;
+}
+template <typename T, int OFF = 0>
+__device__ __forceinline__ T lds(uint32_t a) {
+  if constexpr (sizeof(T) == 4)
+    return lds_f<OFF>(a);
+  else
+    return lds_d<OFF>(a);
+}
+template <typename T>
+__device__ __forceinline__ void sts(uint32_t a, T v) {
+  if constexpr (sizeof(T) == 4)
+    asm volatile("st.shared.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
+  else
+    asm volatile("st.shared.f64 [%0], %1;" ::"r"(a), "d"(v) : "memory");
+}
+// 16 bytes (one chunk of VEC elements) from shared memory into e[VEC].
+template <typename T>
+__device__ __forceinline__ void lds16(uint32_t a, T* e) {
+  if constexpr (sizeof(T) == 4)
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(e[0]), "=f"(e[1]), "=f"(e[2]), "=f"(e[3])
+                 : "r"(a)
+                 : "memory");
+  else
+    asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(e[0]), "=d"(e[1]) : "r"(a) : "memory");
+}
+// VEC/2 consecutive elements (8 bytes for FP32 pairs, one FP64) to / from shared memory.
+template <typename T>
+__device__ __forceinline__ void sts_half(uint32_t a, const T* e) {
+  if constexpr (sizeof(T) == 4)
+    asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"(e[0]), "f"(e[1]) : "memory");
+  else
+    asm volatile("st.shared.f64 [%0], %1;" ::"r"(a), "d"(e[0]) : "memory");
+}
+template <typename T>
+__device__ __forceinline__ void lds_half(uint32_t a, T* e) {
+  if constexpr (sizeof(T) == 4)
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(e[0]), "=f"(e[1]) : "r"(a) : "memory");
+  else
+    asm volatile("ld.shared.f64 %0, [%1];" : "=d"(e[0]) : "r"(a) : "memory");
+}
+__device__ __forceinline__ void cp_async16_s(uint32_t dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes)
+               : "memory");
+}
 
 // Per-thread constants of one phase parity: which phase the thread's group runs on steps
 // of that parity and where its node and the node's left/right neighbours sit in a ring row.
 struct MarchLane {
   int ph;                // phase index
-  int own, left, right;  // element offsets in a ring row (parity half * M + index)
+  int own, left, right;  // byte offsets in a ring row (parity half * M + index, times the element size)
   int qlo, qhi;          // local rows the phase may update (halo shrink, grid rows)
   bool col_ok;           // column inside the shrinking halo and an interior grid column
 };
@@ -236,10 +296,13 @@ __global__ void __launch_bounds__(MarchGeom<T, CFG>::THREADS, MarchGeom<T, CFG>:
   constexpr int C = G::C, HX = G::HX, W = G::W, HY = G::HY, D = G::D, M = Y::M, VEC = Y::VEC;
   constexpr int R = G::R, ROW = Y::ROW, RAWS = Y::RAWS;
   constexpr int LAG = 2 * (4 * NS - 1);  // rows between phase 0 and the last phase
-  T* const sm = reinterpret_cast<T*>(march_smem);  // ring at 0, staging rows at RAW0, coarse staging at EST0
-  constexpr int RAW0 = R * ROW, EST0 = RAW0 + RAWS * ROW;
-  T* const raw = sm + RAW0;
-  T* const estage = sm + EST0;
+  constexpr int E = (int)sizeof(T);      // bytes per element
+  constexpr int ROWB = ROW * E;          // bytes of one ring (or staging) row
+  constexpr int CB = C * E;              // bytes of one array's part of a ring row
+  // shared-memory layout (byte addresses): ring of R rows, RAWS staging rows, coarse staging
+  const uint32_t s_ring = smem_addr(march_smem);
+  const uint32_t s_raw = s_ring + R * ROWB;
+  const uint32_t s_est = s_raw + RAWS * ROWB;
 
   const int t = threadIdx.x;
   const int X0 = blockIdx.x * W, Y0 = blockIdx.y * S;
@@ -264,17 +327,18 @@ __global__ void __launch_bounds__(MarchGeom<T, CFG>::THREADS, MarchGeom<T, CFG>:
                        : la == 4 ? L.cNE : la == 5 ? L.cNW : L.dinv;
   const bool corr = loader && la == 0 && eH != nullptr;
   const int I0b = xl0 >> 1;  // global coarse column of coarse staging column 0 (multiple of VEC)
-  // per chunk of the thread: first global column, whether it lies in the array, offsets in a
-  // staging row and (first even column) in a ring row
-  int lcol[LCH], raw_off[LCH], put_off[LCH];
+  // per chunk of the thread: first global column, whether it lies in the array, byte offsets
+  // in a staging row and (first even column) in a ring row
+  int lcol[LCH];
+  uint32_t raw_off[LCH], put_off[LCH];
   bool lcol_ok[LCH];
 #pragma unroll
   for (int k = 0; k < LCH; ++k) {
     const int lc = lcb + k * LPA;
     lcol[k] = xl0 + lc * VEC;
     lcol_ok[k] = lcol[k] >= 0 && lcol[k] + VEC <= p;
-    raw_off[k] = la * C + lc * VEC;
-    put_off[k] = la * C + lc * (VEC / 2);
+    raw_off[k] = (uint32_t)((la * C + lc * VEC) * E);
+    put_off[k] = (uint32_t)((la * C + lc * (VEC / 2)) * E);
   }
 
   // global row of local row q (wrapped on a periodic level), -1 outside a non-periodic grid
@@ -285,12 +349,13 @@ __global__ void __launch_bounds__(MarchGeom<T, CFG>::THREADS, MarchGeom<T, CFG>:
   };
   // request local row q into staging slot rs, committed as one copy group
   auto issue = [&](int q, int rs) {
-    if (loader && q < Q) {
+    if (q < Q) {
       const int j = grow(q);
+      const T* const rowp = lsrc + (size_t)(j < 0 ? 0 : j) * p;
 #pragma unroll
       for (int k = 0; k < LCH; ++k) {
         const bool ok = lcol_ok[k] && j >= 0;
-        cp_async16(raw + rs * ROW + raw_off[k], ok ? lsrc + (size_t)j * p + lcol[k] : lsrc, ok ? 16 : 0);
+        cp_async16_s(s_raw + rs * ROWB + raw_off[k], ok ? rowp + lcol[k] : lsrc, ok ? 16 : 0);
       }
       if (corr) {
         // coarse rows J = j >> 1 and the next one (wrapped when periodic) over the strip's
@@ -298,12 +363,12 @@ __global__ void __launch_bounds__(MarchGeom<T, CFG>::THREADS, MarchGeom<T, CFG>:
         const int J = j >> 1;
         int Jp = J + 1;
         if (Jp == nyrc) Jp = L.periodic ? 0 : -1;
-        T* ed = estage + rs * Y::ESTAGE;
+        const uint32_t ed = s_est + rs * (Y::ESTAGE * E);
         for (int c = lcb; c < Y::CCHUNKS; c += LPA) {
           const int k = c / (Y::CW / VEC), cc = c % (Y::CW / VEC);
           const int JJ = k ? Jp : J, I = I0b + cc * VEC;
           const bool ev = j >= 0 && JJ >= 0 && I >= 0 && I + VEC <= pitchc;
-          cp_async16(ed + k * Y::CW + cc * VEC, ev ? eH + (size_t)JJ * pitchc + I : eH, ev ? 16 : 0);
+          cp_async16_s(ed + (k * Y::CW + cc * VEC) * E, ev ? eH + (size_t)JJ * pitchc + I : eH, ev ? 16 : 0);
         }
       }
     }
@@ -315,7 +380,7 @@ __global__ void __launch_bounds__(MarchGeom<T, CFG>::THREADS, MarchGeom<T, CFG>:
   // unknown and needs no mask.  The coarse rows were brought by the x-loaders' copies of
   // the same group, so the x-loader warps wait for all of them (named barrier 1).
   auto settle = [&](int q, int rs, int sr) {
-    if (!loader || q >= Q) return;
+    if (q >= Q) return;
     constexpr int K = VEC / 2;  // even (and odd) columns of a chunk
     int j = -1;
     if (corr) {
@@ -326,22 +391,26 @@ __global__ void __launch_bounds__(MarchGeom<T, CFG>::THREADS, MarchGeom<T, CFG>:
     for (int kk = 0; kk < LCH; ++kk) {
       const int lc = lcb + kk * LPA;
       T v[VEC];
-      Vec16<T>::split(*reinterpret_cast<const typename Vec16<T>::type*>(raw + rs * ROW + raw_off[kk]), v);
+      lds16<T>(s_raw + rs * ROWB + raw_off[kk], v);
       if (j >= 0) {
         // local coarse columns K lc .. K lc + K of rows J (a) and J + 1 (c)
-        const T* ed = estage + rs * Y::ESTAGE + K * lc;
+        const uint32_t ed = s_est + rs * (Y::ESTAGE * E) + K * lc * E;
+        T a[K + 1], c[K + 1];
+#pragma unroll
+        for (int e = 0; e <= K; ++e) a[e] = lds<T>(ed + e * E);
         if (!(j & 1)) {
 #pragma unroll
           for (int e = 0; e < K; ++e) {
-            v[2 * e] += ed[e];
-            v[2 * e + 1] += T(0.5) * (ed[e] + ed[e + 1]);
+            v[2 * e] += a[e];
+            v[2 * e + 1] += T(0.5) * (a[e] + a[e + 1]);
           }
         } else {
-          const T* ec = ed + Y::CW;
+#pragma unroll
+          for (int e = 0; e <= K; ++e) c[e] = lds<T>(ed + (Y::CW + e) * E);
 #pragma unroll
           for (int e = 0; e < K; ++e) {
-            v[2 * e] += T(0.5) * (ed[e] + ec[e]);
-            v[2 * e + 1] += T(0.25) * ((ed[e] + ed[e + 1]) + (ec[e] + ec[e + 1]));
+            v[2 * e] += T(0.5) * (a[e] + c[e]);
+            v[2 * e + 1] += T(0.25) * ((a[e] + a[e + 1]) + (c[e] + c[e + 1]));
           }
         }
       }
@@ -351,9 +420,9 @@ __global__ void __launch_bounds__(MarchGeom<T, CFG>::THREADS, MarchGeom<T, CFG>:
         ev[e] = v[2 * e];
         od[e] = v[2 * e + 1];
       }
-      T* row = sm + sr * ROW + put_off[kk];
-      put_half<T, K>(row, ev);      // even columns
-      put_half<T, K>(row + M, od);  // odd columns
+      const uint32_t row = s_ring + sr * ROWB + put_off[kk];
+      sts_half<T>(row, ev);          // even columns
+      sts_half<T>(row + M * E, od);  // odd columns
     }
   };
 
@@ -370,9 +439,9 @@ __global__ void __launch_bounds__(MarchGeom<T, CFG>::THREADS, MarchGeom<T, CFG>:
     const int ci = colour_ci(c);
     const int i = 2 * mm + ci;  // local column; its global column xl0 + i has parity ci
     const int h = ci, o = 1 - ci;
-    z.own = h * M + mm;
-    z.left = o * M + mm - 1 + ci;
-    z.right = o * M + mm + ci;
+    z.own = (h * M + mm) * E;  // byte offsets in a ring row
+    z.left = (o * M + mm - 1 + ci) * E;
+    z.right = (o * M + mm + ci) * E;
     z.col_ok = computer && i >= 1 + z.ph && i <= C - 2 - z.ph && xl0 + i >= 1 && xl0 + i <= L.nx - 2;
     z.qlo = max(1 + z.ph, qrow_lo);
     z.qhi = min(Q - 2 - z.ph, qrow_hi);
@@ -394,13 +463,15 @@ __global__ void __launch_bounds__(MarchGeom<T, CFG>::THREADS, MarchGeom<T, CFG>:
 
   // prologue: rows 0 and 1 settled, rows 2 .. D + 1 in flight (row r stages in slot r mod
   // RAWS; RAWS = D + 1 slots hold the D rows in flight and the one being settled)
-  issue(0, 0);
-  issue(1, 1);
-  cp_async_wait<0>();
-  settle(0, 0, 0);
-  settle(1, 1, 1);
+  if (loader) {
+    issue(0, 0);
+    issue(1, 1);
+    cp_async_wait<0>();
+    settle(0, 0, 0);
+    settle(1, 1, 1);
 #pragma unroll 1
-  for (int q = 2; q < D + 2; ++q) issue(q, q % RAWS);
+    for (int q = 2; q < D + 2; ++q) issue(q, q % RAWS);
+  }
   __syncthreads();
 
   const int last_step = HY + Seff - 1 + LAG + 2;  // the last owned row is written at this step
@@ -420,30 +491,32 @@ __global__ void __launch_bounds__(MarchGeom<T, CFG>::THREADS, MarchGeom<T, CFG>:
         const int q = s - 2 * za.ph;
         if (q >= za.qlo && q <= za.qhi) {
           const int sq = wrapR(sbase + u - 2 * za.ph);
-          const int iR = sq * ROW;  // ring rows q, q + 1, q - 1; arrays at offsets a * C
-          const int iU = (sq + 1 == R ? 0 : sq + 1) * ROW;
-          const int iD = (sq == 0 ? R - 1 : sq - 1) * ROW;
+          const uint32_t bR = s_ring + sq * ROWB;  // ring rows q, q + 1, q - 1
+          const uint32_t bU = s_ring + (sq + 1 == R ? 0 : sq + 1) * ROWB;
+          const uint32_t bD = s_ring + (sq == 0 ? R - 1 : sq - 1) * ROWB;
+          // arrays at byte offsets a CB in a ring row: 0 iterate, 1 b, 2 E, 3 N, 4 NE, 5 NW, 6 1/diag
           auto update = [&](const MarchLane& z) {
-            const int ow = z.own, lf = z.left, rt = z.right;
-            const T* r0 = sm + iR;
-            const T* ru = sm + iU;
-            const T* rd = sm + iD;
-            T acc = r0[2 * C + ow] * r0[rt];
-            acc = fma(r0[2 * C + lf], r0[lf], acc);
-            acc = fma(r0[3 * C + ow], ru[ow], acc);
-            acc = fma(rd[3 * C + ow], rd[ow], acc);
-            acc = fma(r0[4 * C + ow], ru[rt], acc);
-            acc = fma(rd[4 * C + lf], rd[lf], acc);
-            acc = fma(r0[5 * C + ow], ru[lf], acc);
-            acc = fma(rd[5 * C + rt], rd[rt], acc);
-            return (r0[C + ow] - acc) * r0[6 * C + ow];
+            const uint32_t r0o = bR + z.own, r0l = bR + z.left, r0r = bR + z.right;
+            const uint32_t ruo = bU + z.own, rul = bU + z.left, rur = bU + z.right;
+            const uint32_t rdo = bD + z.own, rdl = bD + z.left, rdr = bD + z.right;
+            T acc = lds<T, 2 * CB>(r0o) * lds<T>(r0r);
+            acc = fma(lds<T, 2 * CB>(r0l), lds<T>(r0l), acc);
+            acc = fma(lds<T, 3 * CB>(r0o), lds<T>(ruo), acc);
+            acc = fma(lds<T, 3 * CB>(rdo), lds<T>(rdo), acc);
+            acc = fma(lds<T, 4 * CB>(r0o), lds<T>(rur), acc);
+            acc = fma(lds<T, 4 * CB>(rdl), lds<T>(rdl), acc);
+            acc = fma(lds<T, 5 * CB>(r0o), lds<T>(rul), acc);
+            acc = fma(lds<T, 5 * CB>(rdr), lds<T>(rdr), acc);
+            return (lds<T, CB>(r0o) - acc) * lds<T, 6 * CB>(r0o);
           };
+          // every lane computes (its addresses are inside the ring row whatever its column), and
+          // only lanes of updatable columns store: no divergent branch around the loads
           T v[Y::NPT];
 #pragma unroll
-          for (int k = 0; k < Y::NPT; ++k) v[k] = zz[k].col_ok ? update(zz[k]) : T(0);
+          for (int k = 0; k < Y::NPT; ++k) v[k] = update(zz[k]);
 #pragma unroll
           for (int k = 0; k < Y::NPT; ++k)
-            if (zz[k].col_ok) sm[iR + zz[k].own] = v[k];
+            if (zz[k].col_ok) sts<T>(bR + zz[k].own, v[k]);
         }
       }
       // write-out: local row s - LAG - 2 is final (its last phase ran at step s - 2 at the
@@ -452,10 +525,10 @@ __global__ void __launch_bounds__(MarchGeom<T, CFG>::THREADS, MarchGeom<T, CFG>:
         const int qo = s - LAG - 2;
         if (qo >= HY && qo < HY + Seff) {
           constexpr int K = VEC / 2;
-          const T* xr = sm + wrapR(sbase + u - LAG - 2) * ROW;
+          const uint32_t xr = s_ring + wrapR(sbase + u - LAG - 2) * ROWB;
           T ev[K], od[K], e[VEC];
-          get_half<T, K>(xr + wl / 2, ev);
-          get_half<T, K>(xr + M + wl / 2, od);
+          lds_half<T>(xr + (wl / 2) * E, ev);
+          lds_half<T>(xr + (M + wl / 2) * E, od);
 #pragma unroll
           for (int k = 0; k < K; ++k) {
             e[2 * k] = ev[k];

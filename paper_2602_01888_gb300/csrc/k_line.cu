@@ -23,6 +23,7 @@
 #include <cuda_runtime.h>
 
 #include <type_traits>
+#include <vector>
 
 #include "mg_common.cuh"
 #include "mg_kernels.h"
@@ -292,6 +293,336 @@ __global__ void __launch_bounds__(kLT, sizeof(T) == 8 ? 3 : (LU <= 2 ? 6 : 5))
   for (int t = threadIdx.x; t < N; t += kLT) x[r0 + t + 1] = d[sx<T>(t)];
 }
 
+// ------------------------------------------------------------------ partition solver
+// Rows of kPartMinNp to kPartMaxNp (padded) unknowns are solved by a partition method instead
+// of cyclic reduction over the whole row: the row is cut into kPP segments of S = Np / kPP
+// unknowns; the last unknown of each segment is a separator, the other S - 1 form the
+// segment's interior, coupled to the rest of the row only through the two separators around
+// it.  Eliminating the interiors (one sequential tridiagonal solve per segment, one thread
+// each) leaves a tridiagonal system of kPP separator unknowns (the Schur complement), solved
+// by cyclic reduction in shared memory; the interiors then follow from the two spike vectors
+// of each segment.  The result is the exact solution of the row system, as with cyclic
+// reduction over the whole row, up to rounding order.  A sweep's dependent chain of global
+// loads is thus a few coalesced batches per thread (interior factors stored segment-minor:
+// entry k of every segment contiguous), instead of one round trip per reduction level.
+//
+// Factor layout per row (the same five arrays of Np entries as cyclic reduction):
+//   interior entry k (0 <= k < S - 1) of segment t at k * kPP + t:
+//     alpha: sub-diagonal a_k of the interior system (0 for k = 0),
+//     gamma: 1 / m_k, the reciprocal Thomas pivot,
+//     afin:  c'_k, the eliminated super-diagonal (0 for k = S - 2),
+//     cfin:  w_k, the left spike (interior response to the separator before the segment),
+//     binv:  v_k, the right spike (response to the separator ending the segment);
+//   entries (S - 1) kPP .. Np - 1: the cyclic-reduction factors of the separator system, in
+//   the layout described at the top of this file for a row of kPP unknowns.
+constexpr int kPP = 256;            // segments per row = threads of a partition CTA
+
+// Padded row lengths solved by the partition method: measured faster than cyclic reduction
+// over the whole row on GB300 for 2048 and 4096 (FP32 half-sweeps of 2049^2: 0.078 ms against
+// 0.108; 4097^2: 0.256 against 0.276; FP64 0.147 / 0.516 against 0.205 / 0.579), slower for
+// 8192 (FP32 0.92 against 0.90 ms: segments of 32 make each thread's sequential chain three
+// times 31 dependent steps, and its loads ahead need registers that cost resident rows).
+constexpr int kPartMinNp = 2048, kPartMaxNp = 4096;
+constexpr int kPartCtas = 4;  // resident CTAs per SM (the kernel's register budget)
+
+__host__ __device__ inline bool line_partitioned(int np) { return np >= kPartMinNp && np <= kPartMaxNp; }
+
+// Coefficients (sub, diagonal, super) of unknown ii of a row system; padding rows (ii >= N)
+// are identity equations.
+template <typename T>
+__device__ __forceinline__ void row_coef(const Lvl<T>& L, size_t r0, int N, int ii, T& a, T& bb, T& c) {
+  if (ii < N) {
+    a = ii >= 1 ? L.cE[r0 + ii] : T(0);
+    bb = L.diag[r0 + ii + 1];
+    c = ii <= N - 2 ? L.cE[r0 + ii + 1] : T(0);
+  } else {
+    a = T(0);
+    bb = T(1);
+    c = T(0);
+  }
+}
+
+// Cyclic-reduction factors of a tridiagonal system of n (a power of two) equations held in
+// shared memory (padded index sx), written at offset base of the five factor arrays.  The
+// same recurrences as k_line_factor; a, bb, c are overwritten.
+template <typename T>
+__device__ void cr_factor(T* a, T* bb, T* c, int n, const LineFactors<T>& F, size_t base) {
+  const int K = line_levels(n);
+  for (int k = 0; k < K; ++k) {
+    const int s = 1 << k, off = n - n / s;
+    for (int m = threadIdx.x; m < n / (2 * s); m += blockDim.x) {
+      const int q = sx<T>(2 * s * m + s - 1);
+      F.afin[base + off + m] = a[q];
+      F.cfin[base + off + m] = c[q];
+      F.binv[base + off + m] = T(1) / bb[q];
+    }
+    for (int m = threadIdx.x; m < n / (2 * s); m += blockDim.x) {
+      const int i = 2 * s * (m + 1) - 1;
+      const bool up = i + s < n;
+      const int q = sx<T>(i), qd = sx<T>(i - s), qu = up ? sx<T>(i + s) : q;
+      const T al = -a[q] / bb[qd];
+      const T ga = up ? -c[q] / bb[qu] : T(0);
+      F.alpha[base + off + m] = al;
+      F.gamma[base + off + m] = ga;
+      const T na = al * a[qd];
+      const T nc = up ? ga * c[qu] : T(0);
+      const T nb = bb[q] + al * c[qd] + (up ? ga * a[qu] : T(0));
+      a[q] = na;
+      c[q] = nc;
+      bb[q] = nb;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    F.afin[base + n - 1] = T(0);
+    F.cfin[base + n - 1] = T(0);
+    F.binv[base + n - 1] = T(1) / bb[sx<T>(n - 1)];
+  }
+}
+
+// Partition factors of row blockIdx.x (thread t: segment t).  Shared memory: the separator
+// system's a, b, c (padded rows of kPP) and the spikes' first entries.
+template <typename T>
+__global__ void __launch_bounds__(kPP) k_line_pfactor(Lvl<T> L, LineFactors<T> F) {
+  const int j = blockIdx.x;
+  if (j >= L.nyr || !row_active(L, j)) return;
+  const int N = L.nx - 2, Np = F.np, S = Np / kPP, t = threadIdx.x;
+  extern __shared__ __align__(16) unsigned char line_smem[];
+  const int rs = (int)(line_row_smem<T>(kPP) / sizeof(T));
+  T* sa = reinterpret_cast<T*>(line_smem);
+  T* sb = sa + rs;
+  T* sc = sb + rs;
+  T* w0 = sc + rs;  // w_t[0], v_t[0] of every segment
+  T* v0 = w0 + kPP;
+  const size_t r0 = (size_t)j * L.pitch, f0 = (size_t)j * Np;
+  const int i0 = t * S;  // first unknown of the segment
+  // interior Thomas factorization, k = 0 .. S - 2
+  T cprev = T(0);
+  for (int k = 0; k <= S - 2; ++k) {
+    T a, bb, c;
+    row_coef(L, r0, N, i0 + k, a, bb, c);
+    const T ai = k == 0 ? T(0) : a;      // coupling to the separator before the segment: a spike
+    const T ci = k == S - 2 ? T(0) : c;  // coupling to the separator ending it: a spike
+    const T im = T(1) / (bb - ai * cprev);
+    const T cp = ci * im;
+    const size_t e = f0 + (size_t)k * kPP + t;
+    F.alpha[e] = ai;
+    F.gamma[e] = im;
+    F.afin[e] = cp;
+    cprev = cp;
+  }
+  // spikes: w = T^-1 (a_first e_0), v = T^-1 (c_last e_{S-2}); forward then backward
+  {
+    T a0, b0, c0, al, bl, cl;
+    row_coef(L, r0, N, i0, a0, b0, c0);
+    row_coef(L, r0, N, i0 + S - 2, al, bl, cl);
+    T wp = T(0), vp = T(0);
+    for (int k = 0; k <= S - 2; ++k) {
+      const size_t e = f0 + (size_t)k * kPP + t;
+      const T ai = F.alpha[e], im = F.gamma[e];
+      wp = ((k == 0 ? a0 : T(0)) - ai * wp) * im;
+      vp = ((k == S - 2 ? cl : T(0)) - ai * vp) * im;
+      F.cfin[e] = wp;
+      F.binv[e] = vp;
+    }
+    T wn = T(0), vn = T(0);
+    for (int k = S - 2; k >= 0; --k) {
+      const size_t e = f0 + (size_t)k * kPP + t;
+      const T cp = F.afin[e];
+      const T w = F.cfin[e] - cp * wn, v = F.binv[e] - cp * vn;
+      F.cfin[e] = w;
+      F.binv[e] = v;
+      wn = w;
+      vn = v;
+    }
+    w0[t] = wn;
+    v0[t] = vn;
+  }
+  __syncthreads();
+  // separator system (Schur complement): equation of the separator ending segment t
+  {
+    T as, bs, cs;
+    row_coef(L, r0, N, i0 + S - 1, as, bs, cs);
+    const size_t el = f0 + (size_t)(S - 2) * kPP + t;  // last interior entry of the segment
+    const T wl = F.cfin[el], vl = F.binv[el];
+    const bool nx_ = t + 1 < kPP;
+    const T wn = nx_ ? w0[t + 1] : T(0), vn = nx_ ? v0[t + 1] : T(0);
+    const int q = sx<T>(t);
+    sa[q] = -as * wl;
+    sb[q] = bs - as * vl - cs * wn;
+    sc[q] = -cs * vn;
+  }
+  __syncthreads();
+  cr_factor<T>(sa, sb, sc, kPP, F, f0 + (size_t)(S - 1) * kPP);
+}
+
+// Shared memory of a partition half-sweep: the interior values (segment-minor, rows of
+// kPP + 1 to keep the row-order accesses on distinct banks), the separators, the separator
+// system's right-hand side / solution (padded) and its factors.
+template <typename T>
+__host__ __device__ inline size_t part_smem(int np) {
+  const int S = np / kPP;
+  return ((size_t)(S - 1) * (kPP + 1) + kPP + (line_row_smem<T>(kPP) / sizeof(T)) + 5 * kPP) * sizeof(T);
+}
+
+// One half-sweep with the partition solver: rows j = par, par + 2, ... (one CTA per row).
+// SS = segment length (template, so the per-segment loops unroll and their coalesced global
+// loads are issued ahead of the dependent arithmetic).
+template <typename T, int SS, int LU, int MODE>
+__global__ void __launch_bounds__(kPP, kPartCtas)
+    k_line_part(Lvl<T> L, LineFactors<T> F, T* __restrict__ x, const T* __restrict__ b, int par,
+                const int* __restrict__ skip, const T* __restrict__ eH, int pitch_c) {
+  if (skip && *skip) return;
+  const int j = par + 2 * blockIdx.x;
+  if (j >= L.nyr || !row_active(L, j)) return;
+  constexpr int NI = SS - 1;       // interior unknowns per segment
+  constexpr int RS = kPP + 1;      // row stride of the interior block in shared memory
+  const int N = L.nx - 2, Np = F.np;
+  const int t = threadIdx.x;
+  const size_t f0 = (size_t)j * Np;
+  extern __shared__ __align__(16) unsigned char line_smem[];
+  T* dI = reinterpret_cast<T*>(line_smem);  // interior: entry k of segment t at k * RS + t
+  T* dS = dI + (size_t)NI * RS;             // separators
+  T* dR = dS + kPP;                         // separator system, padded (sx)
+  T* fR = dR + line_row_smem<T>(kPP) / sizeof(T);  // its factors: 5 x kPP
+  // separator-system factors: asynchronous copies now, waited for before its reduction
+  {
+    const size_t base = f0 + (size_t)NI * kPP;
+    for (int e = t; e < 5 * kPP; e += kPP) {
+      const int a = e / kPP, m = e - a * kPP;
+      const T* src = a == 0 ? F.alpha : a == 1 ? F.gamma : a == 2 ? F.afin : a == 3 ? F.cfin : F.binv;
+      cp_async_elem(fR + e, src + base + m);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  }
+  const int p = L.pitch;
+  const int jd = row_dn(j, L.nyr), ju = row_up(j, L.nyr);
+  const size_t r0 = (size_t)j * p, rd = (size_t)jd * p, ru = (size_t)ju * p;
+  // right-hand side of every unknown, in row order, stored by segment
+  for (int t0 = t; t0 < Np; t0 += LU * kPP) {
+    T v[LU];
+#pragma unroll
+    for (int u = 0; u < LU; ++u) {
+      const int tt = t0 + u * kPP;
+      v[u] = T(0);
+      if (tt < N) {
+        const int i = tt + 1;
+        if constexpr (MODE == LM_ZERO) {
+          v[u] = __ldg(b + r0 + i);
+        } else {
+          auto nb = [&](size_t row0, int jn, int c) -> T {
+            T val = __ldg(x + row0 + c);
+            if constexpr (MODE == LM_FUSED)
+              if (c >= 1 && c <= L.nx - 2 && row_active(L, jn)) val += prolong_even_row(eH, pitch_c, jn, c);
+            return val;
+          };
+          T off = __ldg(L.cN + r0 + i) * nb(ru, ju, i);
+          off = fma(__ldg(L.cN + rd + i), nb(rd, jd, i), off);
+          off = fma(__ldg(L.cNE + r0 + i), nb(ru, ju, i + 1), off);
+          off = fma(__ldg(L.cNE + rd + i - 1), nb(rd, jd, i - 1), off);
+          off = fma(__ldg(L.cNW + r0 + i), nb(ru, ju, i - 1), off);
+          off = fma(__ldg(L.cNW + rd + i + 1), nb(rd, jd, i + 1), off);
+          if (i == 1) off = fma(L.cE[r0], __ldg(x + r0), off);
+          if (i == N) off = fma(L.cE[r0 + i], __ldg(x + r0 + i + 1), off);
+          v[u] = __ldg(b + r0 + i) - off;
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < LU; ++u) {
+      const int tt = t0 + u * kPP;
+      if (tt < Np) {
+        const int sg = tt / SS, k = tt - sg * SS;
+        if (k < NI)
+          dI[k * RS + sg] = v[u];
+        else
+          dS[sg] = v[u];
+      }
+    }
+  }
+  __syncthreads();
+  // interior of segment t: forward and backward Thomas substitution in place in shared
+  // memory; the loops unroll, so the coalesced factor loads are issued ahead of the dependent
+  // arithmetic as far as registers allow
+  {
+    const T* fa = F.alpha + f0 + t;
+    const T* fg = F.gamma + f0 + t;
+    const T* fc = F.afin + f0 + t;
+    T dp = T(0);
+#pragma unroll
+    for (int k = 0; k < NI; ++k) {
+      dp = (dI[k * RS + t] - __ldg(fa + (size_t)k * kPP) * dp) * __ldg(fg + (size_t)k * kPP);
+      dI[k * RS + t] = dp;
+    }
+    T yn = T(0);
+#pragma unroll
+    for (int k = NI - 1; k >= 0; --k) {
+      yn = dI[k * RS + t] - __ldg(fc + (size_t)k * kPP) * yn;
+      dI[k * RS + t] = yn;
+    }
+  }
+  __syncthreads();
+  // right-hand side of the separator system: the separator's equation with its neighbouring
+  // interior unknowns replaced by their values for zero separators (y)
+  {
+    const int is = t * SS + SS - 1;  // the separator's unknown index
+    T as = T(0), cs = T(0);
+    if (is < N) {
+      as = is >= 1 ? L.cE[r0 + is] : T(0);
+      cs = is <= N - 2 ? L.cE[r0 + is + 1] : T(0);
+    }
+    const T yl = dI[(NI - 1) * RS + t];
+    const T yr = t + 1 < kPP ? dI[t + 1] : T(0);
+    dR[sx<T>(t)] = dS[t] - as * yl - cs * yr;
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  __syncthreads();
+  // separator system by cyclic reduction, factors in shared memory
+  {
+    constexpr int n = kPP;
+    const int K = line_levels(n);
+    for (int k = 0; k < K; ++k) {
+      const int s = 1 << k, off = n - n / s, cnt = n / (2 * s);
+      for (int m = t; m < cnt; m += kPP) {
+        const int i = 2 * s * (m + 1) - 1, q = sx<T>(i);
+        T v = fma(fR[off + m], dR[sx<T>(i - s)], dR[q]);
+        if (i + s < n) v = fma(fR[n + off + m], dR[sx<T>(i + s)], v);
+        dR[q] = v;
+      }
+      __syncthreads();
+    }
+    if (t == 0) dR[sx<T>(n - 1)] *= fR[4 * n + n - 1];
+    __syncthreads();
+    for (int k = K - 1; k >= 0; --k) {
+      const int s = 1 << k, off = n - n / s, cnt = n / (2 * s);
+      for (int m = t; m < cnt; m += kPP) {
+        const int i = 2 * s * m + s - 1, q = sx<T>(i);
+        T v = dR[q];
+        if (i - s >= 0) v -= fR[2 * n + off + m] * dR[sx<T>(i - s)];
+        v -= fR[3 * n + off + m] * dR[sx<T>(i + s)];
+        dR[q] = v * fR[4 * n + off + m];
+      }
+      __syncthreads();
+    }
+  }
+  // interiors from their separators: x = y - x_left w - x_right v
+  {
+    const T xl = t > 0 ? dR[sx<T>(t - 1)] : T(0);
+    const T xr = dR[sx<T>(t)];
+    const T* fw = F.cfin + f0 + t;
+    const T* fv = F.binv + f0 + t;
+#pragma unroll
+    for (int k = 0; k < NI; ++k)
+      dI[k * RS + t] = dI[k * RS + t] - xl * __ldg(fw + (size_t)k * kPP) - xr * __ldg(fv + (size_t)k * kPP);
+    dS[t] = xr;
+  }
+  __syncthreads();
+  for (int tt = t; tt < N; tt += kPP) {
+    const int sg = tt / SS, k = tt - sg * SS;
+    x[r0 + tt + 1] = k < NI ? dI[k * RS + sg] : dS[sg];
+  }
+}
+
 // ------------------------------------------------------------------ launchers
 template <typename T>
 size_t line_factor_elems(int nx, int ny, int periodic) {
@@ -300,8 +631,9 @@ size_t line_factor_elems(int nx, int ny, int periodic) {
 
 template <typename T>
 bool line_supported(int nx) {
-  return nx >= 3 && 3 * line_row_smem<T>(line_np(nx)) <= kLineSmemMax &&
-         3 * zebra_smem<T>(line_np(nx)) <= kLineSmemMax;
+  const int np = line_np(nx);
+  return nx >= 3 && 3 * line_row_smem<T>(np) <= kLineSmemMax && 3 * zebra_smem<T>(np) <= kLineSmemMax &&
+         (!line_partitioned(np) || kPartCtas * part_smem<T>(np) <= kLineSmemMax);
 }
 
 template <typename T>
@@ -321,6 +653,11 @@ template <typename T>
 cudaError_t launch_line_factor(const Op<T>& A, const LineFactors<T>& F, cudaStream_t s) {
   if (!line_supported<T>(A.nx) || F.np != line_np(A.nx)) return cudaErrorInvalidValue;
   const Lvl<T> L = lvl_of(A);
+  if (line_partitioned(F.np)) {
+    const size_t sm = 3 * line_row_smem<T>(kPP) + 2 * kPP * sizeof(T);
+    k_line_pfactor<T><<<L.nyr, kPP, sm, s>>>(L, F);
+    return cudaGetLastError();
+  }
   const size_t sm = 3 * line_row_smem<T>(F.np);
   static bool attr = false;
   if (!attr) {
@@ -355,12 +692,66 @@ static cudaError_t zebra_attributes() {
   return st;
 }
 
+// Raise the dynamic shared-memory limit of every partition half-sweep variant of precision
+// T, once, and let kPartCtas CTAs share an SM.
+template <typename T>
+static cudaError_t part_attributes() {
+  static const cudaError_t st = [] {
+    std::vector<const void*> ks;
+    auto add = [&](auto ss) {
+      constexpr int SS = decltype(ss)::value;
+      ks.push_back((const void*)k_line_part<T, SS, 2, LM_PLAIN>);
+      ks.push_back((const void*)k_line_part<T, SS, 2, LM_ZERO>);
+      ks.push_back((const void*)k_line_part<T, SS, 2, LM_FUSED>);
+    };
+    add(std::integral_constant<int, kPartMinNp / kPP>());
+    add(std::integral_constant<int, kPartMaxNp / kPP>());
+    for (const void* k : ks) {
+      cudaError_t e =
+          cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kLineSmemMax / kPartCtas));
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }();
+  return st;
+}
+
+template <typename T>
+static cudaError_t launch_part_rows(const Lvl<T>& L, const LineFactors<T>& F, T* x, const T* b, int par,
+                                    int rows, const int* skip, cudaStream_t s, const T* eH, int pitch_c,
+                                    int zero_start) {
+  const cudaError_t ea = part_attributes<T>();
+  if (ea != cudaSuccess) return ea;
+  const size_t sm = part_smem<T>(F.np);
+  auto go = [&](auto ss) -> cudaError_t {
+    constexpr int SS = decltype(ss)::value;
+    if (zero_start)
+      k_line_part<T, SS, 2, LM_ZERO><<<rows, kPP, sm, s>>>(L, F, x, b, par, skip, eH, pitch_c);
+    else if (eH)
+      k_line_part<T, SS, 2, LM_FUSED><<<rows, kPP, sm, s>>>(L, F, x, b, par, skip, eH, pitch_c);
+    else
+      k_line_part<T, SS, 2, LM_PLAIN><<<rows, kPP, sm, s>>>(L, F, x, b, par, skip, eH, pitch_c);
+    return cudaGetLastError();
+  };
+  if (F.np == kPartMinNp) return go(std::integral_constant<int, kPartMinNp / kPP>());
+  if (F.np == kPartMaxNp) return go(std::integral_constant<int, kPartMaxNp / kPP>());
+  return cudaErrorInvalidValue;
+}
+
 template <typename T>
 cudaError_t launch_line_rows(const Op<T>& A, const LineFactors<T>& F, T* x, const T* b, int par,
                              const int* skip, cudaStream_t s, const T* eH, int pitch_c, int zero_start) {
   if (!line_supported<T>(A.nx) || F.np != line_np(A.nx)) return cudaErrorInvalidValue;
   if (eH && (par != 1 || (A.nx - 1) % 2 || (A.ny - 1) % 2)) return cudaErrorInvalidValue;
   const Lvl<T> L = lvl_of(A);
+  if (line_partitioned(F.np)) {
+    const int rows = (L.nyr - par + 1) / 2;
+    if (rows <= 0) return cudaSuccess;
+    return launch_part_rows<T>(L, F, x, b, par, rows, skip, s, eH, pitch_c, zero_start);
+  }
   const size_t sm = zebra_smem<T>(F.np);
   const int rows = (L.nyr - par + 1) / 2;
   if (rows <= 0) return cudaSuccess;

@@ -258,3 +258,60 @@ def test_line_smoother_refuses_too_long_rows(libmg, ctx):
     phi, st = p.solve()
     assert st.rel_residual <= 1e-10
     p.close()
+
+
+# Rows of 1025 to 4095 unknowns (padded lengths 2048 and 4096) are solved by the partition
+# method: segments of Np / 256 unknowns whose interiors are eliminated per thread, then the
+# separator system by cyclic reduction.  Square cells keep FP32 rows well conditioned.
+PART_CASES = {
+    "rect_1027x9": _rect(1027, 9, ("sine_warp", (0.05,)), ly=8.0 / 1026),    # N = 1025: S = 8, most padded
+    "rect_2049x9": _rect(2049, 9, ("sine_warp", (0.05,)), ly=8.0 / 2048),    # S = 8
+    "rect_3073x9": _rect(3073, 9, ("affine", (1.0, 0.2, -0.1, 1.05)), ly=8.0 / 3072),  # S = 16, padded
+    "rect_4097x9": _rect(4097, 9, ("sine_warp", (0.05,)), ly=8.0 / 4096),    # S = 16
+    "annulus_2049": lambda: I.annulus_log(2049),                            # periodic, S = 8
+}
+
+
+@pytest.mark.parametrize("case", list(PART_CASES))
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_partition_half_sweeps_match_oracle(libmg, oracle, cuda, case, prec):
+    torch = cuda
+    inst = PART_CASES[case]()
+    A = oracle.prepare(inst).A
+    dt = torch.float64 if prec == "f64" else torch.float32
+    keep, s = _op(libmg, torch, A, dt)
+    f = _factors(libmg, torch, A, s, dt, prec)
+    phi, b = _data(A, 15)
+    bd = _dev(torch, b, dt)
+    stream = torch.cuda.current_stream().cuda_stream
+    for par in (0, 1):
+        x = _dev(torch, phi, dt)
+        libmg.mgk(f"mgk_line_rows_{prec}", C.byref(s), f.data_ptr(), x.data_ptr(), bd.data_ptr(), par, stream)
+        torch.cuda.synchronize()
+        got = x.double().cpu().numpy()
+        ref = oracle.line_rows(A, phi, b, par)
+        err = _rel(got, ref)
+        assert err < (1e-12 if prec == "f64" else 2e-5), (case, prec, par, err)
+        moved = np.zeros(A.cE.shape, bool)
+        moved[par::2, 1:-1] = True
+        if not A.periodic:
+            moved[0, :] = moved[-1, :] = False
+        start = phi.astype(np.float32).astype(np.float64) if prec == "f32" else phi
+        assert np.array_equal(got[~moved], start[~moved]), (case, prec, par)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("nu", [(1, 1), (2, 2)])
+def test_partition_vcycle_matches_oracle(libmg, oracle, cuda, prec, nu):
+    """A line-smoothed V-cycle whose finest level (2049 wide) uses the partition solver in all
+    three half-sweep forms (stored iterate, zero iterate, coarse correction interpolated in)
+    and whose coarser levels use cyclic reduction, against the oracle's cycle."""
+    inst = I.annulus_log(2049)
+    P = oracle.prepare(inst)
+    ops = oracle.hierarchy(P.A)
+    H = oracle.Hierarchy(P.A, smoother=oracle.SMOOTHER_XLINE, nu1=nu[0], nu2=nu[1])
+    rng = np.random.default_rng(35)
+    r = rng.standard_normal(inst.grid.shape) * inst.grid.interior_mask() * np.abs(P.A.diag).max()
+    ref = H.vcycle(r)
+    got = _gpu_vcycle_line(libmg, cuda, ops, r, prec, nu)
+    assert _rel(got, ref) < (1e-12 if prec == "f64" else 2e-5), (prec, nu)

@@ -473,12 +473,13 @@ def measure_smoother(mg, torch, inst, prec, reps=20, smoother="gs4", family=None
                g.x0, g.y0, g.hx, g.hy, eps.data_ptr() if eps is not None else None, pitch,
                D.data_ptr(), exx.data_ptr(), exy.data_ptr(), eyy.data_ptr(), folded.data_ptr(), s)
     ops = [z() for _ in range(6)]
-    st = mg.op_struct(ops, g.nx, g.ny, g.periodic_y)
+    five = mg.map_five_point(inst.map)  # the solver's own choice for this map
+    st = mg.op_struct(ops, g.nx, g.ny, g.periodic_y, five_point=five)
     mg.mgk("mgk_assemble", C.byref(st), g.hx, g.hy, exx.data_ptr(), exy.data_ptr(), eyy.data_ptr(), s)
     dt = torch.float32 if f32 else torch.float64
     if f32:
         ops32 = [z(torch.float32) for _ in range(6)]
-        st32 = mg.op_struct(ops32, g.nx, g.ny, g.periodic_y, f32=True)
+        st32 = mg.op_struct(ops32, g.nx, g.ny, g.periodic_y, f32=True, five_point=five)
         mg.mgk("mgk_op_to_f32", C.byref(st), C.byref(st32), s)
         st, name = st32, "mgk_smooth_f32"
     else:
@@ -487,7 +488,7 @@ def measure_smoother(mg, torch, inst, prec, reps=20, smoother="gs4", family=None
     x = z(dt)
     b = torch.randn((g.nyr, pitch), dtype=torch.float64, device="cuda").to(dt)
     if smoother == "xline":
-        return _measure_line(mg, torch, g, st, x, b, f32, s, reps)
+        return _measure_line(mg, torch, g, st, x, b, f32, s, reps, five)
     fam, shape = parse_choice(family)
     if fam is None:  # untuned: the size rule of the cycle
         fam = "marching" if g.nx * g.nyr >= MARCH_NODES else "colour"
@@ -577,7 +578,7 @@ def _measure_variant(mg, torch, g, st, x, x2, b, f32, s, reps, family, shape):
     return _fp64_roof(mg, torch, kern, achieved, per_launch_s, g, sweeps_per_launch=ns, note=note)
 
 
-def cycle_model(prec, smoother, nu):
+def cycle_model(prec, smoother, nu, five=False):
     """Algorithmic bytes and flops per fine node of one V(nu1, nu2) cycle, coarser levels
     included (x 4/3).  Point smoother, two sweeps per pass: each pass reads the five
     operator arrays (C = 5 elements) and moves the iterate in and out and b; the residual +
@@ -585,12 +586,18 @@ def cycle_model(prec, smoother, nu):
     post-smoothing pass also reads the quarter-size correction (68 + 3C bytes at FP64 for
     V(2,2)).  Line smoother: 14 elements per sweep (six off-row couplings, iterate in and
     out, b, five factor arrays), plus the residual + restriction pass and a prolongation
-    pass.  Flops: 18 per unknown update and per residual."""
+    pass.  Flops: 18 per unknown update and per residual.  five: the finest operator is a
+    5-point stencil (no NE / NW couplings): 10 elements per line sweep, a residual pass of
+    5 + 1/4, 10 flops per residual and 16 per line update instead of 24."""
     e = 8.0 if prec == "fp64" else 4.0
     n1, n2 = nu
     if smoother == "xline":
-        fine = (n1 + n2) * 14 * e + (7 + 0.25) * e + (2 + 0.25) * e
-        flops = (n1 + n2) * 24.0 + 18.0 + 8.0
+        if five:
+            fine = (n1 + n2) * 10 * e + (5 + 0.25) * e + (2 + 0.25) * e
+            flops = (n1 + n2) * 16.0 + 10.0 + 8.0
+        else:
+            fine = (n1 + n2) * 14 * e + (7 + 0.25) * e + (2 + 0.25) * e
+            flops = (n1 + n2) * 24.0 + 18.0 + 8.0
     else:
         p1, p2 = -(-n1 // 2), -(-n2 // 2)
         fine = (p1 + 1 + p2) * 5 * e + p1 * 3 * e + (2 + 0.25) * e + p2 * 3 * e + 0.25 * e
@@ -598,11 +605,12 @@ def cycle_model(prec, smoother, nu):
     return fine * 4.0 / 3.0, flops * 4.0 / 3.0
 
 
-def _measure_line(mg, torch, g, st, x, b, f32, s, reps):
+def _measure_line(mg, torch, g, st, x, b, f32, s, reps, five=False):
     """Zebra x-line sweep (two launches of k_line_zebra, one per row parity) on the finest
     level.  Bytes-bound; algorithmic bytes per node and sweep: 14 elements (the N, NE, NW
     couplings of every row, read once per half-sweep as own or lower row: 6; the iterate
-    read once and written once: 2; b: 1; the five cyclic-reduction factor arrays: 5)."""
+    read once and written once: 2; b: 1; the five cyclic-reduction factor arrays: 5); 10 for
+    a 5-point operator (no NE / NW couplings: 2 instead of 6)."""
     import ctypes as C
     tag = "f32" if f32 else "f64"
     esz = 4 if f32 else 8
@@ -623,10 +631,11 @@ def _measure_line(mg, torch, g, st, x, b, f32, s, reps):
     e1.record()
     torch.cuda.synchronize()
     per_launch_s = e0.elapsed_time(e1) * 1e-3 / (reps * 2)
-    kern = f"k_line_zebra<{'float' if f32 else 'double'}>"
-    bytes_per_launch = 14.0 * esz * g.nx * g.nyr / 2
+    kern = f"k_line_zebra<{'float' if f32 else 'double'}>" + (" 5-point" if five else "")
+    elems = 10.0 if five else 14.0
+    bytes_per_launch = elems * esz * g.nx * g.nyr / 2
     ach = bytes_per_launch / per_launch_s / 1e9
-    return _hbm_roof(kern, ach, per_launch_s, g)
+    return _hbm_roof(kern, ach, per_launch_s, g, elements_per_node_and_sweep=elems)
 
 
 def measure_grid_generation(mg, torch, ctx, n, r, cpu=False):
@@ -681,15 +690,18 @@ def run_kernel_only(args):
     D, exx, exy, eyy = z(), z(), z(), z()
     folded = torch.zeros(1, dtype=torch.int32, device="cuda")
     s = torch.cuda.current_stream().cuda_stream
-    prm = (C.c_double * 4)(0.1, 0.0, 0.0, 0.0)
-    mg.mgk("mgk_eps_analytic", 1, prm, n, g.ny, 0, 0.0, 0.0, g.hx, g.hy, None, pitch, D.data_ptr(),
+    # the sine-warp operator (9-point); --stencil 5: the sinh stretching's (no cross term), run
+    # by the 5-point forms of the kernels
+    five = args.stencil == 5
+    kind, prm = (3, (C.c_double * 4)(1.0, 0.5, 0.0, 0.0)) if five else (1, (C.c_double * 4)(0.1, 0.0, 0.0, 0.0))
+    mg.mgk("mgk_eps_analytic", kind, prm, n, g.ny, 0, 0.0, 0.0, g.hx, g.hy, None, pitch, D.data_ptr(),
            exx.data_ptr(), exy.data_ptr(), eyy.data_ptr(), folded.data_ptr(), s)
     ops = [z() for _ in range(6)]
-    st = mg.op_struct(ops, n, g.ny, False)
+    st = mg.op_struct(ops, n, g.ny, False, five_point=five)
     mg.mgk("mgk_assemble", C.byref(st), g.hx, g.hy, exx.data_ptr(), exy.data_ptr(), eyy.data_ptr(), s)
     if not f64:
         ops32 = [z(torch.float32) for _ in range(6)]
-        st32 = mg.op_struct(ops32, n, g.ny, False, f32=True)
+        st32 = mg.op_struct(ops32, n, g.ny, False, f32=True, five_point=five)
         mg.mgk("mgk_op_to_f32", C.byref(st), C.byref(st32), s)
         st = st32
     x, b = z(dt), torch.randn((g.nyr, pitch), dtype=torch.float64, device="cuda").to(dt)
@@ -734,7 +746,7 @@ def run_kernel_only(args):
         once()
     e1.record()
     torch.cuda.synchronize()
-    rec = {"kernel": args.kernel, "side": n, "ny": g.ny, "reps": args.reps,
+    rec = {"kernel": args.kernel, "side": n, "ny": g.ny, "reps": args.reps, "stencil": args.stencil,
            "ms_per_call": e0.elapsed_time(e1) / args.reps}
     if args.kernel.startswith(("march", "pipe", "fused")):
         fam = FAMILY_CODES["marching" if args.kernel.startswith("march") else
@@ -839,7 +851,8 @@ def run_ours(args):
         cycle_ms = mg.mg_cycle_time(prob.h, opts, reps=20)
         res[prec] = {"tot": tot, "times": times, "stats": st, "clocks": clocks, "cycle_ms": cycle_ms,
                      "e2e": ws * U * e2e_steps / e2e_t, "levels": len(prob.levels()),
-                     "setup_ms": st.setup_ms, "solve_ms": st.solve_ms}
+                     "setup_ms": st.setup_ms, "solve_ms": st.solve_ms,
+                     "five_point": mg.problem_five_point(prob.h)}
         prob.close()
     del flush
     family = (tuned or {}).get(precisions[0], {}).get(str(g.nx))  # the tuner's choice for the finest level
@@ -862,6 +875,7 @@ def run_ours(args):
             "config": {"workload": args.workload, "precision": h,
                        "outer": f"{outer}+vcycle({nu[0]},{nu[1]})", "smoother": smoother,
                        "rtol": rtols, "unknowns": U, "l2": "flushed between steps (512 MB write)",
+                       "finest_stencil": "5-point (map without cross term)" if rh["five_point"] else "9-point",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
             "iters": rh["stats"].iters, "levels": rh["levels"], "setup_ms": rh["setup_ms"],
             "solve_ms": rh["solve_ms"], "rel_residual": rh["stats"].rel_residual,
@@ -872,7 +886,7 @@ def run_ours(args):
         }
         vc = {}
         for prec in precisions:
-            bpn, fpn = cycle_model(prec, smoother, nu)
+            bpn, fpn = cycle_model(prec, smoother, nu, five=res[prec]["five_point"])
             nodes = g.nx * g.nyr
             t = res[prec]["cycle_ms"] * 1e-3
             ent = {"ms": 1e3 * t, "bytes_per_cycle": bpn * nodes, "achieved_gbs": bpn * nodes / t / 1e9,
@@ -1344,6 +1358,8 @@ def main():
     ap.add_argument("--side", type=int, default=2049)
     ap.add_argument("--ny", type=int, default=0, help="kernel-only: rows (default: --side)")
     ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--stencil", type=int, default=9, choices=(5, 9),
+                    help="kernel-only: 9 = sine-warp operator, 5 = a map without cross term (5-point kernels)")
     ap.add_argument("--variant", type=int, default=-1,
                     help="kernel-only march/pipe/fused: the autotuner's variant index (default: the family's default)")
     args = ap.parse_args()

@@ -188,6 +188,18 @@ mg_status mg_batch_update_transform(mg_ctx *ctx, int count, mg_problem *const *p
 void mg_problem_free(mg_problem *prob);
 /* Levels and per-level sizes (nx_out/ny_out: arrays of at least 24 ints, nullable). */
 mg_status mg_problem_info(const mg_problem *prob, int *levels, int *nx_out, int *ny_out);
+/*
+ * 1 if the map's transformed tensor has no cross term, exactly: eps_xy (Eq. 13) is zero at
+ * every node as computed, because J^T J is diagonal with a zero product in Eq. 13 (the
+ * identity, the polar map of Eq. 29, the sinh stretching of Eq. 52, an affine map with
+ * params[1] = params[2] = 0).  The finest operator of such a map is a 5-point stencil, and
+ * the solver runs the 5-point forms of its finest-level kernels (which skip the zero NE / NW
+ * couplings; results identical to the 9-point forms).  0 otherwise or for NULL.
+ */
+int mg_map_five_point(const mg_map_desc *map);
+/* Whether the problem's current finest operator is handled as a 5-point stencil (the map of
+ * its last coefficient build passed mg_map_five_point): 1 / 0, -1 for NULL. */
+int mg_problem_five_point(const mg_problem *prob);
 
 /*
  * Solve for phi.  rho_phys: rho' at every node (only unknowns are used; rho = rho' det J,

@@ -10,6 +10,12 @@
  *
  * Operator storage (see mg.h): cE, cN, cNE, cNW hold the couplings of node (i, j) to
  * (i+1, j), (i, j+1), (i+1, j+1), (i-1, j+1); diag and dinv = 1/diag the diagonal.
+ * five_point != 0 declares that cNE and cNW are zero at every node (the operator of a map
+ * whose transformed tensor has no cross term: eps_xy of Eq. 13 vanishes identically, as for
+ * the polar map of Eq. 29 and the sinh stretching of Eq. 52); the kernels then neither read
+ * nor multiply them, with results identical to the 9-point form on those zeros.  The two
+ * arrays must still hold zeros (the Galerkin coarsening and the point smoothers read them).
+ * 0 = a general 9-point operator.
  */
 #ifndef MG_KERNELS_H_
 #define MG_KERNELS_H_
@@ -23,18 +29,23 @@ extern "C" {
 typedef struct {
   int nx, ny, periodic, pitch;
   double *cE, *cN, *cNE, *cNW, *diag, *dinv;
+  int five_point;
 } mgk_op_f64;
 
 typedef struct {
   int nx, ny, periodic, pitch;
   float *cE, *cN, *cNE, *cNW, *diag, *dinv;
+  int five_point;
 } mgk_op_f32;
 
 /*
  * Coefficient build, analytic map (kind: MG_MAP_* of mg.h, params as there): Jacobian
  * J_ab = dx'_a/dx_b (Eq. 1) at node x = x0 + i hx, y = y0 + j hy; D = det J; eps from
  * Eqs. 12-15 times eps_phys (nullable, pitched; Eq. 10 with eps' = s I).  *folded
- * (device int) is set to 1 where D <= 0 and left unchanged elsewhere.
+ * (device int) is set to 1 where D <= 0 and left unchanged elsewhere.  For a map without
+ * cross term (mg_map_five_point of mg.h: identity, polar, sinh, shear-free affine) eps_xy
+ * is written as exactly 0, which Eq. 13 is for it (the general formula would leave rounding
+ * residue); D, eps_xx and eps_yy always come from the general formula.
  */
 int mgk_eps_analytic(int kind, const double *params4, int nx, int ny, int periodic, double x0,
                      double y0, double hx, double hy, const double *eps_phys, int pitch, double *D,
@@ -53,7 +64,8 @@ int mgk_eps_grid(int nx, int ny, int periodic, double hx, double hy, const doubl
  * Fine-level operator A = -L_h from nodal eps (symmetric conservative form of the
  * Eq. 18 stencil): E/N couplings -(face mean of eps_xx / eps_yy)/h^2, corner couplings
  * from (Dx E Dy + Dy E Dx) with E = diag(eps_xy), diagonal = -(sum of the 8 couplings)
- * at unknowns, 1 at Dirichlet nodes.  Couplings missing at the grid edge are 0.
+ * at unknowns, 1 at Dirichlet nodes.  Couplings missing at the grid edge are 0.  With
+ * A->five_point set, eps_xy is taken as zero (it is not read) and cNE, cNW are written as 0.
  */
 int mgk_assemble(const mgk_op_f64 *A, double hx, double hy, const double *exx, const double *exy,
                  const double *eyy, void *stream);
@@ -64,7 +76,8 @@ int mgk_rhs(const mgk_op_f64 *A, const double *rho_phys, const double *D, double
 /* Galerkin coarse operator A_H = (1/4) P^T A_h P with bilinear P (Sec. 3: A_H of Eq. 23). */
 int mgk_galerkin(const mgk_op_f64 *fine, const mgk_op_f64 *coarse, void *stream);
 
-/* FP32 copy of an operator (rounded to nearest). */
+/* FP32 copy of an operator (rounded to nearest); with src->five_point set, the NE / NW
+ * arrays of dst are written as 0 without reading src's.  dst->five_point is not used. */
 int mgk_op_to_f32(const mgk_op_f64 *src, const mgk_op_f32 *dst, void *stream);
 
 /* Four-colour Gauss-Seidel (omega = 1, Sec. 2.1), `sweeps` sweeps in colour order

@@ -162,10 +162,11 @@ __host__ __device__ inline size_t zebra_smem(int np) {
 // what shared memory allows there.
 // Right-hand-side variants of a half-sweep (compile-time, so the common one carries no extra
 // code): the iterate as stored; a zero iterate (nothing read); the stored iterate plus the
-// coarse correction interpolated on the fly at the (even) neighbour rows.
+// coarse correction interpolated on the fly at the (even) neighbour rows.  FIVE: a 5-point
+// operator (L.five_point), whose zero NE / NW couplings are neither loaded nor multiplied.
 enum LineMode : int { LM_PLAIN = 0, LM_ZERO = 1, LM_FUSED = 2 };
 
-template <typename T, int LU, int MODE>
+template <typename T, int LU, int MODE, bool FIVE = false>
 __global__ void __launch_bounds__(kLT, sizeof(T) == 8 ? 3 : (LU <= 2 ? 6 : 5))
     k_line_zebra(Lvl<T> L, LineFactors<T> F, T* __restrict__ x, const T* __restrict__ b, int par,
                  const int* __restrict__ skip, const T* __restrict__ eH, int pitch_c) {
@@ -209,10 +210,12 @@ __global__ void __launch_bounds__(kLT, sizeof(T) == 8 ? 3 : (LU <= 2 ? 6 : 5))
           // couplings leaving the row, in the order of the point smoother's sum minus E/W
           T off = __ldg(L.cN + r0 + i) * nb(ru, ju, i);
           off = fma(__ldg(L.cN + rd + i), nb(rd, jd, i), off);
-          off = fma(__ldg(L.cNE + r0 + i), nb(ru, ju, i + 1), off);
-          off = fma(__ldg(L.cNE + rd + i - 1), nb(rd, jd, i - 1), off);
-          off = fma(__ldg(L.cNW + r0 + i), nb(ru, ju, i - 1), off);
-          off = fma(__ldg(L.cNW + rd + i + 1), nb(rd, jd, i + 1), off);
+          if constexpr (!FIVE) {
+            off = fma(__ldg(L.cNE + r0 + i), nb(ru, ju, i + 1), off);
+            off = fma(__ldg(L.cNE + rd + i - 1), nb(rd, jd, i - 1), off);
+            off = fma(__ldg(L.cNW + r0 + i), nb(ru, ju, i - 1), off);
+            off = fma(__ldg(L.cNW + rd + i + 1), nb(rd, jd, i + 1), off);
+          }
           if (i == 1) off = fma(L.cE[r0], __ldg(x + r0), off);
           if (i == N) off = fma(L.cE[r0 + i], __ldg(x + r0 + i + 1), off);
           v[u] = __ldg(b + r0 + i) - off;
@@ -518,10 +521,12 @@ __global__ void __launch_bounds__(kPP, kPartCtas)
           };
           T off = __ldg(L.cN + r0 + i) * nb(ru, ju, i);
           off = fma(__ldg(L.cN + rd + i), nb(rd, jd, i), off);
-          off = fma(__ldg(L.cNE + r0 + i), nb(ru, ju, i + 1), off);
-          off = fma(__ldg(L.cNE + rd + i - 1), nb(rd, jd, i - 1), off);
-          off = fma(__ldg(L.cNW + r0 + i), nb(ru, ju, i - 1), off);
-          off = fma(__ldg(L.cNW + rd + i + 1), nb(rd, jd, i + 1), off);
+          if (!L.five_point) {
+            off = fma(__ldg(L.cNE + r0 + i), nb(ru, ju, i + 1), off);
+            off = fma(__ldg(L.cNE + rd + i - 1), nb(rd, jd, i - 1), off);
+            off = fma(__ldg(L.cNW + r0 + i), nb(ru, ju, i - 1), off);
+            off = fma(__ldg(L.cNW + rd + i + 1), nb(rd, jd, i + 1), off);
+          }
           if (i == 1) off = fma(L.cE[r0], __ldg(x + r0), off);
           if (i == N) off = fma(L.cE[r0 + i], __ldg(x + r0 + i + 1), off);
           v[u] = __ldg(b + r0 + i) - off;
@@ -676,12 +681,21 @@ cudaError_t launch_line_factor(const Op<T>& A, const LineFactors<T>& F, cudaStre
 template <typename T>
 static cudaError_t zebra_attributes() {
   static const cudaError_t st = [] {
-    const void* ks[] = {
-        (const void*)k_line_zebra<T, 1, LM_PLAIN>, (const void*)k_line_zebra<T, 1, LM_ZERO>,
-        (const void*)k_line_zebra<T, 1, LM_FUSED>, (const void*)k_line_zebra<T, 2, LM_PLAIN>,
-        (const void*)k_line_zebra<T, 2, LM_ZERO>,  (const void*)k_line_zebra<T, 2, LM_FUSED>,
-        (const void*)k_line_zebra<T, 4, LM_PLAIN>, (const void*)k_line_zebra<T, 4, LM_ZERO>,
-        (const void*)k_line_zebra<T, 4, LM_FUSED>};
+    std::vector<const void*> ks;
+    auto add = [&](auto lu_c, auto five_c) {
+      constexpr int U = decltype(lu_c)::value;
+      constexpr bool F5 = decltype(five_c)::value;
+      ks.push_back((const void*)k_line_zebra<T, U, LM_PLAIN, F5>);
+      ks.push_back((const void*)k_line_zebra<T, U, LM_ZERO, F5>);
+      ks.push_back((const void*)k_line_zebra<T, U, LM_FUSED, F5>);
+    };
+    auto add_lu = [&](auto lu_c) {
+      add(lu_c, std::false_type());
+      add(lu_c, std::true_type());
+    };
+    add_lu(std::integral_constant<int, 1>());
+    add_lu(std::integral_constant<int, 2>());
+    add_lu(std::integral_constant<int, 4>());
     for (const void* k : ks) {
       const cudaError_t e =
           cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kLineSmemMax / 3));
@@ -764,11 +778,15 @@ cudaError_t launch_line_rows(const Op<T>& A, const LineFactors<T>& F, T* x, cons
     kern<<<rows, kLT, sm, s>>>(L, F, x, b, par, skip, eH, pitch_c);
     return cudaGetLastError();
   };
-  auto mode = [&](auto lu_c) -> cudaError_t {
+  auto mode5 = [&](auto lu_c, auto five_c) -> cudaError_t {
     constexpr int U = decltype(lu_c)::value;
-    if (zero_start) return go(k_line_zebra<T, U, LM_ZERO>);
-    if (eH) return go(k_line_zebra<T, U, LM_FUSED>);
-    return go(k_line_zebra<T, U, LM_PLAIN>);
+    constexpr bool F5 = decltype(five_c)::value;
+    if (zero_start) return go(k_line_zebra<T, U, LM_ZERO, F5>);
+    if (eH) return go(k_line_zebra<T, U, LM_FUSED, F5>);
+    return go(k_line_zebra<T, U, LM_PLAIN, F5>);
+  };
+  auto mode = [&](auto lu_c) -> cudaError_t {
+    return L.five_point ? mode5(lu_c, std::true_type()) : mode5(lu_c, std::false_type());
   };
   if (lu == 4) return mode(std::integral_constant<int, 4>());
   if (lu == 2) return mode(std::integral_constant<int, 2>());

@@ -10,16 +10,18 @@ namespace mg {
 
 static const double kPi = 3.14159265358979323846;
 
-// eps = det(J) J^-1 (s I) J^-T for J = [[a, b], [c, d]] (Eqs. 10, 12-15).
+// eps = det(J) J^-1 (s I) J^-T for J = [[a, b], [c, d]] (Eqs. 10, 12-15).  cross = 0: a map
+// whose Eq. 13 vanishes identically (J^T J diagonal); eps_xy is then written as the exact
+// zero instead of the rounding residue of the general formula.
 __device__ __forceinline__ void store_eps(double a, double b, double c, double d, double s,
                                           size_t k, double* D, double* exx, double* exy,
-                                          double* eyy, int* folded) {
+                                          double* eyy, int* folded, int cross = 1) {
   const double det = a * d - b * c;
   if (!(det > 0.0)) atomicOr(folded, 1);
   D[k] = det;
   const double sd = s / det;            // one division per node
   exx[k] = sd * (d * d + b * b);        // Eq. 12
-  exy[k] = sd * (-d * c - b * a);       // Eq. 13 = Eq. 14
+  exy[k] = cross ? sd * (-d * c - b * a) : 0.0;  // Eq. 13 = Eq. 14
   eyy[k] = sd * (c * c + a * a);        // Eq. 15
 }
 
@@ -36,7 +38,7 @@ __global__ void __launch_bounds__(256) k_eps_analytic(int kind, double p0, doubl
                                                       double hx, double hy,
                                                       const double* __restrict__ eps, int pitch,
                                                       double* D, double* exx, double* exy, double* eyy,
-                                                      int* folded) {
+                                                      int* folded, int cross) {
   __shared__ double colv[4][kEpsTile], rowv[2][kEpsTile];
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int i0 = blockIdx.x * kEpsTile, j0 = blockIdx.y * kEpsTile;
@@ -95,7 +97,7 @@ __global__ void __launch_bounds__(256) k_eps_analytic(int kind, double p0, doubl
         break;
     }
     const size_t k = (size_t)j * pitch + i;
-    store_eps(a, b, c, d, eps ? eps[k] : 1.0, k, D, exx, exy, eyy, folded);
+    store_eps(a, b, c, d, eps ? eps[k] : 1.0, k, D, exx, exy, eyy, folded, cross);
   }
 }
 
@@ -162,12 +164,13 @@ __global__ void k_eps_grid(int nx, int ny, int nyr, int periodic, double i2hx, d
   store_eps(a, b, c, d, eps ? eps[k] : 1.0, k, D, exx, exy, eyy, folded);
 }
 
-// Couplings of the symmetric conservative 9-point operator A = -L_h.
+// Couplings of the symmetric conservative 9-point operator A = -L_h.  five: eps_xy is zero
+// everywhere, so the NE / NW couplings are zero and written without reading it.
 __global__ void k_assemble_couplings(int nx, int ny, int nyr, int periodic, int pitch, double ihx2,
                                      double ihy2, double ixy4, const double* __restrict__ exx,
                                      const double* __restrict__ exy,
                                      const double* __restrict__ eyy, double* cE, double* cN,
-                                     double* cNE, double* cNW) {
+                                     double* cNE, double* cNW, int five) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= nx || j >= nyr) return;
@@ -179,8 +182,10 @@ __global__ void k_assemble_couplings(int nx, int ny, int nyr, int periodic, int 
   if (i + 1 <= nx - 1) e = -0.5 * (exx[k] + exx[k + 1]) * ihx2;
   if (has_up) {
     n = -0.5 * (eyy[k] + eyy[ku]) * ihy2;
-    if (i + 1 <= nx - 1) ne = -(exy[k + 1] + exy[ku]) * ixy4;  // to (i+1, j+1)
-    if (i >= 1) nw = (exy[k - 1] + exy[ku]) * ixy4;             // to (i-1, j+1)
+    if (!five) {
+      if (i + 1 <= nx - 1) ne = -(exy[k + 1] + exy[ku]) * ixy4;  // to (i+1, j+1)
+      if (i >= 1) nw = (exy[k - 1] + exy[ku]) * ixy4;             // to (i-1, j+1)
+    }
   }
   cE[k] = e;
   cN[k] = n;
@@ -188,11 +193,12 @@ __global__ void k_assemble_couplings(int nx, int ny, int nyr, int periodic, int 
   cNW[k] = nw;
 }
 
-// diag = -(sum of the 8 couplings) at unknowns (zero row sums), 1 at Dirichlet nodes.
+// diag = -(sum of the 8 couplings) at unknowns (zero row sums), 1 at Dirichlet nodes; the
+// zero NE / NW terms of a 5-point operator are left out of the sum (which they do not change).
 __global__ void k_assemble_diag(int nx, int ny, int nyr, int periodic, int pitch,
                                 const double* __restrict__ cE, const double* __restrict__ cN,
                                 const double* __restrict__ cNE, const double* __restrict__ cNW,
-                                double* diag, double* dinv) {
+                                double* diag, double* dinv, int five) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= nx || j >= nyr) return;
@@ -205,7 +211,8 @@ __global__ void k_assemble_diag(int nx, int ny, int nyr, int periodic, int pitch
   }
   const int jd = (j == 0) ? nyr - 1 : j - 1;
   const size_t ks = (size_t)jd * pitch + i;
-  const double s = cE[k] + cE[k - 1] + cN[k] + cN[ks] + cNE[k] + cNE[ks - 1] + cNW[k] + cNW[ks + 1];
+  double s = cE[k] + cE[k - 1] + cN[k] + cN[ks];
+  if (!five) s = s + cNE[k] + cNE[ks - 1] + cNW[k] + cNW[ks + 1];
   diag[k] = -s;
   dinv[k] = 1.0 / (-s);
 }
@@ -297,15 +304,15 @@ __global__ void k_op_to_f32(int nx, int nyr, int ps, int pd, const double* __res
                             const double* __restrict__ a1, const double* __restrict__ a2,
                             const double* __restrict__ a3, const double* __restrict__ a4,
                             const double* __restrict__ a5, float* b0, float* b1, float* b2,
-                            float* b3, float* b4, float* b5) {
+                            float* b3, float* b4, float* b5, int five) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= nx || j >= nyr) return;
   const size_t s = (size_t)j * ps + i, d = (size_t)j * pd + i;
   b0[d] = (float)a0[s];
   b1[d] = (float)a1[s];
-  b2[d] = (float)a2[s];
-  b3[d] = (float)a3[s];
+  b2[d] = five ? 0.0f : (float)a2[s];  // a 5-point operator's NE / NW are zero: not read
+  b3[d] = five ? 0.0f : (float)a3[s];
   b4[d] = (float)a4[s];
   b5[d] = (float)a5[s];
 }
@@ -376,7 +383,7 @@ cudaError_t launch_eps_analytic(int kind, const double* prm, int nx, int ny, int
   const int nyr = rows_stored(ny, periodic);
   dim3 b(32, 8), g((nx + kEpsTile - 1) / kEpsTile, (nyr + kEpsTile - 1) / kEpsTile);
   k_eps_analytic<<<g, b, 0, s>>>(kind, prm[0], prm[1], prm[2], prm[3], nx, nyr, x0, y0, hx, hy, eps, pitch,
-                                 D, exx, exy, eyy, folded);
+                                 D, exx, exy, eyy, folded, map_kind_five_point(kind, prm) ? 0 : 1);
   return cudaGetLastError();
 }
 
@@ -405,9 +412,9 @@ cudaError_t launch_assemble(const OpF64& A, double hx, double hy, const double* 
   dim3 b(32, 8);
   k_assemble_couplings<<<grid2(A.nx, nyr, b), b, 0, s>>>(
       A.nx, A.ny, nyr, A.periodic, A.pitch, 1.0 / (hx * hx), 1.0 / (hy * hy), 1.0 / (4.0 * hx * hy),
-      exx, exy, eyy, A.cE, A.cN, A.cNE, A.cNW);
+      exx, exy, eyy, A.cE, A.cN, A.cNE, A.cNW, A.five_point);
   k_assemble_diag<<<grid2(A.nx, nyr, b), b, 0, s>>>(A.nx, A.ny, nyr, A.periodic, A.pitch, A.cE,
-                                                    A.cN, A.cNE, A.cNW, A.diag, A.dinv);
+                                                    A.cN, A.cNE, A.cNW, A.diag, A.dinv, A.five_point);
   return cudaGetLastError();
 }
 
@@ -461,7 +468,7 @@ cudaError_t launch_op_to_f32(const OpF64& A, const OpF32& B, cudaStream_t s) {
   dim3 b(32, 8);
   k_op_to_f32<<<grid2(A.nx, nyr, b), b, 0, s>>>(A.nx, nyr, A.pitch, B.pitch, A.cE, A.cN, A.cNE,
                                                 A.cNW, A.diag, A.dinv, B.cE, B.cN, B.cNE, B.cNW,
-                                                B.diag, B.dinv);
+                                                B.diag, B.dinv, A.five_point);
   return cudaGetLastError();
 }
 

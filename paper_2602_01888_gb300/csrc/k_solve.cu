@@ -293,10 +293,12 @@ __global__ void __launch_bounds__(kNT) k_fcg_pq(Lvl<double> L, const TZ* __restr
     az = fma(L.cE[c0 + i - 1], (double)z[r0 + i - 1], az);
     az = fma(L.cN[c0 + i], (double)z[ru + i], az);
     az = fma(L.cN[cd + i], (double)z[rd + i], az);
-    az = fma(L.cNE[c0 + i], (double)z[ru + i + 1], az);
-    az = fma(L.cNE[cd + i - 1], (double)z[rd + i - 1], az);
-    az = fma(L.cNW[c0 + i], (double)z[ru + i - 1], az);
-    az = fma(L.cNW[cd + i + 1], (double)z[rd + i + 1], az);
+    if (!L.five_point) {
+      az = fma(L.cNE[c0 + i], (double)z[ru + i + 1], az);
+      az = fma(L.cNE[cd + i - 1], (double)z[rd + i - 1], az);
+      az = fma(L.cNW[c0 + i], (double)z[ru + i - 1], az);
+      az = fma(L.cNW[cd + i + 1], (double)z[rd + i + 1], az);
+    }
     az = fma(L.diag[k], (double)z[r0 + i], az);
     const double zz = is * (double)z[r0 + i];
     const double pn = first ? zz : fma(beta, p[k], zz);

@@ -21,6 +21,10 @@ template <typename T>
 struct Lvl {
   int nx, ny, nyr, periodic, pitch;
   const T *cE, *cN, *cNE, *cNW, *diag, *dinv;
+  // 1: the NE / NW couplings are zero at every node (a map without cross term, Eq. 13 = 0)
+  // and are neither read nor multiplied; adding a zero product changes no sum, so the
+  // results equal the 9-point form's.
+  int five_point;
 };
 
 __host__ __device__ inline int rows_stored(int ny, int periodic) { return periodic ? ny - 1 : ny; }
@@ -34,7 +38,8 @@ __device__ __forceinline__ bool is_unknown(const Lvl<T>& L, int i, int j) {
   return L.periodic || (j >= 1 && j <= L.ny - 2);
 }
 
-// Sum of the eight off-diagonal couplings times x at unknown (i, j).
+// Sum of the eight off-diagonal couplings times x at unknown (i, j) (four for a 5-point
+// operator: the diagonal terms are zero and skipped).
 template <typename T>
 __device__ __forceinline__ T offdiag(const Lvl<T>& L, const T* __restrict__ x, int i, int j) {
   const int p = L.pitch;
@@ -44,6 +49,7 @@ __device__ __forceinline__ T offdiag(const Lvl<T>& L, const T* __restrict__ x, i
   s = fma(L.cE[r0 + i - 1], x[r0 + i - 1], s);
   s = fma(L.cN[r0 + i], x[ru + i], s);
   s = fma(L.cN[rd + i], x[rd + i], s);
+  if (L.five_point) return s;
   s = fma(L.cNE[r0 + i], x[ru + i + 1], s);
   s = fma(L.cNE[rd + i - 1], x[rd + i - 1], s);
   s = fma(L.cNW[r0 + i], x[ru + i - 1], s);

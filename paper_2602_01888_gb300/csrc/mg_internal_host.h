@@ -134,7 +134,8 @@ namespace mg {
 mg_status problem_create(mg_ctx* ctx, const mg_grid_desc* grid, const mg_solve_opts& o,
                          mg_problem** out);
 mg_status check_map(const mg_grid_desc* g, const mg_map_desc* m);
-// Work enqueued between the assembly of the finest operator and its coarsening.
+// Work enqueued between the assembly of the finest operator and its coarsening.  It may zero
+// couplings; if it makes a NE / NW coupling nonzero it must clear lev[0]'s five_point.
 using FineHook = std::function<mg_status(mg_problem*, cudaStream_t)>;
 mg_status problem_enqueue_build(mg_problem* P, const mg_map_desc* map, const double* eps_phys,
                                 mg_mem_kind mem, cudaStream_t s, const FineHook* hook = nullptr);

@@ -17,6 +17,7 @@ template <typename T>
 struct Op {
   int nx, ny, periodic, pitch;
   T *cE, *cN, *cNE, *cNW, *diag, *dinv;
+  int five_point = 0;  // cNE, cNW are zero everywhere and are not read (see Lvl)
 };
 using OpF64 = Op<double>;
 using OpF32 = Op<float>;
@@ -35,14 +36,27 @@ inline Lvl<T> lvl_of(const Op<T>& A) {
   L.cNW = A.cNW;
   L.diag = A.diag;
   L.dinv = A.dinv;
+  L.five_point = A.five_point;
   return L;
 }
 
 inline OpF64 op_from(const mgk_op_f64& a) {
-  return OpF64{a.nx, a.ny, a.periodic, a.pitch, a.cE, a.cN, a.cNE, a.cNW, a.diag, a.dinv};
+  return OpF64{a.nx, a.ny, a.periodic, a.pitch, a.cE, a.cN, a.cNE, a.cNW, a.diag, a.dinv,
+               a.five_point ? 1 : 0};
 }
 inline OpF32 op_from(const mgk_op_f32& a) {
-  return OpF32{a.nx, a.ny, a.periodic, a.pitch, a.cE, a.cN, a.cNE, a.cNW, a.diag, a.dinv};
+  return OpF32{a.nx, a.ny, a.periodic, a.pitch, a.cE, a.cN, a.cNE, a.cNW, a.diag, a.dinv,
+               a.five_point ? 1 : 0};
+}
+
+// Whether an analytic map (kind and params as MG_MAP_* of mg.h: 0 identity, 1 sine warp,
+// 2 polar, 3 sinh, 4 affine) has no cross term: J^T J is diagonal, so Eq. 13 vanishes
+// identically and the finest operator is a 5-point stencil.  Identity, polar (Eq. 29) and
+// sinh stretching (Eq. 52) always; an affine map when its shear terms are zero.
+inline int map_kind_five_point(int kind, const double* prm) {
+  if (kind == 0 || kind == 2 || kind == 3) return 1;
+  if (kind == 4) return prm[1] == 0.0 && prm[2] == 0.0;
+  return 0;
 }
 
 inline int coarse_unknowns(int nx, int ny, int periodic) {

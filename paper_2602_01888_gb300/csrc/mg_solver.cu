@@ -335,6 +335,31 @@ mg_status line_prepare(mg_problem* P, cudaStream_t s) {
   return line_enqueue_factor(P, s);
 }
 
+// Whether a map's transformed tensor has no cross term (Eq. 13 vanishes identically; the
+// coefficient build then writes eps_xy = 0 exactly): its finest operator is a 5-point stencil.
+static int map_five_point(const mg_map_desc* map) {
+  return map->kind == MG_MAP_GRID ? 0 : map_kind_five_point(map->kind, map->params);
+}
+
+// A change of the finest operator's 5-point property changes which kernels a solve runs, so
+// graphs captured with the old one (the problem's own, and captured batches holding it) are
+// dropped once the work queued before the build has finished.
+static void set_five_point(mg_problem* P, int five, cudaStream_t s) {
+  if (P->lev[0].A.five_point == five) return;
+  if (!P->graphs.empty()) {
+    cudaStreamSynchronize(s);
+    cudaStreamSynchronize(P->ctx->stream);
+    for (auto& kv : P->graphs) {
+      cudaGraphExecDestroy(kv.second.exec);
+      cudaGraphDestroy(kv.second.graph);
+    }
+    P->graphs.clear();
+  }
+  batch_cache_drop(P->ctx, P);
+  P->lev[0].A.five_point = five;
+  P->lev[0].A32.five_point = five;
+}
+
 // Coefficients of the finest level from the map, then the Galerkin hierarchy and the
 // coarsest inverse, enqueued on stream s.  Reads host or device inputs.  The map and SPD
 // flags land in P->h_flags; problem_check_build reads them once s has been synchronised.
@@ -378,6 +403,7 @@ mg_status problem_enqueue_build(mg_problem* P, const mg_map_desc* map, const dou
     yp_d = P->p;
   }
   (void)nn;
+  set_five_point(P, map_five_point(map), s);
   CU(cudaMemsetAsync(P->flags, 0, 4 * sizeof(int), s));
   if (map->kind == MG_MAP_GRID) {
     CU(launch_eps_grid(nx, ny, g.periodic_y, hx, hy, xp_d, yp_d, map->jump_x, map->jump_y, eps_d, pt,
@@ -414,8 +440,9 @@ mg_status problem_enqueue_build(mg_problem* P, const mg_map_desc* map, const dou
     if (ls) return ls;
     P->setup_kernels += P->nlev - 1;
   }
-  // restore the scratch vectors used as staging
-  CU(cudaMemsetAsync(P->z, 0, 3 * np * sizeof(double), s));
+  // restore the scratch vectors used as staging (solves rely on their zero Dirichlet entries)
+  if (eps_phys || map->kind == MG_MAP_GRID || P->mirror)
+    CU(cudaMemsetAsync(P->z, 0, 3 * np * sizeof(double), s));
   CU(cudaEventRecord(P->evb1, s));
   CU(cudaMemcpyAsync(P->h_flags, P->flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
   return MG_OK;
@@ -542,6 +569,10 @@ extern "C" mg_status mg_setup_transform(mg_ctx* ctx, const mg_grid_desc* grid,
   *out = P;
   return MG_OK;
 }
+
+extern "C" int mg_map_five_point(const mg_map_desc* map) { return map ? map_five_point(map) : 0; }
+
+extern "C" int mg_problem_five_point(const mg_problem* P) { return P ? P->lev[0].A.five_point : -1; }
 
 extern "C" mg_status mg_update_transform(mg_problem* P, const mg_map_desc* map,
                                          const double* eps_phys, mg_mem_kind mem) {

@@ -65,7 +65,8 @@ class mg_solve_stats(C.Structure):
 
 class mgk_op_f64(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("periodic", C.c_int), ("pitch", C.c_int)] + \
-               [(n, C.c_void_p) for n in ("cE", "cN", "cNE", "cNW", "diag", "dinv")]
+               [(n, C.c_void_p) for n in ("cE", "cN", "cNE", "cNW", "diag", "dinv")] + \
+               [("five_point", C.c_int)]
 
 
 class mgk_op_f32(C.Structure):
@@ -111,6 +112,8 @@ _SIGS = {
     "mg_setup_transform": ([C.c_void_p, C.POINTER(mg_grid_desc), C.POINTER(mg_map_desc), C.c_void_p,
                             C.c_int, C.POINTER(mg_solve_opts), C.POINTER(C.c_void_p)], C.c_int),
     "mg_update_transform": ([C.c_void_p, C.POINTER(mg_map_desc), C.c_void_p, C.c_int], C.c_int),
+    "mg_map_five_point": ([C.POINTER(mg_map_desc)], C.c_int),
+    "mg_problem_five_point": ([C.c_void_p], C.c_int),
     "mg_batch_update_transform": ([C.c_void_p, C.c_int, C.POINTER(C.c_void_p), C.POINTER(mg_map_desc),
                                    C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_int)], C.c_int),
     "mg_problem_free": ([C.c_void_p], None),
@@ -337,6 +340,16 @@ def map_desc(mapspec, xp=None, yp=None) -> mg_map_desc:
     return m
 
 
+def map_five_point(mapspec) -> bool:
+    """Whether the library treats this map's finest operator as a 5-point stencil."""
+    m = map_desc(mapspec)
+    return bool(lib().mg_map_five_point(C.byref(m)))
+
+
+def problem_five_point(prob: int) -> bool:
+    return bool(lib().mg_problem_five_point(prob))
+
+
 def mg_setup_transform(ctx: int, grid, mapspec, eps_phys=None, opts: Optional[mg_solve_opts] = None,
                        xp=None, yp=None) -> int:
     """Arrays (xp, yp for a 'grid' map, eps_phys) are numpy (host) or CUDA tensors (device)."""
@@ -504,10 +517,12 @@ def mg_server_stop(srv: int) -> mg_serve_report:
 
 
 # ------------------------------------------------------------------ kernel-level (mgk_*)
-def op_struct(arrays, nx, ny, periodic, f32=False):
-    """mgk_op_f64/f32 from six pitched CUDA tensors (cE, cN, cNE, cNW, diag, dinv)."""
+def op_struct(arrays, nx, ny, periodic, f32=False, five_point=False):
+    """mgk_op_f64/f32 from six pitched CUDA tensors (cE, cN, cNE, cNW, diag, dinv);
+    five_point: the NE / NW arrays hold zeros and the kernels skip them."""
     s = (mgk_op_f32 if f32 else mgk_op_f64)()
     s.nx, s.ny, s.periodic, s.pitch = nx, ny, int(periodic), int(arrays[0].shape[-1])
+    s.five_point = int(bool(five_point))
     for name, a in zip(("cE", "cN", "cNE", "cNW", "diag", "dinv"), arrays):
         setattr(s, name, a.data_ptr())
     return s

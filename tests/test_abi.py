@@ -55,6 +55,36 @@ def test_struct_layouts_match_header(libmg):
     assert ctypes.sizeof(libmg.mg_solve_stats) == 8 + 3 * 8 + 256 * 8 + 8
 
 
+def test_kernel_operator_struct_matches_the_c_compiler(libmg, tmp_path):
+    """mgk_op_f64 / mgk_op_f32 as ctypes lays them out equal the C compiler's layout of
+    mg_kernels.h (size and the offset of every field)."""
+    import ctypes
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    fields = [f for f, _ in libmg.mgk_op_f64._fields_]
+    src = tmp_path / "layout.c"
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "mg_kernels.h"', "int main(void) {"]
+    for t in ("mgk_op_f64", "mgk_op_f32"):
+        lines.append(f'  printf("{t} size %zu\\n", sizeof({t}));')
+        for f in fields:
+            lines.append(f'  printf("{t} {f} %zu\\n", offsetof({t}, {f}));')
+    lines += ["  return 0;", "}"]
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        t, f, v = line.split()
+        got[(t, f)] = int(v)
+    for t, cls in (("mgk_op_f64", libmg.mgk_op_f64), ("mgk_op_f32", libmg.mgk_op_f32)):
+        assert got[(t, "size")] == ctypes.sizeof(cls)
+        for f in fields:
+            assert got[(t, f)] == getattr(cls, f).offset, (t, f)
+
+
 def test_no_oracle_on_the_product_path():
     """The package (product path) never imports the oracle."""
     pkg = os.path.join(ROOT, "paper_2602_01888_gb300")

@@ -80,6 +80,23 @@ __device__ __forceinline__ bool row_active(const Lvl<T>& L, int j) {
   return L.periodic || (j >= 1 && j <= L.ny - 2);
 }
 
+// Coarse-grid correction of the even rows (the rows that coincide with coarse rows): x += P eH
+// at their unknowns, before the first post-smoothing half-sweep solves the odd rows from them.
+// That half-sweep and the next one never read the old values of the rows they solve, so the
+// result equals adding P eH to every row and smoothing, with one pass over half the rows.
+// Grid: (columns / kLT, even rows).
+template <typename T>
+__global__ void __launch_bounds__(256) k_line_prolong_even(Lvl<T> L, T* __restrict__ x,
+                                                           const T* __restrict__ eH, int pitch_c,
+                                                           const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  const int jn = 2 * blockIdx.y;
+  const int c = 1 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (jn >= L.nyr || !row_active(L, jn) || c > L.nx - 2) return;
+  const size_t k = (size_t)jn * L.pitch + c;
+  x[k] = x[k] + prolong_even_row(eH, pitch_c, jn, c);
+}
+
 // Reduction multipliers of row blockIdx.x.  Shared memory: a, b, c of Np entries each
 // (padded rows).
 template <typename T>
@@ -161,15 +178,14 @@ __host__ __device__ inline size_t zebra_smem(int np) {
 // latency); resident CTAs per SM at the longest rows: 6 (FP32) / 3 (FP64), which is also
 // what shared memory allows there.
 // Right-hand-side variants of a half-sweep (compile-time, so the common one carries no extra
-// code): the iterate as stored; a zero iterate (nothing read); the stored iterate plus the
-// coarse correction interpolated on the fly at the (even) neighbour rows.  FIVE: a 5-point
-// operator (L.five_point), whose zero NE / NW couplings are neither loaded nor multiplied.
-enum LineMode : int { LM_PLAIN = 0, LM_ZERO = 1, LM_FUSED = 2 };
+// code): the iterate as stored; a zero iterate (nothing read).  FIVE: a 5-point operator
+// (L.five_point), whose zero NE / NW couplings are neither loaded nor multiplied.
+enum LineMode : int { LM_PLAIN = 0, LM_ZERO = 1 };
 
 template <typename T, int LU, int MODE, bool FIVE = false>
 __global__ void __launch_bounds__(kLT, sizeof(T) == 8 ? 3 : (LU <= 2 ? 6 : 5))
     k_line_zebra(Lvl<T> L, LineFactors<T> F, T* __restrict__ x, const T* __restrict__ b, int par,
-                 const int* __restrict__ skip, const T* __restrict__ eH, int pitch_c) {
+                 const int* __restrict__ skip) {
   if (skip && *skip) return;
   const int j = par + 2 * blockIdx.x;
   if (j >= L.nyr || !row_active(L, j)) return;
@@ -200,13 +216,7 @@ __global__ void __launch_bounds__(kLT, sizeof(T) == 8 ? 3 : (LU <= 2 ? 6 : 5))
         if constexpr (MODE == LM_ZERO) {  // the iterate is zero: every coupling term vanishes
           v[u] = __ldg(b + r0 + i);
         } else {
-          // neighbour rows' values, with the coarse correction added where it is fused
-          auto nb = [&](size_t row0, int jn, int c) -> T {
-            T val = __ldg(x + row0 + c);
-            if constexpr (MODE == LM_FUSED)
-              if (c >= 1 && c <= L.nx - 2 && row_active(L, jn)) val += prolong_even_row(eH, pitch_c, jn, c);
-            return val;
-          };
+          auto nb = [&](size_t row0, int, int c) -> T { return __ldg(x + row0 + c); };
           // couplings leaving the row, in the order of the point smoother's sum minus E/W
           T off = __ldg(L.cN + r0 + i) * nb(ru, ju, i);
           off = fma(__ldg(L.cN + rd + i), nb(rd, jd, i), off);
@@ -474,7 +484,7 @@ __host__ __device__ inline size_t part_smem(int np) {
 template <typename T, int SS, int LU, int MODE>
 __global__ void __launch_bounds__(kPP, kPartCtas)
     k_line_part(Lvl<T> L, LineFactors<T> F, T* __restrict__ x, const T* __restrict__ b, int par,
-                const int* __restrict__ skip, const T* __restrict__ eH, int pitch_c) {
+                const int* __restrict__ skip) {
   if (skip && *skip) return;
   const int j = par + 2 * blockIdx.x;
   if (j >= L.nyr || !row_active(L, j)) return;
@@ -513,12 +523,7 @@ __global__ void __launch_bounds__(kPP, kPartCtas)
         if constexpr (MODE == LM_ZERO) {
           v[u] = __ldg(b + r0 + i);
         } else {
-          auto nb = [&](size_t row0, int jn, int c) -> T {
-            T val = __ldg(x + row0 + c);
-            if constexpr (MODE == LM_FUSED)
-              if (c >= 1 && c <= L.nx - 2 && row_active(L, jn)) val += prolong_even_row(eH, pitch_c, jn, c);
-            return val;
-          };
+          auto nb = [&](size_t row0, int, int c) -> T { return __ldg(x + row0 + c); };
           T off = __ldg(L.cN + r0 + i) * nb(ru, ju, i);
           off = fma(__ldg(L.cN + rd + i), nb(rd, jd, i), off);
           if (!L.five_point) {
@@ -687,7 +692,6 @@ static cudaError_t zebra_attributes() {
       constexpr bool F5 = decltype(five_c)::value;
       ks.push_back((const void*)k_line_zebra<T, U, LM_PLAIN, F5>);
       ks.push_back((const void*)k_line_zebra<T, U, LM_ZERO, F5>);
-      ks.push_back((const void*)k_line_zebra<T, U, LM_FUSED, F5>);
     };
     auto add_lu = [&](auto lu_c) {
       add(lu_c, std::false_type());
@@ -716,7 +720,6 @@ static cudaError_t part_attributes() {
       constexpr int SS = decltype(ss)::value;
       ks.push_back((const void*)k_line_part<T, SS, 2, LM_PLAIN>);
       ks.push_back((const void*)k_line_part<T, SS, 2, LM_ZERO>);
-      ks.push_back((const void*)k_line_part<T, SS, 2, LM_FUSED>);
     };
     add(std::integral_constant<int, kPartMinNp / kPP>());
     add(std::integral_constant<int, kPartMaxNp / kPP>());
@@ -735,19 +738,16 @@ static cudaError_t part_attributes() {
 
 template <typename T>
 static cudaError_t launch_part_rows(const Lvl<T>& L, const LineFactors<T>& F, T* x, const T* b, int par,
-                                    int rows, const int* skip, cudaStream_t s, const T* eH, int pitch_c,
-                                    int zero_start) {
+                                    int rows, const int* skip, cudaStream_t s, int zero_start) {
   const cudaError_t ea = part_attributes<T>();
   if (ea != cudaSuccess) return ea;
   const size_t sm = part_smem<T>(F.np);
   auto go = [&](auto ss) -> cudaError_t {
     constexpr int SS = decltype(ss)::value;
     if (zero_start)
-      k_line_part<T, SS, 2, LM_ZERO><<<rows, kPP, sm, s>>>(L, F, x, b, par, skip, eH, pitch_c);
-    else if (eH)
-      k_line_part<T, SS, 2, LM_FUSED><<<rows, kPP, sm, s>>>(L, F, x, b, par, skip, eH, pitch_c);
+      k_line_part<T, SS, 2, LM_ZERO><<<rows, kPP, sm, s>>>(L, F, x, b, par, skip);
     else
-      k_line_part<T, SS, 2, LM_PLAIN><<<rows, kPP, sm, s>>>(L, F, x, b, par, skip, eH, pitch_c);
+      k_line_part<T, SS, 2, LM_PLAIN><<<rows, kPP, sm, s>>>(L, F, x, b, par, skip);
     return cudaGetLastError();
   };
   if (F.np == kPartMinNp) return go(std::integral_constant<int, kPartMinNp / kPP>());
@@ -761,10 +761,17 @@ cudaError_t launch_line_rows(const Op<T>& A, const LineFactors<T>& F, T* x, cons
   if (!line_supported<T>(A.nx) || F.np != line_np(A.nx)) return cudaErrorInvalidValue;
   if (eH && (par != 1 || (A.nx - 1) % 2 || (A.ny - 1) % 2)) return cudaErrorInvalidValue;
   const Lvl<T> L = lvl_of(A);
+  if (eH) {  // the coarse correction enters through the even rows the odd ones are solved from
+    const int erows = (L.nyr + 1) / 2;
+    const dim3 g((unsigned)((A.nx - 2 + kLT - 1) / kLT), (unsigned)erows);
+    k_line_prolong_even<T><<<g, kLT, 0, s>>>(L, x, eH, pitch_c, skip);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   if (line_partitioned(F.np)) {
     const int rows = (L.nyr - par + 1) / 2;
     if (rows <= 0) return cudaSuccess;
-    return launch_part_rows<T>(L, F, x, b, par, rows, skip, s, eH, pitch_c, zero_start);
+    return launch_part_rows<T>(L, F, x, b, par, rows, skip, s, zero_start);
   }
   const size_t sm = zebra_smem<T>(F.np);
   const int rows = (L.nyr - par + 1) / 2;
@@ -775,14 +782,13 @@ cudaError_t launch_line_rows(const Op<T>& A, const LineFactors<T>& F, T* x, cons
   const cudaError_t ea = zebra_attributes<T>();
   if (ea != cudaSuccess) return ea;
   auto go = [&](auto kern) -> cudaError_t {
-    kern<<<rows, kLT, sm, s>>>(L, F, x, b, par, skip, eH, pitch_c);
+    kern<<<rows, kLT, sm, s>>>(L, F, x, b, par, skip);
     return cudaGetLastError();
   };
   auto mode5 = [&](auto lu_c, auto five_c) -> cudaError_t {
     constexpr int U = decltype(lu_c)::value;
     constexpr bool F5 = decltype(five_c)::value;
     if (zero_start) return go(k_line_zebra<T, U, LM_ZERO, F5>);
-    if (eH) return go(k_line_zebra<T, U, LM_FUSED, F5>);
     return go(k_line_zebra<T, U, LM_PLAIN, F5>);
   };
   auto mode = [&](auto lu_c) -> cudaError_t {

@@ -36,10 +36,10 @@ template <typename T>
 cudaError_t launch_line_factor(const Op<T>& A, const LineFactors<T>& F, cudaStream_t s);
 
 // One half-sweep: solve every row j with j mod 2 == par for its unknowns, in place in x.
-// eH (nullable, par == 1 only): coarse correction (row pitch pitch_c) added on the fly to
-// the even neighbour rows the half-sweep reads, as bilinear prolongation would have added it
-// (the solved rows' old values are never read, so the correction need not be stored when
-// the next half-sweep solves the even rows).  zero_start: x is zero at every unknown.
+// eH (nullable, par == 1 only): coarse correction (row pitch pitch_c), added by bilinear
+// prolongation to the even rows first (the rows the half-sweep reads); the odd rows' old
+// values are never read, so they need not be corrected, and the even rows are solved again
+// by the next half-sweep.  zero_start: x is zero at every unknown.
 template <typename T>
 cudaError_t launch_line_rows(const Op<T>& A, const LineFactors<T>& F, T* x, const T* b, int par,
                              const int* skip, cudaStream_t s, const T* eH = nullptr, int pitch_c = 0,

@@ -111,9 +111,9 @@ cudaError_t emit_vcycle(const VLevels<T>& V, int smoother, int nu1, int nu2, dou
   if (smoother == MG_SMOOTH_XLINE) {
     // zebra x-line Gauss-Seidel on every level but the coarsest.  A coarse level's iterate
     // starts at zero, so with pre-smoothing its first half-sweep reads no iterate and the
-    // restriction need not clear it; the coarse correction is interpolated inside the first
-    // post-smoothing half-sweep instead of being added by a separate pass (see
-    // launch_line_rows): identical values, two fewer passes over each level's iterate.
+    // restriction need not clear it; the coarse correction is added to the even rows only,
+    // just before the first post-smoothing half-sweep solves the odd rows from them (see
+    // launch_line_rows): identical values, one pass over half of each level's iterate.
     const bool zs = nu1 > 0;
     for (int l = 0; l < L - 1; ++l) {
       const int zero = l == 0 ? (x0_zero && zs) : zs;

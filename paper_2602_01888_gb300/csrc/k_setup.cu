@@ -195,6 +195,8 @@ __global__ void k_assemble_couplings(int nx, int ny, int nyr, int periodic, int 
 
 // diag = -(sum of the 8 couplings) at unknowns (zero row sums), 1 at Dirichlet nodes; the
 // zero NE / NW terms of a 5-point operator are left out of the sum (which they do not change).
+// dinv = 1 / diag unless dinv is null (a mixed-precision hierarchy takes its FP32 reciprocal
+// from the FP32 diagonal instead and never reads an FP64 one).
 __global__ void k_assemble_diag(int nx, int ny, int nyr, int periodic, int pitch,
                                 const double* __restrict__ cE, const double* __restrict__ cN,
                                 const double* __restrict__ cNE, const double* __restrict__ cNW,
@@ -206,7 +208,7 @@ __global__ void k_assemble_diag(int nx, int ny, int nyr, int periodic, int pitch
   const bool unk = (i >= 1 && i <= nx - 2) && (periodic || (j >= 1 && j <= ny - 2));
   if (!unk) {
     diag[k] = 1.0;
-    dinv[k] = 1.0;
+    if (dinv) dinv[k] = 1.0;
     return;
   }
   const int jd = (j == 0) ? nyr - 1 : j - 1;
@@ -214,7 +216,7 @@ __global__ void k_assemble_diag(int nx, int ny, int nyr, int periodic, int pitch
   double s = cE[k] + cE[k - 1] + cN[k] + cN[ks];
   if (!five) s = s + cNE[k] + cNE[ks - 1] + cNW[k] + cNW[ks + 1];
   diag[k] = -s;
-  dinv[k] = 1.0 / (-s);
+  if (dinv) dinv[k] = 1.0 / (-s);
 }
 
 __global__ void k_rhs(int nx, int ny, int nyr, int periodic, int pitch,
@@ -250,8 +252,10 @@ __device__ __forceinline__ T fine_entry(const Lvl<T>& F, int fi, int fj, int di,
 // A_H = (1/4) P^T A_h P: for each coarse unknown I, row(I, I+o) = (1/4) sum_k sum_l
 // P(k, I) A(k, l) P(l, I+o) over fine k in the 3x3 support of I and the 9 stencil
 // neighbours l of k.  Every loop is unrolled so the bilinear weights are constants and
-// only the (k, l, o) triples with non-zero weight remain (324 multiply-adds).
-template <typename T>
+// only the (k, l, o) triples with non-zero weight remain (169 multiply-adds).  FIVE: the fine
+// operator is 5-point (F.five_point): its diagonal entries are zero and their products, which
+// would add zeros, are skipped (105 multiply-adds, the same sums).
+template <typename T, bool FIVE>
 __global__ void k_galerkin(Lvl<T> F, int nxc, int nyc, int nyrc, int pitchc, T* cE, T* cN, T* cNE,
                            T* cNW, T* diag, T* dinv) {
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
@@ -281,6 +285,7 @@ __global__ void k_galerkin(Lvl<T> F, int nxc, int nyc, int nyrc, int pitchc, T* 
       for (int lj = -1; lj <= 1; ++lj)
 #pragma unroll
         for (int li = -1; li <= 1; ++li) {
+          if (FIVE && li != 0 && lj != 0) continue;
           const T a = fine_entry(F, fi, fj, li, lj);
 #pragma unroll
           for (int oj = -1; oj <= 1; ++oj)
@@ -304,7 +309,7 @@ __global__ void k_op_to_f32(int nx, int nyr, int ps, int pd, const double* __res
                             const double* __restrict__ a1, const double* __restrict__ a2,
                             const double* __restrict__ a3, const double* __restrict__ a4,
                             const double* __restrict__ a5, float* b0, float* b1, float* b2,
-                            float* b3, float* b4, float* b5, int five) {
+                            float* b3, float* b4, float* b5, int five, int dinv_f32) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= nx || j >= nyr) return;
@@ -313,8 +318,9 @@ __global__ void k_op_to_f32(int nx, int nyr, int ps, int pd, const double* __res
   b1[d] = (float)a1[s];
   b2[d] = five ? 0.0f : (float)a2[s];  // a 5-point operator's NE / NW are zero: not read
   b3[d] = five ? 0.0f : (float)a3[s];
-  b4[d] = (float)a4[s];
-  b5[d] = (float)a5[s];
+  const float dg = (float)a4[s];
+  b4[d] = dg;
+  b5[d] = dinv_f32 ? 1.0f / dg : (float)a5[s];  // dinv_f32: reciprocal of the FP32 diagonal
 }
 
 // Dense matrix of the coarsest level's unknowns, inverted by Gauss-Jordan elimination
@@ -407,14 +413,15 @@ cudaError_t launch_eps_grid(int nx, int ny, int periodic, double hx, double hy, 
 }
 
 cudaError_t launch_assemble(const OpF64& A, double hx, double hy, const double* exx,
-                            const double* exy, const double* eyy, cudaStream_t s) {
+                            const double* exy, const double* eyy, cudaStream_t s, bool dinv) {
   const int nyr = rows_stored(A.ny, A.periodic);
   dim3 b(32, 8);
   k_assemble_couplings<<<grid2(A.nx, nyr, b), b, 0, s>>>(
       A.nx, A.ny, nyr, A.periodic, A.pitch, 1.0 / (hx * hx), 1.0 / (hy * hy), 1.0 / (4.0 * hx * hy),
       exx, exy, eyy, A.cE, A.cN, A.cNE, A.cNW, A.five_point);
   k_assemble_diag<<<grid2(A.nx, nyr, b), b, 0, s>>>(A.nx, A.ny, nyr, A.periodic, A.pitch, A.cE,
-                                                    A.cN, A.cNE, A.cNW, A.diag, A.dinv, A.five_point);
+                                                    A.cN, A.cNE, A.cNW, A.diag, dinv ? A.dinv : nullptr,
+                                                    A.five_point);
   return cudaGetLastError();
 }
 
@@ -431,8 +438,12 @@ template <typename T>
 cudaError_t launch_galerkin(const Op<T>& F, const Op<T>& C, cudaStream_t s) {
   const int nyrc = rows_stored(C.ny, C.periodic);
   dim3 b(32, 4);
-  k_galerkin<T><<<grid2(C.nx, nyrc, b), b, 0, s>>>(lvl_of(F), C.nx, C.ny, nyrc, C.pitch, C.cE, C.cN,
-                                                   C.cNE, C.cNW, C.diag, C.dinv);
+  if (F.five_point)
+    k_galerkin<T, true><<<grid2(C.nx, nyrc, b), b, 0, s>>>(lvl_of(F), C.nx, C.ny, nyrc, C.pitch, C.cE,
+                                                           C.cN, C.cNE, C.cNW, C.diag, C.dinv);
+  else
+    k_galerkin<T, false><<<grid2(C.nx, nyrc, b), b, 0, s>>>(lvl_of(F), C.nx, C.ny, nyrc, C.pitch, C.cE,
+                                                            C.cN, C.cNE, C.cNW, C.diag, C.dinv);
   return cudaGetLastError();
 }
 template cudaError_t launch_galerkin<double>(const OpF64&, const OpF64&, cudaStream_t);
@@ -463,12 +474,12 @@ cudaError_t launch_op_to_f64(const OpF32& A, const OpF64& B, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_op_to_f32(const OpF64& A, const OpF32& B, cudaStream_t s) {
+cudaError_t launch_op_to_f32(const OpF64& A, const OpF32& B, cudaStream_t s, bool dinv_f32) {
   const int nyr = rows_stored(A.ny, A.periodic);
   dim3 b(32, 8);
   k_op_to_f32<<<grid2(A.nx, nyr, b), b, 0, s>>>(A.nx, nyr, A.pitch, B.pitch, A.cE, A.cN, A.cNE,
                                                 A.cNW, A.diag, A.dinv, B.cE, B.cN, B.cNE, B.cNW,
-                                                B.diag, B.dinv, A.five_point);
+                                                B.diag, B.dinv, A.five_point, dinv_f32 ? 1 : 0);
   return cudaGetLastError();
 }
 

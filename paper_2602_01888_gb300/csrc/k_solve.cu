@@ -14,12 +14,38 @@
 
 namespace mg {
 
-constexpr int kNT = 256;
+constexpr int kNT = kRedThreads;
+// kRedBlocks over the 152 SMs: a loop with at most 32 registers a thread runs in one wave.
+constexpr int kRedBlocksPerSM = 8;
 constexpr int kMaxVerifyFail = 4;
 
 #define NODE_LOOP(L)                                                            \
   for (int j = blockIdx.y; j < (L).nyr; j += gridDim.y)                         \
     for (int i = blockIdx.x * kNT + threadIdx.x; i < (L).nx; i += gridDim.x * kNT)
+
+// Elementwise loops that move few bytes per node, over the rows of one column (red_grid covers
+// every column: grids wider than kRedBlocks x kNT are rejected at set-up), B rows at a time:
+// load(u, j) fills slot u from row j (clamped into range, so the loads need no guard and all
+// of a batch's loads are in flight together), then use(u, j) consumes the slots of the rows
+// that exist, in increasing row order (the order of NODE_LOOP, so sums come out identical).
+// With about two hundred rows per thread, one row's loads at a time leave these loops bound
+// by load latency.
+template <int B, typename Load, typename Use>
+__device__ __forceinline__ void rows_batched(int nyr, Load load, Use use) {
+  const int g = gridDim.y;
+  for (int j0 = blockIdx.y; j0 < nyr; j0 += B * g) {
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+      const int j = j0 + u * g;
+      load(u, j < nyr ? j : j0);
+    }
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+      const int j = j0 + u * g;
+      if (j < nyr) use(u, j);
+    }
+  }
+}
 
 __device__ __forceinline__ unsigned nblocks() { return gridDim.x * gridDim.y; }
 __device__ __forceinline__ unsigned bid() { return blockIdx.y * gridDim.x + blockIdx.x; }
@@ -239,7 +265,7 @@ __global__ void k_iter_inc(SolveState* st) {
 // ---- flexible CG (FCG(1)): p = z + beta p_old, beta = -(z . q_old) / (p_old . q_old);
 // alpha = (p . r) / (p . q); x += alpha p; r -= alpha q.
 template <typename TZ>
-__global__ void __launch_bounds__(kNT) k_fcg_zq(Lvl<double> L, const TZ* __restrict__ z, int zp,
+__global__ void __launch_bounds__(kNT, kRedBlocksPerSM) k_fcg_zq(Lvl<double> L, const TZ* __restrict__ z, int zp,
                                                 const double* __restrict__ q, SolveState* st,
                                                 double* part) {
   if (st->done || st->it == 0) {
@@ -251,11 +277,20 @@ __global__ void __launch_bounds__(kNT) k_fcg_zq(Lvl<double> L, const TZ* __restr
   const double is = (sizeof(TZ) == 4) ? st->inv_scale_r32 : 1.0;
   const bool f32ok = pow2_fits_f32(is);
   double s = 0.0;
-  NODE_LOOP(L) {
-    if (is_unknown(L, i, j))
-      s += (sizeof(TZ) == 4 ? from_f32_scaled((float)z[(size_t)j * zp + i], is, f32ok)
-                            : (double)z[(size_t)j * zp + i]) *
-           q[(size_t)j * L.pitch + i];
+  const int i = blockIdx.x * kNT + threadIdx.x;
+  if (i < L.nx) {
+    TZ zv[4];
+    double qv[4];
+    rows_batched<4>(
+        L.nyr,
+        [&](int u, int j) {
+          zv[u] = z[(size_t)j * zp + i];
+          qv[u] = q[(size_t)j * L.pitch + i];
+        },
+        [&](int u, int j) {
+          if (is_unknown(L, i, j))
+            s += (sizeof(TZ) == 4 ? from_f32_scaled((float)zv[u], is, f32ok) : (double)zv[u]) * qv[u];
+        });
   }
   const double a0 = block_sum<kNT>(s, sh);
   if (threadIdx.x == 0) part[bid()] = a0;
@@ -328,18 +363,28 @@ __global__ void __launch_bounds__(kNT) k_fcg_pq(Lvl<double> L, const TZ* __restr
 
 // Split form for an FP32 z (the fused form would widen nine FP32 neighbours per node on
 // the FP64 pipe): p = inv_scale z + beta p elementwise, then q = A p with the FP64 stencil.
-__global__ void __launch_bounds__(kNT) k_fcg_p32(Lvl<double> L, const float* __restrict__ z, int zp,
+__global__ void __launch_bounds__(kNT, kRedBlocksPerSM) k_fcg_p32(Lvl<double> L, const float* __restrict__ z, int zp,
                                                  double* __restrict__ p, const SolveState* st) {
   if (st->done) return;
   const double is = st->inv_scale_r32;
   const bool f32ok = pow2_fits_f32(is);
   const double beta = st->beta;
   const bool first = (st->it == 0);
-  NODE_LOOP(L) {
-    if (!is_unknown(L, i, j)) continue;
-    const size_t k = (size_t)j * L.pitch + i;
-    const double zz = from_f32_scaled(z[(size_t)j * zp + i], is, f32ok);
-    p[k] = first ? zz : fma(beta, p[k], zz);
+  const int i = blockIdx.x * kNT + threadIdx.x;
+  if (i < L.nx) {
+    float zv[4];
+    double pv[4];
+    rows_batched<4>(
+        L.nyr,
+        [&](int u, int j) {
+          zv[u] = z[(size_t)j * zp + i];
+          pv[u] = p[(size_t)j * L.pitch + i];
+        },
+        [&](int u, int j) {
+          if (!is_unknown(L, i, j)) return;
+          const double zz = from_f32_scaled(zv[u], is, f32ok);
+          p[(size_t)j * L.pitch + i] = first ? zz : fma(beta, pv[u], zz);
+        });
   }
 }
 

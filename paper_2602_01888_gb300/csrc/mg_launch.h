@@ -77,14 +77,17 @@ cudaError_t launch_eps_grid(int nx, int ny, int periodic, double hx, double hy, 
 cudaError_t launch_mirror_eps(int nx, int n, int ps, const double* D0, const double* exx0,
                               const double* exy0, const double* eyy0, int pd, double* D, double* exx,
                               double* exy, double* eyy, cudaStream_t s);
+// dinv = false: A.dinv is not written (a mixed-precision hierarchy's FP64 level 0, whose
+// reciprocal diagonal is taken in FP32 by launch_op_to_f32 with dinv_f32).
 cudaError_t launch_assemble(const OpF64& A, double hx, double hy, const double* exx,
-                            const double* exy, const double* eyy, cudaStream_t s);
+                            const double* exy, const double* eyy, cudaStream_t s, bool dinv = true);
 cudaError_t launch_rhs(const OpF64& A, const double* rho, int rho_pitch, const double* D, double* b,
                        cudaStream_t s);
 template <typename T>
 cudaError_t launch_galerkin(const Op<T>& F, const Op<T>& C, cudaStream_t s);
 cudaError_t launch_op_to_f64(const OpF32& A, const OpF64& B, cudaStream_t s);
-cudaError_t launch_op_to_f32(const OpF64& A, const OpF32& B, cudaStream_t s);
+// dinv_f32: B.dinv = 1 / B.diag in FP32 instead of the rounded A.dinv (A.dinv is not read).
+cudaError_t launch_op_to_f32(const OpF64& A, const OpF32& B, cudaStream_t s, bool dinv_f32 = false);
 cudaError_t launch_coarse_factor(const OpF64& A, double* inv, int* status, cudaStream_t s);
 
 // ---- cycle (k_cycle.cu).  `skip` (nullable device int): when *skip != 0 the kernel

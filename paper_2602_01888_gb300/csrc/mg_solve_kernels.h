@@ -8,6 +8,7 @@
 namespace mg {
 
 constexpr int kRedBlocks = 1216;  // upper bound of blocks (and partial sums) per reduction
+constexpr int kRedThreads = 256;  // threads per block of the finest-level loops (one column each)
 
 // Per-solve arguments read by the kernels through device memory, so one captured graph
 // serves every call: the caller's arrays (contiguous rows of user_pitch elements).

@@ -418,7 +418,9 @@ mg_status problem_enqueue_build(mg_problem* P, const mg_map_desc* map, const dou
     exy = P->z;
     eyy = P->p;
   }
-  CU(launch_assemble(F.A, hx, hy, exx, exy, eyy, s));
+  // a mixed hierarchy never runs an FP64 smoother: its level-0 reciprocal diagonal is the FP32
+  // one, taken from the FP32 diagonal, so the FP64 division per node is skipped
+  CU(launch_assemble(F.A, hx, hy, exx, exy, eyy, s, !P->mixed));
   if (hook && *hook) {  // a caller's change of the finest operator before coarsening
     mg_status hs = (*hook)(P, s);
     if (hs) return hs;
@@ -428,7 +430,7 @@ mg_status problem_enqueue_build(mg_problem* P, const mg_map_desc* map, const dou
   } else {
     // the FP32 cycle only needs FP32 coarse operators: Galerkin products in FP32, and the
     // coarsest one widened to FP64 for its dense inverse
-    CU(launch_op_to_f32(F.A, F.A32, s));
+    CU(launch_op_to_f32(F.A, F.A32, s, true));
     for (int l = 1; l < P->nlev; ++l) CU(launch_galerkin<float>(P->lev[l - 1].A32, P->lev[l].A32, s));
     if (P->nlev > 1) CU(launch_op_to_f64(P->lev[P->nlev - 1].A32, P->lev[P->nlev - 1].A, s));
   }
@@ -475,6 +477,8 @@ static mg_status check_grid(const mg_grid_desc* g, int coarse_max, int* nlev, in
     return set_error(MG_ERR_SIZE, "periodic y needs an even number of rows (ny-1=%d)", g->ny - 1);
   if ((size_t)g->nx * g->ny > ((size_t)1 << 31))
     return set_error(MG_ERR_SIZE, "grid larger than 2^31 nodes");
+  if (g->nx > kRedBlocks * kRedThreads)  // the finest-level loops give each thread one column
+    return set_error(MG_ERR_SIZE, "grid wider than %d nodes", kRedBlocks * kRedThreads);
   if (coarse_max < 1 || coarse_max > kCoarseMax)
     return set_error(MG_ERR_ARG, "coarse_max must be in [1, %d]", kCoarseMax);
   *nlev = count_levels(g->nx, g->ny, g->periodic_y, coarse_max, nxs, nys);

@@ -55,7 +55,8 @@ def test_profiled_traffic_against_the_algorithmic_bytes():
     four launches (2-3.5x their share of a sweep's bytes); the marching and line kernels move
     their algorithmic bytes (0.9-1.2x).  Scaling to another level size goes by node count."""
     band = {"k_gs_colour<double>": (2.0, 3.5), "k_gs_colour<float>": (2.0, 3.5),
-            "k_smooth_march<float> w240/2": (0.9, 1.2), "k_line_zebra<float>": (0.9, 1.2)}
+            "k_smooth_march<float> w240/2": (0.9, 1.2), "k_line_zebra<float>": (0.9, 1.2),
+            "k_line_zebra<float> 5-point": (0.9, 1.2)}
     entries = bench._traffic_table()
     assert entries
     for e in entries:
@@ -69,7 +70,8 @@ def test_profiled_traffic_against_the_algorithmic_bytes():
         algo = {"k_gs_colour<double>": 64.0 * nodes / 4,       # a sweep's 8 FP64 arrays over 4 launches
                 "k_gs_colour<float>": 32.0 * nodes / 4,
                 "k_smooth_march<float> w240/2": 32.0 * nodes,  # two sweeps, each array once
-                "k_line_zebra<float>": 14 * 4.0 * nodes / 2}[kern]
+                "k_line_zebra<float>": 14 * 4.0 * nodes / 2,
+                "k_line_zebra<float> 5-point": 10 * 4.0 * nodes / 2}[kern]
         lo, hi = band[kern]
         assert lo <= traffic / algo <= hi, (kern, traffic / algo)
         assert bench.profiled_traffic(kern, 2 * nx, rows) == pytest.approx(2 * traffic)

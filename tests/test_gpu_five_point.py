@@ -129,6 +129,30 @@ def test_five_point_kernels_equal_the_nine_point_forms(libmg, cuda, case, prec):
     assert not torch.equal(out["5"][0], x0)  # the sweeps did change the iterate
 
 
+@pytest.mark.parametrize("case", ["annulus_65", "sinh_65", "identity_33x17"])
+def test_five_point_galerkin_equals_the_nine_point_form(libmg, cuda, case):
+    """The coarse operator from a 5-point fine operator skips the zero products: same arrays."""
+    torch = cuda
+    inst = CASES[case]()
+    g = _grid_of(inst)
+    pitch = (g.nx + 31) // 32 * 32
+    st, ops = _operator(libmg, torch, inst, False, pitch)
+    nc, mc = (g.nx - 1) // 2 + 1, (g.ny - 1) // 2 + 1
+    mrc = mc - 1 if g.periodic_y else mc
+    pc = (nc + 31) // 32 * 32
+    out = {}
+    for five in (False, True):
+        fine = libmg.op_struct(ops, g.nx, g.ny, g.periodic_y, five_point=five)
+        co = [torch.full((mrc, pc), 3.0, dtype=torch.float64, device="cuda") for _ in range(6)]
+        cs = libmg.op_struct(co, nc, mc, g.periodic_y)
+        libmg.mgk("mgk_galerkin", C.byref(fine), C.byref(cs), _stream(torch))
+        torch.cuda.synchronize()
+        out[five] = [a[:, :nc] for a in co]
+    for a, b in zip(out[False], out[True]):
+        assert torch.equal(a, b)
+    assert torch.count_nonzero(out[True][2]).item() > 0  # the coarse level is 9-point
+
+
 def _ref(oracle, inst):
     P = oracle.prepare(inst)
     phi, it, hist = oracle.pcg_solve(P.A, P.b, P.phi0, rtol=0.0, max_iters=400, stagnate=10)

@@ -205,7 +205,10 @@ int mg_problem_five_point(const mg_problem *prob);
  * Solve for phi.  rho_phys: rho' at every node (only unknowns are used; rho = rho' det J,
  * Eq. 11).  bc: node array whose Dirichlet-side values are the boundary data (NULL = 0).
  * phi: out = solution at every node (Dirichlet sides = bc); in = initial guess of the
- * unknowns when opts->warm_start.  All three arrays have the memory kind `mem`.
+ * unknowns when opts->warm_start.  All three arrays have the memory kind `mem`.  Host arrays
+ * that are all page-locked (cudaHostAlloc, cudaHostRegister) are read and written in place by
+ * the solve's first and last kernels over the host link; otherwise they are copied through
+ * device staging arrays.  Either way the call returns once phi is written.
  * Errors: MG_ERR_NOT_CONVERGED (phi and stats still written), MG_ERR_DIVERGED, MG_ERR_ARG,
  * MG_ERR_CUDA.
  */

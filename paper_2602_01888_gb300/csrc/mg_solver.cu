@@ -1129,6 +1129,17 @@ extern "C" mg_status mg_cycle_time(mg_problem* P, const mg_solve_opts* opts, int
   return MG_OK;
 }
 
+// Device address of a page-locked (cudaHostAlloc / cudaHostRegister) host array, through
+// which kernels read and write it over the host link; nullptr for pageable memory.
+static double* pinned_view(const double* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();  // an unknown pointer leaves a (non-sticky) error: clear it
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? static_cast<double*>(a.devicePointer) : nullptr;
+}
+
 extern "C" mg_status mg_solve(mg_problem* P, const double* rho_phys, const double* bc, double* phi,
                               mg_mem_kind mem, const mg_solve_opts* opts, mg_solve_stats* stats) {
   if (!P || !rho_phys || !phi) return set_error(MG_ERR_ARG, "mg_solve: NULL argument");
@@ -1141,7 +1152,23 @@ extern "C" mg_status mg_solve(mg_problem* P, const double* rho_phys, const doubl
   const size_t n = (size_t)P->user.nx * rows_stored(P->user.ny, P->user.periodic_y);
   const double *rho = rho_phys, *bcd = bc, *pin = phi;
   double* pout = phi;
+  bool staged = false;
   if (mem == MG_MEM_HOST) {
+    // page-locked arrays: the solve's first kernel reads rho, bc (and a warm start) and its
+    // last kernel writes phi in place over the host link, each once, instead of a copy to and
+    // from staging arrays around the solve
+    double* rv = pinned_view(rho_phys);
+    double* bv = bc ? pinned_view(bc) : nullptr;
+    double* pv = pinned_view(phi);
+    if (rv && (!bc || bv) && pv) {
+      rho = rv;
+      bcd = bv;
+      pin = pout = pv;
+      mem = MG_MEM_DEVICE;
+    }
+  }
+  if (mem == MG_MEM_HOST) {
+    staged = true;
     if (!P->stage) {
       P->stage = palloc<double>(P, 3 * n);
       if (!P->stage) return set_error(MG_ERR_OOM, "device memory budget exhausted (staging)");
@@ -1159,8 +1186,7 @@ extern "C" mg_status mg_solve(mg_problem* P, const double* rho_phys, const doubl
   }
   st = enqueue_solve(P, o, rho, bcd, pin, pout, s);
   if (st) return st;
-  if (mem == MG_MEM_HOST)
-    CU(cudaMemcpyAsync(phi, pout, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (staged) CU(cudaMemcpyAsync(phi, pout, n * sizeof(double), cudaMemcpyDeviceToHost, s));
   CU(cudaStreamSynchronize(s));
   return finish_solve(P, stats);
 }

@@ -91,6 +91,33 @@ def test_host_and_device_memory_give_identical_results(libmg, ctx, cuda):
     assert np.array_equal(phi_h, phi_h2)
 
 
+def test_page_locked_host_arrays_are_used_in_place(libmg, ctx, cuda):
+    """Page-locked host arrays (read and written by the kernels over the host link), pageable
+    ones (staged) and device arrays give the same solution, cold and warm started."""
+    torch = cuda
+    inst = I.annulus_log(129)
+    opts = libmg.make_opts("mixed", "fcg", rtol=1e-10, smoother="xline", nu1=1, nu2=1)
+    prob = libmg.Problem(ctx, inst, opts)
+    rho, bc = np.ascontiguousarray(inst.rho_phys), np.ascontiguousarray(inst.bc)
+    pin = lambda a: torch.from_numpy(np.array(a)).pin_memory()
+    rho_p, bc_p = pin(rho), pin(bc)
+    phi_p = torch.zeros(inst.grid.shape, dtype=torch.float64).pin_memory()
+    phi_h = np.zeros(inst.grid.shape)
+    prob.solve(rho=rho, bc=bc, phi=phi_h)
+    libmg.mg_solve(prob.h, rho_p.numpy(), bc_p.numpy(), phi_p.numpy(), opts)
+    phi_d = torch.zeros(inst.grid.shape, dtype=torch.float64, device="cuda")
+    libmg.mg_solve(prob.h, torch.from_numpy(rho).cuda(), torch.from_numpy(bc).cuda(), phi_d, opts)
+    torch.cuda.synchronize()
+    assert np.array_equal(phi_p.numpy(), phi_h)
+    assert np.array_equal(phi_d.cpu().numpy(), phi_h)
+    warm = libmg.make_opts("mixed", "fcg", rtol=1e-10, smoother="xline", nu1=1, nu2=1, warm_start=True)
+    st = libmg.mg_solve(prob.h, rho_p.numpy(), bc_p.numpy(), phi_p.numpy(), warm)
+    assert st.iters <= 1  # started from the converged solution, read in place
+    ring = ~inst.grid.interior_mask()
+    assert np.array_equal(phi_p.numpy()[ring], bc[ring])
+    prob.close()
+
+
 def test_warm_start_from_solution(libmg, ctx):
     inst = I.config1(65)
     opts = libmg.make_opts("fp64", "fcg", rtol=1e-9)

@@ -157,6 +157,56 @@ __device__ void tail_smooth(const TailLevel<T>& v, int sweeps, int rev) {
     }
 }
 
+// Zebra x-line Gauss-Seidel on a tail level (shared memory, pitch = nx): the rows of one
+// parity, then the other (reverse order when rev), one thread per row solving its
+// tridiagonal system (diagonal and E couplings) by the Thomas algorithm: the rows of the tail
+// levels have at most a few dozen unknowns, fewer sequential steps than cyclic reduction's
+// barriers.  Right-hand side: b minus the couplings to the rows above and below and to the
+// row's two Dirichlet ends, as in k_line_zebra.  The eliminated super-diagonal goes to the
+// level's scratch array t and the eliminated right-hand side into x itself (a row's old
+// values are never read), then the back substitution runs in place.
+template <typename T>
+__device__ void tail_line(const TailLevel<T>& v, int sweeps, int rev) {
+  const Lvl<T>& L = v.L;
+  const int N = L.nx - 2, p = L.pitch;
+  T* x = v.x;
+  T* cp = v.t;
+  for (int s = 0; s < sweeps; ++s)
+    for (int h = 0; h < 2; ++h) {
+      const int par = rev ? 1 - h : h;
+      const int nrows = (L.nyr - par + 1) / 2;
+      for (int r = threadIdx.x; r < nrows; r += blockDim.x) {
+        const int j = par + 2 * r;
+        if (!(L.periodic || (j >= 1 && j <= L.ny - 2))) continue;
+        const int jd = row_dn(j, L.nyr), ju = row_up(j, L.nyr);
+        const int r0 = j * p, rd = jd * p, ru = ju * p;
+        T cprev = T(0), dprev = T(0);
+        for (int i = 1; i <= N; ++i) {
+          T off = L.cN[r0 + i] * x[ru + i];
+          off = fma(L.cN[rd + i], x[rd + i], off);
+          if (!L.five_point) {
+            off = fma(L.cNE[r0 + i], x[ru + i + 1], off);
+            off = fma(L.cNE[rd + i - 1], x[rd + i - 1], off);
+            off = fma(L.cNW[r0 + i], x[ru + i - 1], off);
+            off = fma(L.cNW[rd + i + 1], x[rd + i + 1], off);
+          }
+          if (i == 1) off = fma(L.cE[r0], x[r0], off);
+          if (i == N) off = fma(L.cE[r0 + i], x[r0 + i + 1], off);
+          const T rhs = v.b[r0 + i] - off;
+          const T a = i > 1 ? L.cE[r0 + i - 1] : T(0);  // coupling to the left unknown
+          const T c = i < N ? L.cE[r0 + i] : T(0);      // and to the right one
+          const T rm = T(1) / (L.diag[r0 + i] - a * cprev);
+          cprev = c * rm;
+          dprev = (rhs - a * dprev) * rm;
+          cp[r0 + i] = cprev;
+          x[r0 + i] = dprev;
+        }
+        for (int i = N - 1; i >= 1; --i) x[r0 + i] = x[r0 + i] - cp[r0 + i] * x[r0 + i + 1];
+      }
+      __syncthreads();
+    }
+}
+
 // Bytes of shared memory that hold every array of the tail levels.
 template <typename T>
 size_t tail_smem_bytes(const TailArgs<T>& a) {
@@ -211,7 +261,8 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(TailArgs<T> a, const int*
   for (int l = 0; l < nl - 1; ++l) {
     const TailLevel<T>& f = S[l];
     const TailLevel<T>& g = S[l + 1];
-    tail_smooth(f, a.nu1, 0);
+    if (a.line) tail_line(f, a.nu1, 0);
+    else tail_smooth(f, a.nu1, 0);
     for (int t = threadIdx.x; t < f.L.nx * f.L.nyr; t += blockDim.x) {
       const int i = t % f.L.nx, j = t / f.L.nx;
       f.t[t] = is_unknown(f.L, i, j) ? f.b[t] - fma(f.L.diag[t], f.x[t], offdiag_nr(f.L, f.x, i, j)) : T(0);
@@ -255,7 +306,8 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(TailArgs<T> a, const int*
       if (is_unknown(f.L, i, j)) f.x[t] += interp<T>(g.x, g.L.nx, g.L.nyr, i, j);
     }
     __syncthreads();
-    tail_smooth(f, a.nu2, 1);
+    if (a.line) tail_line(f, a.nu2, 1);
+    else tail_smooth(f, a.nu2, 1);
   }
   {
     const Lvl<T>& G = a.lv[0].L;

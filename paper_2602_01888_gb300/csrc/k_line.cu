@@ -175,15 +175,16 @@ __host__ __device__ inline size_t zebra_smem(int np) {
 // factors.  A half-sweep reads rows of the other parity only (and the Dirichlet row ends),
 // which no CTA of the launch writes, so x is read through the read-only path.  LU: loop
 // iterations whose global loads a thread issues together (the kernel is bound by load
-// latency); resident CTAs per SM at the longest rows: 6 (FP32) / 3 (FP64), which is also
-// what shared memory allows there.
+// latency); resident CTAs per SM at the longest rows: 6 (FP32; 5 for the 9-point form with
+// four iterations' loads, whose registers do not fit six) / 3 (FP64), which is also what
+// shared memory allows there.
 // Right-hand-side variants of a half-sweep (compile-time, so the common one carries no extra
 // code): the iterate as stored; a zero iterate (nothing read).  FIVE: a 5-point operator
 // (L.five_point), whose zero NE / NW couplings are neither loaded nor multiplied.
 enum LineMode : int { LM_PLAIN = 0, LM_ZERO = 1 };
 
 template <typename T, int LU, int MODE, bool FIVE = false>
-__global__ void __launch_bounds__(kLT, sizeof(T) == 8 ? 3 : (LU <= 2 ? 6 : 5))
+__global__ void __launch_bounds__(kLT, sizeof(T) == 8 ? 3 : (LU <= 2 || FIVE ? 6 : 5))
     k_line_zebra(Lvl<T> L, LineFactors<T> F, T* __restrict__ x, const T* __restrict__ b, int par,
                  const int* __restrict__ skip) {
   if (skip && *skip) return;

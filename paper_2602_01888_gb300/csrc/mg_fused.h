@@ -25,7 +25,8 @@ struct TailLevel {
 // Levels lv[0] (finest handled by the tail) .. lv[nlev-1] (coarsest, dense inverse inv).
 template <typename T>
 struct TailArgs {
-  int nlev, nu1, nu2, pad;
+  int nlev, nu1, nu2;
+  int line;  // 1: zebra x-line Gauss-Seidel on the tail levels, 0: four-colour Gauss-Seidel
   const double* inv;
   TailLevel<T> lv[kMaxTail];
 };

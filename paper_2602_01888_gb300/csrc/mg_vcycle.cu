@@ -43,6 +43,18 @@ int tail_nodes() {
   return v;
 }
 
+// Largest level the zebra x-line cycle leaves to the tail kernel.  Its levels must also fit
+// the tail's shared memory together (FP32: 65^2 and below, 204 KB; FP64: 33^2 and below).
+template <typename T>
+int line_tail_nodes() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = getenv(sizeof(T) == 8 ? "MG_LINE_TAIL_NODES_F64" : "MG_LINE_TAIL_NODES_F32");
+    v = e ? atoi(e) : 4300;
+  }
+  return v;
+}
+
 // Levels with more nodes than this use the per-colour smoothing kernels (four launches
 // a sweep); smaller levels above the tail use the fused tile kernel.
 template <typename T>
@@ -114,17 +126,50 @@ cudaError_t emit_vcycle(const VLevels<T>& V, int smoother, int nu1, int nu2, dou
     // restriction need not clear it; the coarse correction is added to the even rows only,
     // just before the first post-smoothing half-sweep solves the odd rows from them (see
     // launch_line_rows): identical values, one pass over half of each level's iterate.
+    // The smallest levels (at most line_tail_nodes each, all in the tail kernel's shared
+    // memory) run with the coarsest solve in the single-CTA tail kernel, which smooths them
+    // row by row: one launch instead of about six per level, each of them latency-bound.
     const bool zs = nu1 > 0;
-    for (int l = 0; l < L - 1; ++l) {
+    int t = L - 1;
+    const int thr = line_tail_nodes<T>();
+    for (int l = 1; l < L - 1; ++l) {
+      const long long nodes = (long long)V.A[l].nx * rows_stored(V.A[l].ny, V.A[l].periodic);
+      size_t bytes = 0;
+      for (int q = l; q < L; ++q)
+        bytes += (size_t)9 * sizeof(T) * V.A[q].nx * rows_stored(V.A[q].ny, V.A[q].periodic);
+      if (nodes <= thr && L - l <= kMaxTail && bytes <= kTailSmemMax) {
+        t = l;
+        break;
+      }
+    }
+    for (int l = 0; l < t; ++l) {
       const int zero = l == 0 ? (x0_zero && zs) : zs;
       if ((e = launch_line_smooth(V.A[l], V.lf[l], cur[l], V.b[l], nu1, 0, skip, s, (const T*)nullptr, 0, zero)))
         return e;
-      if ((e = launch_resid_restrict(V.A[l], cur[l], V.b[l], V.b[l + 1], zs ? nullptr : cur[l + 1],
+      // the tail kernel reads the iterate of its first level: clear it there
+      if ((e = launch_resid_restrict(V.A[l], cur[l], V.b[l], V.b[l + 1], zs && l + 1 < t ? nullptr : cur[l + 1],
                                      V.A[l + 1].pitch, skip, s)))
         return e;
     }
-    if ((e = launch_coarse_solve(V.A[L - 1], V.inv, V.b[L - 1], cur[L - 1], skip, s))) return e;
-    for (int l = L - 2; l >= 0; --l) {
+    if (t == L - 1) {
+      if ((e = launch_coarse_solve(V.A[L - 1], V.inv, V.b[L - 1], cur[L - 1], skip, s))) return e;
+    } else {
+      TailArgs<T> ta;
+      memset(&ta, 0, sizeof ta);
+      ta.nlev = L - t;
+      ta.nu1 = nu1;
+      ta.nu2 = nu2;
+      ta.line = 1;
+      ta.inv = V.inv;
+      for (int l = t; l < L; ++l) {
+        ta.lv[l - t].L = lvl_of(V.A[l]);
+        ta.lv[l - t].x = cur[l];
+        ta.lv[l - t].b = V.b[l];
+        ta.lv[l - t].t = alt[l];
+      }
+      if ((e = launch_tail(ta, skip, s))) return e;
+    }
+    for (int l = t - 1; l >= 0; --l) {
       if (nu2 > 0) {
         if ((e = launch_line_smooth(V.A[l], V.lf[l], cur[l], V.b[l], nu2, 1, skip, s, (const T*)cur[l + 1],
                                     V.A[l + 1].pitch, 0)))

@@ -97,37 +97,62 @@ __global__ void __launch_bounds__(256) k_line_prolong_even(Lvl<T> L, T* __restri
   x[k] = x[k] + prolong_even_row(eH, pitch_c, jn, c);
 }
 
-// Reduction multipliers of row blockIdx.x.  Shared memory: a, b, c of Np entries each
-// (padded rows).
+// Reduction multipliers of row blockIdx.x.  The first level reads the row's three diagonals
+// from global memory (each entry once) and keeps only the Np / 2 equations it leaves
+// (the odd ones), compacted, in shared memory: a, b, c of Np / 2 entries each, half of what
+// the whole row would take, so that twice as many rows are factored at once (the kernel is
+// bound by its dependent chain of levels, not by its few bytes).  Equation i' of the compacted
+// system is equation 2 i' + 1 of the row, and level k of the row is level k - 1 of the
+// compacted system, with the same arithmetic in the same order.
+template <typename T>
+__device__ __forceinline__ void row_diags(const Lvl<T>& L, size_t r0, int N, int t, T& a, T& b, T& c) {
+  if (t < N) {
+    const int i = t + 1;
+    a = t >= 1 ? L.cE[r0 + i - 1] : T(0);
+    b = L.diag[r0 + i];
+    c = t <= N - 2 ? L.cE[r0 + i] : T(0);
+  } else {  // padding: identity equations
+    a = T(0);
+    b = T(1);
+    c = T(0);
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kLT) k_line_factor(Lvl<T> L, LineFactors<T> F) {
   const int j = blockIdx.x;
   if (j >= L.nyr || !row_active(L, j)) return;
-  const int N = L.nx - 2, Np = F.np, K = line_levels(Np);
+  const int N = L.nx - 2, Np = F.np, K = line_levels(Np), Nh = Np / 2;
   extern __shared__ __align__(16) unsigned char line_smem[];
-  const int rs = (int)(line_row_smem<T>(Np) / sizeof(T));
+  const int rs = (int)(line_row_smem<T>(Nh) / sizeof(T));
   T* a = reinterpret_cast<T*>(line_smem);
   T* bb = a + rs;
   T* c = bb + rs;
   const size_t r0 = (size_t)j * L.pitch, f0 = (size_t)j * Np;
-  for (int t = threadIdx.x; t < Np; t += blockDim.x) {
-    const int q = sx<T>(t);
-    if (t < N) {
-      const int i = t + 1;
-      a[q] = t >= 1 ? L.cE[r0 + i - 1] : T(0);
-      bb[q] = L.diag[r0 + i];
-      c[q] = t <= N - 2 ? L.cE[r0 + i] : T(0);
-    } else {  // padding: identity equations
-      a[q] = T(0);
-      bb[q] = T(1);
-      c[q] = T(0);
-    }
+  // level 0: equations 2m are final; equations 2m + 1 absorb their two neighbours
+  for (int m = threadIdx.x; m < Nh; m += blockDim.x) {
+    T ae, be, ce, ad, bd, cd, au = T(0), bu = T(1), cu = T(0);
+    row_diags(L, r0, N, 2 * m, ad, bd, cd);  // the eliminated equation below
+    row_diags(L, r0, N, 2 * m + 1, ae, be, ce);
+    const bool up = 2 * m + 2 < Np;
+    if (up) row_diags(L, r0, N, 2 * m + 2, au, bu, cu);
+    F.afin[f0 + m] = ad;
+    F.cfin[f0 + m] = cd;
+    F.binv[f0 + m] = T(1) / bd;
+    const T al = -ae / bd;
+    const T ga = up ? -ce / bu : T(0);
+    F.alpha[f0 + m] = al;
+    F.gamma[f0 + m] = ga;
+    const int q = sx<T>(m);
+    a[q] = al * ad;
+    c[q] = up ? ga * cu : T(0);
+    bb[q] = be + al * cd + (up ? ga * au : T(0));
   }
   __syncthreads();
-  for (int k = 0; k < K; ++k) {
-    const int s = 1 << k, off = Np - Np / s;
+  for (int k = 1; k < K; ++k) {
+    const int s = 1 << (k - 1), off = Np - Np / (1 << k);  // s: distance in the compacted system
     // equations eliminated at this level (i = 2s m + s - 1) are final now
-    for (int m = threadIdx.x; m < Np / (2 * s); m += blockDim.x) {
+    for (int m = threadIdx.x; m < Nh / (2 * s); m += blockDim.x) {
       const int q = sx<T>(2 * s * m + s - 1);
       F.afin[f0 + off + m] = a[q];
       F.cfin[f0 + off + m] = c[q];
@@ -135,9 +160,9 @@ __global__ void __launch_bounds__(kLT) k_line_factor(Lvl<T> L, LineFactors<T> F)
     }
     // combining equations i = 2s(m + 1) - 1 absorb their neighbours at distance s; the
     // neighbours are not combining at this level, so reading and writing do not overlap
-    for (int m = threadIdx.x; m < Np / (2 * s); m += blockDim.x) {
+    for (int m = threadIdx.x; m < Nh / (2 * s); m += blockDim.x) {
       const int i = 2 * s * (m + 1) - 1;
-      const bool up = i + s < Np;
+      const bool up = i + s < Nh;
       const int q = sx<T>(i), qd = sx<T>(i - s), qu = up ? sx<T>(i + s) : q;
       const T al = -a[q] / bb[qd];
       const T ga = up ? -c[q] / bb[qu] : T(0);
@@ -155,7 +180,7 @@ __global__ void __launch_bounds__(kLT) k_line_factor(Lvl<T> L, LineFactors<T> F)
   if (threadIdx.x == 0) {  // the root: no neighbour left
     F.afin[f0 + Np - 1] = T(0);
     F.cfin[f0 + Np - 1] = T(0);
-    F.binv[f0 + Np - 1] = T(1) / bb[sx<T>(Np - 1)];
+    F.binv[f0 + Np - 1] = T(1) / bb[sx<T>(Nh - 1)];
   }
 }
 
@@ -669,11 +694,14 @@ cudaError_t launch_line_factor(const Op<T>& A, const LineFactors<T>& F, cudaStre
     k_line_pfactor<T><<<L.nyr, kPP, sm, s>>>(L, F);
     return cudaGetLastError();
   }
-  const size_t sm = 3 * line_row_smem<T>(F.np);
+  const size_t sm = 3 * line_row_smem<T>(F.np / 2);
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k_line_factor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kLineSmemMax);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_line_factor<T>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     attr = true;
   }

@@ -43,14 +43,17 @@ int tail_nodes() {
   return v;
 }
 
-// Largest level the zebra x-line cycle leaves to the tail kernel.  Its levels must also fit
-// the tail's shared memory together (FP32: 65^2 and below, 204 KB; FP64: 33^2 and below).
+// Largest level the zebra x-line cycle leaves to the tail kernel (its levels must also fit the
+// tail's shared memory together).  Measured on the 8193^2 annulus cycle: FP32 2.730 ms with no
+// tail, 2.713 ms with the levels up to 33^2 (1200 nodes) in it, 2.742 ms up to 65^2 (the
+// single CTA's sequential row solves then cost more than the launches they replace); FP64
+// 6.164 ms with no tail, 6.254 ms up to 33^2, so FP64 keeps the launches.
 template <typename T>
 int line_tail_nodes() {
   static int v = -1;
   if (v < 0) {
     const char* e = getenv(sizeof(T) == 8 ? "MG_LINE_TAIL_NODES_F64" : "MG_LINE_TAIL_NODES_F32");
-    v = e ? atoi(e) : 4300;
+    v = e ? atoi(e) : (sizeof(T) == 8 ? 0 : 1200);
   }
   return v;
 }

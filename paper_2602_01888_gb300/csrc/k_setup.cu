@@ -251,10 +251,11 @@ __device__ __forceinline__ T fine_entry(const Lvl<T>& F, int fi, int fj, int di,
 
 // A_H = (1/4) P^T A_h P: for each coarse unknown I, row(I, I+o) = (1/4) sum_k sum_l
 // P(k, I) A(k, l) P(l, I+o) over fine k in the 3x3 support of I and the 9 stencil
-// neighbours l of k.  Every loop is unrolled so the bilinear weights are constants and
-// only the (k, l, o) triples with non-zero weight remain (169 multiply-adds).  FIVE: the fine
-// operator is 5-point (F.five_point): its diagonal entries are zero and their products, which
-// would add zeros, are skipped (105 multiply-adds, the same sums).
+// neighbours l of k, for the five entries stored (o = centre, E, N, NE, NW; the others are
+// the symmetric partners' entries).  Every loop is unrolled so the bilinear weights are
+// constants and only the (k, l, o) triples with non-zero weight remain (109 multiply-adds).
+// FIVE: the fine operator is 5-point (F.five_point): its diagonal entries are zero and their
+// products, which would add zeros, are skipped (69 multiply-adds, the same sums).
 template <typename T, bool FIVE>
 __global__ void k_galerkin(Lvl<T> F, int nxc, int nyc, int nyrc, int pitchc, T* cE, T* cN, T* cNE,
                            T* cNW, T* diag, T* dinv) {
@@ -288,9 +289,10 @@ __global__ void k_galerkin(Lvl<T> F, int nxc, int nyc, int nyrc, int pitchc, T* 
           if (FIVE && li != 0 && lj != 0) continue;
           const T a = fine_entry(F, fi, fj, li, lj);
 #pragma unroll
-          for (int oj = -1; oj <= 1; ++oj)
+          for (int oj = 0; oj <= 1; ++oj)
 #pragma unroll
             for (int oi = -1; oi <= 1; ++oi) {
+              if (oj == 0 && oi < 0) continue;  // W: not stored
               const double w = 0.25 * pw(ki) * pw(kj) * pw(ki + li - 2 * oi) * pw(kj + lj - 2 * oj);
               if (w != 0.0) row[oi + 1][oj + 1] = fma((T)w, a, row[oi + 1][oj + 1]);
             }

@@ -85,6 +85,20 @@ def test_kernel_operator_struct_matches_the_c_compiler(libmg, tmp_path):
             assert got[(t, f)] == getattr(cls, f).offset, (t, f)
 
 
+def test_map_classification_for_the_five_point_form(libmg):
+    """mg_map_five_point (host logic, no GPU): maps whose J^T J is diagonal (Eq. 13 vanishes
+    identically) are handled as 5-point operators; maps with a cross term are not."""
+    from paper_2602_01888_gb300 import inputs as I
+    yes = [I.MapSpec("identity"), I.MapSpec("polar"), I.MapSpec("sinh", (5.0, 0.6)),
+           I.MapSpec("affine", (1.1, 0.0, 0.0, 0.9))]
+    no = [I.MapSpec("sine_warp", (0.1,)), I.MapSpec("affine", (1.1, 0.2, -0.1, 0.9)),
+          I.MapSpec("affine", (1.0, 0.0, 0.3, 1.0))]
+    assert all(libmg.map_five_point(m) for m in yes)
+    assert not any(libmg.map_five_point(m) for m in no)
+    assert libmg.lib().mg_map_five_point(None) == 0
+    assert libmg.lib().mg_problem_five_point(None) == -1
+
+
 def test_no_oracle_on_the_product_path():
     """The package (product path) never imports the oracle."""
     pkg = os.path.join(ROOT, "paper_2602_01888_gb300")

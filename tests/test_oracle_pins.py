@@ -66,6 +66,35 @@ def test_polar_closed_form(oracle):
     assert np.allclose(P.D, r, rtol=1e-14)
 
 
+def test_polar_cross_term_residue_moves_the_solution_by_rounding_only(oracle):
+    """Reading r13: for the polar map Eq. 13 vanishes identically and the general formula
+    leaves only rounding residue in eps_xy; the 5-point operator (eps_xy = 0) then has the
+    same discrete solution up to rounding.  At 257^2 dropping the residue moves the oracle's
+    annulus solution by 2e-14 (the solver's own stagnation level; 1.9e-13 at 2049^2), while
+    the closed-form tensor, whose few-ulp differences from the general formula are systematic
+    along theta, moves it by 4e-13, a gap that grows like n^2 (1.4e-12 at 513^2, 2.9e-10 at
+    8193^2, where it would break the FP64 bound)."""
+    inst = I.annulus_log(257)
+    g = inst.grid
+    P = oracle.prepare(inst)
+    emag = max(np.abs(P.exx).max(), np.abs(P.eyy).max())
+    assert np.abs(P.exy).max() <= 1e-15 * emag          # residue only
+    assert np.count_nonzero(P.exy) > 0                    # ... but not exactly zero
+    r, _ = g.coords()
+    kw = dict(rtol=0.0, max_iters=60, stagnate=4, smoother=oracle.SMOOTHER_XLINE, nu1=1, nu2=1)
+    sol = {}
+    for name, (exx, exy, eyy) in {"general": (P.exx, P.exy, P.eyy),
+                                  "no_residue": (P.exx, np.zeros_like(P.exy), P.eyy),
+                                  "closed_form": (r, np.zeros_like(r), 1.0 / r)}.items():
+        A = oracle.assemble(g, exx, exy, eyy)
+        sol[name], _, _ = oracle.pcg_solve(A, P.b, P.phi0, **kw)
+    m = g.interior_mask()
+    d_res = oracle.rel_l2(sol["no_residue"], sol["general"], m)
+    d_closed = oracle.rel_l2(sol["closed_form"], sol["general"], m)
+    assert d_res < 1e-13
+    assert 5 * d_res < d_closed < 1e-11
+
+
 def test_sinh_closed_form_offdiagonal_vanishes(oracle):
     g = I.Grid(33, 33, -3.0, -3.0, 6.0, 6.0)
     mp = I.MapSpec("sinh", (5.0, 0.6))

@@ -22,6 +22,7 @@
 // strided accesses of the reduction levels (stride 2^(k+1)) hit distinct banks.
 #include <cuda_runtime.h>
 
+#include <cstdint>
 #include <type_traits>
 #include <vector>
 
@@ -84,17 +85,32 @@ __device__ __forceinline__ bool row_active(const Lvl<T>& L, int j) {
 // at their unknowns, before the first post-smoothing half-sweep solves the odd rows from them.
 // That half-sweep and the next one never read the old values of the rows they solve, so the
 // result equals adding P eH to every row and smoothing, with one pass over half the rows.
-// Grid: (columns / kLT, even rows).
-template <typename T>
+// VEC: each thread takes one 16-byte chunk of a row and corrects the chunk's unknowns (the
+// launcher chooses it when every row starts 16-byte aligned); otherwise one element each.
+// Grid: (chunks or columns / kLT, even rows).
+template <typename T, bool VEC>
 __global__ void __launch_bounds__(256) k_line_prolong_even(Lvl<T> L, T* __restrict__ x,
                                                            const T* __restrict__ eH, int pitch_c,
                                                            const int* __restrict__ skip) {
   if (skip && *skip) return;
+  constexpr int V = VEC ? 16 / (int)sizeof(T) : 1;
   const int jn = 2 * blockIdx.y;
-  const int c = 1 + blockIdx.x * blockDim.x + threadIdx.x;
-  if (jn >= L.nyr || !row_active(L, jn) || c > L.nx - 2) return;
-  const size_t k = (size_t)jn * L.pitch + c;
-  x[k] = x[k] + prolong_even_row(eH, pitch_c, jn, c);
+  const int c0 = (blockIdx.x * blockDim.x + threadIdx.x) * V;
+  if (jn >= L.nyr || !row_active(L, jn) || c0 > L.nx - 2) return;
+  T* const r = x + (size_t)jn * L.pitch + c0;
+  if constexpr (VEC) {
+    using V16 = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+    V16 w = *reinterpret_cast<V16*>(r);
+    T* const e = reinterpret_cast<T*>(&w);
+#pragma unroll
+    for (int u = 0; u < V; ++u) {
+      const int c = c0 + u;
+      if (c >= 1 && c <= L.nx - 2) e[u] = e[u] + prolong_even_row(eH, pitch_c, jn, c);
+    }
+    *reinterpret_cast<V16*>(r) = w;
+  } else if (c0 >= 1) {
+    r[0] = r[0] + prolong_even_row(eH, pitch_c, jn, c0);
+  }
 }
 
 // Reduction multipliers of row blockIdx.x.  The first level reads the row's three diagonals
@@ -791,9 +807,12 @@ cudaError_t launch_line_rows(const Op<T>& A, const LineFactors<T>& F, T* x, cons
   if (eH && (par != 1 || (A.nx - 1) % 2 || (A.ny - 1) % 2)) return cudaErrorInvalidValue;
   const Lvl<T> L = lvl_of(A);
   if (eH) {  // the coarse correction enters through the even rows the odd ones are solved from
-    const int erows = (L.nyr + 1) / 2;
-    const dim3 g((unsigned)((A.nx - 2 + kLT - 1) / kLT), (unsigned)erows);
-    k_line_prolong_even<T><<<g, kLT, 0, s>>>(L, x, eH, pitch_c, skip);
+    constexpr int V = 16 / (int)sizeof(T);
+    const bool vec = A.pitch % V == 0 && reinterpret_cast<uintptr_t>(x) % 16 == 0;
+    const int erows = (L.nyr + 1) / 2, cols = vec ? (A.nx - 1 + V - 1) / V : A.nx - 1;
+    const dim3 g((unsigned)((cols + kLT - 1) / kLT), (unsigned)erows);
+    if (vec) k_line_prolong_even<T, true><<<g, kLT, 0, s>>>(L, x, eH, pitch_c, skip);
+    else k_line_prolong_even<T, false><<<g, kLT, 0, s>>>(L, x, eH, pitch_c, skip);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

@@ -806,7 +806,7 @@ def run_ours(args):
         (1 if inst.bc is not None else 0)
     for prec in precisions:
         opts = mg.make_opts(prec, outer, rtol=rtols[prec], max_iters=400, smoother=smoother, nu1=nu[0],
-                            nu2=nu[1])
+                            nu2=nu[1], coarse_op=args.coarse_op)
         prob = mg.Problem(ctx, inst, opts, device_inputs=True)
 
         def step():
@@ -876,6 +876,7 @@ def run_ours(args):
                        "outer": f"{outer}+vcycle({nu[0]},{nu[1]})", "smoother": smoother,
                        "rtol": rtols, "unknowns": U, "l2": "flushed between steps (512 MB write)",
                        "finest_stencil": "5-point (map without cross term)" if rh["five_point"] else "9-point",
+                       "coarse_op": args.coarse_op,
                        "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
             "iters": rh["stats"].iters, "levels": rh["levels"], "setup_ms": rh["setup_ms"],
             "solve_ms": rh["solve_ms"], "rel_residual": rh["stats"].rel_residual,
@@ -1358,6 +1359,9 @@ def main():
     ap.add_argument("--side", type=int, default=2049)
     ap.add_argument("--ny", type=int, default=0, help="kernel-only: rows (default: --side)")
     ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--coarse-op", dest="coarse_op", default="galerkin", choices=["galerkin", "rediscretize"],
+                    help="coarse operators of the single-instance workloads: Galerkin products or the "
+                         "assembly on each coarse grid from the coarsened tensor")
     ap.add_argument("--stencil", type=int, default=9, choices=(5, 9),
                     help="kernel-only: 9 = sine-warp operator, 5 = a map without cross term (5-point kernels)")
     ap.add_argument("--variant", type=int, default=-1,

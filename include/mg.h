@@ -108,6 +108,13 @@ typedef struct {
   double jump_x, jump_y;
 } mg_map_desc;
 
+/* Coarse operators (Sec. 3 names A_H only): the Galerkin product R A P (default, 9-point
+ * on every coarse level), or the fine assembly (Eqs. 12-18 in the conservative form) applied
+ * on each coarse grid to the tensor coarsened from the level above: full weighting at coarse
+ * unknowns, injection on the boundary ring.  A rediscretized hierarchy of a map without cross
+ * term stays 5-point on every level. */
+typedef enum { MG_COARSE_GALERKIN = 0, MG_COARSE_REDISCRETIZE = 1 } mg_coarse_op;
+
 typedef struct {
   int precision;      /* mg_precision */
   int outer;          /* mg_outer: plain V-cycles, or flexible CG preconditioned by one V-cycle */
@@ -118,6 +125,7 @@ typedef struct {
   int max_iters;      /* cycles (VCYCLE), CG iterations (FCG) or SOR iterations of nu1 sweeps (SOR) */
   int coarse_max;     /* coarsest level: first level with at most this many unknowns (<= 256) */
   int warm_start;     /* 1: phi holds the initial guess of the unknowns */
+  int coarse_op;      /* mg_coarse_op: how the coarse operators are built (fixed at set-up) */
 } mg_solve_opts;
 
 #define MG_HIST_MAX 256

@@ -73,6 +73,15 @@ int mgk_assemble(const mgk_op_f64 *A, double hx, double hy, const double *exx, c
 /* b = rho_phys * D at unknowns (Eq. 11), 0 at Dirichlet nodes. */
 int mgk_rhs(const mgk_op_f64 *A, const double *rho_phys, const double *D, double *b, void *stream);
 
+/* Tensor of the next coarser level of a rediscretized hierarchy (MG_COARSE_REDISCRETIZE of
+ * mg.h): each field e0, e1, e2 (eps_xx, eps_xy, eps_yy on fine's layout) at the coarse nodes
+ * (c0, c1, c2 on coarse's layout): full weighting (1/16)[1 2 1; 2 4 2; 1 2 1] about the
+ * coincident fine node at coarse unknowns, the coincident fine value on the boundary ring.
+ * Only the sizes, periodicity and pitches of fine and coarse are used; coarse must be fine's
+ * next level.  The coarse operator is then mgk_assemble on coarse with twice the spacing. */
+int mgk_coarsen_eps(const mgk_op_f64 *fine, const mgk_op_f64 *coarse, const double *e0, const double *e1,
+                    const double *e2, double *c0, double *c1, double *c2, void *stream);
+
 /* Galerkin coarse operator A_H = (1/4) P^T A_h P with bilinear P (Sec. 3: A_H of Eq. 23). */
 int mgk_galerkin(const mgk_op_f64 *fine, const mgk_op_f64 *coarse, void *stream);
 

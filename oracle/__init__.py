@@ -77,6 +77,7 @@ def lib():
             "orc_smooth": [i, i, i, D, D, D, D, D, D, D, i, i, i, d],
             "orc_gs_colour": [i, i, i, D, D, D, D, D, D, D, i],
             "orc_restrict": [i, i, i, D, D],
+            "orc_coarsen_nodal": [i, i, i, D, D],
             "orc_prolong_add": [i, i, i, D, D],
             "orc_dense_solve": [i, i, i, D, D, D, D, D, D, D],
             "orc_paper_sor": [i, i, d, d, D, D, D, D, D, d, d, i],
@@ -200,6 +201,28 @@ def hierarchy(A0: Operator, coarse_max=DEFAULT_COARSE_MAX):
     ops = [A0]
     for _ in range(num_levels(A0.nx, A0.ny, A0.periodic, coarse_max) - 1):
         ops.append(galerkin(ops[-1]))
+    return ops
+
+
+def coarsen_nodal(nxf, nyf, periodic, f):
+    """A nodal field at the coarse nodes: full weighting inside, injection on the boundary."""
+    nxc, nyc = (nxf - 1) // 2 + 1, (nyf - 1) // 2 + 1
+    fc = np.zeros(((nyc - 1) if periodic else nyc, nxc))
+    lib().orc_coarsen_nodal(nxf, nyf, int(periodic), _p(_f64(f)), _p(fc))
+    return fc
+
+
+def rediscretized_hierarchy(grid, exx, exy, eyy, coarse_max=DEFAULT_COARSE_MAX):
+    """Operators of every level assembled from the tensor coarsened level by level
+    (coarsen_nodal) on grids of twice the spacing: the alternative to the Galerkin product.
+    The grid is the one the operator lives on (the doubled periodic grid for Neumann sides)."""
+    levels = num_levels(grid.nx, grid.ny, grid.periodic_y, coarse_max)
+    g, e = grid, (exx, exy, eyy)
+    ops = [assemble(g, *e)]
+    for _ in range(levels - 1):
+        e = tuple(coarsen_nodal(g.nx, g.ny, g.periodic_y, a) for a in e)
+        g = replace(g, nx=(g.nx - 1) // 2 + 1, ny=(g.ny - 1) // 2 + 1)
+        ops.append(assemble(g, *e))
     return ops
 
 

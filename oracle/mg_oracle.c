@@ -835,6 +835,34 @@ int orc_restrict(int nxf, int nyf, int periodic, const double *r, double *bH) {
   return ORC_OK;
 }
 
+/* Rediscretized coarse levels (the alternative to the Galerkin product): a nodal field f of
+ * the fine grid (the tensor components eps_xx, eps_xy, eps_yy) at the coarse nodes, full
+ * weighting (1/16)[1 2 1; 2 4 2; 1 2 1] about the coincident fine node (2I, 2J) at coarse nodes
+ * whose eight fine neighbours exist (rows wrap when periodic), and injection (the coincident
+ * fine value) on the coarse boundary ring.  The coarse operator is then assembled from the
+ * coarsened tensor on the coarse grid (spacing 2h) exactly as the fine one (orc_assemble). */
+int orc_coarsen_nodal(int nxf, int nyf, int periodic, const double *f, double *fc) {
+  const int nxc = (nxf - 1) / 2 + 1, nyc = (nyf - 1) / 2 + 1;
+  const int nyrf = periodic ? nyf - 1 : nyf, nyrc = periodic ? nyc - 1 : nyc;
+  for (int J = 0; J < nyrc; ++J)
+    for (int I = 0; I < nxc; ++I) {
+      const int fi = 2 * I, fj = 2 * J;
+      const int inner_x = I >= 1 && I <= nxc - 2;
+      const int inner_y = periodic || (J >= 1 && J <= nyc - 2);
+      double v;
+      if (inner_x && inner_y) {
+        const int jd = fj == 0 ? nyrf - 1 : fj - 1, ju = fj + 1 == nyrf ? 0 : fj + 1;
+        const double *r0 = f + (size_t)nxf * fj, *rd = f + (size_t)nxf * jd, *ru = f + (size_t)nxf * ju;
+        v = (4.0 * r0[fi] + 2.0 * (r0[fi - 1] + r0[fi + 1] + rd[fi] + ru[fi]) +
+             (rd[fi - 1] + rd[fi + 1] + ru[fi - 1] + ru[fi + 1])) / 16.0;
+      } else {
+        v = f[(size_t)nxf * fj + fi];
+      }
+      fc[(size_t)nxc * J + I] = v;
+    }
+  return ORC_OK;
+}
+
 int orc_prolong_add(int nxf, int nyf, int periodic, const double *eH, double *phi) {
   int nxc = (nxf - 1) / 2 + 1, nyc = (nyf - 1) / 2 + 1;
   op_t Af = {nxf, nyf, periodic ? nyf - 1 : nyf, periodic, 0, 0, 0, 0, 0};

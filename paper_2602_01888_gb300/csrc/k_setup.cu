@@ -230,6 +230,35 @@ __global__ void k_rhs(int nx, int ny, int nyr, int periodic, int pitch,
   b[k] = unk ? rho[(size_t)j * rho_pitch + i] * D[k] : 0.0;  // Eq. 11
 }
 
+// Tensor of the next coarser level of a rediscretized hierarchy: each of the three nodal
+// fields at coarse node (I, J), full weighting (1/16)[1 2 1; 2 4 2; 1 2 1] about fine node
+// (2I, 2J) where all eight fine neighbours exist (rows wrap when periodic), the coincident
+// fine value on the coarse boundary ring.
+__global__ void k_coarsen_eps(int nxf, int nyrf, int pf, int nxc, int nyc, int nyrc, int pc, int periodic,
+                              const double* __restrict__ f0, const double* __restrict__ f1,
+                              const double* __restrict__ f2, double* c0, double* c1, double* c2) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = blockIdx.y * blockDim.y + threadIdx.y;
+  if (I >= nxc || J >= nyrc) return;
+  const int fi = 2 * I, fj = 2 * J;
+  const bool inner = (I >= 1 && I <= nxc - 2) && (periodic || (J >= 1 && J <= nyc - 2));
+  const int jd = fj == 0 ? nyrf - 1 : fj - 1, ju = fj + 1 == nyrf ? 0 : fj + 1;
+  const size_t r0 = (size_t)fj * pf, rd = (size_t)jd * pf, ru = (size_t)ju * pf, K = (size_t)J * pc + I;
+  const double* const f[3] = {f0, f1, f2};
+  double* const c[3] = {c0, c1, c2};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const double* g = f[a];
+    double v;
+    if (inner)
+      v = (4.0 * g[r0 + fi] + 2.0 * (g[r0 + fi - 1] + g[r0 + fi + 1] + g[rd + fi] + g[ru + fi]) +
+           (g[rd + fi - 1] + g[rd + fi + 1] + g[ru + fi - 1] + g[ru + fi + 1])) / 16.0;
+    else
+      v = g[r0 + fi];
+    c[a][K] = v;
+  }
+}
+
 // Bilinear weight of a fine offset d from a coarse node (in fine units).
 __host__ __device__ constexpr double pw(int d) { return d == 0 ? 1.0 : ((d == 1 || d == -1) ? 0.5 : 0.0); }
 
@@ -436,6 +465,16 @@ cudaError_t launch_rhs(const OpF64& A, const double* rho, int rho_pitch, const d
   return cudaGetLastError();
 }
 
+cudaError_t launch_coarsen_eps(const OpF64& F, const OpF64& C, const double* const* e, double* const* c,
+                               cudaStream_t s) {
+  const int nyrc = rows_stored(C.ny, C.periodic);
+  dim3 b(32, 8);
+  k_coarsen_eps<<<grid2(C.nx, nyrc, b), b, 0, s>>>(F.nx, rows_stored(F.ny, F.periodic), F.pitch, C.nx, C.ny,
+                                                    nyrc, C.pitch, C.periodic, e[0], e[1], e[2], c[0], c[1],
+                                                    c[2]);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_galerkin(const Op<T>& F, const Op<T>& C, cudaStream_t s) {
   const int nyrc = rows_stored(C.ny, C.periodic);
@@ -543,6 +582,20 @@ extern "C" int mgk_rhs(const mgk_op_f64* A, const double* rho_phys, const double
   if (!A || A->nx < 3 || A->ny < 3 || A->pitch < A->nx || !rho_phys || !D || !b) return 1;
   return launch_rhs(op_from(*A), rho_phys, A->pitch, D, b, (cudaStream_t)stream) == cudaSuccess
              ? 0 : 4;
+}
+
+extern "C" int mgk_coarsen_eps(const mgk_op_f64* fine, const mgk_op_f64* coarse, const double* e0,
+                               const double* e1, const double* e2, double* c0, double* c1, double* c2,
+                               void* stream) {
+  if (!fine || !coarse || !e0 || !e1 || !e2 || !c0 || !c1 || !c2 || fine->nx < 3 || fine->ny < 3 ||
+      fine->pitch < fine->nx || coarse->pitch < coarse->nx || (fine->nx - 1) % 2 || (fine->ny - 1) % 2 ||
+      coarse->nx != (fine->nx - 1) / 2 + 1 || coarse->ny != (fine->ny - 1) / 2 + 1 ||
+      coarse->periodic != fine->periodic)
+    return 1;
+  const double* e[3] = {e0, e1, e2};
+  double* c[3] = {c0, c1, c2};
+  return launch_coarsen_eps(op_from(*fine), op_from(*coarse), e, c, (cudaStream_t)stream) == cudaSuccess ? 0
+                                                                                                        : 4;
 }
 
 extern "C" int mgk_galerkin(const mgk_op_f64* fine, const mgk_op_f64* coarse, void* stream) {

@@ -107,6 +107,7 @@ struct mg_problem {
   mg_grid_desc user{};  // the caller's grid (its arrays' layout)
   int mirror = 0;       // Neumann sides: ny - 1 of the caller's grid, else 0
   int nlev = 0, coarse_max = 64, mixed = 0;
+  int coarse_op = 0;  // mg_coarse_op of the set-up
   int nxs[mg::kMaxLevels] = {}, nys[mg::kMaxLevels] = {};
   mg::LevelMem lev[mg::kMaxLevels];
   double *D = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;

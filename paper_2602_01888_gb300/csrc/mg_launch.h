@@ -77,6 +77,10 @@ cudaError_t launch_eps_grid(int nx, int ny, int periodic, double hx, double hy, 
 cudaError_t launch_mirror_eps(int nx, int n, int ps, const double* D0, const double* exx0,
                               const double* exy0, const double* eyy0, int pd, double* D, double* exx,
                               double* exy, double* eyy, cudaStream_t s);
+// Nodal tensor (e[0..2]: eps_xx, eps_xy, eps_yy of level F) coarsened to level C (c[0..2]):
+// full weighting inside, injection on the boundary ring (rediscretized hierarchies).
+cudaError_t launch_coarsen_eps(const OpF64& F, const OpF64& C, const double* const* e, double* const* c,
+                               cudaStream_t s);
 // dinv = false: A.dinv is not written (a mixed-precision hierarchy's FP64 level 0, whose
 // reciprocal diagonal is taken in FP32 by launch_op_to_f32 with dinv_f32).
 cudaError_t launch_assemble(const OpF64& A, double hx, double hy, const double* exx,

@@ -93,8 +93,9 @@ static size_t nodes_of(const mg_grid_desc& g) {
 // hierarchy does not fit the memory budget.
 static std::string shape_key(const mg_grid_desc& g, const mg_solve_opts& o) {
   char k[256];
-  snprintf(k, sizeof k, "%d:%d:%d:%d:%.17g:%.17g:%.17g:%.17g:%d:%d:%d", g.nx, g.ny, g.periodic_y, g.neumann_y,
-           g.x0, g.y0, g.lx, g.ly, (int)o.precision, o.coarse_max, (int)o.outer);
+  snprintf(k, sizeof k, "%d:%d:%d:%d:%.17g:%.17g:%.17g:%.17g:%d:%d:%d:%d", g.nx, g.ny, g.periodic_y,
+           g.neumann_y, g.x0, g.y0, g.lx, g.ly, (int)o.precision, o.coarse_max, (int)o.outer,
+           o.coarse_op);
   return k;
 }
 

@@ -160,6 +160,7 @@ extern "C" void mg_default_opts(mg_solve_opts* o) {
   o->max_iters = 200;
   o->coarse_max = 64;
   o->warm_start = 0;
+  o->coarse_op = MG_COARSE_GALERKIN;
 }
 
 extern "C" mg_status mg_create(int device, size_t mem_budget, mg_ctx** out) {
@@ -356,8 +357,13 @@ static void set_five_point(mg_problem* P, int five, cudaStream_t s) {
     P->graphs.clear();
   }
   batch_cache_drop(P->ctx, P);
-  P->lev[0].A.five_point = five;
-  P->lev[0].A32.five_point = five;
+  // a rediscretized hierarchy keeps the property on every level (the coarsened cross term of a
+  // zero one is zero); Galerkin coarse levels are 9-point
+  for (int l = 0; l < P->nlev; ++l) {
+    const int f = (l == 0 || P->coarse_op == MG_COARSE_REDISCRETIZE) ? five : 0;
+    P->lev[l].A.five_point = f;
+    P->lev[l].A32.five_point = f;
+  }
 }
 
 // Coefficients of the finest level from the map, then the Galerkin hierarchy and the
@@ -425,7 +431,30 @@ mg_status problem_enqueue_build(mg_problem* P, const mg_map_desc* map, const dou
     mg_status hs = (*hook)(P, s);
     if (hs) return hs;
   }
-  if (!P->mixed) {
+  if (P->coarse_op == MG_COARSE_REDISCRETIZE) {
+    // each coarse level: the tensor of the level above coarsened (into the level's scratch
+    // arrays x, b, t), then assembled on the coarse grid like the finest level
+    const double* e[3] = {exx, exy, eyy};
+    double hxl = hx, hyl = hy;
+    for (int l = 1; l < P->nlev; ++l) {
+      LevelMem& C = P->lev[l];
+      double* c[3] = {C.x, C.b, C.t};
+      CU(launch_coarsen_eps(P->lev[l - 1].A, C.A, e, c, s));
+      hxl *= 2.0;
+      hyl *= 2.0;
+      CU(launch_assemble(C.A, hxl, hyl, c[0], c[1], c[2], s, !P->mixed));
+      for (int k = 0; k < 3; ++k) e[k] = c[k];
+    }
+    // the coarse levels' iterates, right-hand sides and scratch held the tensors: zero them
+    // again (the cycles rely on zero Dirichlet rings on coarse levels)
+    for (int l = 1; l < P->nlev; ++l) {
+      const LevelMem& C = P->lev[l];
+      const size_t n = (size_t)C.A.pitch * rows_stored(C.A.ny, C.A.periodic);
+      CU(cudaMemsetAsync(C.x, 0, 3 * n * sizeof(double), s));  // x, b, t are contiguous
+    }
+    if (P->mixed)  // FP32 levels: reciprocal diagonals of the FP32 diagonals, as above
+      for (int l = 0; l < P->nlev; ++l) CU(launch_op_to_f32(P->lev[l].A, P->lev[l].A32, s, true));
+  } else if (!P->mixed) {
     for (int l = 1; l < P->nlev; ++l) CU(launch_galerkin<double>(P->lev[l - 1].A, P->lev[l].A, s));
   } else {
     // the FP32 cycle only needs FP32 coarse operators: Galerkin products in FP32, and the
@@ -435,8 +464,11 @@ mg_status problem_enqueue_build(mg_problem* P, const mg_map_desc* map, const dou
     if (P->nlev > 1) CU(launch_op_to_f64(P->lev[P->nlev - 1].A32, P->lev[P->nlev - 1].A, s));
   }
   CU(launch_coarse_factor(P->lev[P->nlev - 1].A, P->inv, P->flags + 1, s));
-  P->setup_kernels = 1 + 2 + (P->mixed ? 1 + (P->nlev - 1) + (P->nlev > 1 ? 1 : 0) : P->nlev - 1) + 1 +
-                     (P->mirror ? 1 : 0);
+  P->setup_kernels =
+      P->coarse_op == MG_COARSE_REDISCRETIZE
+          ? 1 + 2 + 3 * (P->nlev - 1) + (P->mixed ? P->nlev : 0) + 1 + (P->mirror ? 1 : 0)
+          : 1 + 2 + (P->mixed ? 1 + (P->nlev - 1) + (P->nlev > 1 ? 1 : 0) : P->nlev - 1) + 1 +
+                (P->mirror ? 1 : 0);
   if (P->line) {  // the line smoother's row factors follow the new operators
     mg_status ls = line_enqueue_factor(P, s);
     if (ls) return ls;
@@ -508,6 +540,8 @@ namespace mg {
 mg_status problem_create(mg_ctx* ctx, const mg_grid_desc* grid, const mg_solve_opts& o,
                          mg_problem** out) {
   *out = nullptr;
+  if (o.coarse_op != MG_COARSE_GALERKIN && o.coarse_op != MG_COARSE_REDISCRETIZE)
+    return set_error(MG_ERR_ARG, "bad coarse_op %d", o.coarse_op);
   cudaSetDevice(ctx->device);
   mg_problem* P = new mg_problem();
   P->ctx = ctx;
@@ -526,6 +560,7 @@ mg_status problem_create(mg_ctx* ctx, const mg_grid_desc* grid, const mg_solve_o
     P->grid.neumann_y = 0;
   }
   P->coarse_max = o.coarse_max;
+  P->coarse_op = o.coarse_op;
   P->mixed = (o.precision == MG_PREC_MIXED);
   mg_status st = check_grid(&P->grid, o.coarse_max, &P->nlev, P->nxs, P->nys);
   if (!st) st = problem_alloc(P, P->mixed);
@@ -963,6 +998,8 @@ mg_status check_opts(const mg_problem* P, const mg_solve_opts& o) {
   if (o.max_iters < 1 || !(o.rtol >= 0)) return set_error(MG_ERR_ARG, "bad rtol / max_iters");
   if (o.coarse_max != P->coarse_max)
     return set_error(MG_ERR_ARG, "coarse_max differs from the one the problem was set up with");
+  if (o.coarse_op != P->coarse_op)
+    return set_error(MG_ERR_ARG, "coarse_op differs from the one the problem was set up with");
   return MG_OK;
 }
 

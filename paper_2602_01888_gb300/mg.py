@@ -50,7 +50,8 @@ class mg_map_desc(C.Structure):
 class mg_solve_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("outer", C.c_int), ("smoother", C.c_int),
                 ("nu1", C.c_int), ("nu2", C.c_int), ("omega_j", C.c_double), ("rtol", C.c_double),
-                ("max_iters", C.c_int), ("coarse_max", C.c_int), ("warm_start", C.c_int)]
+                ("max_iters", C.c_int), ("coarse_max", C.c_int), ("warm_start", C.c_int),
+                ("coarse_op", C.c_int)]
 
 
 class mg_solve_stats(C.Structure):
@@ -143,6 +144,7 @@ _SIGS = {
                       C.c_void_p, C.c_void_p], C.c_int),
     "mgk_rhs": ([C.POINTER(mgk_op_f64), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "mgk_galerkin": ([C.POINTER(mgk_op_f64), C.POINTER(mgk_op_f64), C.c_void_p], C.c_int),
+    "mgk_coarsen_eps": ([C.POINTER(mgk_op_f64), C.POINTER(mgk_op_f64)] + [C.c_void_p] * 7, C.c_int),
     "mgk_op_to_f32": ([C.POINTER(mgk_op_f64), C.POINTER(mgk_op_f32), C.c_void_p], C.c_int),
     "mgk_smooth_f64": ([C.POINTER(mgk_op_f64), C.c_void_p, C.c_void_p, C.c_int, C.c_int,
                         C.c_void_p], C.c_int),
@@ -631,8 +633,12 @@ class Problem:
             pass
 
 
+_COARSE_OPS = {"galerkin": 0, "rediscretize": 1}
+
+
 def make_opts(precision="fp64", outer="fcg", rtol=1e-10, max_iters=200, nu1=2, nu2=2,
-              smoother="gs4", coarse_max=64, omega_j=0.8, warm_start=False) -> mg_solve_opts:
+              smoother="gs4", coarse_max=64, omega_j=0.8, warm_start=False,
+              coarse_op="galerkin") -> mg_solve_opts:
     o = mg_default_opts()
     o.precision = MG_PREC_MIXED if precision == "mixed" else MG_PREC_FP64
     if outer not in _OUTERS:
@@ -643,4 +649,7 @@ def make_opts(precision="fp64", outer="fcg", rtol=1e-10, max_iters=200, nu1=2, n
     o.smoother = _SMOOTHERS[smoother]
     o.rtol, o.max_iters, o.nu1, o.nu2 = rtol, max_iters, nu1, nu2
     o.coarse_max, o.omega_j, o.warm_start = coarse_max, omega_j, int(warm_start)
+    if coarse_op not in _COARSE_OPS:
+        raise ValueError(f"unknown coarse operator {coarse_op!r} (one of {sorted(_COARSE_OPS)})")
+    o.coarse_op = _COARSE_OPS[coarse_op]
     return o

@@ -649,3 +649,45 @@ def test_gaussian_potential_solves_the_radial_equation():
         assert abs(lap - want) < 1e-6 * max(1.0, want), (r, lap, want)
     c = f([0.0, 1e-4])
     assert abs(c[1] - c[0]) < 1e-5
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+def test_nodal_coarsening_is_full_weighting_inside_and_injection_on_the_ring(oracle, periodic):
+    """The tensor coarsening of the rediscretized hierarchy: at coarse unknowns it is the
+    full-weighting restriction (pinned by R = P^T / 4), on the boundary ring the coincident
+    fine value, and it reproduces a linear field exactly inside."""
+    rng = np.random.default_rng(5)
+    g = I.Grid(33, 33, periodic_y=periodic)
+    gc = I.Grid(17, 17, periodic_y=periodic)
+    f = rng.standard_normal(g.shape)
+    fc = oracle.coarsen_nodal(g.nx, g.ny, periodic, f)
+    inner = gc.interior_mask()
+    r = oracle.restrict(g.nx, g.ny, periodic, f)
+    assert np.abs(fc[inner] - r[inner]).max() < 1e-15 * np.abs(f).max()
+    ring = ~inner
+    assert np.array_equal(fc[ring], f[::2, ::2][: fc.shape[0]][ring])
+    x, y = g.coords()
+    lin = 0.3 + 1.7 * x - 0.9 * y if not periodic else 0.3 + 1.7 * x  # periodic rows: no y trend
+    xc, yc = gc.coords()
+    lin_c = 0.3 + 1.7 * xc - 0.9 * yc if not periodic else 0.3 + 1.7 * xc
+    assert np.abs(oracle.coarsen_nodal(g.nx, g.ny, periodic, lin) - lin_c).max() < 1e-14
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+def test_rediscretized_identity_levels_are_textbook_laplacians(oracle, periodic):
+    """For the identity map every rediscretized level is the 5-point Laplacian of its own
+    spacing (the coarsened tensor stays the identity)."""
+    g = I.Grid(65, 65, 0.0, 0.0, 1.0, 2.0, periodic_y=periodic)
+    P = oracle.prepare(I.Instance("id", g, I.MapSpec("identity"), np.zeros(g.shape)))
+    ops = oracle.rediscretized_hierarchy(g, P.exx, P.exy, P.eyy)
+    assert len(ops) >= 3
+    hx, hy = g.hx, g.hy
+    for A in ops:
+        gl = I.Grid(A.nx, A.ny, 0.0, 0.0, 1.0, 2.0, periodic_y=periodic)
+        m = gl.interior_mask()
+        assert np.allclose(A.diag[m], 2 / hx ** 2 + 2 / hy ** 2, rtol=1e-13)
+        inner_e = m.copy()
+        inner_e[:, -2:] = False
+        assert np.allclose(A.cE[inner_e], -1 / hx ** 2, rtol=1e-13)
+        assert np.abs(A.cNE).max() == 0 and np.abs(A.cNW).max() == 0
+        hx, hy = 2 * hx, 2 * hy

@@ -77,8 +77,9 @@ int mgk_rhs(const mgk_op_f64 *A, const double *rho_phys, const double *D, double
  * mg.h): each field e0, e1, e2 (eps_xx, eps_xy, eps_yy on fine's layout) at the coarse nodes
  * (c0, c1, c2 on coarse's layout): full weighting (1/16)[1 2 1; 2 4 2; 1 2 1] about the
  * coincident fine node at coarse unknowns, the coincident fine value on the boundary ring.
- * Only the sizes, periodicity and pitches of fine and coarse are used; coarse must be fine's
- * next level.  The coarse operator is then mgk_assemble on coarse with twice the spacing. */
+ * Only the sizes, periodicity and pitches of fine and coarse (and coarse->five_point: c1 is
+ * then written as 0 without reading e1) are used; coarse must be fine's next level.  The
+ * coarse operator is then mgk_assemble on coarse with twice the spacing. */
 int mgk_coarsen_eps(const mgk_op_f64 *fine, const mgk_op_f64 *coarse, const double *e0, const double *e1,
                     const double *e2, double *c0, double *c1, double *c2, void *stream);
 

@@ -166,11 +166,12 @@ __global__ void k_eps_grid(int nx, int ny, int nyr, int periodic, double i2hx, d
 
 // Couplings of the symmetric conservative 9-point operator A = -L_h.  five: eps_xy is zero
 // everywhere, so the NE / NW couplings are zero and written without reading it.
-__global__ void k_assemble_couplings(int nx, int ny, int nyr, int periodic, int pitch, double ihx2,
-                                     double ihy2, double ixy4, const double* __restrict__ exx,
-                                     const double* __restrict__ exy,
-                                     const double* __restrict__ eyy, double* cE, double* cN,
-                                     double* cNE, double* cNW, int five) {
+template <typename T>
+__global__ void k_assemble_couplings(int nx, int ny, int nyr, int periodic, int pitch, T ihx2,
+                                     T ihy2, T ixy4, const T* __restrict__ exx,
+                                     const T* __restrict__ exy,
+                                     const T* __restrict__ eyy, T* cE, T* cN,
+                                     T* cNE, T* cNW, int five) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= nx || j >= nyr) return;
@@ -178,10 +179,10 @@ __global__ void k_assemble_couplings(int nx, int ny, int nyr, int periodic, int 
   const bool has_up = periodic || (j + 1 <= ny - 1);
   const int ju = (j + 1 == nyr) ? 0 : j + 1;
   const size_t ku = (size_t)ju * pitch + i;
-  double e = 0.0, n = 0.0, ne = 0.0, nw = 0.0;
-  if (i + 1 <= nx - 1) e = -0.5 * (exx[k] + exx[k + 1]) * ihx2;
+  T e = T(0), n = T(0), ne = T(0), nw = T(0);
+  if (i + 1 <= nx - 1) e = T(-0.5) * (exx[k] + exx[k + 1]) * ihx2;
   if (has_up) {
-    n = -0.5 * (eyy[k] + eyy[ku]) * ihy2;
+    n = T(-0.5) * (eyy[k] + eyy[ku]) * ihy2;
     if (!five) {
       if (i + 1 <= nx - 1) ne = -(exy[k + 1] + exy[ku]) * ixy4;  // to (i+1, j+1)
       if (i >= 1) nw = (exy[k - 1] + exy[ku]) * ixy4;             // to (i-1, j+1)
@@ -197,26 +198,27 @@ __global__ void k_assemble_couplings(int nx, int ny, int nyr, int periodic, int 
 // zero NE / NW terms of a 5-point operator are left out of the sum (which they do not change).
 // dinv = 1 / diag unless dinv is null (a mixed-precision hierarchy takes its FP32 reciprocal
 // from the FP32 diagonal instead and never reads an FP64 one).
+template <typename T>
 __global__ void k_assemble_diag(int nx, int ny, int nyr, int periodic, int pitch,
-                                const double* __restrict__ cE, const double* __restrict__ cN,
-                                const double* __restrict__ cNE, const double* __restrict__ cNW,
-                                double* diag, double* dinv, int five) {
+                                const T* __restrict__ cE, const T* __restrict__ cN,
+                                const T* __restrict__ cNE, const T* __restrict__ cNW,
+                                T* diag, T* dinv, int five) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= nx || j >= nyr) return;
   const size_t k = (size_t)j * pitch + i;
   const bool unk = (i >= 1 && i <= nx - 2) && (periodic || (j >= 1 && j <= ny - 2));
   if (!unk) {
-    diag[k] = 1.0;
-    if (dinv) dinv[k] = 1.0;
+    diag[k] = T(1);
+    if (dinv) dinv[k] = T(1);
     return;
   }
   const int jd = (j == 0) ? nyr - 1 : j - 1;
   const size_t ks = (size_t)jd * pitch + i;
-  double s = cE[k] + cE[k - 1] + cN[k] + cN[ks];
+  T s = cE[k] + cE[k - 1] + cN[k] + cN[ks];
   if (!five) s = s + cNE[k] + cNE[ks - 1] + cNW[k] + cNW[ks + 1];
   diag[k] = -s;
-  if (dinv) dinv[k] = 1.0 / (-s);
+  if (dinv) dinv[k] = T(1) / (-s);
 }
 
 __global__ void k_rhs(int nx, int ny, int nyr, int periodic, int pitch,
@@ -234,9 +236,12 @@ __global__ void k_rhs(int nx, int ny, int nyr, int periodic, int pitch,
 // fields at coarse node (I, J), full weighting (1/16)[1 2 1; 2 4 2; 1 2 1] about fine node
 // (2I, 2J) where all eight fine neighbours exist (rows wrap when periodic), the coincident
 // fine value on the coarse boundary ring.
+// TS / TD: precision of the fine and of the coarse fields (the mixed path coarsens in FP32).
+// five: the cross term is zero on the fine level, so on the coarse one (written, not computed).
+template <typename TS, typename TD>
 __global__ void k_coarsen_eps(int nxf, int nyrf, int pf, int nxc, int nyc, int nyrc, int pc, int periodic,
-                              const double* __restrict__ f0, const double* __restrict__ f1,
-                              const double* __restrict__ f2, double* c0, double* c1, double* c2) {
+                              const TS* __restrict__ f0, const TS* __restrict__ f1,
+                              const TS* __restrict__ f2, TD* c0, TD* c1, TD* c2, int five) {
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   const int J = blockIdx.y * blockDim.y + threadIdx.y;
   if (I >= nxc || J >= nyrc) return;
@@ -244,17 +249,22 @@ __global__ void k_coarsen_eps(int nxf, int nyrf, int pf, int nxc, int nyc, int n
   const bool inner = (I >= 1 && I <= nxc - 2) && (periodic || (J >= 1 && J <= nyc - 2));
   const int jd = fj == 0 ? nyrf - 1 : fj - 1, ju = fj + 1 == nyrf ? 0 : fj + 1;
   const size_t r0 = (size_t)fj * pf, rd = (size_t)jd * pf, ru = (size_t)ju * pf, K = (size_t)J * pc + I;
-  const double* const f[3] = {f0, f1, f2};
-  double* const c[3] = {c0, c1, c2};
+  const TS* const f[3] = {f0, f1, f2};
+  TD* const c[3] = {c0, c1, c2};
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const double* g = f[a];
-    double v;
+    if (a == 1 && five) {
+      c[a][K] = TD(0);
+      continue;
+    }
+    const TS* g = f[a];
+    TD v;
     if (inner)
-      v = (4.0 * g[r0 + fi] + 2.0 * (g[r0 + fi - 1] + g[r0 + fi + 1] + g[rd + fi] + g[ru + fi]) +
-           (g[rd + fi - 1] + g[rd + fi + 1] + g[ru + fi - 1] + g[ru + fi + 1])) / 16.0;
+      v = (TD(4) * TD(g[r0 + fi]) +
+           TD(2) * (TD(g[r0 + fi - 1]) + TD(g[r0 + fi + 1]) + TD(g[rd + fi]) + TD(g[ru + fi])) +
+           (TD(g[rd + fi - 1]) + TD(g[rd + fi + 1]) + TD(g[ru + fi - 1]) + TD(g[ru + fi + 1]))) / TD(16);
     else
-      v = g[r0 + fi];
+      v = TD(g[r0 + fi]);
     c[a][K] = v;
   }
 }
@@ -443,18 +453,23 @@ cudaError_t launch_eps_grid(int nx, int ny, int periodic, double hx, double hy, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_assemble(const OpF64& A, double hx, double hy, const double* exx,
-                            const double* exy, const double* eyy, cudaStream_t s, bool dinv) {
+template <typename T>
+cudaError_t launch_assemble(const Op<T>& A, double hx, double hy, const T* exx, const T* exy, const T* eyy,
+                            cudaStream_t s, bool dinv) {
   const int nyr = rows_stored(A.ny, A.periodic);
   dim3 b(32, 8);
-  k_assemble_couplings<<<grid2(A.nx, nyr, b), b, 0, s>>>(
-      A.nx, A.ny, nyr, A.periodic, A.pitch, 1.0 / (hx * hx), 1.0 / (hy * hy), 1.0 / (4.0 * hx * hy),
+  k_assemble_couplings<T><<<grid2(A.nx, nyr, b), b, 0, s>>>(
+      A.nx, A.ny, nyr, A.periodic, A.pitch, T(1.0 / (hx * hx)), T(1.0 / (hy * hy)), T(1.0 / (4.0 * hx * hy)),
       exx, exy, eyy, A.cE, A.cN, A.cNE, A.cNW, A.five_point);
-  k_assemble_diag<<<grid2(A.nx, nyr, b), b, 0, s>>>(A.nx, A.ny, nyr, A.periodic, A.pitch, A.cE,
-                                                    A.cN, A.cNE, A.cNW, A.diag, dinv ? A.dinv : nullptr,
-                                                    A.five_point);
+  k_assemble_diag<T><<<grid2(A.nx, nyr, b), b, 0, s>>>(A.nx, A.ny, nyr, A.periodic, A.pitch, A.cE,
+                                                       A.cN, A.cNE, A.cNW, A.diag, dinv ? A.dinv : nullptr,
+                                                       A.five_point);
   return cudaGetLastError();
 }
+template cudaError_t launch_assemble<double>(const OpF64&, double, double, const double*, const double*,
+                                             const double*, cudaStream_t, bool);
+template cudaError_t launch_assemble<float>(const OpF32&, double, double, const float*, const float*,
+                                            const float*, cudaStream_t, bool);
 
 cudaError_t launch_rhs(const OpF64& A, const double* rho, int rho_pitch, const double* D, double* b,
                        cudaStream_t s) {
@@ -465,15 +480,22 @@ cudaError_t launch_rhs(const OpF64& A, const double* rho, int rho_pitch, const d
   return cudaGetLastError();
 }
 
-cudaError_t launch_coarsen_eps(const OpF64& F, const OpF64& C, const double* const* e, double* const* c,
+template <typename TS, typename TD>
+cudaError_t launch_coarsen_eps(const Op<TS>& F, const Op<TD>& C, const TS* const* e, TD* const* c,
                                cudaStream_t s) {
   const int nyrc = rows_stored(C.ny, C.periodic);
   dim3 b(32, 8);
-  k_coarsen_eps<<<grid2(C.nx, nyrc, b), b, 0, s>>>(F.nx, rows_stored(F.ny, F.periodic), F.pitch, C.nx, C.ny,
-                                                    nyrc, C.pitch, C.periodic, e[0], e[1], e[2], c[0], c[1],
-                                                    c[2]);
+  k_coarsen_eps<TS, TD><<<grid2(C.nx, nyrc, b), b, 0, s>>>(F.nx, rows_stored(F.ny, F.periodic), F.pitch, C.nx,
+                                                            C.ny, nyrc, C.pitch, C.periodic, e[0], e[1], e[2],
+                                                            c[0], c[1], c[2], C.five_point);
   return cudaGetLastError();
 }
+template cudaError_t launch_coarsen_eps<double, double>(const OpF64&, const OpF64&, const double* const*,
+                                                        double* const*, cudaStream_t);
+template cudaError_t launch_coarsen_eps<double, float>(const OpF64&, const OpF32&, const double* const*,
+                                                       float* const*, cudaStream_t);
+template cudaError_t launch_coarsen_eps<float, float>(const OpF32&, const OpF32&, const float* const*,
+                                                      float* const*, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_galerkin(const Op<T>& F, const Op<T>& C, cudaStream_t s) {

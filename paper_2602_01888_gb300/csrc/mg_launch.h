@@ -79,12 +79,15 @@ cudaError_t launch_mirror_eps(int nx, int n, int ps, const double* D0, const dou
                               double* exy, double* eyy, cudaStream_t s);
 // Nodal tensor (e[0..2]: eps_xx, eps_xy, eps_yy of level F) coarsened to level C (c[0..2]):
 // full weighting inside, injection on the boundary ring (rediscretized hierarchies).
-cudaError_t launch_coarsen_eps(const OpF64& F, const OpF64& C, const double* const* e, double* const* c,
+template <typename TS, typename TD>
+cudaError_t launch_coarsen_eps(const Op<TS>& F, const Op<TD>& C, const TS* const* e, TD* const* c,
                                cudaStream_t s);
 // dinv = false: A.dinv is not written (a mixed-precision hierarchy's FP64 level 0, whose
 // reciprocal diagonal is taken in FP32 by launch_op_to_f32 with dinv_f32).
-cudaError_t launch_assemble(const OpF64& A, double hx, double hy, const double* exx,
-                            const double* exy, const double* eyy, cudaStream_t s, bool dinv = true);
+// In FP32 for the coarse levels of a mixed rediscretized hierarchy.
+template <typename T>
+cudaError_t launch_assemble(const Op<T>& A, double hx, double hy, const T* exx, const T* exy, const T* eyy,
+                            cudaStream_t s, bool dinv = true);
 cudaError_t launch_rhs(const OpF64& A, const double* rho, int rho_pitch, const double* D, double* b,
                        cudaStream_t s);
 template <typename T>

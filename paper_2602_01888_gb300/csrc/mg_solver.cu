@@ -433,27 +433,45 @@ mg_status problem_enqueue_build(mg_problem* P, const mg_map_desc* map, const dou
   }
   if (P->coarse_op == MG_COARSE_REDISCRETIZE) {
     // each coarse level: the tensor of the level above coarsened (into the level's scratch
-    // arrays x, b, t), then assembled on the coarse grid like the finest level
-    const double* e[3] = {exx, exy, eyy};
+    // arrays x, b, t), then assembled on the coarse grid like the finest level; a mixed
+    // hierarchy does it in FP32 (its cycle runs on FP32 operators; the coarsest is widened to
+    // FP64 for its dense inverse, as with Galerkin products)
     double hxl = hx, hyl = hy;
-    for (int l = 1; l < P->nlev; ++l) {
-      LevelMem& C = P->lev[l];
-      double* c[3] = {C.x, C.b, C.t};
-      CU(launch_coarsen_eps(P->lev[l - 1].A, C.A, e, c, s));
-      hxl *= 2.0;
-      hyl *= 2.0;
-      CU(launch_assemble(C.A, hxl, hyl, c[0], c[1], c[2], s, !P->mixed));
-      for (int k = 0; k < 3; ++k) e[k] = c[k];
+    if (!P->mixed) {
+      const double* e[3] = {exx, exy, eyy};
+      for (int l = 1; l < P->nlev; ++l) {
+        LevelMem& C = P->lev[l];
+        double* c[3] = {C.x, C.b, C.t};
+        CU((launch_coarsen_eps<double, double>(P->lev[l - 1].A, C.A, e, c, s)));
+        hxl *= 2.0;
+        hyl *= 2.0;
+        CU(launch_assemble<double>(C.A, hxl, hyl, c[0], c[1], c[2], s));
+        for (int k = 0; k < 3; ++k) e[k] = c[k];
+      }
+    } else {
+      CU(launch_op_to_f32(F.A, F.A32, s, true));
+      const double* e64[3] = {exx, exy, eyy};
+      const float* e[3] = {nullptr, nullptr, nullptr};
+      for (int l = 1; l < P->nlev; ++l) {
+        LevelMem& C = P->lev[l];
+        float* c[3] = {C.x32, C.b32, C.t32};
+        if (l == 1) CU((launch_coarsen_eps<double, float>(F.A, C.A32, e64, c, s)));
+        else CU((launch_coarsen_eps<float, float>(P->lev[l - 1].A32, C.A32, e, c, s)));
+        hxl *= 2.0;
+        hyl *= 2.0;
+        CU(launch_assemble<float>(C.A32, hxl, hyl, c[0], c[1], c[2], s));
+        for (int k = 0; k < 3; ++k) e[k] = c[k];
+      }
+      if (P->nlev > 1) CU(launch_op_to_f64(P->lev[P->nlev - 1].A32, P->lev[P->nlev - 1].A, s));
     }
     // the coarse levels' iterates, right-hand sides and scratch held the tensors: zero them
     // again (the cycles rely on zero Dirichlet rings on coarse levels)
     for (int l = 1; l < P->nlev; ++l) {
       const LevelMem& C = P->lev[l];
       const size_t n = (size_t)C.A.pitch * rows_stored(C.A.ny, C.A.periodic);
-      CU(cudaMemsetAsync(C.x, 0, 3 * n * sizeof(double), s));  // x, b, t are contiguous
+      if (P->mixed) CU(cudaMemsetAsync(C.x32, 0, 3 * n * sizeof(float), s));  // x32, b32, t32 contiguous
+      else CU(cudaMemsetAsync(C.x, 0, 3 * n * sizeof(double), s));            // x, b, t contiguous
     }
-    if (P->mixed)  // FP32 levels: reciprocal diagonals of the FP32 diagonals, as above
-      for (int l = 0; l < P->nlev; ++l) CU(launch_op_to_f32(P->lev[l].A, P->lev[l].A32, s, true));
   } else if (!P->mixed) {
     for (int l = 1; l < P->nlev; ++l) CU(launch_galerkin<double>(P->lev[l - 1].A, P->lev[l].A, s));
   } else {
@@ -466,7 +484,7 @@ mg_status problem_enqueue_build(mg_problem* P, const mg_map_desc* map, const dou
   CU(launch_coarse_factor(P->lev[P->nlev - 1].A, P->inv, P->flags + 1, s));
   P->setup_kernels =
       P->coarse_op == MG_COARSE_REDISCRETIZE
-          ? 1 + 2 + 3 * (P->nlev - 1) + (P->mixed ? P->nlev : 0) + 1 + (P->mirror ? 1 : 0)
+          ? 1 + 2 + 3 * (P->nlev - 1) + (P->mixed ? 1 + (P->nlev > 1 ? 1 : 0) : 0) + 1 + (P->mirror ? 1 : 0)
           : 1 + 2 + (P->mixed ? 1 + (P->nlev - 1) + (P->nlev > 1 ? 1 : 0) : P->nlev - 1) + 1 +
                 (P->mirror ? 1 : 0);
   if (P->line) {  // the line smoother's row factors follow the new operators

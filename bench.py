@@ -586,18 +586,24 @@ def cycle_model(prec, smoother, nu, five=False):
     post-smoothing pass also reads the quarter-size correction (68 + 3C bytes at FP64 for
     V(2,2)).  Line smoother: 14 elements per sweep (six off-row couplings, iterate in and
     out, b, five factor arrays), plus the residual + restriction pass and a prolongation
-    pass.  Flops: 18 per unknown update and per residual.  five: the finest operator is a
-    5-point stencil (no NE / NW couplings): 10 elements per line sweep, a residual pass of
-    5 + 1/4, 10 flops per residual and 16 per line update instead of 24."""
+    pass.  After line pre-smoothing the residual is computed on the even rows only (the odd
+    rows were just solved exactly): x of every row, b, diag and the E coupling of the even
+    rows, the N, NE and NW couplings of every row (they couple an even row to both of its
+    neighbours): 5.5 elements + 1/4, 9 flops per fine node; with nu1 = 0 the whole residual,
+    7 + 1/4 elements and 18 flops.  Flops: 18 per unknown update.  five: the finest operator
+    is a 5-point stencil (no NE / NW couplings): 10 elements per line sweep, a residual pass
+    of 3.5 + 1/4 (5 + 1/4 in full), 5 flops per fine node (10 in full) and 16 per line update
+    instead of 24."""
     e = 8.0 if prec == "fp64" else 4.0
     n1, n2 = nu
     if smoother == "xline":
+        half = 0.5 if n1 > 0 else 1.0  # share of the rows whose residual is computed
         if five:
-            fine = (n1 + n2) * 10 * e + (5 + 0.25) * e + (2 + 0.25) * e
-            flops = (n1 + n2) * 16.0 + 10.0 + 8.0
+            fine = (n1 + n2) * 10 * e + (3.5 if n1 > 0 else 5.0) * e + 0.25 * e + (2 + 0.25) * e
+            flops = (n1 + n2) * 16.0 + 10.0 * half + 8.0
         else:
-            fine = (n1 + n2) * 14 * e + (7 + 0.25) * e + (2 + 0.25) * e
-            flops = (n1 + n2) * 24.0 + 18.0 + 8.0
+            fine = (n1 + n2) * 14 * e + (5.5 if n1 > 0 else 7.0) * e + 0.25 * e + (2 + 0.25) * e
+            flops = (n1 + n2) * 24.0 + 18.0 * half + 8.0
     else:
         p1, p2 = -(-n1 // 2), -(-n2 // 2)
         fine = (p1 + 1 + p2) * 5 * e + p1 * 3 * e + (2 + 0.25) * e + p2 * 3 * e + 0.25 * e
@@ -730,6 +736,8 @@ def run_kernel_only(args):
                    b.data_ptr(), 0, bH.data_ptr() if corr else None, pc if corr else 0, None, s)
         elif args.kernel.startswith("smooth"):
             mg.mgk(f"mgk_smooth_{sfx}", C.byref(st), x.data_ptr(), b.data_ptr(), 1, 0, s)
+        elif args.kernel.startswith("restricte"):  # the even-row form used after line pre-smoothing
+            mg.mgk(f"mgk_resid_restrict_even_{sfx}", C.byref(st), x.data_ptr(), b.data_ptr(), bH.data_ptr(), pc, s)
         elif args.kernel.startswith("restrict"):
             mg.mgk(f"mgk_resid_restrict_{sfx}", C.byref(st), x.data_ptr(), b.data_ptr(), bH.data_ptr(), pc, s)
         elif args.kernel.startswith("prolong"):
@@ -1355,7 +1363,7 @@ def main():
     ap.add_argument("--kernel-only", dest="kernel", default=None,
                     help="smooth64|smooth32|fused64|fused32|pipe64|pipe32|march32|march32p|march64|march64p|"
                          "line64|line32|"
-                         "restrict64|restrict32|prolong64|prolong32|fp64peak|fp32peak")
+                         "restrict64|restrict32|restricte64|restricte32|prolong64|prolong32|fp64peak|fp32peak")
     ap.add_argument("--side", type=int, default=2049)
     ap.add_argument("--ny", type=int, default=0, help="kernel-only: rows (default: --side)")
     ap.add_argument("--reps", type=int, default=5)

@@ -123,6 +123,17 @@ int mgk_resid_restrict_f64(const mgk_op_f64 *A, const double *phi, const double 
 int mgk_resid_restrict_f32(const mgk_op_f32 *A, const float *phi, const float *b, float *bH,
                            int pitch_c, void *stream);
 
+/* The same restriction for a phi whose odd rows (j odd) were the last ones solved exactly by
+ * a zebra x-line half-sweep (Sec. 2.1 smoothing with whole rows as blocks): b - A phi is zero
+ * on those rows up to the rounding of the row solves, so it is taken as zero there and
+ * bH(I,J) = (1/16)(2 r(2I-1,2J) + 4 r(2I,2J) + 2 r(2I+1,2J)) from the even rows alone.
+ * Same arguments, sizes and error returns as mgk_resid_restrict_*; it equals them exactly
+ * when the odd rows' residual is exactly zero. */
+int mgk_resid_restrict_even_f64(const mgk_op_f64 *A, const double *phi, const double *b,
+                                double *bH, int pitch_c, void *stream);
+int mgk_resid_restrict_even_f32(const mgk_op_f32 *A, const float *phi, const float *b, float *bH,
+                                int pitch_c, void *stream);
+
 /* phi += I_H^h eH (bilinear interpolation, Eq. 24) at fine unknowns; A gives the fine
  * sizes and pitch, eH the coarse array with pitch pitch_c. */
 int mgk_prolong_add_f64(const mgk_op_f64 *A, double *phi, const double *eH, int pitch_c,

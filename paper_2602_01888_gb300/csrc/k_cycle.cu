@@ -103,6 +103,44 @@ __global__ void __launch_bounds__(kRRX* kRRY)
   }
 }
 
+// Residual and full weighting after zebra x-line pre-smoothing, whose last half-sweep solved
+// every odd row exactly from its even neighbours: b - A x is then zero on the odd rows up to
+// the rounding of the row solves, and full weighting at coarse node (I, J) keeps only the
+// fine row 2J, bH = (4 r(2I) + 2 (r(2I-1) + r(2I+1))) / 16 (the stencil's odd-row and corner
+// terms vanish).  Half of the fine residuals are computed, from even rows of b, diag and the
+// couplings and from all rows of x.  One thread per coarse node computes r(2I) and r(2I+1)
+// of row 2J; r(2I-1) is its left neighbour's r(2I+1), handed over in shared memory (the
+// block's first thread computes the one left of the block).  Summation order as in
+// k_resid_restrict with the odd-row terms zero.
+template <typename T>
+__global__ void __launch_bounds__(kREven) k_resid_restrict_even(Lvl<T> L, const T* __restrict__ x,
+                                                                const T* __restrict__ b, T* __restrict__ bH,
+                                                                T* __restrict__ xH, int nxc, int nyc,
+                                                                int pitchc, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  __shared__ T rodd[kREven + 1];
+  const int J = blockIdx.y, j = 2 * J;
+  const int I = blockIdx.x * kREven + threadIdx.x;
+  const auto res = [&](int i) -> T {
+    if (!is_unknown(L, i, j)) return T(0);
+    const size_t k = (size_t)j * L.pitch + i;
+    return b[k] - fma(L.diag[k], x[k], offdiag(L, x, i, j));
+  };
+  T r0 = T(0), r1 = T(0);
+  if (I < nxc) {
+    r0 = res(2 * I);
+    r1 = res(2 * I + 1);
+  }
+  if (threadIdx.x == 0) rodd[0] = res(2 * I - 1);
+  rodd[threadIdx.x + 1] = r1;
+  __syncthreads();
+  if (I >= nxc) return;
+  const bool unk = (I >= 1 && I <= nxc - 2) && (L.periodic || (J >= 1 && J <= nyc - 2));
+  const size_t K = (size_t)J * pitchc + I;
+  bH[K] = unk ? (T(4) * r0 + T(2) * (rodd[threadIdx.x] + r1)) * T(0.0625) : T(0);
+  if (xH) xH[K] = T(0);
+}
+
 // x += P eH (bilinear: injection at coincident nodes, 1/2 on edges, 1/4 at centres).
 template <typename T>
 __global__ void __launch_bounds__(256) k_prolong_add(Lvl<T> L, T* __restrict__ x,
@@ -221,6 +259,17 @@ cudaError_t launch_resid_restrict(const Op<T>& A, const T* phi, const T* b, T* b
 }
 
 template <typename T>
+cudaError_t launch_resid_restrict_even(const Op<T>& A, const T* phi, const T* b, T* bH, T* phiH,
+                                       int pitch_c, const int* skip, cudaStream_t s) {
+  const Lvl<T> L = lvl_of(A);
+  const int nxc = (A.nx - 1) / 2 + 1, nyc = (A.ny - 1) / 2 + 1;
+  const int nyrc = rows_stored(nyc, A.periodic);
+  dim3 grid((nxc + kREven - 1) / kREven, nyrc);
+  k_resid_restrict_even<T><<<grid, kREven, 0, s>>>(L, phi, b, bH, phiH, nxc, nyc, pitch_c, skip);
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_prolong_add(const Op<T>& A, T* phi, const T* eH, int pitch_c, const int* skip,
                                cudaStream_t s) {
   const Lvl<T> L = lvl_of(A);
@@ -251,6 +300,8 @@ cudaError_t launch_coarse_solve(const Op<T>& A, const double* inv, const T* b, T
                                         const int*, cudaStream_t);                               \
   template cudaError_t launch_resid_restrict<T>(const Op<T>&, const T*, const T*, T*, T*, int, \
                                                 const int*, cudaStream_t);                       \
+  template cudaError_t launch_resid_restrict_even<T>(const Op<T>&, const T*, const T*, T*, T*,  \
+                                                     int, const int*, cudaStream_t);             \
   template cudaError_t launch_prolong_add<T>(const Op<T>&, T*, const T*, int, const int*,      \
                                              cudaStream_t);                                      \
   template cudaError_t launch_coarse_solve<T>(const Op<T>&, const double*, const T*, T*,       \
@@ -317,6 +368,22 @@ extern "C" int mgk_resid_restrict_f32(const mgk_op_f32* A, const float* phi, con
     return 1;
   return rc(launch_resid_restrict(op_from(*A), phi, b, bH, (float*)nullptr, pitch_c, nullptr,
                                   (cudaStream_t)stream));
+}
+extern "C" int mgk_resid_restrict_even_f64(const mgk_op_f64* A, const double* phi, const double* b,
+                                           double* bH, int pitch_c, void* stream) {
+  if (!opk(A) || !phi || !b || !bH || (A->nx - 1) % 2 || (A->ny - 1) % 2 ||
+      pitch_c < (A->nx - 1) / 2 + 1)
+    return 1;
+  return rc(launch_resid_restrict_even(op_from(*A), phi, b, bH, (double*)nullptr, pitch_c, nullptr,
+                                       (cudaStream_t)stream));
+}
+extern "C" int mgk_resid_restrict_even_f32(const mgk_op_f32* A, const float* phi, const float* b,
+                                           float* bH, int pitch_c, void* stream) {
+  if (!opk(A) || !phi || !b || !bH || (A->nx - 1) % 2 || (A->ny - 1) % 2 ||
+      pitch_c < (A->nx - 1) / 2 + 1)
+    return 1;
+  return rc(launch_resid_restrict_even(op_from(*A), phi, b, bH, (float*)nullptr, pitch_c, nullptr,
+                                       (cudaStream_t)stream));
 }
 extern "C" int mgk_prolong_add_f64(const mgk_op_f64* A, double* phi, const double* eH,
                                    int pitch_c, void* stream) {

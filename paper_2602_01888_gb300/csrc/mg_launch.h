@@ -12,6 +12,7 @@ constexpr int kCoarseThreads = 256;  // threads of the single-CTA coarsest solve
 constexpr int kCoarseFactorThreads = 1024;
 constexpr int kCoarseSmemM = 128;    // coarsest inverses up to this order are formed in shared memory
 constexpr int kRRX = 16, kRRY = 16;  // coarse tile of the residual + restriction kernel
+constexpr int kREven = 128;          // coarse nodes (threads) per block of the even-row form
 
 template <typename T>
 struct Op {
@@ -119,6 +120,11 @@ cudaError_t launch_jacobi(const Op<T>& A, T* phi, const T* b, T* tmp, int sweeps
 template <typename T>
 cudaError_t launch_resid_restrict(const Op<T>& A, const T* phi, const T* b, T* bH, T* phiH,
                                   int pitch_c, const int* skip, cudaStream_t s);
+// The same after a pre-smoothing whose last half-sweep solved every odd row exactly (zebra
+// x-line): the odd rows' residual is taken as zero and only the even rows' is computed.
+template <typename T>
+cudaError_t launch_resid_restrict_even(const Op<T>& A, const T* phi, const T* b, T* bH, T* phiH,
+                                       int pitch_c, const int* skip, cudaStream_t s);
 template <typename T>
 cudaError_t launch_prolong_add(const Op<T>& A, T* phi, const T* eH, int pitch_c, const int* skip,
                                cudaStream_t s);

@@ -149,9 +149,12 @@ cudaError_t emit_vcycle(const VLevels<T>& V, int smoother, int nu1, int nu2, dou
       const int zero = l == 0 ? (x0_zero && zs) : zs;
       if ((e = launch_line_smooth(V.A[l], V.lf[l], cur[l], V.b[l], nu1, 0, skip, s, (const T*)nullptr, 0, zero)))
         return e;
-      // the tail kernel reads the iterate of its first level: clear it there
-      if ((e = launch_resid_restrict(V.A[l], cur[l], V.b[l], V.b[l + 1], zs && l + 1 < t ? nullptr : cur[l + 1],
-                                     V.A[l + 1].pitch, skip, s)))
+      // the tail kernel reads the iterate of its first level: clear it there.  After
+      // pre-smoothing, whose last half-sweep solved the odd rows, only the even rows'
+      // residual is restricted (launch_resid_restrict_even).
+      T* const xc = zs && l + 1 < t ? nullptr : cur[l + 1];
+      if ((e = zs ? launch_resid_restrict_even(V.A[l], cur[l], V.b[l], V.b[l + 1], xc, V.A[l + 1].pitch, skip, s)
+                  : launch_resid_restrict(V.A[l], cur[l], V.b[l], V.b[l + 1], xc, V.A[l + 1].pitch, skip, s)))
         return e;
     }
     if (t == L - 1) {

@@ -162,6 +162,10 @@ _SIGS = {
                                 C.c_void_p], C.c_int),
     "mgk_resid_restrict_f32": ([C.POINTER(mgk_op_f32), C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                                 C.c_void_p], C.c_int),
+    "mgk_resid_restrict_even_f64": ([C.POINTER(mgk_op_f64), C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                                     C.c_void_p], C.c_int),
+    "mgk_resid_restrict_even_f32": ([C.POINTER(mgk_op_f32), C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                                     C.c_void_p], C.c_int),
     "mgk_prolong_add_f64": ([C.POINTER(mgk_op_f64), C.c_void_p, C.c_void_p, C.c_int, C.c_void_p],
                             C.c_int),
     "mgk_prolong_add_f32": ([C.POINTER(mgk_op_f32), C.c_void_p, C.c_void_p, C.c_int, C.c_void_p],

@@ -28,12 +28,23 @@ def test_point_cycle_bytes_match_the_three_pass_count():
 
 
 def test_line_cycle_bytes():
-    """x-line V(1,1): two sweeps of 14 elements, the residual + restriction pass (7.25) and
-    the prolongation pass (2.25): 150 B per fine node at FP32."""
-    b, _ = bench.cycle_model("mixed", "xline", (1, 1))
-    assert b == pytest.approx(150.0 * 4 / 3)
+    """x-line V(1,1): two sweeps of 14 elements, the even-row residual + restriction pass
+    (5.5 + 0.25: x of all rows, b, diag and cE of the even rows, cN, cNE and cNW of all rows)
+    and the prolongation pass (2.25): 144 B per fine node at FP32; 5-point finest level:
+    two sweeps of 10, 3.5 + 0.25 and 2.25: 104 B.  Without pre-smoothing the residual pass
+    reads everything (7.25, 5.25)."""
+    b, f = bench.cycle_model("mixed", "xline", (1, 1))
+    assert b == pytest.approx(144.0 * 4 / 3)
+    assert f == pytest.approx((2 * 24 + 9 + 8) * 4 / 3)
     b64, _ = bench.cycle_model("fp64", "xline", (1, 1))
     assert b64 == pytest.approx(2 * b)
+    b5, f5 = bench.cycle_model("mixed", "xline", (1, 1), five=True)
+    assert b5 == pytest.approx(104.0 * 4 / 3)
+    assert f5 == pytest.approx((2 * 16 + 5 + 8) * 4 / 3)
+    b01, _ = bench.cycle_model("mixed", "xline", (0, 1))
+    assert b01 == pytest.approx((56 + 29 + 9) * 4 / 3)
+    b015, _ = bench.cycle_model("mixed", "xline", (0, 1), five=True)
+    assert b015 == pytest.approx((40 + 21 + 9) * 4 / 3)
 
 
 def _args(workload, smoother=None, nu=None):

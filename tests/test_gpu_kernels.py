@@ -220,6 +220,44 @@ def test_residual_restriction_and_prolongation_match_oracle(libmg, oracle, cuda,
         assert np.abs(_host(x, g.nx) - ref_x).max() <= tol * 10
 
 
+@pytest.mark.parametrize("case", ["sine_97x65", "incl_129", "annulus_65", "rect_33x17", "tiny_5", "periodic_17",
+                                  "sinh_65"])
+def test_even_row_restriction_matches_oracle(libmg, oracle, cuda, case):
+    """mgk_resid_restrict_even (the restriction after zebra x-line pre-smoothing): on any
+    iterate it is the oracle's full weighting of the residual with the odd rows set to zero;
+    after one oracle zebra sweep (even rows, then odd rows) it is the oracle's full weighting
+    of the true residual, whose odd rows are then rounding residue."""
+    torch = cuda
+    inst = CASES[case]()
+    P = oracle.prepare(inst)
+    g = inst.grid
+    gc = _coarse_grid(g)
+    rng = np.random.default_rng(12)
+    phi0 = rng.standard_normal(g.shape)
+    b = rng.standard_normal(g.shape) * np.abs(P.A.diag).max()
+    r0 = oracle.residual(P.A, phi0, b)
+    r0[1::2, :] = 0.0
+    phi1 = oracle.smooth(P.A, phi0, b, sweeps=1, smoother=oracle.SMOOTHER_XLINE)
+    refs = ((phi0, oracle.restrict(g.nx, g.ny, g.periodic_y, r0)),
+            (phi1, oracle.restrict(g.nx, g.ny, g.periodic_y, oracle.residual(P.A, phi1, b))))
+    pc = gc.nx + 5
+    for dt, tol, f32 in ((torch.float64, 1e-13, False), (torch.float32, 2e-6, True)):
+        ops = _op_tensors(torch, P.A, dtype=dt)
+        s = libmg.op_struct(ops, g.nx, g.ny, g.periodic_y, f32=f32)
+        for phi, ref in refs:
+            bH = torch.full((gc.nyr, pc), float("nan"), dtype=dt, device="cuda")
+            p_d, b_d = _dev(torch, phi, dtype=dt), _dev(torch, b, dtype=dt)  # held until the launch ran
+            libmg.mgk("mgk_resid_restrict_even_f32" if f32 else "mgk_resid_restrict_even_f64", C.byref(s),
+                      p_d.data_ptr(), b_d.data_ptr(), bH.data_ptr(), pc, _stream(torch))
+            torch.cuda.synchronize()
+            scale = np.abs(P.A.diag).max() * np.abs(phi).max()
+            assert np.abs(_host(bH, gc.nx) - ref).max() <= tol * scale, (case, f32)
+    with pytest.raises(Exception):  # missing arrays are refused before any launch
+        libmg.mgk("mgk_resid_restrict_even_f64", C.byref(libmg.op_struct(_op_tensors(torch, P.A), g.nx, g.ny,
+                                                                           g.periodic_y)),
+                  None, None, None, pc, _stream(torch))
+
+
 @pytest.mark.parametrize("case", ["tiny_5", "periodic_17", "rect_33x17"])
 def test_coarsest_inverse_solve_matches_dense_oracle(libmg, oracle, cuda, case):
     torch = cuda

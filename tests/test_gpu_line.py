@@ -104,8 +104,8 @@ def test_sweeps_match_oracle(libmg, oracle, cuda, case, prec, sweeps, rev):
     keep, s = _op(libmg, torch, A, dt)
     f = _factors(libmg, torch, A, s, dt, prec)
     phi, b = _data(A, 7)
-    x = _dev(torch, phi, dt)
-    libmg.mgk(f"mgk_line_smooth_{prec}", C.byref(s), f.data_ptr(), x.data_ptr(), _dev(torch, b, dt).data_ptr(),
+    x, b_d = _dev(torch, phi, dt), _dev(torch, b, dt)
+    libmg.mgk(f"mgk_line_smooth_{prec}", C.byref(s), f.data_ptr(), x.data_ptr(), b_d.data_ptr(),
               sweeps, rev, torch.cuda.current_stream().cuda_stream)
     torch.cuda.synchronize()
     ref = oracle.smooth(A, phi, b, sweeps=sweeps, reverse=bool(rev), smoother=oracle.SMOOTHER_XLINE)
@@ -128,8 +128,8 @@ def test_longest_rows(libmg, oracle, cuda, prec, nx):
     phi, b = _data(A, 9)
     x = _dev(torch, phi, dt)
     stream = torch.cuda.current_stream().cuda_stream
-    libmg.mgk(f"mgk_line_smooth_{prec}", C.byref(s), f.data_ptr(), x.data_ptr(), _dev(torch, b, dt).data_ptr(),
-              1, 0, stream)
+    b_d = _dev(torch, b, dt)
+    libmg.mgk(f"mgk_line_smooth_{prec}", C.byref(s), f.data_ptr(), x.data_ptr(), b_d.data_ptr(), 1, 0, stream)
     torch.cuda.synchronize()
     ref = oracle.smooth(A, phi, b, sweeps=1, smoother=oracle.SMOOTHER_XLINE)
     assert _rel(x.double().cpu().numpy(), ref) < (1e-12 if prec == "f64" else 2e-5)

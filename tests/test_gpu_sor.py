@@ -40,8 +40,8 @@ def test_sor_sweeps_match_oracle(libmg, oracle, cuda, case, prec, omega, sweeps)
     rng = np.random.default_rng(11)
     phi = rng.standard_normal(A.cE.shape)
     b = rng.standard_normal(A.cE.shape) * np.abs(A.diag).max()
-    x = _dev(torch, phi, dt)
-    libmg.mgk(f"mgk_sor_{prec}", C.byref(s), x.data_ptr(), _dev(torch, b, dt).data_ptr(), sweeps, omega,
+    x, b_d = _dev(torch, phi, dt), _dev(torch, b, dt)
+    libmg.mgk(f"mgk_sor_{prec}", C.byref(s), x.data_ptr(), b_d.data_ptr(), sweeps, omega,
               torch.cuda.current_stream().cuda_stream)
     torch.cuda.synchronize()
     ref = oracle.smooth(A, phi, b, sweeps=sweeps, smoother=oracle.SMOOTHER_SOR4, omega_j=omega)

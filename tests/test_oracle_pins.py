@@ -397,6 +397,33 @@ def test_line_half_sweep_zeroes_the_residual_on_its_rows(oracle, case, parity):
     assert np.array_equal(phi[keep | other], phi0[keep | other])
 
 
+@pytest.mark.parametrize("case", ["sine", "annulus", "inclusion"])
+def test_zebra_sweep_leaves_a_residual_on_the_even_rows_only(oracle, case):
+    """After a zebra sweep (even rows, then odd rows) the residual is rounding residue on the
+    odd rows, so full weighting of it reduces to the even rows: at coarse node (I, J),
+    (2 r(2I-1, 2J) + 4 r(2I, 2J) + 2 r(2I+1, 2J)) / 16.  The restriction after line
+    pre-smoothing relies on this; here it is the oracle's full weighting of the whole
+    residual against that one-row sum written out."""
+    inst = {"sine": lambda: I.config1(33), "annulus": lambda: I.annulus_log(33),
+            "inclusion": lambda: I.inclusion_instance(65, 0.25, 10.0, 3)}[case]()
+    P = oracle.prepare(inst)
+    g = inst.grid
+    rng = np.random.default_rng(4)
+    phi0 = P.phi0 + rng.standard_normal(P.phi0.shape) * g.interior_mask()
+    phi = oracle.smooth(P.A, phi0, P.b, sweeps=1, smoother=oracle.SMOOTHER_XLINE)
+    r = oracle.residual(P.A, phi, P.b)
+    scale = np.abs(P.A.diag).max() * np.abs(phi).max()
+    assert np.abs(r[1::2, :]).max() < 1e-12 * scale < np.abs(r[0::2, :]).max()
+    full = oracle.restrict(g.nx, g.ny, g.periodic_y, r)
+    gc = I.Grid((g.nx - 1) // 2 + 1, (g.ny - 1) // 2 + 1, periodic_y=g.periodic_y)
+    even = np.zeros(gc.shape)
+    ev = r[0::2, :]
+    even[:, 1:-1] = (2 * ev[: gc.shape[0], 1:-2:2] + 4 * ev[: gc.shape[0], 2:-1:2] + 2 * ev[: gc.shape[0], 3::2]) / 16
+    even *= gc.interior_mask()
+    assert np.abs(full - even).max() < 1e-12 * scale
+    assert np.abs(full).max() > 1e-3 * scale
+
+
 def test_line_smoothing_of_decoupled_rows_is_an_exact_solve(oracle):
     """With every coupling between rows removed the rows are independent one-dimensional
     problems; one zebra sweep solves them exactly (compared with numpy's dense solve)."""

@@ -70,6 +70,14 @@ int mgk_eps_grid(int nx, int ny, int periodic, double hx, double hy, const doubl
 int mgk_assemble(const mgk_op_f64 *A, double hx, double hy, const double *exx, const double *exy,
                  const double *eyy, void *stream);
 
+/* mgk_assemble for an operator without cross term (A->five_point must be set; eps_xy is not
+ * an argument), in one pass that also writes, when B is not NULL, B as mgk_op_to_f32 would
+ * with B->dinv = 1 / B->diag computed in FP32.  B has A's sizes and periodicity and its own
+ * pitch.  The values are bitwise those of mgk_assemble (and of the FP32 conversion).
+ * Returns 1 on a bad argument (A not five_point included), 4 on a launch error. */
+int mgk_assemble_five(const mgk_op_f64 *A, const mgk_op_f32 *B, double hx, double hy, const double *exx,
+                      const double *eyy, void *stream);
+
 /* b = rho_phys * D at unknowns (Eq. 11), 0 at Dirichlet nodes. */
 int mgk_rhs(const mgk_op_f64 *A, const double *rho_phys, const double *D, double *b, void *stream);
 

@@ -221,6 +221,52 @@ __global__ void k_assemble_diag(int nx, int ny, int nyr, int periodic, int pitch
   if (dinv) dinv[k] = T(1) / (-s);
 }
 
+// One pass for an operator without cross term (5-point, eps_xy = 0): the E and N couplings
+// of k_assemble_couplings, the diagonal (and its reciprocal when dinv is given) of
+// k_assemble_diag, whose two couplings to the W and S neighbours are recomputed here from the
+// same operands, and, when fE is given, the FP32 copy of k_op_to_f32 with the reciprocal of
+// the FP32 diagonal (pitch pf).  Every product and sum is rounded on its own (__dmul_rn,
+// __dadd_rn: no multiply-add is contracted), so the values are bitwise those of the separate
+// kernels, which round each coupling when they store it.  The NE / NW arrays get zeros, as
+// from k_assemble_couplings, for the kernels that have no 5-point form.
+__global__ void k_assemble_five(int nx, int ny, int nyr, int periodic, int pitch, double ihx2, double ihy2,
+                                const double* __restrict__ exx, const double* __restrict__ eyy, double* cE,
+                                double* cN, double* cNE, double* cNW, double* diag, double* dinv, int pf,
+                                float* fE, float* fN, float* fNE, float* fNW, float* fdiag, float* fdinv) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= nx || j >= nyr) return;
+  const size_t k = (size_t)j * pitch + i;
+  const int ju = (j + 1 == nyr) ? 0 : j + 1;
+  // coupling from node kk to its E neighbour, and from kk to the node kn above it
+  const auto ce = [&](size_t kk) { return __dmul_rn(__dmul_rn(-0.5, __dadd_rn(exx[kk], exx[kk + 1])), ihx2); };
+  const auto cn = [&](size_t kk, size_t kn) { return __dmul_rn(__dmul_rn(-0.5, __dadd_rn(eyy[kk], eyy[kn])), ihy2); };
+  const double e = (i + 1 <= nx - 1) ? ce(k) : 0.0;
+  const double n = (periodic || j + 1 <= ny - 1) ? cn(k, (size_t)ju * pitch + i) : 0.0;
+  cE[k] = e;
+  cN[k] = n;
+  cNE[k] = 0.0;
+  cNW[k] = 0.0;
+  const bool unk = (i >= 1 && i <= nx - 2) && (periodic || (j >= 1 && j <= ny - 2));
+  double d = 1.0;
+  if (unk) {
+    const size_t ks = (size_t)((j == 0) ? nyr - 1 : j - 1) * pitch + i;
+    d = -__dadd_rn(__dadd_rn(__dadd_rn(e, ce(k - 1)), n), cn(ks, k));
+  }
+  diag[k] = d;
+  if (dinv) dinv[k] = unk ? 1.0 / d : 1.0;
+  if (fE) {
+    const size_t kf = (size_t)j * pf + i;
+    fE[kf] = (float)e;
+    fN[kf] = (float)n;
+    fNE[kf] = 0.0f;
+    fNW[kf] = 0.0f;
+    const float dg = (float)d;
+    fdiag[kf] = dg;
+    fdinv[kf] = 1.0f / dg;
+  }
+}
+
 __global__ void k_rhs(int nx, int ny, int nyr, int periodic, int pitch,
                       const double* __restrict__ rho, int rho_pitch, const double* __restrict__ D,
                       double* b) {
@@ -471,6 +517,17 @@ template cudaError_t launch_assemble<double>(const OpF64&, double, double, const
 template cudaError_t launch_assemble<float>(const OpF32&, double, double, const float*, const float*,
                                             const float*, cudaStream_t, bool);
 
+cudaError_t launch_assemble_five(const OpF64& A, const OpF32* B, double hx, double hy, const double* exx,
+                                 const double* eyy, cudaStream_t s, bool dinv) {
+  const int nyr = rows_stored(A.ny, A.periodic);
+  dim3 b(32, 8);
+  k_assemble_five<<<grid2(A.nx, nyr, b), b, 0, s>>>(
+      A.nx, A.ny, nyr, A.periodic, A.pitch, 1.0 / (hx * hx), 1.0 / (hy * hy), exx, eyy, A.cE, A.cN, A.cNE,
+      A.cNW, A.diag, dinv ? A.dinv : nullptr, B ? B->pitch : 0, B ? B->cE : nullptr, B ? B->cN : nullptr,
+      B ? B->cNE : nullptr, B ? B->cNW : nullptr, B ? B->diag : nullptr, B ? B->dinv : nullptr);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_rhs(const OpF64& A, const double* rho, int rho_pitch, const double* D, double* b,
                        cudaStream_t s) {
   const int nyr = rows_stored(A.ny, A.periodic);
@@ -596,6 +653,18 @@ extern "C" int mgk_assemble(const mgk_op_f64* A, double hx, double hy, const dou
                             const double* exy, const double* eyy, void* stream) {
   if (!op_ok(A) || !exx || !exy || !eyy || !(hx > 0) || !(hy > 0)) return 1;
   return launch_assemble(op_from(*A), hx, hy, exx, exy, eyy, (cudaStream_t)stream) == cudaSuccess
+             ? 0 : 4;
+}
+
+extern "C" int mgk_assemble_five(const mgk_op_f64* A, const mgk_op_f32* B, double hx, double hy,
+                                 const double* exx, const double* eyy, void* stream) {
+  if (!op_ok(A) || !A->five_point || !exx || !eyy || !(hx > 0) || !(hy > 0)) return 1;
+  if (B && (B->nx != A->nx || B->ny != A->ny || B->periodic != A->periodic || B->pitch < B->nx || !B->cE ||
+            !B->cN || !B->cNE || !B->cNW || !B->diag || !B->dinv))
+    return 1;
+  const OpF32 b = B ? op_from(*B) : OpF32();
+  return launch_assemble_five(op_from(*A), B ? &b : nullptr, hx, hy, exx, eyy, (cudaStream_t)stream, true) ==
+                 cudaSuccess
              ? 0 : 4;
 }
 

@@ -89,6 +89,11 @@ cudaError_t launch_coarsen_eps(const Op<TS>& F, const Op<TD>& C, const TS* const
 template <typename T>
 cudaError_t launch_assemble(const Op<T>& A, double hx, double hy, const T* exx, const T* exy, const T* eyy,
                             cudaStream_t s, bool dinv = true);
+// The same for an operator without cross term (A.five_point) in one pass, with the FP32 copy of
+// op_to_f32 (reciprocal of the FP32 diagonal) when B is given; bitwise the separate kernels'
+// values.  dinv: write A's FP64 reciprocal diagonal.
+cudaError_t launch_assemble_five(const OpF64& A, const OpF32* B, double hx, double hy, const double* exx,
+                                 const double* eyy, cudaStream_t s, bool dinv);
 cudaError_t launch_rhs(const OpF64& A, const double* rho, int rho_pitch, const double* D, double* b,
                        cudaStream_t s);
 template <typename T>

@@ -425,8 +425,13 @@ mg_status problem_enqueue_build(mg_problem* P, const mg_map_desc* map, const dou
     eyy = P->p;
   }
   // a mixed hierarchy never runs an FP64 smoother: its level-0 reciprocal diagonal is the FP32
-  // one, taken from the FP32 diagonal, so the FP64 division per node is skipped
-  CU(launch_assemble(F.A, hx, hy, exx, exy, eyy, s, !P->mixed));
+  // one, taken from the FP32 diagonal, so the FP64 division per node is skipped.  Without a
+  // cross term (and without a caller's change of the finest operator, which the FP32 copy
+  // must follow) couplings, diagonal and the FP32 copy come from one pass.
+  const bool five_pass = F.A.five_point && !(hook && *hook);
+  const bool f32_done = five_pass && P->mixed;
+  if (five_pass) CU(launch_assemble_five(F.A, P->mixed ? &F.A32 : nullptr, hx, hy, exx, eyy, s, !P->mixed));
+  else CU(launch_assemble(F.A, hx, hy, exx, exy, eyy, s, !P->mixed));
   if (hook && *hook) {  // a caller's change of the finest operator before coarsening
     mg_status hs = (*hook)(P, s);
     if (hs) return hs;
@@ -449,7 +454,7 @@ mg_status problem_enqueue_build(mg_problem* P, const mg_map_desc* map, const dou
         for (int k = 0; k < 3; ++k) e[k] = c[k];
       }
     } else {
-      CU(launch_op_to_f32(F.A, F.A32, s, true));
+      if (!f32_done) CU(launch_op_to_f32(F.A, F.A32, s, true));
       const double* e64[3] = {exx, exy, eyy};
       const float* e[3] = {nullptr, nullptr, nullptr};
       for (int l = 1; l < P->nlev; ++l) {
@@ -477,7 +482,7 @@ mg_status problem_enqueue_build(mg_problem* P, const mg_map_desc* map, const dou
   } else {
     // the FP32 cycle only needs FP32 coarse operators: Galerkin products in FP32, and the
     // coarsest one widened to FP64 for its dense inverse
-    CU(launch_op_to_f32(F.A, F.A32, s, true));
+    if (!f32_done) CU(launch_op_to_f32(F.A, F.A32, s, true));
     for (int l = 1; l < P->nlev; ++l) CU(launch_galerkin<float>(P->lev[l - 1].A32, P->lev[l].A32, s));
     if (P->nlev > 1) CU(launch_op_to_f64(P->lev[P->nlev - 1].A32, P->lev[P->nlev - 1].A, s));
   }
@@ -487,6 +492,7 @@ mg_status problem_enqueue_build(mg_problem* P, const mg_map_desc* map, const dou
           ? 1 + 2 + 3 * (P->nlev - 1) + (P->mixed ? 1 + (P->nlev > 1 ? 1 : 0) : 0) + 1 + (P->mirror ? 1 : 0)
           : 1 + 2 + (P->mixed ? 1 + (P->nlev - 1) + (P->nlev > 1 ? 1 : 0) : P->nlev - 1) + 1 +
                 (P->mirror ? 1 : 0);
+  if (five_pass) P->setup_kernels -= f32_done ? 2 : 1;  // one kernel for two (three with the FP32 copy)
   if (P->line) {  // the line smoother's row factors follow the new operators
     mg_status ls = line_enqueue_factor(P, s);
     if (ls) return ls;

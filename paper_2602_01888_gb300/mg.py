@@ -142,6 +142,8 @@ _SIGS = {
                       C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "mgk_assemble": ([C.POINTER(mgk_op_f64), C.c_double, C.c_double, C.c_void_p, C.c_void_p,
                       C.c_void_p, C.c_void_p], C.c_int),
+    "mgk_assemble_five": ([C.POINTER(mgk_op_f64), C.POINTER(mgk_op_f32), C.c_double, C.c_double, C.c_void_p,
+                           C.c_void_p, C.c_void_p], C.c_int),
     "mgk_rhs": ([C.POINTER(mgk_op_f64), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "mgk_galerkin": ([C.POINTER(mgk_op_f64), C.POINTER(mgk_op_f64), C.c_void_p], C.c_int),
     "mgk_coarsen_eps": ([C.POINTER(mgk_op_f64), C.POINTER(mgk_op_f64)] + [C.c_void_p] * 7, C.c_int),

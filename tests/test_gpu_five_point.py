@@ -87,6 +87,53 @@ def test_five_point_assembly_equals_the_nine_point_form(libmg, cuda, case):
 
 
 @pytest.mark.parametrize("case", list(CASES))
+def test_one_pass_assembly_equals_the_separate_kernels(libmg, cuda, case):
+    """mgk_assemble_five (couplings, diagonal and the FP32 copy of the level in one pass, which
+    the solver uses for maps without cross term) against mgk_assemble followed by
+    mgk_op_to_f32 on the same tensor: bitwise equal arrays; the FP32 reciprocal diagonal
+    equals the FP32 division of the FP32 diagonal.  A 9-point operator is refused."""
+    torch = cuda
+    inst = CASES[case]()
+    g = inst.grid
+    pitch = (g.nx + 31) // 32 * 32
+    pf = pitch + 32  # the FP32 copy with a pitch of its own
+    st = _stream(torch)
+    z = lambda: torch.zeros((g.nyr, pitch), dtype=torch.float64, device="cuda")
+    D, exx, exy, eyy = z(), z(), z(), z()
+    folded = torch.zeros(1, dtype=torch.int32, device="cuda")
+    prm = (C.c_double * 4)(*(list(inst.map.params) + [0.0] * 4)[:4])
+    libmg.mgk("mgk_eps_analytic", libmg.MAP_CODES[inst.map.kind], prm, g.nx, g.ny, int(g.periodic_y), g.x0, g.y0,
+              g.hx, g.hy, None, pitch, D.data_ptr(), exx.data_ptr(), exy.data_ptr(), eyy.data_ptr(),
+              folded.data_ptr(), st)
+    ref = [z() for _ in range(6)]
+    sref = libmg.op_struct(ref, g.nx, g.ny, g.periodic_y, five_point=True)
+    libmg.mgk("mgk_assemble", C.byref(sref), g.hx, g.hy, exx.data_ptr(), exy.data_ptr(), eyy.data_ptr(), st)
+    ref32 = [torch.zeros((g.nyr, pf), dtype=torch.float32, device="cuda") for _ in range(6)]
+    sref32 = libmg.op_struct(ref32, g.nx, g.ny, g.periodic_y, f32=True, five_point=True)
+    libmg.mgk("mgk_op_to_f32", C.byref(sref), C.byref(sref32), st)
+    full = lambda shape, dt: torch.full(shape, 7.0, dtype=dt, device="cuda")
+    got = [full((g.nyr, pitch), torch.float64) for _ in range(6)]
+    got32 = [full((g.nyr, pf), torch.float32) for _ in range(6)]
+    alone = [full((g.nyr, pitch), torch.float64) for _ in range(6)]
+    sgot = libmg.op_struct(got, g.nx, g.ny, g.periodic_y, five_point=True)
+    sgot32 = libmg.op_struct(got32, g.nx, g.ny, g.periodic_y, f32=True, five_point=True)
+    salone = libmg.op_struct(alone, g.nx, g.ny, g.periodic_y, five_point=True)
+    libmg.mgk("mgk_assemble_five", C.byref(sgot), C.byref(sgot32), g.hx, g.hy, exx.data_ptr(), eyy.data_ptr(), st)
+    libmg.mgk("mgk_assemble_five", C.byref(salone), None, g.hx, g.hy, exx.data_ptr(), eyy.data_ptr(), st)
+    torch.cuda.synchronize()
+    n = g.nx
+    for a, b, c in zip(ref, got, alone):
+        assert torch.equal(a[:, :n], b[:, :n]) and torch.equal(a[:, :n], c[:, :n])
+    for a, b in zip(ref32[:5], got32[:5]):
+        assert torch.equal(a[:, :n], b[:, :n])
+    assert torch.equal(got32[5][:, :n], 1.0 / got32[4][:, :n])
+    assert torch.count_nonzero(got[2][:, :n]).item() == 0 and torch.count_nonzero(got32[3][:, :n]).item() == 0
+    s9 = libmg.op_struct(got, g.nx, g.ny, g.periodic_y, five_point=False)
+    with pytest.raises(Exception):
+        libmg.mgk("mgk_assemble_five", C.byref(s9), None, g.hx, g.hy, exx.data_ptr(), eyy.data_ptr(), st)
+
+
+@pytest.mark.parametrize("case", list(CASES))
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 def test_five_point_kernels_equal_the_nine_point_forms(libmg, cuda, case, prec):
     """Gauss-Seidel sweeps, residual + restriction and zebra line sweeps on one operator,

@@ -223,47 +223,64 @@ __global__ void k_assemble_diag(int nx, int ny, int nyr, int periodic, int pitch
 
 // One pass for an operator without cross term (5-point, eps_xy = 0): the E and N couplings
 // of k_assemble_couplings, the diagonal (and its reciprocal when dinv is given) of
-// k_assemble_diag, whose two couplings to the W and S neighbours are recomputed here from the
-// same operands, and, when fE is given, the FP32 copy of k_op_to_f32 with the reciprocal of
-// the FP32 diagonal (pitch pf).  Every product and sum is rounded on its own (__dmul_rn,
-// __dadd_rn: no multiply-add is contracted), so the values are bitwise those of the separate
-// kernels, which round each coupling when they store it.  The NE / NW arrays get zeros, as
-// from k_assemble_couplings, for the kernels that have no 5-point form.
-__global__ void k_assemble_five(int nx, int ny, int nyr, int periodic, int pitch, double ihx2, double ihy2,
-                                const double* __restrict__ exx, const double* __restrict__ eyy, double* cE,
-                                double* cN, double* cNE, double* cNW, double* diag, double* dinv, int pf,
-                                float* fE, float* fN, float* fNE, float* fNW, float* fdiag, float* fdinv) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i >= nx || j >= nyr) return;
-  const size_t k = (size_t)j * pitch + i;
-  const int ju = (j + 1 == nyr) ? 0 : j + 1;
-  // coupling from node kk to its E neighbour, and from kk to the node kn above it
-  const auto ce = [&](size_t kk) { return __dmul_rn(__dmul_rn(-0.5, __dadd_rn(exx[kk], exx[kk + 1])), ihx2); };
-  const auto cn = [&](size_t kk, size_t kn) { return __dmul_rn(__dmul_rn(-0.5, __dadd_rn(eyy[kk], eyy[kn])), ihy2); };
-  const double e = (i + 1 <= nx - 1) ? ce(k) : 0.0;
-  const double n = (periodic || j + 1 <= ny - 1) ? cn(k, (size_t)ju * pitch + i) : 0.0;
-  cE[k] = e;
-  cN[k] = n;
-  cNE[k] = 0.0;
-  cNW[k] = 0.0;
-  const bool unk = (i >= 1 && i <= nx - 2) && (periodic || (j >= 1 && j <= ny - 2));
-  double d = 1.0;
-  if (unk) {
-    const size_t ks = (size_t)((j == 0) ? nyr - 1 : j - 1) * pitch + i;
-    d = -__dadd_rn(__dadd_rn(__dadd_rn(e, ce(k - 1)), n), cn(ks, k));
-  }
-  diag[k] = d;
-  if (dinv) dinv[k] = unk ? 1.0 / d : 1.0;
-  if (fE) {
-    const size_t kf = (size_t)j * pf + i;
-    fE[kf] = (float)e;
-    fN[kf] = (float)n;
-    fNE[kf] = 0.0f;
-    fNW[kf] = 0.0f;
-    const float dg = (float)d;
-    fdiag[kf] = dg;
-    fdinv[kf] = 1.0f / dg;
+// k_assemble_diag and, when fE is given, the FP32 copy of k_op_to_f32 with the reciprocal of
+// the FP32 diagonal (pitch pf).  A warp covers 32 columns of a row and each thread marches
+// down kAsmRows rows: the coupling to the W neighbour is the left lane's E coupling (shuffle),
+// the one to the S neighbour the thread's N coupling of the row before; the first lane and the
+// first row of a strip compute theirs again.  A coupling is rounded like the separate
+// kernel's: -(1/2)(a + b) / h^2 is the sum times the exact constant -(1/2) / h^2 (halving is
+// exact), one rounding per operation (__dadd_rn, __dmul_rn: no contracted multiply-add), so
+// the values are bitwise those of the separate kernels.  NE / NW get zeros, as from
+// k_assemble_couplings, for the kernels that have no 5-point form.  GB300 issues FP64 at a
+// low rate: ten FP64 operations per node here, as many as the three separate kernels take.
+constexpr int kAsmRows = 8;
+
+__global__ void __launch_bounds__(256) k_assemble_five(int nx, int ny, int nyr, int periodic, int pitch, double mx,
+                                                       double my, const double* __restrict__ exx,
+                                                       const double* __restrict__ eyy, double* cE, double* cN,
+                                                       double* cNE, double* cNW, double* diag, double* dinv, int pf,
+                                                       float* fE, float* fN, float* fNE, float* fNW, float* fdiag,
+                                                       float* fdinv) {
+  const int i = blockIdx.x * 32 + threadIdx.x;
+  const int jb = (blockIdx.y * blockDim.y + threadIdx.y) * kAsmRows;
+  const bool col = i < nx;
+  const bool has_e = i + 1 <= nx - 1;
+  double n_prev = 0.0;
+  for (int r = 0; r < kAsmRows; ++r) {
+    const int j = jb + r;
+    if (j >= nyr) break;  // the same for the whole warp (one row per warp)
+    const size_t k = (size_t)j * pitch + i;
+    const int ju = (j + 1 == nyr) ? 0 : j + 1;
+    const double e = (col && has_e) ? __dmul_rn(__dadd_rn(exx[k], exx[k + 1]), mx) : 0.0;
+    const double n = (col && (periodic || j + 1 <= ny - 1))
+                         ? __dmul_rn(__dadd_rn(eyy[k], eyy[(size_t)ju * pitch + i]), my) : 0.0;
+    double ew = __shfl_up_sync(0xffffffffu, e, 1);
+    double ns = n_prev;
+    n_prev = n;
+    if (!col) continue;
+    const bool unk = (i >= 1 && i <= nx - 2) && (periodic || (j >= 1 && j <= ny - 2));
+    double d = 1.0;
+    if (unk) {
+      if (threadIdx.x == 0) ew = __dmul_rn(__dadd_rn(exx[k - 1], exx[k]), mx);
+      if (r == 0) ns = __dmul_rn(__dadd_rn(eyy[(size_t)((j == 0) ? nyr - 1 : j - 1) * pitch + i], eyy[k]), my);
+      d = -__dadd_rn(__dadd_rn(__dadd_rn(e, ew), n), ns);
+    }
+    cE[k] = e;
+    cN[k] = n;
+    cNE[k] = 0.0;
+    cNW[k] = 0.0;
+    diag[k] = d;
+    if (dinv) dinv[k] = unk ? 1.0 / d : 1.0;
+    if (fE) {
+      const size_t kf = (size_t)j * pf + i;
+      fE[kf] = (float)e;
+      fN[kf] = (float)n;
+      fNE[kf] = 0.0f;
+      fNW[kf] = 0.0f;
+      const float dg = (float)d;
+      fdiag[kf] = dg;
+      fdinv[kf] = 1.0f / dg;
+    }
   }
 }
 
@@ -520,9 +537,10 @@ template cudaError_t launch_assemble<float>(const OpF32&, double, double, const 
 cudaError_t launch_assemble_five(const OpF64& A, const OpF32* B, double hx, double hy, const double* exx,
                                  const double* eyy, cudaStream_t s, bool dinv) {
   const int nyr = rows_stored(A.ny, A.periodic);
-  dim3 b(32, 8);
-  k_assemble_five<<<grid2(A.nx, nyr, b), b, 0, s>>>(
-      A.nx, A.ny, nyr, A.periodic, A.pitch, 1.0 / (hx * hx), 1.0 / (hy * hy), exx, eyy, A.cE, A.cN, A.cNE,
+  dim3 b(32, 8), g((A.nx + 31) / 32, (nyr + 8 * kAsmRows - 1) / (8 * kAsmRows));
+  // -(1/2) / h^2 exactly (halving is exact), as k_assemble_couplings rounds its couplings
+  k_assemble_five<<<g, b, 0, s>>>(
+      A.nx, A.ny, nyr, A.periodic, A.pitch, -0.5 * (1.0 / (hx * hx)), -0.5 * (1.0 / (hy * hy)), exx, eyy, A.cE, A.cN, A.cNE,
       A.cNW, A.diag, dinv ? A.dinv : nullptr, B ? B->pitch : 0, B ? B->cE : nullptr, B ? B->cN : nullptr,
       B ? B->cNE : nullptr, B ? B->cNW : nullptr, B ? B->diag : nullptr, B ? B->dinv : nullptr);
   return cudaGetLastError();

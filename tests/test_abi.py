@@ -108,3 +108,38 @@ def test_no_oracle_on_the_product_path():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
                 assert "mg_oracle" not in txt, f
+
+
+def test_kernel_entries_refuse_bad_arguments_before_any_launch(libmg):
+    """Argument checks of the even-row restriction and the one-pass 5-point assembly (host
+    logic, no GPU): missing arrays, even grid sizes, a 9-point operator for the 5-point pass,
+    a non-positive spacing and an FP32 copy of other sizes all return 1 before anything is
+    launched.  The pointers below are never dereferenced."""
+    import ctypes as C
+    lib = libmg.lib()
+    fake = 4096
+
+    def op(cls, nx, ny, five):
+        s = cls()
+        s.nx, s.ny, s.periodic, s.pitch, s.five_point = nx, ny, 0, nx + 3, five
+        for f in ("cE", "cN", "cNE", "cNW", "diag", "dinv"):
+            setattr(s, f, fake)
+        return s
+
+    a = op(libmg.mgk_op_f64, 65, 33, 1)
+    a32 = op(libmg.mgk_op_f32, 65, 33, 1)
+    for name, A in (("mgk_resid_restrict_even_f64", a), ("mgk_resid_restrict_even_f32", a32)):
+        f = getattr(lib, name)
+        assert f(None, fake, fake, fake, 40, None) == 1
+        assert f(C.byref(A), None, fake, fake, 40, None) == 1
+        assert f(C.byref(A), fake, fake, None, 40, None) == 1
+        assert f(C.byref(A), fake, fake, fake, 32, None) == 1  # coarse pitch below the 33 coarse columns
+    even = op(libmg.mgk_op_f64, 64, 33, 1)
+    assert lib.mgk_resid_restrict_even_f64(C.byref(even), fake, fake, fake, 40, None) == 1
+    nine = op(libmg.mgk_op_f64, 65, 33, 0)
+    other = op(libmg.mgk_op_f32, 65, 17, 1)
+    f = lib.mgk_assemble_five
+    assert f(C.byref(nine), None, 0.1, 0.1, fake, fake, None) == 1
+    assert f(C.byref(a), None, 0.0, 0.1, fake, fake, None) == 1
+    assert f(C.byref(a), None, 0.1, 0.1, None, fake, None) == 1
+    assert f(C.byref(a), C.byref(other), 0.1, 0.1, fake, fake, None) == 1
